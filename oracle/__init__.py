@@ -1,0 +1,12 @@
+"""Plain FP64 CPU oracle for the (X)MS-CASPT2 amplitude, lambda and density path.
+
+TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the CPU
+baseline leg of bench.py may import this package.  The product library never
+calls it and shares no code with it; the two meet only through the seeded
+inputs of the `synth` package.
+
+  o1_determinant  brute force in the full determinant space (tiny spaces):
+                  explicit excitation operators, explicit overlap / zeroth-order
+                  Hamiltonian matrices, explicit expectation values.
+  mp2_closed_form textbook closed-shell MP2 (nact = 0 special case), used as a pin.
+"""

@@ -1,0 +1,205 @@
+"""Pins of the brute-force oracle O1 against facts fixed by the paper and by
+mathematics (no GPU): the nact = 0 closed form, rotation invariances, the
+single-state reductions, stationarity and finite differences of the energy."""
+import numpy as np
+import pytest
+
+from synth import make_problem, ActiveSpace
+from oracle import o1_determinant as o1
+from oracle.mp2_closed_form import mp2_energy
+
+
+def _eri(B):
+    return np.einsum("Ppq,Prs->pqrs", B, B)
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    # 2 closed, 3 active (2 electrons), 2 virtual, 2 states
+    return make_problem(2, 3, 2, 18, 2, seed=11, nelact=2)
+
+
+@pytest.fixture(scope="module")
+def small():
+    # 2 closed, 4 active (4 electrons), 2 virtual, 2 states: every class populated
+    return make_problem(2, 4, 2, 24, 2, seed=5)
+
+
+@pytest.mark.parametrize("shift", [0.0, 0.3])
+def test_nact0_is_closed_shell_mp2(shift):
+    """P3: with no active orbitals only E_ai,bj survives; E2 is textbook MP2."""
+    p = make_problem(3, 0, 4, 30, 1, seed=3)
+    r = o1.solve_problem(p, shift=shift, densities=False)
+    c = p.nclosed
+    eri = _eri(p.B)
+    K = eri[c:, :c, c:, :c].transpose(1, 0, 3, 2)
+    e2 = mp2_energy(np.diag(p.f)[:c], np.diag(p.f)[c:], K, shift)
+    assert abs((r.Ems[0] - r.Ecore) - e2) <= 1e-12 * abs(e2)
+    assert abs(r.Href[0, 0] - r.Ecore) < 1e-12
+    for cls in "ABCDEFG":
+        assert np.all(r.e_class[cls] == 0.0)
+
+
+def test_oracle_embedding_matches_generator_rdm(small):
+    """The embedded reference states reproduce the generator's active 1-RDMs."""
+    p = small
+    sp_ = o1.FullSpace(p.nmo, 2 * p.nclosed + p.nelact)
+    ref = sp_.embed(p.nclosed, p.ci, p.det_alpha, p.det_beta)
+    act = slice(p.nclosed, p.nclosed + p.nact)
+    g1 = p.rdm[1].reshape(p.nstate, p.nstate, p.nact, p.nact)
+    for m in range(p.nstate):
+        for n in range(p.nstate):
+            t = sp_.tdm1(ref[:, m], ref[:, n])
+            assert np.allclose(t[act, act], g1[m, n], atol=1e-13)
+            assert np.allclose(np.diag(t)[: p.nclosed], 2.0 * (m == n), atol=1e-13)
+
+
+def test_references_are_casci_eigenstates(small):
+    """Sec. II.A: the reference states diagonalise H inside the active space."""
+    r = o1.solve_problem(small, xms=False, densities=False)
+    off = r.Href - np.diag(np.diag(r.Href))
+    assert np.abs(off).max() < 1e-10
+
+
+def test_xms_invariant_to_reference_rotation(small):
+    """P5: XMS (MS-MR) energies do not depend on a rotation of the input states."""
+    th = 0.7
+    Q = np.array([[np.cos(th), -np.sin(th)], [np.sin(th), np.cos(th)]])
+    a = o1.solve_problem(small, shift=0.2, densities=False)
+    b = o1.solve_problem(small, shift=0.2, ci=small.ci @ Q, densities=False)
+    assert np.abs(a.Ems - b.Ems).max() < 1e-10
+    # ... while plain MS energies do change (XMS exists for this reason)
+    c = o1.solve_problem(small, shift=0.2, xms=False, densities=False)
+    d = o1.solve_problem(small, shift=0.2, xms=False, ci=small.ci @ Q, densities=False)
+    assert np.abs(c.Ems - d.Ems).max() > 1e-4
+
+
+def test_xms_equals_ms_on_prerotated_states(small):
+    """P5 / Sec. II.A: MS is XMS with U = 1."""
+    a = o1.solve_problem(small, shift=0.2, densities=False)
+    b = o1.solve_problem(small, shift=0.2, xms=False, ci=small.ci @ a.U, densities=False)
+    assert np.abs(a.Ems - b.Ems).max() < 1e-10
+    assert np.abs(a.Heff - b.Heff).max() < 1e-10
+
+
+def test_single_state_reductions():
+    """P4: one state -> MS-MR == SS-SR; with E_s = 0 lambda equals T."""
+    p = make_problem(2, 4, 2, 24, 1, seed=6)
+    a = o1.solve_problem(p, scheme="msmr", densities=False)
+    b = o1.solve_problem(p, scheme="sssr", densities=False)
+    assert abs(a.Ems[0] - b.Ems[0]) <= 1e-12 * abs(a.Ems[0])
+    assert np.abs(a.lam[0] - a.t[0]).max() <= 1e-12 * np.abs(a.t[0]).max()
+
+
+def test_explicit_energy_expression(small):
+    """Sec. II.B: the explicit E^MS equals the eigenvalue of H^eff."""
+    for scheme in ("msmr", "sssr"):
+        r = o1.solve_problem(small, shift=0.2, scheme=scheme, densities=False)
+        assert abs(r.Ems_explicit - r.Ems[0]) < 1e-11
+
+
+def test_overlap_threshold_insensitive(small):
+    """A3: moving the truncation threshold by a decade either way changes nothing."""
+    a = o1.solve_problem(small, shift=0.2, thresh=1e-8, densities=False)
+    b = o1.solve_problem(small, shift=0.2, thresh=1e-10, densities=False)
+    assert np.abs(a.Ems - b.Ems).max() < 1e-10
+
+
+def test_orbital_rotation_invariance(small):
+    """P6: rotations inside the closed and inside the virtual space leave energies
+    unchanged (f then has off-diagonal closed-closed / virtual-virtual blocks)."""
+    p = small
+    rng = np.random.default_rng(1)
+    Q = np.eye(p.nmo)
+    for lo, hi in ((0, p.nclosed), (p.nclosed + p.nact, p.nmo)):
+        m = rng.standard_normal((hi - lo, hi - lo))
+        q, _ = np.linalg.qr(m)
+        Q[lo:hi, lo:hi] = q
+    f2 = Q.T @ p.f @ Q
+    B2 = np.einsum("xp,Pxy,yq->Ppq", Q, p.B, Q)
+    a = o1.solve_problem(p, shift=0.2, densities=False)
+    b = o1.solve_problem(p, shift=0.2, f=f2, B=B2, densities=False)
+    assert np.abs(a.Ems - b.Ems).max() < 1e-10
+
+
+def test_shift_stationarity_single_state():
+    """P8: for one state, dE/dE_s vanishes at E_s = 0 (the shift correction cancels
+    the first order)."""
+    p = make_problem(2, 3, 2, 18, 1, seed=12, nelact=2)
+    h = 1e-4
+    ep = o1.solve_problem(p, shift=h, densities=False).Ems[0]
+    em = o1.solve_problem(p, shift=-h, densities=False).Ems[0]
+    assert abs((ep - em) / (2 * h)) < 1e-7
+
+
+def test_shift_derivative_lagrangian(tiny):
+    """P8: dE/dE_s = sum_L <lambda_L|S T_L> - sum_L R_LP^2 <T_L|S T_L>."""
+    s0, h = 0.2, 1e-4
+    r = o1.solve_problem(tiny, shift=s0, densities=False)
+    an = sum(r.lam[L] @ r.S[L] @ r.t[L] - r.R[L, 0] ** 2 * r.t[L] @ r.S[L] @ r.t[L]
+             for L in range(tiny.nstate))
+    ep = o1.solve_problem(tiny, shift=s0 + h, densities=False).Ems[0]
+    em = o1.solve_problem(tiny, shift=s0 - h, densities=False).Ems[0]
+    fd = (ep - em) / (2 * h)
+    assert abs(fd - an) <= 1e-6 * abs(an) + 1e-9
+
+
+def _h_of(p, r):
+    eri = _eri(p.B)
+    d = np.zeros((p.nmo, p.nmo))
+    d[np.arange(p.nclosed), np.arange(p.nclosed)] = 2.0
+    act = slice(p.nclosed, p.nclosed + p.nact)
+    g1 = p.rdm[1].reshape(p.nstate, p.nstate, p.nact, p.nact)
+    d[act, act] = sum(g1[m, m] for m in range(p.nstate)) / p.nstate
+    return p.f - o1.g_matrix(eri, d)
+
+
+@pytest.mark.parametrize("scheme", ["msmr", "sssr"])
+def test_densities_by_finite_differences(tiny, scheme):
+    """P9: with h, f and B treated as independent inputs (MS, so U is fixed),
+    dE/dh = <P|E|P> + d(1), dE/df = d(2), dE/dB = (Gamma2_P + D(1)) . B."""
+    p = tiny
+    s0, step = 0.2, 1e-4
+    kw = dict(shift=s0, xms=False, scheme=scheme)
+    r = o1.solve_problem(p, **kw)
+    h0 = _h_of(p, r)
+    rng = np.random.default_rng(7)
+    for _ in range(2):
+        dh = rng.standard_normal((p.nmo, p.nmo))
+        dh = dh + dh.T
+        dh /= np.linalg.norm(dh)
+        e = [o1.solve_problem(p, h=h0 + sgn * step * dh, densities=False, **kw).Ems[0]
+             for sgn in (1, -1)]
+        fd = (e[0] - e[1]) / (2 * step)
+        an = np.sum((r.gammaP + r.d1) * dh)
+        assert abs(fd - an) <= 1e-6 * abs(an) + 1e-9
+
+        df = rng.standard_normal((p.nmo, p.nmo))
+        df = df + df.T
+        df /= np.linalg.norm(df)
+        e = [o1.solve_problem(p, h=h0, f=p.f + sgn * step * df, densities=False, **kw).Ems[0]
+             for sgn in (1, -1)]
+        fd = (e[0] - e[1]) / (2 * step)
+        an = np.sum(r.d2 * df)
+        assert abs(fd - an) <= 1e-6 * abs(an) + 1e-9
+
+        dB = rng.standard_normal(p.B.shape)
+        dB = dB + dB.transpose(0, 2, 1)
+        dB /= np.linalg.norm(dB)
+        e = [o1.solve_problem(p, h=h0, B=p.B + sgn * step * dB, densities=False, **kw).Ems[0]
+             for sgn in (1, -1)]
+        fd = (e[0] - e[1]) / (2 * step)
+        D = r.Gamma2P + r.D1
+        an = np.einsum("Pxy,xyzw,Pzw->", dB, D, p.B)
+        assert abs(fd - an) <= 1e-6 * abs(an) + 1e-9
+
+
+def test_rdm_sum_rules():
+    """Generator RDMs obey sum_r Gamma_{..,rr} = (N - k + 1) Gamma_{..}."""
+    p = make_problem(1, 4, 1, 8, 2, seed=2)
+    n, a, N = p.nstate, p.nact, p.nelact
+    g = {k: p.rdm[k].reshape((n, n) + (a,) * (2 * k)) for k in (1, 2, 3, 4)}
+    assert np.allclose(np.einsum("mnrr->mn", g[1]), N * np.eye(n), atol=1e-12)
+    for k in (2, 3, 4):
+        lhs = np.trace(g[k], axis1=-2, axis2=-1)
+        assert np.allclose(lhs, (N - k + 1) * g[k - 1], atol=1e-12)
