@@ -1,0 +1,130 @@
+/*
+ * caspt2.h -- C ABI of the GB300 (sm_103a) library for the (X)MS-CASPT2
+ * amplitude / effective-Hamiltonian path of Vlaisavljevich & Shiozaki,
+ * "Nuclear energy gradients for internally contracted complete active space
+ * second-order perturbation theory: multistate extensions".
+ *
+ * Conventions (all calls):
+ *   - orbitals are ordered [closed | active | virtual]; nmo = nclosed + nact + nvirt;
+ *     i, j closed; r, s, t, u active; a, b virtual; x, y, z, w general (Sec. II).
+ *   - every array is row-major FP64 (double).
+ *   - spin-free RDMs between reference states M, N (unrotated, as supplied):
+ *       rdm1[M][N][r][s]          = <M|E_rs|N>
+ *       rdm2[M][N][r][s][t][u]    = <M|E_rs,tu|N>,  E_rs,tu = sum a+_r a+_t a_u a_s
+ *       rdm3 / rdm4 likewise with 6 / 8 active indices.
+ *   - the caller owns every buffer it passes; the library keeps no caller
+ *     pointer once a call returns (inputs are copied into the context).
+ *   - return value: 0 = OK, negative = error (CASPT2_E*), positive = warning.
+ *     No call exits or aborts the process.
+ *   - one context serves one stream at a time; contexts are independent.
+ */
+#ifndef CASPT2_H
+#define CASPT2_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define CASPT2_OK            0
+#define CASPT2_EINVAL      (-1)   /* bad sizes, options or pointers               */
+#define CASPT2_ENOMEM      (-2)   /* device allocation failed                     */
+#define CASPT2_ENOTCONV    (-3)   /* an eigensolver or iteration did not converge */
+#define CASPT2_ENAN        (-4)   /* NaN/Inf found in inputs or results           */
+#define CASPT2_ETIMEOUT    (-5)   /* a bounded device wait gave up                */
+#define CASPT2_ECUDA       (-6)   /* a CUDA runtime call failed                   */
+#define CASPT2_ESTATE      (-7)   /* call out of order (e.g. solve before inputs) */
+#define CASPT2_WINTRUDER     1    /* smallest |denominator| below 1e-3 Eh          */
+
+/* memory kinds for caspt2_set_inputs */
+#define CASPT2_MEM_HOST      0
+#define CASPT2_MEM_DEVICE    1
+
+/* contraction schemes (Sec. II.B, Eq. wfp and Eq. wfp2) */
+#define CASPT2_MSMR          0
+#define CASPT2_SSSR          1
+
+/* excitation classes (Eq. class): A E_ri,st  B E_ri,sj  C E_ar,st  D E_ai,rs + E_ar,si
+ *                                  E E_ai,rj  F E_ar,bs  G E_ar,bi  H E_ai,bj        */
+enum { CASPT2_CLASS_A = 0, CASPT2_CLASS_B, CASPT2_CLASS_C, CASPT2_CLASS_D,
+       CASPT2_CLASS_E, CASPT2_CLASS_F, CASPT2_CLASS_G, CASPT2_CLASS_H, CASPT2_NCLASS };
+
+typedef struct caspt2_ctx caspt2_ctx;
+
+typedef struct {
+    int nclosed, nact, nvirt, naux, nstate;
+} caspt2_dims;
+
+typedef struct {
+    int    xms;          /* 1: XMS rotation U from <L|f|M> (Sec. II.A); 0: MS, U = 1           */
+    int    scheme;       /* CASPT2_MSMR or CASPT2_SSSR                                         */
+    double shift;        /* vertical shift E_s >= 0, enters as (f - E0_L + E_s), Eq. (ampeq)  */
+    double ovl_thresh;   /* overlap eigenvalue cut, default 1e-9 (Sec. II.B)                   */
+    double enuc;         /* constant added to the diagonal of H^ref                            */
+    int    target_state; /* P for lambda and densities; -1 = energies only                     */
+    unsigned class_mask; /* bit k set = class k is included (default: all supported)           */
+} caspt2_options;
+
+/* Fill *opt with defaults: XMS, MS-MR, shift 0, 1e-9, enuc 0, target 0, all classes. */
+void caspt2_default_options(caspt2_options* opt);
+
+/* Create a context for the given sizes.  Allocates its device buffers
+ * (sizes fixed by dims) on the current device.  Errors: EINVAL, ENOMEM, ECUDA. */
+int caspt2_create(caspt2_ctx** ctx, const caspt2_dims* dims, const caspt2_options* opt);
+
+/* Copy the inputs into the context (Sec. II.A, II.B: reference states through their
+ * RDMs, the state-averaged Fock matrix f and the DF factors defining (xy|zw)).
+ *   mem   CASPT2_MEM_HOST or CASPT2_MEM_DEVICE (pointers on the context's device)
+ *   fock  [nmo][nmo] symmetric SA Fock matrix f = h + g(d_sa)
+ *   dfB   [naux][nmo][nmo] DF factors, (xy|zw) = sum_P B[P][x][y] B[P][z][w], symmetric in x,y
+ *   rdm1  [n][n][a][a], rdm2 [n][n][a^4]   (required)
+ *   rdm3, rdm4 may be NULL while only classes that do not need them are enabled.
+ * Errors: EINVAL (NULL required pointer), ECUDA. */
+int caspt2_set_inputs(caspt2_ctx* ctx, int mem, const double* fock, const double* dfB,
+                      const double* rdm1, const double* rdm2, const double* rdm3,
+                      const double* rdm4);
+
+/* Run the path on `cuda_stream` (a cudaStream_t, NULL = legacy default stream):
+ * SA density and core Fock (Sec. II.B), XMS rotation and H^ref (Sec. II.A),
+ * first-order amplitudes of the enabled classes (Eq. ampeq), the effective
+ * Hamiltonian and its eigenpairs (Sec. II.B).  Synchronises the stream before
+ * returning.  Returns WINTRUDER if a denominator fell below 1e-3 Eh.
+ * Errors: ESTATE (no inputs), ENOTCONV, ENAN, ECUDA. */
+int caspt2_solve(caspt2_ctx* ctx, void* cuda_stream);
+
+/* Copy results of the last solve to host buffers (any pointer may be NULL):
+ *   U [n][n] XMS rotation (columns = rotated states), E0 [n] zeroth-order energies,
+ *   Href [n][n], Heff [n][n], Ems [n] ascending, R [n][n] (columns = eigenvectors;
+ *   each column signed so that its largest-|.| entry is positive). */
+int caspt2_get_energies(caspt2_ctx* ctx, double* U, double* E0, double* Href, double* Heff,
+                        double* Ems, double* R);
+
+/* Per-class pieces of the last solve (Sec. II.B effective Hamiltonian):
+ *   e[L][L'] = <Psi1_L|H|L'~> restricted to class cls, norm[L] = <Psi1_L|Psi1_L> of that class.
+ * Either pointer may be NULL.  Errors: EINVAL (class not enabled / out of range). */
+int caspt2_get_class_energy(caspt2_ctx* ctx, int cls, double* e, double* norm);
+
+/* Core energy E_core = <core|H|core> (closed orbitals doubly occupied) of the last solve. */
+int caspt2_get_core_energy(caspt2_ctx* ctx, double* ecore);
+
+/* Device time in milliseconds of the last solve, measured with CUDA events on the
+ * solve stream: times[0] setup, [1] class H stage, [2] other classes, [3] effective
+ * Hamiltonian, [4] the class-H DF-GEMM kernel alone (0 if class H is off).
+ *   times[k] is written for k < *count on input; *count = number of entries on output. */
+int caspt2_get_timings(caspt2_ctx* ctx, double* times, int* count);
+
+/* Number of CUDA kernels the library launched during the last solve (-1 if ctx is NULL). */
+long caspt2_get_kernel_launches(caspt2_ctx* ctx);
+
+/* Bitmask of the classes this build implements. */
+unsigned caspt2_supported_classes(void);
+
+void caspt2_destroy(caspt2_ctx* ctx);
+const char* caspt2_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CASPT2_H */

@@ -1,0 +1,198 @@
+"""Python binding of libcaspt2.so (argument marshalling only).
+
+Every computation runs in the CUDA library; this module converts arrays to
+pointers, calls the C ABI declared in include/caspt2.h and raises on error.
+There is no CPU fallback: if the library is missing, importing the binding
+functions raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(HERE, "libcaspt2.so")
+
+OK, EINVAL, ENOMEM, ENOTCONV, ENAN, ETIMEOUT, ECUDA, ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
+WINTRUDER = 1
+MEM_HOST, MEM_DEVICE = 0, 1
+MSMR, SSSR = 0, 1
+CLASSES = "ABCDEFGH"
+
+
+class Dims(C.Structure):
+    _fields_ = [("nclosed", C.c_int), ("nact", C.c_int), ("nvirt", C.c_int),
+                ("naux", C.c_int), ("nstate", C.c_int)]
+
+
+class Options(C.Structure):
+    _fields_ = [("xms", C.c_int), ("scheme", C.c_int), ("shift", C.c_double),
+                ("ovl_thresh", C.c_double), ("enuc", C.c_double), ("target_state", C.c_int),
+                ("class_mask", C.c_uint)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libcaspt2.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIBPATH):
+            raise RuntimeError(f"{LIBPATH} is missing: build it with "
+                               "`python -m paper_1606_01273_gb300.build`")
+        L = C.CDLL(LIBPATH)
+        P = C.c_void_p
+        dp = C.POINTER(C.c_double)
+        L.caspt2_default_options.argtypes = [C.POINTER(Options)]
+        L.caspt2_default_options.restype = None
+        L.caspt2_create.argtypes = [C.POINTER(P), C.POINTER(Dims), C.POINTER(Options)]
+        L.caspt2_set_inputs.argtypes = [P, C.c_int, P, P, P, P, P, P]
+        L.caspt2_solve.argtypes = [P, P]
+        L.caspt2_get_energies.argtypes = [P, dp, dp, dp, dp, dp, dp]
+        L.caspt2_get_class_energy.argtypes = [P, C.c_int, dp, dp]
+        L.caspt2_get_core_energy.argtypes = [P, dp]
+        L.caspt2_get_timings.argtypes = [P, dp, C.POINTER(C.c_int)]
+        L.caspt2_get_kernel_launches.argtypes = [P]
+        L.caspt2_get_kernel_launches.restype = C.c_long
+        L.caspt2_supported_classes.argtypes = []
+        L.caspt2_supported_classes.restype = C.c_uint
+        L.caspt2_destroy.argtypes = [P]
+        L.caspt2_destroy.restype = None
+        L.caspt2_strerror.argtypes = [C.c_int]
+        L.caspt2_strerror.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+class CASPT2Error(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {lib().caspt2_strerror(status).decode()} ({status})")
+        self.status = status
+
+
+def _check(st: int, where: str, warn_ok: bool = False) -> int:
+    if st < 0 or (st > 0 and not warn_ok):
+        raise CASPT2Error(st, where)
+    return st
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _ptr(x):
+    """Host numpy array (C-contiguous float64) or torch CUDA tensor -> (void*, mem kind)."""
+    if x is None:
+        return None, None
+    if isinstance(x, np.ndarray):
+        assert x.dtype == np.float64 and x.flags.c_contiguous
+        return C.c_void_p(x.ctypes.data), MEM_HOST
+    # torch tensor on the device
+    assert x.dtype.is_floating_point and x.element_size() == 8 and x.is_contiguous()
+    return C.c_void_p(x.data_ptr()), (MEM_DEVICE if x.is_cuda else MEM_HOST)
+
+
+def default_options(**kw) -> Options:
+    o = Options()
+    lib().caspt2_default_options(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def supported_classes() -> str:
+    m = lib().caspt2_supported_classes()
+    return "".join(c for k, c in enumerate(CLASSES) if m >> k & 1)
+
+
+@dataclass
+class Result:
+    U: np.ndarray
+    E0: np.ndarray
+    Href: np.ndarray
+    Heff: np.ndarray
+    Ems: np.ndarray
+    R: np.ndarray
+    Ecore: float
+    e_class: dict
+    norm_class: dict
+    status: int
+    timings_ms: list
+    launches: int
+
+
+class Context:
+    """One library context (device buffers sized for `dims`)."""
+
+    def __init__(self, nclosed, nact, nvirt, naux, nstate, **opts):
+        self.dims = Dims(nclosed, nact, nvirt, naux, nstate)
+        self.opts = default_options(**opts)
+        h = C.c_void_p()
+        _check(lib().caspt2_create(C.byref(h), C.byref(self.dims), C.byref(self.opts)),
+               "caspt2_create")
+        self._h = h
+        self.n = nstate
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().caspt2_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def set_inputs(self, fock, dfB, rdm1, rdm2, rdm3=None, rdm4=None):
+        ptrs = [_ptr(x) for x in (fock, dfB, rdm1, rdm2, rdm3, rdm4)]
+        mems = {m for p, m in ptrs if m is not None}
+        if len(mems) != 1:
+            raise ValueError("all inputs must live in the same memory (host or device)")
+        self._keep = (fock, dfB, rdm1, rdm2, rdm3, rdm4)
+        _check(lib().caspt2_set_inputs(self._h, mems.pop(), *[p for p, _ in ptrs]),
+               "caspt2_set_inputs")
+
+    def solve(self, stream=None) -> int:
+        s = C.c_void_p(stream) if stream is not None else None
+        return _check(lib().caspt2_solve(self._h, s), "caspt2_solve", warn_ok=True)
+
+    def result(self, status: int = 0) -> Result:
+        n = self.n
+        U, Href, Heff, R = (np.zeros((n, n)) for _ in range(4))
+        E0, Ems = np.zeros(n), np.zeros(n)
+        _check(lib().caspt2_get_energies(self._h, _dp(U), _dp(E0), _dp(Href), _dp(Heff),
+                                         _dp(Ems), _dp(R)), "caspt2_get_energies")
+        ec = C.c_double()
+        _check(lib().caspt2_get_core_energy(self._h, C.byref(ec)), "caspt2_get_core_energy")
+        e_cls, n_cls = {}, {}
+        for k, name in enumerate(CLASSES):
+            if self.opts.class_mask >> k & 1:
+                e, nr = np.zeros((n, n)), np.zeros(n)
+                _check(lib().caspt2_get_class_energy(self._h, k, _dp(e), _dp(nr)),
+                       "caspt2_get_class_energy")
+                e_cls[name], n_cls[name] = e, nr
+        t = np.zeros(8)
+        cnt = C.c_int(8)
+        _check(lib().caspt2_get_timings(self._h, _dp(t), C.byref(cnt)), "caspt2_get_timings")
+        return Result(U, E0, Href, Heff, Ems, R, ec.value, e_cls, n_cls, status,
+                      list(t[: cnt.value]), int(lib().caspt2_get_kernel_launches(self._h)))
+
+
+def problem_inputs(prob):
+    """Host arrays of a synth.Problem in the layout of caspt2_set_inputs."""
+    a = prob.nact
+    n = prob.nstate
+    r = [np.ascontiguousarray(prob.rdm[k].reshape(n, n, -1)) for k in (1, 2)]
+    return (np.ascontiguousarray(prob.f), np.ascontiguousarray(prob.B), r[0], r[1])
+
+
+def solve_problem(prob, **opts) -> Result:
+    """Create a context, copy a synth.Problem from host memory, solve, fetch results."""
+    ctx = Context(prob.nclosed, prob.nact, prob.nvirt, prob.naux, prob.nstate, **opts)
+    try:
+        ctx.set_inputs(*problem_inputs(prob))
+        st = ctx.solve()
+        return ctx.result(st)
+    finally:
+        ctx.close()

@@ -1,0 +1,338 @@
+// C ABI of the CASPT2 library: context lifetime, input staging and the solve
+// pipeline.  Host code only orchestrates; every arithmetic step runs in the
+// kernels of setup.cu and class_*.cu on the caller's stream.
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "kernels.cuh"
+
+using namespace caspt2;
+
+namespace {
+
+constexpr int kNumStages = 4;  // setup, class H, other classes, H^eff
+constexpr int kNumTimes = kNumStages + 1;  // + the class-H GEMM kernel alone
+
+struct DevBuf {
+  double* p = nullptr;
+  size_t n = 0;
+};
+
+}  // namespace
+
+struct caspt2_ctx {
+  Dims d{};
+  caspt2_options opt{};
+  int device = 0;
+  bool have_inputs = false;
+  bool have_rdm3 = false, have_rdm4 = false;
+  bool solved = false;
+  std::vector<void*> allocs;
+
+  // inputs (device copies)
+  double *f = nullptr, *B = nullptr, *rdm1 = nullptr, *rdm2 = nullptr, *rdm3 = nullptr,
+         *rdm4 = nullptr;
+  // setup work
+  double *dact = nullptr, *gam = nullptr, *Y = nullptr, *g = nullptr, *bsum = nullptr,
+         *bfro = nullptr, *ecore = nullptr, *fref = nullptr, *U = nullptr, *Etil = nullptr,
+         *Ftil = nullptr, *E0 = nullptr, *rdm1r = nullptr, *rdm2r = nullptr, *eri = nullptr,
+         *href = nullptr;
+  // classes
+  double *ecls = nullptr, *ncls = nullptr, *mindenom = nullptr;
+  ClassHWork hw{};
+  // results
+  double *heff = nullptr, *ems = nullptr, *R = nullptr;
+  int* status = nullptr;
+  cudaEvent_t ev[kNumStages + 1] = {};
+
+  // host copies of the last results
+  std::vector<double> hU, hE0, hHref, hHeff, hEms, hR, hEcls, hNcls;
+  double hEcore = 0.0, hMinDenom = 0.0;
+  double times[kNumTimes] = {};
+  long launches = 0;
+
+  template <class T>
+  int alloc(T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    void* q = nullptr;
+    if (cudaMalloc(&q, count * sizeof(T)) != cudaSuccess) return CASPT2_ENOMEM;
+    allocs.push_back(q);
+    *p = static_cast<T*>(q);
+    return CASPT2_OK;
+  }
+};
+
+extern "C" {
+
+void caspt2_default_options(caspt2_options* o) {
+  if (!o) return;
+  o->xms = 1;
+  o->scheme = CASPT2_MSMR;
+  o->shift = 0.0;
+  o->ovl_thresh = 1e-9;
+  o->enuc = 0.0;
+  o->target_state = 0;
+  o->class_mask = caspt2_supported_classes();
+}
+
+unsigned caspt2_supported_classes(void) { return 1u << CASPT2_CLASS_H; }
+
+const char* caspt2_strerror(int st) {
+  switch (st) {
+    case CASPT2_OK: return "ok";
+    case CASPT2_EINVAL: return "invalid argument (sizes, options or pointers)";
+    case CASPT2_ENOMEM: return "device allocation failed";
+    case CASPT2_ENOTCONV: return "an eigensolver or iteration did not converge";
+    case CASPT2_ENAN: return "NaN or Inf in inputs or results";
+    case CASPT2_ETIMEOUT: return "a bounded device wait gave up";
+    case CASPT2_ECUDA: return "CUDA runtime error";
+    case CASPT2_ESTATE: return "call out of order";
+    case CASPT2_WINTRUDER: return "warning: a denominator is below 1e-3 Eh (intruder state)";
+    default: return "unknown status";
+  }
+}
+
+void caspt2_destroy(caspt2_ctx* ctx) {
+  if (!ctx) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(ctx->device);
+  for (void* p : ctx->allocs) cudaFree(p);
+  for (auto& e : ctx->ev)
+    if (e) cudaEventDestroy(e);
+  if (ctx->hw.ev_gemm0) cudaEventDestroy(ctx->hw.ev_gemm0);
+  if (ctx->hw.ev_gemm1) cudaEventDestroy(ctx->hw.ev_gemm1);
+  cudaSetDevice(cur);
+  delete ctx;
+}
+
+int caspt2_create(caspt2_ctx** out, const caspt2_dims* dims, const caspt2_options* opt) {
+  if (!out || !dims) return CASPT2_EINVAL;
+  *out = nullptr;
+  const caspt2_dims& q = *dims;
+  if (q.nclosed < 0 || q.nact < 0 || q.nvirt < 0 || q.naux <= 0 || q.nstate <= 0 ||
+      q.nstate > kMaxStates)
+    return CASPT2_EINVAL;
+  caspt2_options o;
+  caspt2_default_options(&o);
+  if (opt) o = *opt;
+  if (o.scheme != CASPT2_MSMR && o.scheme != CASPT2_SSSR) return CASPT2_EINVAL;
+  if (!(o.shift >= 0.0) || !(o.ovl_thresh > 0.0)) return CASPT2_EINVAL;
+  if (o.class_mask & ~caspt2_supported_classes()) return CASPT2_EINVAL;
+  if (o.target_state >= q.nstate) return CASPT2_EINVAL;
+
+  caspt2_ctx* c = new (std::nothrow) caspt2_ctx();
+  if (!c) return CASPT2_ENOMEM;
+  c->d = Dims{q.nclosed, q.nact, q.nvirt, q.naux, q.nstate};
+  c->opt = o;
+  cudaGetDevice(&c->device);
+  const Dims& d = c->d;
+  const size_t nmo = d.nmo(), n = d.n, a = d.a, X = d.X;
+  const size_t a2 = a * a, a4 = a2 * a2;
+  int st = CASPT2_OK;
+#define ALLOC(ptr, cnt) \
+  if (st == CASPT2_OK) st = c->alloc(&(ptr), (cnt))
+  ALLOC(c->f, nmo * nmo);
+  ALLOC(c->B, X * nmo * nmo);
+  ALLOC(c->rdm1, n * n * a2);
+  ALLOC(c->rdm2, n * n * a4);
+  ALLOC(c->dact, a2);
+  ALLOC(c->gam, X);
+  ALLOC(c->Y, X * nmo * (a ? a : 1));
+  ALLOC(c->g, nmo * nmo);
+  ALLOC(c->bsum, X);
+  ALLOC(c->bfro, X);
+  ALLOC(c->ecore, 1);
+  ALLOC(c->fref, n * n);
+  ALLOC(c->U, n * n);
+  ALLOC(c->Etil, n);
+  ALLOC(c->Ftil, n * n);
+  ALLOC(c->E0, n);
+  ALLOC(c->rdm1r, n * n * a2);
+  ALLOC(c->rdm2r, n * n * a4);
+  ALLOC(c->eri, a4);
+  ALLOC(c->href, n * n);
+  ALLOC(c->ecls, (size_t)CASPT2_NCLASS * n * n);
+  ALLOC(c->ncls, (size_t)CASPT2_NCLASS * n);
+  ALLOC(c->mindenom, 1);
+  ALLOC(c->heff, n * n);
+  ALLOC(c->ems, n);
+  ALLOC(c->R, n * n);
+  ALLOC(c->status, 1);
+  // class H work
+  c->hw.nblocks = classH_blocks(d);
+  const size_t nshift = (size_t)classH_nshift(d, o.scheme);
+  ALLOC(c->hw.Bp, (size_t)d.c * X * d.v);
+  ALLOC(c->hw.eps, nmo);
+  ALLOC(c->hw.W, n * n);
+  ALLOC(c->hw.omega, n);
+  ALLOC(c->hw.shifts, nshift);
+  ALLOC(c->hw.partial, (size_t)c->hw.nblocks * (2 * nshift + 1));
+  ALLOC(c->hw.sums, 2 * nshift + 1);
+#undef ALLOC
+  for (auto& e : c->ev)
+    if (st == CASPT2_OK && cudaEventCreate(&e) != cudaSuccess) st = CASPT2_ECUDA;
+  if (st == CASPT2_OK && (cudaEventCreate(&c->hw.ev_gemm0) != cudaSuccess ||
+                          cudaEventCreate(&c->hw.ev_gemm1) != cudaSuccess))
+    st = CASPT2_ECUDA;
+  if (st != CASPT2_OK) {
+    caspt2_destroy(c);
+    return st;
+  }
+  c->hU.assign(n * n, 0.0);
+  c->hE0.assign(n, 0.0);
+  c->hHref.assign(n * n, 0.0);
+  c->hHeff.assign(n * n, 0.0);
+  c->hEms.assign(n, 0.0);
+  c->hR.assign(n * n, 0.0);
+  c->hEcls.assign((size_t)CASPT2_NCLASS * n * n, 0.0);
+  c->hNcls.assign((size_t)CASPT2_NCLASS * n, 0.0);
+  *out = c;
+  return CASPT2_OK;
+}
+
+int caspt2_set_inputs(caspt2_ctx* c, int mem, const double* fock, const double* dfB,
+                      const double* rdm1, const double* rdm2, const double* rdm3,
+                      const double* rdm4) {
+  if (!c || !fock || !dfB || !rdm1 || !rdm2) return CASPT2_EINVAL;
+  if (mem != CASPT2_MEM_HOST && mem != CASPT2_MEM_DEVICE) return CASPT2_EINVAL;
+  const Dims& d = c->d;
+  const size_t nmo = d.nmo(), n = d.n, a2 = (size_t)d.a * d.a;
+  const cudaMemcpyKind k = mem == CASPT2_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  CASPT2_CUDA_TRY(cudaSetDevice(c->device));
+  CASPT2_CUDA_TRY(cudaMemcpy(c->f, fock, sizeof(double) * nmo * nmo, k));
+  CASPT2_CUDA_TRY(cudaMemcpy(c->B, dfB, sizeof(double) * d.X * nmo * nmo, k));
+  CASPT2_CUDA_TRY(cudaMemcpy(c->rdm1, rdm1, sizeof(double) * n * n * a2, k));
+  CASPT2_CUDA_TRY(cudaMemcpy(c->rdm2, rdm2, sizeof(double) * n * n * a2 * a2, k));
+  c->have_rdm3 = rdm3 != nullptr;
+  c->have_rdm4 = rdm4 != nullptr;
+  c->have_inputs = true;
+  c->solved = false;
+  return CASPT2_OK;
+}
+
+int caspt2_solve(caspt2_ctx* c, void* stream) {
+  if (!c) return CASPT2_EINVAL;
+  if (!c->have_inputs) return CASPT2_ESTATE;
+  CASPT2_CUDA_TRY(cudaSetDevice(c->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const Dims& d = c->d;
+  const caspt2_options& o = c->opt;
+  const int n = d.n;
+  const long a2 = (long)d.a * d.a;
+  const double big = 1e300;
+  const long launches0 = launch_counter();
+  CASPT2_CUDA_TRY(cudaMemsetAsync(c->status, 0, sizeof(int), s));
+  CASPT2_CUDA_TRY(cudaMemcpyAsync(c->mindenom, &big, sizeof(double), cudaMemcpyHostToDevice, s));
+  CASPT2_CUDA_TRY(cudaMemsetAsync(c->ecls, 0, sizeof(double) * CASPT2_NCLASS * n * n, s));
+  CASPT2_CUDA_TRY(cudaMemsetAsync(c->ncls, 0, sizeof(double) * CASPT2_NCLASS * n, s));
+
+  // ---- stage 0: setup (Sec. II.A, II.B)
+  CASPT2_CUDA_TRY(cudaEventRecord(c->ev[0], s));
+  CASPT2_CUDA_TRY(launch_dsa(c->rdm1, d, c->dact, s));
+  CASPT2_CUDA_TRY(launch_gmat(c->B, c->dact, d, c->gam, c->Y, c->g, s));
+  CASPT2_CUDA_TRY(launch_ecore(c->f, c->g, c->B, d, c->bsum, c->bfro, c->ecore, s));
+  CASPT2_CUDA_TRY(launch_fref(c->f, c->rdm1, d, c->fref, s));
+  CASPT2_CUDA_TRY(launch_sym_eig(c->fref, n, c->U, c->Etil, o.xms ? 0 : 1, c->status, s));
+  CASPT2_CUDA_TRY(launch_congruence(c->fref, c->U, n, c->Ftil, s));
+  CASPT2_CUDA_TRY(launch_diag(c->Ftil, n, c->E0, s));
+  CASPT2_CUDA_TRY(launch_rotate_rdm(c->rdm1, c->U, n, a2, c->rdm1r, s));
+  CASPT2_CUDA_TRY(launch_rotate_rdm(c->rdm2, c->U, n, a2 * a2, c->rdm2r, s));
+  CASPT2_CUDA_TRY(launch_eri_act(c->B, d, c->eri, s));
+  CASPT2_CUDA_TRY(launch_href(c->f, c->g, c->rdm1r, c->rdm2r, c->eri, c->ecore, o.enuc, d,
+                              c->href, s));
+  CASPT2_CUDA_TRY(cudaEventRecord(c->ev[1], s));
+
+  // ---- stage 1: class H (direct)
+  if (o.class_mask >> CASPT2_CLASS_H & 1u) {
+    CASPT2_CUDA_TRY(launch_classH(c->f, c->B, c->Ftil, c->E0, o.shift, o.scheme, d, c->hw,
+                                  c->status, c->ecls + (long)CASPT2_CLASS_H * n * n,
+                                  c->ncls + (long)CASPT2_CLASS_H * n, c->mindenom, s));
+  }
+  CASPT2_CUDA_TRY(cudaEventRecord(c->ev[2], s));
+  // ---- stage 2: other classes (none yet in this build)
+  CASPT2_CUDA_TRY(cudaEventRecord(c->ev[3], s));
+  // ---- stage 3: effective Hamiltonian and its eigenpairs (Sec. II.B)
+  CASPT2_CUDA_TRY(launch_heff(c->href, c->ecls, c->ncls, o.class_mask, o.shift, n, c->heff, s));
+  CASPT2_CUDA_TRY(launch_sym_eig(c->heff, n, c->R, c->ems, 0, c->status, s));
+  CASPT2_CUDA_TRY(cudaEventRecord(c->ev[4], s));
+
+  // results back to the host copies
+  int hst = 0;
+  CASPT2_CUDA_TRY(cudaMemcpyAsync(c->hU.data(), c->U, sizeof(double) * n * n, cudaMemcpyDeviceToHost, s));
+  CASPT2_CUDA_TRY(cudaMemcpyAsync(c->hE0.data(), c->E0, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+  CASPT2_CUDA_TRY(cudaMemcpyAsync(c->hHref.data(), c->href, sizeof(double) * n * n, cudaMemcpyDeviceToHost, s));
+  CASPT2_CUDA_TRY(cudaMemcpyAsync(c->hHeff.data(), c->heff, sizeof(double) * n * n, cudaMemcpyDeviceToHost, s));
+  CASPT2_CUDA_TRY(cudaMemcpyAsync(c->hEms.data(), c->ems, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+  CASPT2_CUDA_TRY(cudaMemcpyAsync(c->hR.data(), c->R, sizeof(double) * n * n, cudaMemcpyDeviceToHost, s));
+  CASPT2_CUDA_TRY(cudaMemcpyAsync(c->hEcls.data(), c->ecls, sizeof(double) * CASPT2_NCLASS * n * n, cudaMemcpyDeviceToHost, s));
+  CASPT2_CUDA_TRY(cudaMemcpyAsync(c->hNcls.data(), c->ncls, sizeof(double) * CASPT2_NCLASS * n, cudaMemcpyDeviceToHost, s));
+  CASPT2_CUDA_TRY(cudaMemcpyAsync(&c->hEcore, c->ecore, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CASPT2_CUDA_TRY(cudaMemcpyAsync(&c->hMinDenom, c->mindenom, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CASPT2_CUDA_TRY(cudaMemcpyAsync(&hst, c->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CASPT2_CUDA_TRY(cudaStreamSynchronize(s));
+  for (int k = 0; k < kNumStages; ++k) {
+    float ms = 0.f;
+    CASPT2_CUDA_TRY(cudaEventElapsedTime(&ms, c->ev[k], c->ev[k + 1]));
+    c->times[k] = ms;
+  }
+  c->times[kNumStages] = 0.0;
+  if ((o.class_mask >> CASPT2_CLASS_H & 1u) && d.c > 0 && d.v > 0) {
+    float ms = 0.f;
+    CASPT2_CUDA_TRY(cudaEventElapsedTime(&ms, c->hw.ev_gemm0, c->hw.ev_gemm1));
+    c->times[kNumStages] = ms;
+  }
+  c->launches = launch_counter() - launches0;
+  c->solved = true;
+  if (hst != 0) return hst;
+  for (double x : c->hEms)
+    if (!(x == x) || x > 1e300 || x < -1e300) return CASPT2_ENAN;
+  if (c->hMinDenom < 1e-3) return CASPT2_WINTRUDER;
+  return CASPT2_OK;
+}
+
+int caspt2_get_energies(caspt2_ctx* c, double* U, double* E0, double* Href, double* Heff,
+                        double* Ems, double* R) {
+  if (!c) return CASPT2_EINVAL;
+  if (!c->solved) return CASPT2_ESTATE;
+  const size_t n = c->d.n;
+  if (U) std::memcpy(U, c->hU.data(), sizeof(double) * n * n);
+  if (E0) std::memcpy(E0, c->hE0.data(), sizeof(double) * n);
+  if (Href) std::memcpy(Href, c->hHref.data(), sizeof(double) * n * n);
+  if (Heff) std::memcpy(Heff, c->hHeff.data(), sizeof(double) * n * n);
+  if (Ems) std::memcpy(Ems, c->hEms.data(), sizeof(double) * n);
+  if (R) std::memcpy(R, c->hR.data(), sizeof(double) * n * n);
+  return CASPT2_OK;
+}
+
+int caspt2_get_class_energy(caspt2_ctx* c, int cls, double* e, double* norm) {
+  if (!c || cls < 0 || cls >= CASPT2_NCLASS) return CASPT2_EINVAL;
+  if (!(c->opt.class_mask >> cls & 1u)) return CASPT2_EINVAL;
+  if (!c->solved) return CASPT2_ESTATE;
+  const size_t n = c->d.n;
+  if (e) std::memcpy(e, c->hEcls.data() + cls * n * n, sizeof(double) * n * n);
+  if (norm) std::memcpy(norm, c->hNcls.data() + cls * n, sizeof(double) * n);
+  return CASPT2_OK;
+}
+
+int caspt2_get_core_energy(caspt2_ctx* c, double* ecore) {
+  if (!c || !ecore) return CASPT2_EINVAL;
+  if (!c->solved) return CASPT2_ESTATE;
+  *ecore = c->hEcore;
+  return CASPT2_OK;
+}
+
+int caspt2_get_timings(caspt2_ctx* c, double* times, int* count) {
+  if (!c || !count) return CASPT2_EINVAL;
+  int m = *count < kNumTimes ? *count : kNumTimes;
+  for (int k = 0; k < m && times; ++k) times[k] = c->times[k];
+  *count = kNumTimes;
+  return CASPT2_OK;
+}
+
+long caspt2_get_kernel_launches(caspt2_ctx* c) { return c ? c->launches : -1; }
+
+}  // extern "C"

@@ -1,0 +1,262 @@
+// Class H (E_ai,bj, Eq. class) of the first-order amplitudes, FP64, direct.
+//
+// For block-diagonal f the E_ai,bj E_Omega|N~> functions couple to the
+// reference index only through the active Fock matrix: with U^T Fref U =
+// W diag(omega) W^T, the amplitude equation (Eq. ampeq) for state L becomes, in
+// the eigenbasis nu, a closed-shell pair equation with denominator
+//     D = e_a + e_b - e_i - e_j + omega_nu - E0_L + E_s.
+// The contributions to the effective Hamiltonian (Sec. II.B) are then
+//     <Psi1_L|H|L'~>_H = -sum_nu W_Lnu W_L'nu sum_ijab K(2K - K')/D
+//     <Psi1_L|Psi1_L>_H =  sum_nu W_Lnu^2     sum_ijab K(2K - K')/D^2
+// with K = (ai|bj) = sum_P B_Pai B_Pbj, K' = (aj|bi).  Under SS-SR (Eq. wfp2) only
+// nu = L survives and D = e_a + e_b - e_i - e_j + E_s.
+//
+// The amplitudes are never stored: one CTA forms a 64x64 tile of K_ij and of
+// K_ji (= K_ij transposed) over the DF index, and the epilogue applies every
+// denominator shift and reduces the energy and norm sums.  Per-CTA partial
+// sums are reduced afterwards in a fixed order, so results are bitwise
+// reproducible run to run.
+#include "kernels.cuh"
+
+namespace caspt2 {
+
+constexpr int kHT = 64;   // tile edge in a and in b
+constexpr int kHK = 16;   // DF-index chunk
+constexpr int kHThreads = 256;
+constexpr int kMaxShift = kMaxStates * kMaxStates;
+
+// Bp[i][P][a] = B[P][i][vo + a]
+__global__ void k_pack_cv(const double* __restrict__ B, int c, int v, int X, int nmo, int vo,
+                          double* __restrict__ Bp) {
+  long total = (long)c * X * v;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long)gridDim.x * blockDim.x) {
+    int a = idx % v;
+    long iP = idx / v;
+    int P = iP % X;
+    int i = iP / X;
+    Bp[idx] = B[((long)P * nmo + i) * nmo + vo + a];
+  }
+}
+
+// eps[0..c) = closed orbital energies, eps[c..c+v) = virtual orbital energies
+__global__ void k_eps_cv(const double* __restrict__ f, int nmo, int c, int a, int v, double* eps) {
+  int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x < c) eps[x] = f[(long)x * nmo + x];
+  else if (x < c + v) eps[x] = f[(long)(x + a) * nmo + x + a];
+}
+
+// shifts[nu*n + L] = omega_nu - E0_L + E_s (MS-MR) ; shifts[0] = E_s (SS-SR)
+__global__ void k_classH_shifts(const double* __restrict__ omega, const double* __restrict__ E0,
+                                double shift, int n, int scheme, double* shifts) {
+  int k = threadIdx.x;
+  if (scheme == CASPT2_SSSR) {
+    if (k == 0) shifts[0] = shift;
+    return;
+  }
+  if (k < n * n) shifts[k] = omega[k / n] - E0[k % n] + shift;
+}
+
+__global__ void __launch_bounds__(kHThreads)
+k_classH(const double* __restrict__ Bp, const double* __restrict__ eps,
+         const double* __restrict__ shifts, int nshift, int c, int v, int X, int ntile,
+         double* __restrict__ partial) {
+  __shared__ double sAi[kHK][kHT], sBj[kHK][kHT], sAj[kHK][kHT], sBi[kHK][kHT];
+  __shared__ double sEa[kHT], sEb[kHT];
+  __shared__ double sShift[kMaxShift];
+  __shared__ double red[32];
+
+  long bid = blockIdx.x;
+  const int tb = bid % ntile; bid /= ntile;
+  const int ta = bid % ntile; bid /= ntile;
+  int pair = (int)bid, i = 0;
+  while (pair >= c - i) { pair -= c - i; ++i; }
+  const int j = i + pair;
+  const bool same = (i == j);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int a0 = ta * kHT, b0 = tb * kHT;
+  const double* bi = Bp + (long)i * X * v;
+  const double* bj = Bp + (long)j * X * v;
+
+  for (int k = threadIdx.x; k < nshift; k += kHThreads) sShift[k] = shifts[k];
+  for (int k = threadIdx.x; k < kHT; k += kHThreads) {
+    sEa[k] = (a0 + k < v) ? eps[c + a0 + k] : 0.0;   // eps holds closed then virtual energies
+    sEb[k] = (b0 + k < v) ? eps[c + b0 + k] : 0.0;
+  }
+  __syncthreads();
+
+  double t1[4][4], t2[4][4];
+#pragma unroll
+  for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) t1[ii][jj] = t2[ii][jj] = 0.0;
+
+  for (int P0 = 0; P0 < X; P0 += kHK) {
+    for (int l = threadIdx.x; l < kHK * kHT; l += kHThreads) {
+      const int kk = l / kHT, col = l % kHT;
+      const int P = P0 + kk;
+      const bool okP = P < X;
+      const int a = a0 + col, b = b0 + col;
+      sAi[kk][col] = (okP && a < v) ? bi[(long)P * v + a] : 0.0;
+      sBj[kk][col] = (okP && b < v) ? bj[(long)P * v + b] : 0.0;
+      if (!same) {
+        sAj[kk][col] = (okP && a < v) ? bj[(long)P * v + a] : 0.0;
+        sBi[kk][col] = (okP && b < v) ? bi[(long)P * v + b] : 0.0;
+      }
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < kHK; ++kk) {
+      double ra[4], rb[4];
+#pragma unroll
+      for (int ii = 0; ii < 4; ++ii) ra[ii] = sAi[kk][ty + 16 * ii];
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) rb[jj] = sBj[kk][tx + 16 * jj];
+#pragma unroll
+      for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) t1[ii][jj] = fma(ra[ii], rb[jj], t1[ii][jj]);
+      if (!same) {
+#pragma unroll
+        for (int ii = 0; ii < 4; ++ii) ra[ii] = sAj[kk][ty + 16 * ii];
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) rb[jj] = sBi[kk][tx + 16 * jj];
+#pragma unroll
+        for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj) t2[ii][jj] = fma(ra[ii], rb[jj], t2[ii][jj]);
+      }
+    }
+    __syncthreads();
+  }
+
+  // epilogue: numerators and shift-free denominators of this thread's 16 (a, b)
+  const double ei = eps[i], ej = eps[j];
+  double num[16], d0[16];
+#pragma unroll
+  for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+      const int la = ty + 16 * ii, lb = tx + 16 * jj;
+      const bool ok = (a0 + la < v) && (b0 + lb < v);
+      const double k1 = t1[ii][jj];
+      const double k2 = same ? k1 : t2[ii][jj];
+      // K_ij^ab (2K_ij^ab - K_ij^ba) + (i != j) K_ji^ab (2K_ji^ab - K_ji^ba)
+      double nm = k1 * (2.0 * k1 - k2);
+      if (!same) nm += k2 * (2.0 * k2 - k1);
+      num[ii * 4 + jj] = ok ? nm : 0.0;
+      d0[ii * 4 + jj] = ok ? (sEa[la] + sEb[lb] - ei - ej) : 1.0;
+    }
+  double* out = partial + blockIdx.x * (long)(2 * nshift + 1);
+  double dmin = 1e300;
+  for (int k = 0; k < nshift; ++k) {
+    const double sh = sShift[k];
+    double e = 0.0, nr = 0.0;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const double inv = 1.0 / (d0[q] + sh);
+      e = fma(num[q], inv, e);
+      nr = fma(num[q] * inv, inv, nr);
+      if (num[q] != 0.0) dmin = fmin(dmin, fabs(d0[q] + sh));
+    }
+    e = block_sum(e, red);
+    if (threadIdx.x == 0) out[k] = e;
+    nr = block_sum(nr, red);
+    if (threadIdx.x == 0) out[nshift + k] = nr;
+  }
+  dmin = block_min(dmin, red);
+  if (threadIdx.x == 0) out[2 * nshift] = dmin;
+}
+
+// sums[col] = fixed-order reduction of partial[.][col]; the last column is a min.
+__global__ void k_reduce_cols(const double* __restrict__ partial, long nblocks, int ncol,
+                              double* __restrict__ sums) {
+  __shared__ double red[32];
+  const int col = blockIdx.x;
+  const bool is_min = (col == ncol - 1);
+  double acc = is_min ? 1e300 : 0.0;
+  for (long b = threadIdx.x; b < nblocks; b += blockDim.x) {
+    double x = partial[b * ncol + col];
+    acc = is_min ? fmin(acc, x) : acc + x;
+  }
+  acc = is_min ? block_min(acc, red) : block_sum(acc, red);
+  if (threadIdx.x == 0) sums[col] = acc;
+}
+
+// e[L][L'] = -sum_nu W_Lnu W_L'nu S_e[nu,L]; norm[L] = sum_nu W_Lnu^2 S_n[nu,L]
+__global__ void k_classH_combine(const double* __restrict__ sums, const double* __restrict__ W,
+                                 int n, int scheme, double* ecls, double* ncls, double* mindenom,
+                                 int* status) {
+  int idx = threadIdx.x;
+  const int nshift = (scheme == CASPT2_SSSR) ? 1 : n * n;
+  if (idx < n * n) {
+    int L = idx / n, Lp = idx % n;
+    double e = 0.0;
+    if (scheme == CASPT2_SSSR) {
+      e = (L == Lp) ? -sums[0] : 0.0;
+    } else {
+      for (int nu = 0; nu < n; ++nu) e -= W[L * n + nu] * W[Lp * n + nu] * sums[nu * n + L];
+    }
+    ecls[idx] = e;
+  }
+  if (idx < n) {
+    double nr = 0.0;
+    if (scheme == CASPT2_SSSR) {
+      nr = sums[nshift];
+    } else {
+      for (int nu = 0; nu < n; ++nu) nr += W[idx * n + nu] * W[idx * n + nu] * sums[nshift + nu * n + idx];
+    }
+    ncls[idx] = nr;
+  }
+  if (idx == 0) {
+    double dm = sums[2 * nshift];
+    *mindenom = fmin(*mindenom, dm);
+    if (!(dm == dm)) atomicExch(status, CASPT2_ENAN);
+  }
+}
+
+long classH_blocks(const Dims& d) {
+  long ntile = (d.v + kHT - 1) / kHT;
+  long npair = (long)d.c * (d.c + 1) / 2;
+  return npair * ntile * ntile;
+}
+
+int classH_nshift(const Dims& d, int scheme) { return scheme == CASPT2_SSSR ? 1 : d.n * d.n; }
+
+cudaError_t launch_classH(const double* f, const double* B, const double* Ftil, const double* E0,
+                          double shift, int scheme, const Dims& d, ClassHWork& w, int* status,
+                          double* ecls, double* ncls, double* mindenom, cudaStream_t s) {
+  const int n = d.n, nmo = d.nmo();
+  const int nshift = classH_nshift(d, scheme);
+  cudaError_t e;
+  if (d.c == 0 || d.v == 0) {
+    e = cudaMemsetAsync(ecls, 0, sizeof(double) * n * n, s);
+    if (e != cudaSuccess) return e;
+    return cudaMemsetAsync(ncls, 0, sizeof(double) * n, s);
+  }
+  ++launch_counter();
+  k_eps_cv<<<(d.c + d.v + 127) / 128, 128, 0, s>>>(f, nmo, d.c, d.a, d.v, w.eps);
+  long tp = (long)d.c * d.X * d.v;
+  ++launch_counter();
+  k_pack_cv<<<(int)std::min<long>((tp + 255) / 256, 152 * 32), 256, 0, s>>>(
+      B, d.c, d.v, d.X, nmo, d.c + d.a, w.Bp);
+  e = launch_sym_eig(Ftil, n, w.W, w.omega, 0, status, s);
+  if (e != cudaSuccess) return e;
+  ++launch_counter();
+  k_classH_shifts<<<1, kMaxShift, 0, s>>>(w.omega, E0, shift, n, scheme, w.shifts);
+  const int ntile = (d.v + kHT - 1) / kHT;
+  const long nb = classH_blocks(d);
+  if (w.ev_gemm0) cudaEventRecord(w.ev_gemm0, s);
+  ++launch_counter();
+  k_classH<<<(unsigned)nb, kHThreads, 0, s>>>(w.Bp, w.eps, w.shifts, nshift, d.c, d.v, d.X, ntile,
+                                             w.partial);
+  if (w.ev_gemm1) cudaEventRecord(w.ev_gemm1, s);
+  const int ncol = 2 * nshift + 1;
+  ++launch_counter();
+  k_reduce_cols<<<ncol, 256, 0, s>>>(w.partial, nb, ncol, w.sums);
+  ++launch_counter();
+  k_classH_combine<<<1, kMaxShift, 0, s>>>(w.sums, w.W, n, scheme, ecls, ncls, mindenom, status);
+  return cudaGetLastError();
+}
+
+}  // namespace caspt2

@@ -1,0 +1,63 @@
+// Internal launcher declarations (host side) for the CASPT2 kernels.
+#pragma once
+#include "common.cuh"
+
+namespace caspt2 {
+
+struct Dims {
+  int c, a, v, X, n;
+  int nmo() const { return c + a + v; }
+};
+
+// ---- setup (setup.cu) --------------------------------------------------------
+// d_act = (1/n) sum_N rdm1[N][N]                         (Sec. II.B, d^(0)sa)
+cudaError_t launch_dsa(const double* rdm1, const Dims& d, double* dact, cudaStream_t s);
+// g = g(d_act) over all nmo x nmo (Sec. II.B, g(d) with d nonzero in the active block)
+cudaError_t launch_gmat(const double* B, const double* dact, const Dims& d, double* gam,
+                        double* Y, double* g, cudaStream_t s);
+// E_core = <core|H|core>, with h = f - g(d_sa)
+cudaError_t launch_ecore(const double* f, const double* g, const double* B, const Dims& d,
+                         double* bsum, double* bfro, double* ecore, cudaStream_t s);
+// Fref[M][N] = sum_rs f_rs rdm1[M][N][r][s]             (Sec. II.A, XMS Fock)
+cudaError_t launch_fref(const double* f, const double* rdm1, const Dims& d, double* fref,
+                        cudaStream_t s);
+// symmetric eigenpairs of an n x n matrix (n <= 16), ascending, canonical column signs
+cudaError_t launch_sym_eig(const double* A, int n, double* V, double* w, int identity,
+                           int* status, cudaStream_t s);
+// out = U^T A U (n x n)
+cudaError_t launch_congruence(const double* A, const double* U, int n, double* out,
+                              cudaStream_t s);
+// E0[L] = out[L][L]
+cudaError_t launch_diag(const double* A, int n, double* e0, cudaStream_t s);
+// dst[M][N][e] = sum_KL U[K][M] U[L][N] src[K][L][e]     (Sec. II.A, rotated RDMs)
+cudaError_t launch_rotate_rdm(const double* src, const double* U, int n, long len, double* dst,
+                              cudaStream_t s);
+// eri[r][s][t][u] = (rs|tu) over the active block
+cudaError_t launch_eri_act(const double* B, const Dims& d, double* eri, cudaStream_t s);
+// H^ref_MN = d_MN (E_core + E_nuc) + sum fc_rs G1~ + 1/2 sum (rs|tu) G2~      (Sec. II.A)
+cudaError_t launch_href(const double* f, const double* g, const double* rdm1r, const double* rdm2r,
+                        const double* eri, const double* ecore, double enuc, const Dims& d,
+                        double* href, cudaStream_t s);
+// H^eff = H^ref + 1/2 (e + e^T) - diag(E_s * norm) summed over enabled classes (Sec. II.B)
+cudaError_t launch_heff(const double* href, const double* ecls, const double* ncls, unsigned mask,
+                        double shift, int n, double* heff, cudaStream_t s);
+
+// ---- class H (class_h.cu) ----------------------------------------------------
+struct ClassHWork {
+  double* Bp;        // [c][X][v]   packed (ai|P) factors
+  double* eps;       // [nmo]       diagonal of f
+  double* W;         // [n][n]      eigenvectors of U^T Fref U
+  double* omega;     // [n]
+  double* shifts;    // [nshift]    omega_nu - E0_L + E_s
+  double* partial;   // [nblocks][2*nshift + 1]
+  double* sums;      // [2*nshift + 1]
+  long    nblocks;
+  cudaEvent_t ev_gemm0 = nullptr, ev_gemm1 = nullptr;  // optional: bracket the GEMM kernel
+};
+long classH_blocks(const Dims& d);
+int  classH_nshift(const Dims& d, int scheme);
+cudaError_t launch_classH(const double* f, const double* B, const double* Ftil, const double* E0,
+                          double shift, int scheme, const Dims& d, ClassHWork& w, int* status,
+                          double* ecls, double* ncls, double* mindenom, cudaStream_t s);
+
+}  // namespace caspt2

@@ -216,36 +216,65 @@ class ActiveSpace:
         return np.ascontiguousarray(total.transpose(perm))
 
 
+def hamiltonian_matrix(space: ActiveSpace, h1: np.ndarray, eri: np.ndarray) -> np.ndarray:
+    """Dense H = sum h1_rs E_rs + 1/2 sum (rs|tu) E_{rs,tu} over the Sz = 0 determinants.
+
+    With E_rs = e^a_rs + e^b_rs: H = H_a (x) 1 + 1 (x) H_b + sum (rs|tu) e_rs (x) e_tu,
+    H_s = sum k_rs e_rs + 1/2 sum (rs|tu) e_rs e_tu, k = h1 - 1/2 sum_s (rs|st)."""
+    n = space.norb
+    e = space.e.reshape(n * n, *space.e.shape[2:])          # [rs, I, J]
+    ns = e.shape[1]
+    k = (h1 - 0.5 * np.einsum("rsst->rt", eri)).reshape(n * n)
+    v = eri.reshape(n * n, n * n)
+    g = np.tensordot(v, e, axes=(1, 0))                      # G_rs = sum_tu (rs|tu) e_tu
+    hs = np.tensordot(k, e, axes=(0, 0)) + 0.5 * np.einsum("rij,rjk->ik", e, g)
+    eye = np.eye(ns)
+    hm = np.kron(hs, eye) + np.kron(eye, hs)
+    ab = np.tensordot(e.reshape(n * n, ns * ns).T, g.reshape(n * n, ns * ns), axes=(1, 0))
+    hm += ab.reshape(ns, ns, ns, ns).transpose(0, 2, 1, 3).reshape(ns * ns, ns * ns)
+    return 0.5 * (hm + hm.T)
+
+
+def s2_matrix(space: ActiveSpace) -> np.ndarray:
+    """S^2 = N_b - sum_pq e^a_qp (x) e^b_pq  (Sz = 0)."""
+    n = space.norb
+    ns = space.e.shape[2]
+    ea = space.e.transpose(1, 0, 2, 3).reshape(n * n, ns * ns)   # e_qp at index (p, q)
+    eb = space.e.reshape(n * n, ns * ns)                          # e_pq
+    m = -(ea.T @ eb).reshape(ns, ns, ns, ns).transpose(0, 2, 1, 3).reshape(ns * ns, ns * ns)
+    m += space.nb * np.eye(ns * ns)
+    return 0.5 * (m + m.T)
+
+
 def lowest_singlets(space: ActiveSpace, h1: np.ndarray, eri: np.ndarray, nstate: int,
                     penalty: float = 1.0, tol: float = 1e-6):
     """Lowest nstate singlet eigenvectors of the active-space Hamiltonian.
 
-    H + penalty * S^2 is diagonalised exactly (dense); states with <S^2> above
-    tol are skipped.  Each vector is signed so that its largest-|.| component
-    is positive.  Returns (energies without the penalty, ci[ndet, nstate])."""
+    H + penalty * S^2 is diagonalised exactly (dense, lowest eigenpairs only);
+    states with <S^2> above tol are skipped.  Each vector is signed so that its
+    largest-|.| component is positive.  Returns (energies without the penalty,
+    ci[ndet, nstate])."""
+    import scipy.linalg as sl
     nd = space.ndet
-    if nd > 8000:
-        raise ValueError("dense CASCI limited to 8000 determinants")
-    hm = np.zeros((nd, nd))
-    s2 = np.zeros((nd, nd))
-    blk = 512
-    for c0 in range(0, nd, blk):
-        eye = np.zeros((nd, min(blk, nd - c0)))
-        eye[np.arange(c0, c0 + eye.shape[1]), np.arange(eye.shape[1])] = 1.0
-        hm[:, c0:c0 + eye.shape[1]] = space.sigma(eye, h1, eri)
-        s2[:, c0:c0 + eye.shape[1]] = space.s_squared(eye)
-    hm = 0.5 * (hm + hm.T)
-    s2 = 0.5 * (s2 + s2.T)
-    w, v = np.linalg.eigh(hm + penalty * s2)
+    if nd > 20000:
+        raise ValueError("dense CASCI limited to 20000 determinants")
+    hm = hamiltonian_matrix(space, h1, eri)
+    s2 = s2_matrix(space)
     keep_e, keep_v = [], []
-    for j in range(nd):
-        c = v[:, j]
-        sv = float(c @ s2 @ c)
-        if sv < tol:
-            keep_e.append(float(c @ hm @ c))
-            keep_v.append(c)
-        if len(keep_v) == nstate:
+    nwant = min(nd, 4 * nstate + 4)
+    while True:
+        w, v = sl.eigh(hm + penalty * s2, subset_by_index=[0, nwant - 1])
+        keep_e, keep_v = [], []
+        for j in range(v.shape[1]):
+            c = v[:, j]
+            if float(c @ s2 @ c) < tol:
+                keep_e.append(float(c @ hm @ c))
+                keep_v.append(c)
+            if len(keep_v) == nstate:
+                break
+        if len(keep_v) == nstate or nwant == nd:
             break
+        nwant = min(nd, 2 * nwant)
     if len(keep_v) < nstate:
         raise ValueError("not enough singlet states in the active space")
     ci = np.stack(keep_v, axis=1)

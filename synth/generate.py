@@ -95,7 +95,7 @@ def make_problem(nclosed: int, nact: int, nvirt: int, naux: int, nstate: int,
     if nact == 0:
         return Problem(nclosed, 0, nvirt, naux, 1 if nstate < 1 else nstate, 0, seed, f, B,
                        np.ones((1, 1)), np.zeros(1, dtype=np.int64), np.zeros(1, dtype=np.int64),
-                       np.zeros(1), {k: np.ones((1, 1)) for k in range(1, kmax + 1)})
+                       np.zeros(1), {k: np.zeros((1, 1, 0)) for k in range(1, kmax + 1)})
 
     act = slice(nclosed, ov)
     Bact = B[:, act, act].reshape(naux, nact * nact)

@@ -1,0 +1,51 @@
+"""The C ABI library builds for sm_103a and exports every function include/caspt2.h
+declares; host-only entry points answer without a GPU."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def so():
+    from paper_1606_01273_gb300 import build as b
+    if not os.path.exists(b.LIB):
+        b.build()
+    return C.CDLL(b.LIB)
+
+
+def _declared():
+    hdr = open(os.path.join(ROOT, "include", "caspt2.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    return sorted(set(re.findall(r"\b(caspt2_\w+)\s*\(", hdr)))
+
+
+def test_every_declared_symbol_is_exported(so):
+    names = _declared()
+    assert len(names) >= 12
+    missing = [n for n in names if not hasattr(so, n)]
+    assert not missing, missing
+
+
+def test_host_only_entry_points(so):
+    so.caspt2_strerror.restype = C.c_char_p
+    assert so.caspt2_strerror(0) == b"ok"
+    assert b"invalid" in so.caspt2_strerror(-1)
+    so.caspt2_supported_classes.restype = C.c_uint
+    assert so.caspt2_supported_classes() & (1 << 7)
+    so.caspt2_create.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+    assert so.caspt2_create(None, None, None) == -1      # EINVAL before touching the GPU
+    so.caspt2_get_kernel_launches.restype = C.c_long
+    so.caspt2_get_kernel_launches.argtypes = [C.c_void_p]
+    assert so.caspt2_get_kernel_launches(None) == -1
+
+
+def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
+    import paper_1606_01273_gb300 as cp
+    monkeypatch.setattr(cp, "LIBPATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(cp, "_lib", None)
+    with pytest.raises(RuntimeError):
+        cp.lib()
