@@ -36,6 +36,7 @@ extern "C" {
 #define CASPT2_ETIMEOUT    (-5)   /* a bounded device wait gave up                */
 #define CASPT2_ECUDA       (-6)   /* a CUDA runtime call failed                   */
 #define CASPT2_ESTATE      (-7)   /* call out of order (e.g. solve before inputs) */
+#define CASPT2_ESCRATCH    (-8)   /* too large for the fixed scratch of caspt2_classH_noalloc */
 #define CASPT2_WINTRUDER     1    /* smallest |denominator| below 1e-3 Eh          */
 
 /* memory kinds for caspt2_set_inputs */
@@ -123,6 +124,32 @@ unsigned caspt2_supported_classes(void);
 
 void caspt2_destroy(caspt2_ctx* ctx);
 const char* caspt2_strerror(int status);
+
+/* Size of the fixed device scratch array used by caspt2_classH_noalloc. */
+#define CASPT2_NOALLOC_SCRATCH_BYTES ((size_t)4 << 20)
+
+/* Class-H pieces e[L][L'] = <Psi1_L|H|L'~>_H and norm[L] = <Psi1_L|Psi1_L>_H (the same
+ * values caspt2_get_class_energy returns for class H after caspt2_solve), computed
+ * without allocating any device memory.  The paper has no counterpart: this entry
+ * point exists for callers that cannot call cudaMalloc (code running inside another
+ * framework's memory pool or a pre-sized arena, plugins in hosts that forbid
+ * allocation after start-up, loops that must never enter the allocator).
+ *   dims, opt     as for caspt2_create (opt->xms, scheme, shift are used)
+ *   fock, dfB     device pointers, layouts as in caspt2_set_inputs
+ *   rdm1          device pointer [n][n][a][a] (may be NULL when nact = 0)
+ *   e, norm       device pointers to [n][n] and [n] outputs (written, caller-owned)
+ *   cuda_stream   cudaStream_t to run on; the call synchronises it before returning
+ * All intermediates live in one file-scope device array of CASPT2_NOALLOC_SCRATCH_BYTES
+ * that every GPU loading the library keeps until the process exits.  The first call on
+ * each device looks up that array's device address (cudaGetSymbolAddress) with the
+ * device current; make that first call before any stream capture.  Calls share the
+ * array: calls that overlap on the GPU (other threads or streams) race and must be
+ * serialised by the caller.  Returns ESCRATCH when the problem needs more scratch than
+ * the array holds (about 4 MiB: n <= 16 and nclosed + nvirt up to ~2e5 fit), EINVAL for
+ * bad sizes or NULL pointers, ENOTCONV / ENAN / ECUDA, or WINTRUDER as caspt2_solve. */
+int caspt2_classH_noalloc(const caspt2_dims* dims, const caspt2_options* opt,
+                          const double* fock, const double* dfB, const double* rdm1,
+                          double* e, double* norm, void* cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -16,7 +16,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIBPATH = os.path.join(HERE, "libcaspt2.so")
 
-OK, EINVAL, ENOMEM, ENOTCONV, ENAN, ETIMEOUT, ECUDA, ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
+OK, EINVAL, ENOMEM, ENOTCONV, ENAN, ETIMEOUT, ECUDA, ESTATE, ESCRATCH = 0, -1, -2, -3, -4, -5, -6, -7, -8
 WINTRUDER = 1
 MEM_HOST, MEM_DEVICE = 0, 1
 MSMR, SSSR = 0, 1
@@ -62,6 +62,7 @@ def lib():
         L.caspt2_supported_classes.restype = C.c_uint
         L.caspt2_destroy.argtypes = [P]
         L.caspt2_destroy.restype = None
+        L.caspt2_classH_noalloc.argtypes = [C.POINTER(Dims), C.POINTER(Options), P, P, P, P, P, P]
         L.caspt2_strerror.argtypes = [C.c_int]
         L.caspt2_strerror.restype = C.c_char_p
         _lib = L
@@ -177,6 +178,19 @@ class Context:
         _check(lib().caspt2_get_timings(self._h, _dp(t), C.byref(cnt)), "caspt2_get_timings")
         return Result(U, E0, Href, Heff, Ems, R, ec.value, e_cls, n_cls, status,
                       list(t[: cnt.value]), int(lib().caspt2_get_kernel_launches(self._h)))
+
+
+def classH_noalloc(dims: Dims, opts: Options, fock, dfB, rdm1, e, norm, stream=None) -> int:
+    """caspt2_classH_noalloc on device tensors (no device allocation inside the call).
+
+    For callers that cannot allocate device memory: every intermediate lives in the
+    library's fixed 4 MiB device scratch array.  Returns the status (warnings > 0);
+    raises on errors."""
+    ptr = lambda t: None if t is None else C.c_void_p(t.data_ptr())
+    s = C.c_void_p(stream) if stream is not None else None
+    st = lib().caspt2_classH_noalloc(C.byref(dims), C.byref(opts), ptr(fock), ptr(dfB),
+                                     ptr(rdm1), ptr(e), ptr(norm), s)
+    return _check(st, "caspt2_classH_noalloc", warn_ok=True)
 
 
 def problem_inputs(prob):

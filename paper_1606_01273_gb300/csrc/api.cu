@@ -90,6 +90,8 @@ const char* caspt2_strerror(int st) {
     case CASPT2_ETIMEOUT: return "a bounded device wait gave up";
     case CASPT2_ECUDA: return "CUDA runtime error";
     case CASPT2_ESTATE: return "call out of order";
+    case CASPT2_ESCRATCH:
+      return "problem exceeds the fixed 4 MiB device scratch of caspt2_classH_noalloc";
     case CASPT2_WINTRUDER: return "warning: a denominator is below 1e-3 Eh (intruder state)";
     default: return "unknown status";
   }
