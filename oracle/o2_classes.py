@@ -1,0 +1,308 @@
+"""O2 for the excitation classes A-G: overlap, Fock and source matrices from RDMs.
+
+TEST INFRASTRUCTURE (see oracle/__init__.py).  Every matrix element is produced by
+the normal-ordering engine in oracle/wick.py from the operator families of
+Eq. (class) and evaluated with numpy.einsum over the rotated RDMs (Sec. II.F: the
+RDMs <M~|E..|N~> are the only reference-state information the contractions use).
+
+For block-diagonal f (closed and virtual blocks diagonal) a class's overlap and
+Fock matrices couple external index tuples only through Kronecker deltas, i.e.
+through the identity or, for classes with two closed (or two virtual) indices, the
+swap of that pair.  The class is then solved per external tuple in the symmetric (+)
+and antisymmetric (-) combinations of the pair:
+
+  S^+- = S^id +- S^sw ,  F^+- = e_ext S^+- + F_act^+- ,
+  T = -Y diag(1/(e_ext + omega - E0_L + E_s)) Y^T V,   Y = X Q,
+
+with X = V_S s^(-1/2) over overlap eigenvalues >= threshold (Sec. II.B) and
+(Q, omega) the eigenpairs of X^T F_act X.  The + sector includes the tuples with
+coinciding pair indices (i = j or a = b).
+"""
+from __future__ import annotations
+
+import itertools
+import string
+from functools import lru_cache
+
+import numpy as np
+
+from .wick import Builder, expect
+
+# class -> (families, external slots, pair slots, active slots); a family lists the
+# (slot, space) of E_{pq,rs} in the order p, q, r, s (Eq. class)
+CLASS_DEF = {
+    "A": ([(("r", "a"), ("i", "c"), ("s", "a"), ("t", "a"))], ["i"], None, ["r", "s", "t"]),
+    "B": ([(("r", "a"), ("i", "c"), ("s", "a"), ("j", "c"))], ["i", "j"], ("i", "j"), ["r", "s"]),
+    "C": ([(("a", "v"), ("r", "a"), ("s", "a"), ("t", "a"))], ["a"], None, ["r", "s", "t"]),
+    "D": ([(("a", "v"), ("i", "c"), ("r", "a"), ("s", "a")),
+           (("a", "v"), ("r", "a"), ("s", "a"), ("i", "c"))], ["a", "i"], None, ["r", "s"]),
+    "E": ([(("a", "v"), ("i", "c"), ("r", "a"), ("j", "c"))], ["a", "i", "j"], ("i", "j"), ["r"]),
+    "F": ([(("a", "v"), ("r", "a"), ("b", "v"), ("s", "a"))], ["a", "b"], ("a", "b"), ["r", "s"]),
+    "G": ([(("a", "v"), ("r", "a"), ("b", "v"), ("i", "c"))], ["a", "b", "i"], ("a", "b"), ["r"]),
+}
+
+
+def _space_of_slot(cls):
+    fams = CLASS_DEF[cls][0]
+    sp = {}
+    for fam in fams:
+        for slot, s in fam:
+            sp[slot] = s
+    return sp
+
+
+def _ket_ops(b, fam, tag):
+    (p, _), (q, _), (r, _), (s, _) = fam
+    return b.E2(p + tag, q + tag, r + tag, s + tag)
+
+
+def _bra_ops(b, fam, tag):
+    # (E_{pq,rs})^dagger = E_{qp,sr}
+    (p, _), (q, _), (r, _), (s, _) = fam
+    return b.E2(q + tag, p + tag, s + tag, r + tag)
+
+
+@lru_cache(maxsize=None)
+def overlap_terms(cls, fb, fk, with_fock):
+    """Terms of <M|E_bra^dag (E_uw) E_ket|N> for families fb, fk of a class."""
+    fams = CLASS_DEF[cls][0]
+    sp = {}
+    for slot, s in _space_of_slot(cls).items():
+        sp[slot + "_b"] = s
+        sp[slot + "_k"] = s
+    b = Builder()
+    ops = _bra_ops(b, fams[fb], "_b")
+    if with_fock:
+        sp["u"] = sp["w"] = "a"
+        ops = ops + b.E("u", "w")
+    ops = ops + _ket_ops(b, fams[fk], "_k")
+    return tuple(expect(ops, sp))
+
+
+@lru_cache(maxsize=None)
+def source_terms(cls, fb):
+    """Terms of <M|E_bra^dag H|L> with H = sum h_pq E_pq + 1/2 sum (pq|rt) E_pq,rt, the
+    general indices split over closed / active / virtual."""
+    fams = CLASS_DEF[cls][0]
+    out = []
+    base = {slot + "_b": s for slot, s in _space_of_slot(cls).items()}
+    for sp1 in itertools.product("cav", repeat=2):
+        b = Builder()
+        sp = dict(base)
+        sp.update({"p": sp1[0], "q": sp1[1]})
+        for t in expect(_bra_ops(b, fams[fb], "_b") + b.E("p", "q"), sp):
+            out.append(("h", sp1, 1.0, t))
+    for sp2 in itertools.product("cav", repeat=4):
+        b = Builder()
+        sp = dict(base)
+        sp.update({"p": sp2[0], "q": sp2[1], "r": sp2[2], "t": sp2[3]})
+        for t in expect(_bra_ops(b, fams[fb], "_b") + b.E2("p", "q", "r", "t"), sp):
+            out.append(("g", sp2, 0.5, t))
+    return tuple(out)
+
+
+class _Letters:
+    def __init__(self):
+        self.m = {}
+        self.pool = iter(string.ascii_letters.replace("M", "").replace("N", "").replace("P", ""))
+
+    def __call__(self, label):
+        if label not in self.m:
+            self.m[label] = next(self.pool)
+        return self.m[label]
+
+
+def _ext_perm(cls, deltas):
+    """'id' or 'sw' from the bra-ket deltas between external labels."""
+    ext = CLASS_DEF[cls][1]
+    pair = CLASS_DEF[cls][2]
+    mp = {}
+    for x, y in deltas:
+        for u, w in ((x, y), (y, x)):
+            if u.endswith("_b") and w.endswith("_k") and u[:-2] in ext and w[:-2] in ext:
+                mp[u[:-2]] = w[:-2]
+    if all(mp.get(e) == e for e in ext):
+        return "id"
+    if pair is not None:
+        i, j = pair
+        if mp.get(i) == j and mp.get(j) == i and all(mp.get(e) == e for e in ext if e not in pair):
+            return "sw"
+    raise AssertionError(f"unexpected external pattern {deltas} for class {cls}")
+
+
+def active_matrices(cls, rdm, n, a, f_act=None):
+    """S_act^pi (and F_act^pi if f_act is given) as arrays
+    [fam_b, act_b..., M, fam_k, act_k..., N] for pi in ('id', 'sw')."""
+    fams, ext, pair, act = CLASS_DEF[cls]
+    nf = len(fams)
+    shape = (nf,) + (a,) * len(act) + (n,) + (nf,) + (a,) * len(act) + (n,)
+    out = {}
+    for which in (("S", False),) + ((("F", True),) if f_act is not None else ()):
+        name, fock = which
+        mats = {"id": np.zeros(shape), "sw": np.zeros(shape)}
+        for fb in range(nf):
+            for fk in range(nf):
+                for t in overlap_terms(cls, fb, fk, fock):
+                    pi = _ext_perm(cls, t.deltas)
+                    L = _Letters()
+                    subs, opnds = [], []
+                    k = len(t.rdm)
+                    if k == 0:
+                        subs.append("MN")
+                        opnds.append(np.eye(n))
+                    else:
+                        subs.append("MN" + "".join(L(p) + L(q) for p, q in t.rdm))
+                        opnds.append(rdm[k])
+                    for x, y in t.deltas:
+                        if x[:-2] in ext and (x.endswith("_b") or x.endswith("_k")):
+                            continue
+                        subs.append(L(x) + L(y))
+                        opnds.append(np.eye(a))
+                    if fock:
+                        subs.append(L("u") + L("w"))
+                        opnds.append(f_act)
+                    outsub = ("".join(L(s + "_b") for s in act) + "M"
+                              + "".join(L(s + "_k") for s in act) + "N")
+                    val = np.einsum(",".join(subs) + "->" + outsub, *opnds, optimize=True)
+                    idx = (fb,) + (slice(None),) * (len(act) + 1) + (fk,)
+                    mats[pi][idx] += t.coeff * val
+        out[name] = mats
+    return out
+
+
+def sources(cls, rdm, n, a, blocks):
+    """V[fam, ext..., act..., M, L] = <M~|E_Omega^dag H|L~> (Eq. ampeq source)."""
+    fams, ext, pair, act = CLASS_DEF[cls]
+    dims = blocks["dims"]
+    sp = _space_of_slot(cls)
+    shape = (len(fams),) + tuple(dims[sp[e]] for e in ext) + (a,) * len(act) + (n, n)
+    V = np.zeros(shape)
+    for fb in range(len(fams)):
+        for kind, spc, w, t in source_terms(cls, fb):
+            L = _Letters()
+            subs, opnds = [], []
+            k = len(t.rdm)
+            if k == 0:
+                subs.append("MN")
+                opnds.append(np.eye(n))
+            else:
+                subs.append("MN" + "".join(L(p) + L(q) for p, q in t.rdm))
+                opnds.append(rdm[k])
+            lab_space = {"p": spc[0], "q": spc[1]} if kind == "h" else \
+                dict(zip("pqrt", spc))
+            for s_ in sp:
+                lab_space[s_ + "_b"] = sp[s_]
+            if kind == "h":
+                subs.append(L("p") + L("q"))
+                opnds.append(blocks["h"][spc[0] + spc[1]])
+            else:
+                subs.append("P" + L("p") + L("q"))
+                opnds.append(blocks["B"][spc[0] + spc[1]])
+                subs.append("P" + L("r") + L("t"))
+                opnds.append(blocks["B"][spc[2] + spc[3]])
+            for x, y in t.deltas:
+                subs.append(L(x) + L(y))
+                opnds.append(np.eye(dims[lab_space[x]]))
+            outsub = ("".join(L(e + "_b") for e in ext) + "".join(L(s + "_b") for s in act) + "MN")
+            val = np.einsum(",".join(subs) + "->" + outsub, *opnds, optimize=True)
+            V[fb] += w * t.coeff * val
+    return V
+
+
+def integral_blocks(prob, h):
+    c, a, v = prob.nclosed, prob.nact, prob.nvirt
+    sl = {"c": slice(0, c), "a": slice(c, c + a), "v": slice(c + a, c + a + v)}
+    hb = {x + y: h[sl[x], sl[y]] for x in "cav" for y in "cav"}
+    Bb = {x + y: prob.B[:, sl[x], sl[y]] for x in "cav" for y in "cav"}
+    return {"h": hb, "B": Bb, "dims": {"c": c, "a": a, "v": v}}
+
+
+def class_energy(prob, st, cls, shift=0.0, scheme="msmr", thresh=1e-9, h=None):
+    """Per-class pieces e[L, L'] = <Psi1_L|H|L'~>_X and norm[L] = <Psi1_L|Psi1_L>_X for
+    block-diagonal f, from the rotated RDMs of `st` (an o2_rdm.Setup with kmax >= 4)."""
+    from .o2_rdm import g_of
+    c, a, v, n = prob.nclosed, prob.nact, prob.nvirt, prob.nstate
+    fams, ext, pair, act = CLASS_DEF[cls]
+    sp = _space_of_slot(cls)
+    dims = {"c": c, "a": a, "v": v}
+    if any(dims[sp[e]] == 0 for e in ext) or a == 0:
+        return np.zeros((n, n)), np.zeros(n)
+    if h is None:
+        nmo = prob.nmo
+        d = np.zeros((nmo, nmo))
+        d[np.arange(c), np.arange(c)] = 2.0
+        g1 = prob.rdm[1].reshape(n, n, a, a)
+        d[c:c + a, c:c + a] = sum(g1[m, m] for m in range(n)) / n
+        h = prob.f - g_of(prob.B, d)
+    f_act = prob.f[c:c + a, c:c + a]
+    rdm = st.rdm
+    mats = active_matrices(cls, rdm, n, a, f_act)
+    V = sources(cls, rdm, n, a, integral_blocks(prob, h))
+    eps = np.diag(prob.f)
+    ec, ev = eps[:c], eps[c + a:]
+    nf = len(fams)
+    m = nf * a ** len(act) * n
+    S = {k: x.reshape(m, m) for k, x in mats["S"].items()}
+    F = {k: x.reshape(m, m) for k, x in mats["F"].items()}
+    # external tuples and their energies
+    ranges = [range(dims[sp[e]]) for e in ext]
+    e_out = np.zeros((n, n))
+    n_out = np.zeros(n)
+    Vr = V.reshape((nf,) + V.shape[1:1 + len(ext)] + (a ** len(act), n, n))
+
+    def eext(tup):
+        val = 0.0
+        for e_, x in zip(ext, tup):
+            val += ev[x] if sp[e_] == "v" else -ec[x]
+        return val
+
+    def vec(tup):  # [(fam, act, M), L]
+        return np.moveaxis(Vr[(slice(None),) + tuple(tup)], 0, 0).reshape(m, n)
+
+    sectors = [("+", 1.0), ("-", -1.0)] if pair is not None else [("id", 0.0)]
+    for name, sgn in sectors:
+        if pair is None:
+            Ssec, Fsec = S["id"], F["id"]
+        else:
+            Ssec, Fsec = S["id"] + sgn * S["sw"], F["id"] + sgn * F["sw"]
+        Ssec = 0.5 * (Ssec + Ssec.T)
+        Fsec = 0.5 * (Fsec + Fsec.T)
+        if pair is not None:
+            pi_, pj_ = ext.index(pair[0]), ext.index(pair[1])
+        for Lsel in (range(n) if scheme == "sssr" else [None]):
+            if Lsel is None:
+                keep_idx = np.arange(m)
+            else:
+                keep_idx = np.array([k for k in range(m) if k % n == Lsel])
+            Ss = Ssec[np.ix_(keep_idx, keep_idx)]
+            Fs = Fsec[np.ix_(keep_idx, keep_idx)]
+            s_, q_ = np.linalg.eigh(Ss)
+            keep = s_ >= thresh
+            if not keep.any():
+                continue
+            X = q_[:, keep] / np.sqrt(s_[keep])
+            om, Q = np.linalg.eigh(X.T @ Fs @ X)
+            Y = X @ Q
+            for tup in itertools.product(*ranges):
+                if pair is not None:
+                    ti, tj = tup[pi_], tup[pj_]
+                    if ti > tj or (name == "-" and ti == tj):
+                        continue
+                    if ti == tj:
+                        vv = vec(tup)
+                    else:
+                        sw = list(tup)
+                        sw[pi_], sw[pj_] = tj, ti
+                        vv = (vec(tup) + sgn * vec(tuple(sw))) / np.sqrt(2.0)
+                else:
+                    vv = vec(tup)
+                vv = vv[keep_idx]
+                Vt = Y.T @ vv                      # [mu, L']
+                ee = eext(tup)
+                Ls = range(n) if Lsel is None else [Lsel]
+                for L in Ls:
+                    D = ee + om - st.E0[L] + shift
+                    amp = -Vt[:, L] / D
+                    e_out[L, :] += amp @ Vt
+                    n_out[L] += amp @ amp
+    return e_out, n_out

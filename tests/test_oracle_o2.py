@@ -40,3 +40,44 @@ def test_class_h_matches_o1(prob, xms, scheme, shift):
     scale = max(1.0, np.abs(r.e_class["H"]).max())
     assert np.allclose(e, r.e_class["H"], atol=1e-11 * scale)
     assert np.allclose(nr, r.norm_class["H"], atol=1e-11)
+
+
+CLASS_CASES = [
+    dict(nclosed=2, nact=4, nvirt=2, naux=24, nstate=2, seed=5),
+    dict(nclosed=2, nact=3, nvirt=2, naux=20, nstate=3, seed=8, nelact=2),
+    dict(nclosed=1, nact=4, nvirt=3, naux=16, nstate=1, seed=14, nelact=4),
+]
+
+
+@pytest.fixture(scope="module", params=range(len(CLASS_CASES)))
+def cprob(request):
+    return make_problem(**CLASS_CASES[request.param])
+
+
+@pytest.mark.parametrize("xms,scheme,shift", [(True, "msmr", 0.2), (False, "msmr", 0.0),
+                                              (True, "sssr", 0.1), (False, "sssr", 0.3)])
+def test_classes_a_to_g_match_o1(cprob, xms, scheme, shift):
+    """Per-class <Psi1_L|H|L'~> and <Psi1_L|Psi1_L> of classes A-G from RDMs (normal-
+    ordering engine + per-sector solve) equal the determinant-space values."""
+    from oracle import o2_classes as oc
+    r = o1.solve_problem(cprob, xms=xms, scheme=scheme, shift=shift, densities=False)
+    st = o2.setup(cprob, xms=xms, kmax=4)
+    for cls in "ABCDEFG":
+        e, nr = oc.class_energy(cprob, st, cls, shift=shift, scheme=scheme)
+        scale = max(1.0, np.abs(r.e_class[cls]).max())
+        assert np.abs(e - r.e_class[cls]).max() <= 1e-11 * scale, cls
+        assert np.abs(nr - r.norm_class[cls]).max() <= 1e-11 * max(1.0, np.abs(nr).max()), cls
+
+
+def test_wick_engine_identities():
+    """Textbook identities: <E_ij> = 2 delta_ij over the core, E_rs E_tu = E_rs,tu +
+    delta_st E_ru, <E_ir E_r'i'> = delta_ii'(2 delta_rr' - Gamma_r'r)."""
+    from oracle.wick import Builder, expect
+    sp = {"i": "c", "j": "c", "r": "a", "s": "a", "t": "a", "u": "a", "a": "v", "b": "v"}
+    b = Builder()
+    assert [(x.coeff, x.deltas, x.rdm) for x in expect(b.E("i", "j"), sp)] == [(2, (("i", "j"),), ())]
+    assert expect(b.E("a", "b"), sp) == []
+    got = {(x.coeff, x.deltas, x.rdm) for x in expect(b.E("r", "s") + b.E("t", "u"), sp)}
+    assert got == {(1, (), (("r", "s"), ("t", "u"))), (1, (("s", "t"),), (("r", "u"),))}
+    got = {(x.coeff, x.deltas, x.rdm) for x in expect(b.E("i", "r") + b.E("s", "j"), sp)}
+    assert got == {(2, (("i", "j"), ("r", "s")), ()), (-1, (("i", "j"),), (("s", "r"),))}
