@@ -217,6 +217,14 @@ def integral_blocks(prob, h):
     return {"h": hb, "B": Bb, "dims": {"c": c, "a": a, "v": v}}
 
 
+def all_classes(prob, st, shift=0.0, scheme="msmr", thresh=1e-9):
+    """{class: (e, norm)} for A-G from RDMs and H from the closed form (o2_rdm.class_h)."""
+    from .o2_rdm import class_h
+    out = {cls: class_energy(prob, st, cls, shift, scheme, thresh) for cls in "ABCDEFG"}
+    out["H"] = class_h(prob, st, shift=shift, scheme=scheme)
+    return out
+
+
 def class_energy(prob, st, cls, shift=0.0, scheme="msmr", thresh=1e-9, h=None):
     """Per-class pieces e[L, L'] = <Psi1_L|H|L'~>_X and norm[L] = <Psi1_L|Psi1_L>_X for
     block-diagonal f, from the rotated RDMs of `st` (an o2_rdm.Setup with kmax >= 4)."""
@@ -250,59 +258,56 @@ def class_energy(prob, st, cls, shift=0.0, scheme="msmr", thresh=1e-9, h=None):
     n_out = np.zeros(n)
     Vr = V.reshape((nf,) + V.shape[1:1 + len(ext)] + (a ** len(act), n, n))
 
-    def eext(tup):
-        val = 0.0
-        for e_, x in zip(ext, tup):
-            val += ev[x] if sp[e_] == "v" else -ec[x]
-        return val
+    sp_list = [sp[e] for e in ext]
+    grids = np.meshgrid(*[np.arange(r.stop) for r in ranges], indexing="ij")
+    tup_all = np.stack([g.ravel() for g in grids], axis=1)            # [ntup, next]
+    eext_all = np.zeros(len(tup_all))
+    for k, s_ in enumerate(sp_list):
+        eext_all += ev[tup_all[:, k]] if s_ == "v" else -ec[tup_all[:, k]]
+    Vflat = Vr.reshape((nf,) + (int(np.prod([r.stop for r in ranges])),) + (a ** len(act), n, n))
+    ext_shape = [r.stop for r in ranges]
 
-    def vec(tup):  # [(fam, act, M), L]
-        return np.moveaxis(Vr[(slice(None),) + tuple(tup)], 0, 0).reshape(m, n)
+    def flat(tups):
+        return np.ravel_multi_index(tuple(tups.T), ext_shape)
 
     sectors = [("+", 1.0), ("-", -1.0)] if pair is not None else [("id", 0.0)]
     for name, sgn in sectors:
         if pair is None:
             Ssec, Fsec = S["id"], F["id"]
+            sel = np.arange(len(tup_all))
+            vmat = Vflat[:, sel]                                          # [nf, T, A, M, L]
         else:
             Ssec, Fsec = S["id"] + sgn * S["sw"], F["id"] + sgn * F["sw"]
+            pi_, pj_ = ext.index(pair[0]), ext.index(pair[1])
+            ti, tj = tup_all[:, pi_], tup_all[:, pj_]
+            sel = np.nonzero((ti < tj) if name == "-" else (ti <= tj))[0]
+            swp = tup_all[sel].copy()
+            swp[:, [pi_, pj_]] = swp[:, [pj_, pi_]]
+            v1 = Vflat[:, sel]
+            v2 = Vflat[:, flat(swp)]
+            diag = (ti[sel] == tj[sel])[None, :, None, None, None]
+            vmat = np.where(diag, v1, (v1 + sgn * v2) / np.sqrt(2.0))
         Ssec = 0.5 * (Ssec + Ssec.T)
         Fsec = 0.5 * (Fsec + Fsec.T)
-        if pair is not None:
-            pi_, pj_ = ext.index(pair[0]), ext.index(pair[1])
+        ee_sel = eext_all[sel]
+        # rows (fam, act, M), columns (tuple, L)
+        Vm = np.moveaxis(vmat, 1, 3).reshape(m, len(sel), n)
         for Lsel in (range(n) if scheme == "sssr" else [None]):
-            if Lsel is None:
-                keep_idx = np.arange(m)
-            else:
-                keep_idx = np.array([k for k in range(m) if k % n == Lsel])
+            keep_idx = np.arange(m) if Lsel is None else np.arange(Lsel, m, n)
             Ss = Ssec[np.ix_(keep_idx, keep_idx)]
             Fs = Fsec[np.ix_(keep_idx, keep_idx)]
             s_, q_ = np.linalg.eigh(Ss)
             keep = s_ >= thresh
-            if not keep.any():
+            if not keep.any() or len(sel) == 0:
                 continue
             X = q_[:, keep] / np.sqrt(s_[keep])
             om, Q = np.linalg.eigh(X.T @ Fs @ X)
             Y = X @ Q
-            for tup in itertools.product(*ranges):
-                if pair is not None:
-                    ti, tj = tup[pi_], tup[pj_]
-                    if ti > tj or (name == "-" and ti == tj):
-                        continue
-                    if ti == tj:
-                        vv = vec(tup)
-                    else:
-                        sw = list(tup)
-                        sw[pi_], sw[pj_] = tj, ti
-                        vv = (vec(tup) + sgn * vec(tuple(sw))) / np.sqrt(2.0)
-                else:
-                    vv = vec(tup)
-                vv = vv[keep_idx]
-                Vt = Y.T @ vv                      # [mu, L']
-                ee = eext(tup)
-                Ls = range(n) if Lsel is None else [Lsel]
-                for L in Ls:
-                    D = ee + om - st.E0[L] + shift
-                    amp = -Vt[:, L] / D
-                    e_out[L, :] += amp @ Vt
-                    n_out[L] += amp @ amp
+            Vt = np.einsum("ku,ktl->utl", Y, Vm[keep_idx])              # [mu, tuple, L']
+            Ls = range(n) if Lsel is None else [Lsel]
+            for L in Ls:
+                D = ee_sel[None, :] + om[:, None] - st.E0[L] + shift      # [mu, tuple]
+                amp = -Vt[:, :, L] / D
+                e_out[L, :] += np.einsum("ut,utl->l", amp, Vt)
+                n_out[L] += np.sum(amp * amp)
     return e_out, n_out

@@ -193,12 +193,13 @@ def classH_noalloc(dims: Dims, opts: Options, fock, dfB, rdm1, e, norm, stream=N
     return _check(st, "caspt2_classH_noalloc", warn_ok=True)
 
 
-def problem_inputs(prob):
-    """Host arrays of a synth.Problem in the layout of caspt2_set_inputs."""
-    a = prob.nact
+def problem_inputs(prob, kmax: int = 4):
+    """Host arrays (f, B, rdm1, rdm2, rdm3, rdm4) of a synth.Problem in the layout of
+    caspt2_set_inputs; RDMs above kmax (or absent) are None."""
     n = prob.nstate
-    r = [np.ascontiguousarray(prob.rdm[k].reshape(n, n, -1)) for k in (1, 2)]
-    return (np.ascontiguousarray(prob.f), np.ascontiguousarray(prob.B), r[0], r[1])
+    r = [np.ascontiguousarray(prob.rdm[k].reshape(n, n, -1)) if (k <= kmax and k in prob.rdm)
+         else None for k in (1, 2, 3, 4)]
+    return (np.ascontiguousarray(prob.f), np.ascontiguousarray(prob.B), *r)
 
 
 def solve_problem(prob, **opts) -> Result:

@@ -6,19 +6,20 @@
 #include <new>
 #include <vector>
 
+#include <algorithm>
+#include <cmath>
+#include <map>
+
+#include "class_ag.cuh"
 #include "kernels.cuh"
+#include "linalg.cuh"
 
 using namespace caspt2;
 
 namespace {
 
-constexpr int kNumStages = 4;  // setup, class H, other classes, H^eff
+constexpr int kNumStages = 4;  // setup, class H, classes A-G, H^eff
 constexpr int kNumTimes = kNumStages + 1;  // + the class-H GEMM kernel alone
-
-struct DevBuf {
-  double* p = nullptr;
-  size_t n = 0;
-};
 
 }  // namespace
 
@@ -42,6 +43,15 @@ struct caspt2_ctx {
   // classes
   double *ecls = nullptr, *ncls = nullptr, *mindenom = nullptr;
   ClassHWork hw{};
+  // classes A-G
+  int kmax = 2;                       // highest RDM rank the enabled classes read
+  ClassWork cw[7];
+  bool cw_on[7] = {};
+  SectorWork sw{};
+  double *rdm3r = nullptr, *rdm4r = nullptr, *h = nullptr, *fact = nullptr, *eps = nullptr;
+  double *pack0 = nullptr, *pack1 = nullptr;
+  std::map<int, double*> eri_blk;     // canonical space key -> (pq|rt) block
+  EriBlocks eri_tab{};
   // results
   double *heff = nullptr, *ems = nullptr, *R = nullptr;
   int* status = nullptr;
@@ -78,7 +88,7 @@ void caspt2_default_options(caspt2_options* o) {
   o->class_mask = caspt2_supported_classes();
 }
 
-unsigned caspt2_supported_classes(void) { return 1u << CASPT2_CLASS_H; }
+unsigned caspt2_supported_classes(void) { return (1u << CASPT2_NCLASS) - 1u; }
 
 const char* caspt2_strerror(int st) {
   switch (st) {
@@ -174,6 +184,77 @@ int caspt2_create(caspt2_ctx** out, const caspt2_dims* dims, const caspt2_option
   ALLOC(c->hw.shifts, nshift);
   ALLOC(c->hw.partial, (size_t)c->hw.nblocks * (2 * nshift + 1));
   ALLOC(c->hw.sums, 2 * nshift + 1);
+  // classes A-G: plans, class matrices, sources, sector work space, integral blocks
+  {
+    long m2max = 0, wmax = 0, pmax = 0;
+    long packmax = 0;
+    std::map<int, long> eri_need;
+    for (int k = 0; k < 7 && st == CASPT2_OK; ++k) {
+      if (!(o.class_mask >> k & 1u)) continue;
+      ClassWork& w = c->cw[k];
+      class_setup(k, d, w);
+      if (w.vsize == 0 || a == 0) continue;
+      c->cw_on[k] = true;
+      std::vector<ActPlan> S, F;
+      std::vector<SrcPlan> V;
+      build_act_plans(k, false, S);
+      build_act_plans(k, true, F);
+      build_src_plans(k, V);
+      for (auto& t : S) c->kmax = std::max<int>(c->kmax, t.rank);
+      for (auto& t : F) c->kmax = std::max<int>(c->kmax, t.rank);
+      for (auto& t : V) {
+        c->kmax = std::max<int>(c->kmax, t.rank);
+        if (t.kind == 1) {
+          const int dims3[3] = {d.c, d.a, d.v};
+          int key = ((t.ispace[0] * 3 + t.ispace[1]) * 3 + t.ispace[2]) * 3 + t.ispace[3];
+          eri_need[key] = (long)dims3[t.ispace[0]] * dims3[t.ispace[1]] * dims3[t.ispace[2]] *
+                          dims3[t.ispace[3]];
+          packmax = std::max(packmax, (long)X * dims3[t.ispace[0]] * dims3[t.ispace[1]]);
+          packmax = std::max(packmax, (long)X * dims3[t.ispace[2]] * dims3[t.ispace[3]]);
+        }
+      }
+      ALLOC(w.dS, S.size());
+      ALLOC(w.dF, F.size());
+      ALLOC(w.dV, V.size());
+      if (st == CASPT2_OK && class_upload_plans(w, S, F, V) != cudaSuccess) st = CASPT2_ECUDA;
+      ALLOC(w.Sact, 2 * (size_t)w.m * w.m);
+      ALLOC(w.Fact, 2 * (size_t)w.m * w.m);
+      ALLOC(w.V, (size_t)w.vsize);
+      m2max = std::max(m2max, (long)w.m * w.m);
+      long ps = 0;
+      wmax = std::max(wmax, class_sector_wsize(w, d, o.scheme, &ps));
+      pmax = std::max(pmax, ps);
+    }
+    if (m2max > 0) {
+      SectorWork& q = c->sw;
+      const long mx = (long)std::sqrt((double)m2max) + 1;
+      ALLOC(q.Ssec, m2max); ALLOC(q.Fsec, m2max); ALLOC(q.s, mx); ALLOC(q.Qs, m2max);
+      ALLOC(q.X, m2max); ALLOC(q.FX, m2max); ALLOC(q.Ft, m2max); ALLOC(q.omega, mx);
+      ALLOC(q.Qf, m2max); ALLOC(q.Y, m2max); ALLOC(q.mask, mx); ALLOC(q.jac, 2 * m2max + 2);
+      ALLOC(q.W, wmax); ALLOC(q.Vt, wmax); ALLOC(q.part, pmax); ALLOC(q.partn, pmax);
+      ALLOC(c->h, nmo * nmo);
+      ALLOC(c->fact, a2);
+      ALLOC(c->eps, nmo);
+      if (packmax > 0) {
+        ALLOC(c->pack0, packmax);
+        ALLOC(c->pack1, packmax);
+      }
+      for (auto& kv : eri_need) {
+        double* p = nullptr;
+        ALLOC(p, (size_t)std::max<long>(kv.second, 1));
+        c->eri_blk[kv.first] = p;
+        c->eri_tab.p[kv.first] = p;
+      }
+      if (c->kmax >= 3) {
+        ALLOC(c->rdm3, n * n * a2 * a2 * a2);
+        ALLOC(c->rdm3r, n * n * a2 * a2 * a2);
+      }
+      if (c->kmax >= 4) {
+        ALLOC(c->rdm4, n * n * a4 * a4);
+        ALLOC(c->rdm4r, n * n * a4 * a4);
+      }
+    }
+  }
 #undef ALLOC
   for (auto& e : c->ev)
     if (st == CASPT2_OK && cudaEventCreate(&e) != cudaSuccess) st = CASPT2_ECUDA;
@@ -209,6 +290,11 @@ int caspt2_set_inputs(caspt2_ctx* c, int mem, const double* fock, const double* 
   CASPT2_CUDA_TRY(cudaMemcpy(c->B, dfB, sizeof(double) * d.X * nmo * nmo, k));
   CASPT2_CUDA_TRY(cudaMemcpy(c->rdm1, rdm1, sizeof(double) * n * n * a2, k));
   CASPT2_CUDA_TRY(cudaMemcpy(c->rdm2, rdm2, sizeof(double) * n * n * a2 * a2, k));
+  if ((c->kmax >= 3 && !rdm3) || (c->kmax >= 4 && !rdm4)) return CASPT2_EINVAL;
+  if (c->kmax >= 3)
+    CASPT2_CUDA_TRY(cudaMemcpy(c->rdm3, rdm3, sizeof(double) * n * n * a2 * a2 * a2, k));
+  if (c->kmax >= 4)
+    CASPT2_CUDA_TRY(cudaMemcpy(c->rdm4, rdm4, sizeof(double) * n * n * a2 * a2 * a2 * a2, k));
   c->have_rdm3 = rdm3 != nullptr;
   c->have_rdm4 = rdm4 != nullptr;
   c->have_inputs = true;
@@ -255,7 +341,32 @@ int caspt2_solve(caspt2_ctx* c, void* stream) {
                                   c->ncls + (long)CASPT2_CLASS_H * n, c->mindenom, s));
   }
   CASPT2_CUDA_TRY(cudaEventRecord(c->ev[2], s));
-  // ---- stage 2: other classes (none yet in this build)
+  // ---- stage 2: classes A-G
+  {
+    bool any = false;
+    for (int k = 0; k < 7; ++k) any = any || c->cw_on[k];
+    if (any) {
+      CASPT2_CUDA_TRY(launch_hcore(c->f, c->g, c->B, c->bsum, d, c->h, s));
+      CASPT2_CUDA_TRY(launch_active_block(c->f, d, c->fact, s));
+      CASPT2_CUDA_TRY(launch_eps_cv(c->f, d, c->eps, s));
+      if (c->kmax >= 3)
+        CASPT2_CUDA_TRY(launch_rotate_rdm(c->rdm3, c->U, n, a2 * a2 * a2, c->rdm3r, s));
+      if (c->kmax >= 4)
+        CASPT2_CUDA_TRY(launch_rotate_rdm(c->rdm4, c->U, n, a2 * a2 * a2 * a2, c->rdm4r, s));
+      for (auto& kv : c->eri_blk) {
+        int sp4[4] = {kv.first / 27, (kv.first / 9) % 3, (kv.first / 3) % 3, kv.first % 3};
+        CASPT2_CUDA_TRY(eri_block(c->B, d, sp4, c->pack0, c->pack1, kv.second, s));
+      }
+      RdmPtrs g{{nullptr, c->rdm1r, c->rdm2r, c->rdm3r, c->rdm4r}};
+      for (int k = 0; k < 7; ++k) {
+        if (!c->cw_on[k]) continue;
+        int st = class_solve(c->cw[k], c->sw, d, o.scheme, o.shift, o.ovl_thresh, g, c->fact, c->h,
+                             c->eri_tab, c->E0, c->eps, c->ecls + (long)k * n * n,
+                             c->ncls + (long)k * n, c->mindenom, s);
+        if (st != CASPT2_OK) return st;
+      }
+    }
+  }
   CASPT2_CUDA_TRY(cudaEventRecord(c->ev[3], s));
   // ---- stage 3: effective Hamiltonian and its eigenpairs (Sec. II.B)
   CASPT2_CUDA_TRY(launch_heff(c->href, c->ecls, c->ncls, o.class_mask, o.shift, n, c->heff, s));

@@ -1,0 +1,522 @@
+// Classes A-G of Eq. (class): overlap, active Fock and source matrices from the
+// rotated RDMs (plans from terms.cpp), then the amplitude equation (Eq. ampeq) per
+// external tuple for block-diagonal f.  The overlap and Fock matrices couple
+// external tuples only through identity and (for classes with two closed or two
+// virtual indices) the swap of that pair, so each class is solved in the symmetric
+// and antisymmetric combinations:
+//   S^+- = S^id +- S^sw,   F^+- = e_ext S^+- + F_act^+-,
+//   X = Q_S s^(-1/2) over overlap eigenvalues >= threshold (Sec. II.B),
+//   X^T F_act X = Q diag(omega) Q^T,  Y = X Q,
+//   T(tuple, L) = -Y diag(1/(e_ext + omega - E0_L + E_s)) Y^T V(tuple, L),
+// and the pieces of the effective Hamiltonian are
+//   e[L][L'] = sum_tuples V(L')^T T(L),  norm[L] = T(L)^T S T(L).
+#include <cmath>
+#include <vector>
+
+#include "class_ag.cuh"
+#include "linalg.cuh"
+
+namespace caspt2 {
+
+namespace {
+
+__device__ __forceinline__ long ipow(int a, int k) {
+  long r = 1;
+  for (int i = 0; i < k; ++i) r *= a;
+  return r;
+}
+
+__device__ __forceinline__ double rdm_at(const double* const* g, int rank, int n, int a, int M,
+                                         int N, const int* vals, const int8_t* idx) {
+  if (rank == 0) return M == N ? 1.0 : 0.0;
+  long off = 0;
+  for (int j = 0; j < 2 * rank; ++j) off = off * a + vals[idx[j]];
+  return g[rank][((long)M * n + N) * ipow(a, 2 * rank) + off];
+}
+
+}  // namespace
+
+// S or F_act for all (row, col) of the m x m class matrix; out[pi][row][col].
+// row = ((fam * a^nact + act) * n + M), act digits in slot order (first slot slowest).
+__global__ void k_act_eval(const ActPlan* __restrict__ plans, int nplan, DevClass C, int a, int n,
+                           RdmPtrs g, const double* __restrict__ f_act, double* __restrict__ out,
+                           int m) {
+  const long total = (long)m * m;
+  const long A = ipow(a, C.nact);
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    const int row = e / m, col = e % m;
+    int vals[24];
+    const int M = row % n, N = col % n;
+    long ab = row / n, ak = col / n;
+    const int fb = ab / A, fk = ak / A;
+    ab %= A;
+    ak %= A;
+    for (int k = C.nact - 1; k >= 0; --k) {
+      vals[kRefBra + k] = ab % a;
+      ab /= a;
+      vals[kRefKet + k] = ak % a;
+      ak /= a;
+    }
+    double acc0 = 0.0, acc1 = 0.0;
+    for (int t = 0; t < nplan; ++t) {
+      const ActPlan& P = plans[t];
+      if (P.fb != fb || P.fk != fk) continue;
+      bool ok = true;
+      for (int q = 0; q < P.neq; ++q)
+        if (vals[P.eq[q][0]] != vals[P.eq[q][1]]) ok = false;
+      if (!ok) continue;
+      const int nl = P.nloop;
+      const int niter = nl == 0 ? 1 : (nl == 1 ? a : a * a);
+      double s = 0.0;
+      for (int it = 0; it < niter; ++it) {
+        if (nl >= 1) vals[kRefLoop] = it % a;
+        if (nl >= 2) vals[kRefLoop + 1] = it / a;
+        double x = rdm_at(g.p, P.rank, n, a, M, N, vals, P.idx);
+        if (P.has_f) x *= f_act[vals[P.fidx[0]] * a + vals[P.fidx[1]]];
+        s += x;
+      }
+      if (P.pi == 0) acc0 += P.coeff * s; else acc1 += P.coeff * s;
+    }
+    out[e] = acc0;
+    out[total + e] = acc1;
+  }
+}
+
+// Sources V[fam][ext...][act...][M][L] = <M~|E_Omega^dag H|L~> (Eq. ampeq).
+__global__ void k_src_eval(const SrcPlan* __restrict__ plans, int nplan, DevClass C, Dims d,
+                           RdmPtrs g, const double* __restrict__ h, EriBlocks eri,
+                           double* __restrict__ V, long total) {
+  const int n = d.n, a = d.a, nmo = d.nmo();
+  const int dimsp[3] = {d.c, d.a, d.v};
+  const int offsp[3] = {0, d.c, d.c + d.a};
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    long r = e;
+    const int L = r % n; r /= n;
+    const int M = r % n; r /= n;
+    int vals[24];
+    for (int k = C.nact - 1; k >= 0; --k) {
+      vals[kRefBra + C.act[k]] = r % a;
+      r /= a;
+    }
+    for (int k = C.next - 1; k >= 0; --k) {
+      const int dm = dimsp[C.slot_space[C.ext[k]]];
+      vals[kRefBra + C.ext[k]] = r % dm;
+      r /= dm;
+    }
+    const int fam = (int)r;
+    double acc = 0.0;
+    for (int t = 0; t < nplan; ++t) {
+      const SrcPlan& P = plans[t];
+      if (P.fb != fam) continue;
+      bool ok = true;
+      for (int q = 0; q < P.neq; ++q)
+        if (vals[P.eq[q][0]] != vals[P.eq[q][1]]) ok = false;
+      if (!ok) continue;
+      long niter = 1;
+      for (int j = 0; j < P.nloop; ++j) niter *= dimsp[P.loop_space[j]];
+      const double* blk = nullptr;
+      long bd[4] = {1, 1, 1, 1};
+      if (P.kind == 1) {
+        const int key = ((P.ispace[0] * 3 + P.ispace[1]) * 3 + P.ispace[2]) * 3 + P.ispace[3];
+        blk = eri.p[key];
+        for (int j = 0; j < 4; ++j) bd[j] = dimsp[P.ispace[j]];
+      }
+      double s = 0.0;
+      for (long it = 0; it < niter; ++it) {
+        long q = it;
+        for (int j = 0; j < P.nloop; ++j) {
+          const int dm = dimsp[P.loop_space[j]];
+          vals[kRefLoop + j] = q % dm;
+          q /= dm;
+        }
+        double x;
+        if (P.kind == 0) {
+          x = h[(long)(offsp[P.ispace[0]] + vals[P.iidx[0]]) * nmo + offsp[P.ispace[1]] +
+                vals[P.iidx[1]]];
+        } else {
+          x = blk[((vals[P.iidx[0]] * bd[1] + vals[P.iidx[1]]) * bd[2] + vals[P.iidx[2]]) * bd[3] +
+                  vals[P.iidx[3]]];
+        }
+        if (x != 0.0) x *= rdm_at(g.p, P.rank, n, a, M, L, vals, P.idx);
+        s += x;
+      }
+      acc += P.coeff * s;
+    }
+    V[e] = acc;
+  }
+}
+
+// Pack B[P][off0 + x][off1 + y] -> out[P][x][y]
+__global__ void k_pack_block(const double* __restrict__ B, int X, int nmo, int off0, int n0,
+                             int off1, int n1, double* __restrict__ out) {
+  const long total = (long)X * n0 * n1;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    const int y = e % n1;
+    const long r = e / n1;
+    const int x = r % n0;
+    const long P = r / n0;
+    out[e] = B[(P * nmo + off0 + x) * nmo + off1 + y];
+  }
+}
+
+// Sector matrices: out = sym(S_id + sgn S_sw) restricted to rows/cols with state Lsel
+// (Lsel < 0: all), into an msec x msec buffer.
+__global__ void k_sector(const double* __restrict__ in, int m, int n, double sgn, int Lsel,
+                         double* __restrict__ out, int msec) {
+  const long total = (long)msec * msec;
+  const long mm = (long)m * m;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    const int i = e / msec, j = e % msec;
+    const int ri = Lsel < 0 ? i : i * n + Lsel;
+    const int rj = Lsel < 0 ? j : j * n + Lsel;
+    const double x = in[(long)ri * m + rj] + sgn * in[mm + (long)ri * m + rj];
+    const double y = in[(long)rj * m + ri] + sgn * in[mm + (long)rj * m + ri];
+    out[e] = 0.5 * (x + y);
+  }
+}
+
+// X[:, k] = Q[:, k] / sqrt(s_k) for s_k >= thresh, else 0; mask[k] = kept
+__global__ void k_range_basis(const double* __restrict__ Q, const double* __restrict__ s, int m,
+                              double thresh, double* __restrict__ X, double* __restrict__ mask) {
+  const long total = (long)m * m;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    const int k = e % m;
+    const bool keep = s[k] >= thresh;
+    X[e] = keep ? Q[e] / sqrt(s[k]) : 0.0;
+    if (e < m) mask[e] = s[e] >= thresh ? 1.0 : 0.0;
+  }
+}
+
+__device__ __forceinline__ void tri_decode(long t, int R, bool strict, int& x, int& y) {
+  // enumerate x <= y (or x < y) row-major by x over [0, R)
+  const int w = strict ? R - 1 : R;
+  double b = 2.0 * w + 1.0;
+  int xx = (int)floor((b - sqrt(b * b - 8.0 * (double)t)) * 0.5);
+  if (xx < 0) xx = 0;
+  auto start = [&](int q) { return (long)q * w - (long)q * (q - 1) / 2; };
+  while (xx > 0 && start(xx) > t) --xx;
+  while (start(xx + 1) <= t) ++xx;
+  x = xx;
+  y = (int)(t - start(xx)) + xx + (strict ? 1 : 0);
+}
+
+// Sector tuple -> coordinates of the external slots (output order of C.ext) and the
+// partner tuple with the pair swapped.
+__device__ void sector_tuple(const DevClass& C, const int* extdim, int sector, long t, int* co,
+                             int* co_sw) {
+  if (C.pair0 < 0) {
+    for (int k = C.next - 1; k >= 0; --k) {
+      co[k] = t % extdim[k];
+      t /= extdim[k];
+      co_sw[k] = co[k];
+    }
+    return;
+  }
+  int ip = -1, jp = -1;
+  for (int k = 0; k < C.next; ++k) {
+    if (C.ext[k] == C.pair0) ip = k;
+    if (C.ext[k] == C.pair1) jp = k;
+  }
+  const int R = extdim[ip];
+  const bool strict = sector == 1;
+  const long npairs = strict ? (long)R * (R - 1) / 2 : (long)R * (R + 1) / 2;
+  const long pidx = t % npairs;
+  t /= npairs;
+  for (int k = C.next - 1; k >= 0; --k) {
+    if (k == ip || k == jp) continue;
+    co[k] = t % extdim[k];
+    t /= extdim[k];
+  }
+  int x, y;
+  tri_decode(pidx, R, strict, x, y);
+  co[ip] = x;
+  co[jp] = y;
+  for (int k = 0; k < C.next; ++k) co_sw[k] = co[k];
+  co_sw[ip] = y;
+  co_sw[jp] = x;
+}
+
+// W[row][(tuple, L')] for the sector: rows (fam, act, M) (M == Lsel under SS-SR)
+__global__ void k_sector_src(const double* __restrict__ V, DevClass C, ExtDims ed, int a, int n,
+                             int sector, int Lsel, long ntup, int msec, double* __restrict__ W) {
+  const long A = ipow(a, C.nact);
+  const long ncol = ntup * n;
+  const long total = (long)msec * ncol;
+  const double isq2 = 0.70710678118654752440;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    const int row = e / ncol;
+    const long cidx = e % ncol;
+    const int Lp = cidx % n;
+    const long t = cidx / n;
+    int co[3], cs[3];
+    sector_tuple(C, ed.d, sector, t, co, cs);
+    const int M = Lsel < 0 ? row % n : Lsel;
+    const long fa = Lsel < 0 ? row / n : row;   // fam * A + act
+    const int fam = fa / A;
+    const long act = fa % A;
+    long off = fam, offs = fam;
+    for (int k = 0; k < C.next; ++k) {
+      off = off * ed.d[k] + co[k];
+      offs = offs * ed.d[k] + cs[k];
+    }
+    const long tail = (act * n + M) * n + Lp;
+    const long ia = off * A * n * n + tail, ib = offs * A * n * n + tail;
+    double w;
+    if (C.pair0 < 0) w = V[ia];
+    else if (sector == 0) w = (ia == ib) ? V[ia] : (V[ia] + V[ib]) * isq2;
+    else w = (V[ia] - V[ib]) * isq2;
+    W[e] = w;
+  }
+}
+
+// Per (tuple, L, L'): sum_mu -Vt[mu][t,L] Vt[mu][t,L'] / D and, for L == L', sum (Vt/D)^2,
+// D = e_ext(t) + omega_mu - E0_L + E_s over kept mu.  Written to part[t][L][L'], partn[t][L].
+__global__ void k_sector_energy(const double* __restrict__ Vt, const double* __restrict__ omega,
+                                const double* __restrict__ mask, const double* __restrict__ E0,
+                                const double* __restrict__ eps, DevClass C, ExtDims ed, int c,
+                                int n, int sector, int Lsel, long ntup, int msec, double shift,
+                                double* __restrict__ part, double* __restrict__ partn,
+                                double* __restrict__ mindenom) {
+  const long ncol = ntup * n;
+  const int nL = Lsel < 0 ? n : 1;
+  const long total = ntup * nL * n;
+  double dmin = 1e300;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    const int Lp = e % n;
+    const int Li = (e / n) % nL;
+    const long t = e / ((long)n * nL);
+    const int L = Lsel < 0 ? Li : Lsel;
+    int co[3], cs[3];
+    sector_tuple(C, ed.d, sector, t, co, cs);
+    double ee = 0.0;
+    for (int k = 0; k < C.next; ++k)
+      ee += (C.slot_space[C.ext[k]] == SP_V) ? eps[c + co[k]] : -eps[co[k]];
+    double se = 0.0, sn = 0.0;
+    for (int mu = 0; mu < msec; ++mu) {
+      if (mask[mu] == 0.0) continue;
+      const double D = ee + omega[mu] - E0[L] + shift;
+      const double vl = Vt[(long)mu * ncol + t * n + L];
+      const double amp = -vl / D;
+      se += amp * Vt[(long)mu * ncol + t * n + Lp];
+      if (Lp == L) sn += amp * amp;
+      dmin = fmin(dmin, fabs(D));
+    }
+    part[(t * nL + Li) * n + Lp] = se;
+    if (Lp == L) partn[t * nL + Li] = sn;
+  }
+  // per-thread minimum -> one slot per thread block (fixed reduction later is not needed
+  // for a minimum: fmin is order independent)
+  __shared__ double red[32];
+  dmin = block_min(dmin, red);
+  if (threadIdx.x == 0) atomicMin_double(mindenom, dmin);
+}
+
+// column sums of part[rows][ncol] in fixed order -> out[ncol] (accumulated: out += sum)
+__global__ void k_colsum_acc(const double* __restrict__ part, long rows, int ncol,
+                             double* __restrict__ out, int stride_out, int offset_out) {
+  __shared__ double red[32];
+  const int col = blockIdx.x;
+  double acc = 0.0;
+  for (long r = threadIdx.x; r < rows; r += blockDim.x) acc += part[r * ncol + col];
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) out[offset_out + col * stride_out] += acc;
+}
+
+}  // namespace caspt2
+
+// ============================================================== host side
+namespace caspt2 {
+
+namespace {
+int launch_blocks(long total, int threads = 256) {
+  long b = (total + threads - 1) / threads;
+  return (int)std::max<long>(1, std::min<long>(b, 152L * 32));
+}
+int space_dim(const Dims& d, int sp) { return sp == SP_C ? d.c : (sp == SP_A ? d.a : d.v); }
+int space_off(const Dims& d, int sp) { return sp == SP_C ? 0 : (sp == SP_A ? d.c : d.c + d.a); }
+
+long sector_tuples(const ClassWork& w, int sector) {
+  const DevClass& C = w.dc;
+  if (C.pair0 < 0) {
+    long t = 1;
+    for (int k = 0; k < C.next; ++k) t *= w.ed.d[k];
+    return sector == 0 ? t : 0;
+  }
+  long t = 1, R = 0;
+  for (int k = 0; k < C.next; ++k) {
+    if (C.ext[k] == C.pair0) R = w.ed.d[k];
+    else if (C.ext[k] != C.pair1) t *= w.ed.d[k];
+  }
+  return t * (sector == 0 ? R * (R + 1) / 2 : R * (R - 1) / 2);
+}
+}  // namespace
+
+// g(d_core)_xy = sum_P B_Pxy bsum_P * 2 - sum_P sum_j B_Pxj B_Pjy; h = f - g_act - g_core
+__global__ void k_hcore(const double* __restrict__ f, const double* __restrict__ gact,
+                        const double* __restrict__ B, const double* __restrict__ bsum, int X,
+                        int nmo, int c, double* __restrict__ h) {
+  const long total = (long)nmo * nmo;
+  for (long xy = blockIdx.x * (long)blockDim.x + threadIdx.x; xy < total;
+       xy += (long)gridDim.x * blockDim.x) {
+    const int x = xy / nmo, y = xy % nmo;
+    double jc = 0.0, kc = 0.0;
+    for (int P = 0; P < X; ++P) {
+      const double* Bp = B + (long)P * nmo * nmo;
+      jc += Bp[xy] * bsum[P];
+      for (int j = 0; j < c; ++j) kc += Bp[(long)x * nmo + j] * Bp[(long)j * nmo + y];
+    }
+    h[xy] = f[xy] - gact[xy] - (2.0 * jc - kc);
+  }
+}
+
+cudaError_t launch_hcore(const double* f, const double* g_act, const double* B, const double* bsum,
+                         const Dims& d, double* h, cudaStream_t s) {
+  const long tot = (long)d.nmo() * d.nmo();
+  ++launch_counter();
+  k_hcore<<<launch_blocks(tot, 128), 128, 0, s>>>(f, g_act, B, bsum, d.X, d.nmo(), d.c, h);
+  return cudaGetLastError();
+}
+
+cudaError_t eri_block(const double* B, const Dims& d, const int sp[4], double* pack0, double* pack1,
+                      double* out, cudaStream_t s) {
+  const int n0 = space_dim(d, sp[0]), n1 = space_dim(d, sp[1]);
+  const int n2 = space_dim(d, sp[2]), n3 = space_dim(d, sp[3]);
+  if ((long)n0 * n1 * n2 * n3 == 0) return cudaSuccess;
+  const long t0 = (long)d.X * n0 * n1, t1 = (long)d.X * n2 * n3;
+  ++launch_counter();
+  k_pack_block<<<launch_blocks(t0), 256, 0, s>>>(B, d.X, d.nmo(), space_off(d, sp[0]), n0,
+                                                space_off(d, sp[1]), n1, pack0);
+  ++launch_counter();
+  k_pack_block<<<launch_blocks(t1), 256, 0, s>>>(B, d.X, d.nmo(), space_off(d, sp[2]), n2,
+                                                space_off(d, sp[3]), n3, pack1);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return dgemm(n0 * n1, n2 * n3, d.X, 1.0, pack0, n0 * n1, true, pack1, n2 * n3, false, 0.0, out,
+               n2 * n3, s);
+}
+
+void class_setup(int cls, const Dims& d, ClassWork& w) {
+  const ClassDef& C = class_def(cls);
+  w.cls = cls;
+  DevClass& dc = w.dc;
+  dc.nfam = C.nfam;
+  dc.nslot = C.nslot;
+  dc.next = C.next;
+  dc.nact = C.nact;
+  for (int k = 0; k < 4; ++k) dc.slot_space[k] = C.slot_space[k];
+  for (int k = 0; k < 3; ++k) {
+    dc.ext[k] = C.ext[k];
+    dc.act[k] = C.act[k];
+  }
+  dc.pair0 = C.pair0;
+  dc.pair1 = C.pair1;
+  w.A = 1;
+  for (int k = 0; k < C.nact; ++k) w.A *= d.a;
+  w.m = (int)(C.nfam * w.A * d.n);
+  long ext = 1;
+  for (int k = 0; k < C.next; ++k) {
+    w.ed.d[k] = space_dim(d, C.slot_space[C.ext[k]]);
+    ext *= w.ed.d[k];
+  }
+  w.vsize = C.nfam * ext * w.A * d.n * d.n;
+}
+
+long class_sector_wsize(const ClassWork& w, const Dims& d, int scheme, long* partsize) {
+  long wmax = 0, pmax = 0;
+  for (int sec = 0; sec < 2; ++sec) {
+    const long nt = sector_tuples(w, sec);
+    const long msec = scheme == CASPT2_SSSR ? w.m / d.n : w.m;
+    wmax = std::max(wmax, msec * nt * d.n);
+    pmax = std::max(pmax, nt * (long)d.n * d.n);
+  }
+  if (partsize) *partsize = pmax;
+  return wmax;
+}
+
+cudaError_t class_upload_plans(ClassWork& w, const std::vector<ActPlan>& S,
+                               const std::vector<ActPlan>& F, const std::vector<SrcPlan>& V) {
+  cudaError_t e;
+  if ((e = cudaMemcpy(w.dS, S.data(), sizeof(ActPlan) * S.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+  if ((e = cudaMemcpy(w.dF, F.data(), sizeof(ActPlan) * F.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+  if ((e = cudaMemcpy(w.dV, V.data(), sizeof(SrcPlan) * V.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+  w.nS = (int)S.size();
+  w.nF = (int)F.size();
+  w.nV = (int)V.size();
+  return cudaSuccess;
+}
+
+int class_solve(ClassWork& w, SectorWork& sw, const Dims& d, int scheme, double shift,
+                double thresh, RdmPtrs rdm, const double* f_act, const double* h,
+                const EriBlocks& eri, const double* E0, const double* eps_cv, double* ecls,
+                double* ncls, double* mindenom, cudaStream_t s) {
+  const int m = w.m, n = d.n;
+  if (w.vsize == 0 || m == 0) return CASPT2_OK;
+  const long mm = (long)m * m;
+  // overlap, active Fock, sources
+  ++launch_counter();
+  k_act_eval<<<launch_blocks(mm), 256, 0, s>>>(w.dS, w.nS, w.dc, d.a, n, rdm, f_act, w.Sact, m);
+  ++launch_counter();
+  k_act_eval<<<launch_blocks(mm), 256, 0, s>>>(w.dF, w.nF, w.dc, d.a, n, rdm, f_act, w.Fact, m);
+  ++launch_counter();
+  k_src_eval<<<launch_blocks(w.vsize), 256, 0, s>>>(w.dV, w.nV, w.dc, d, rdm, h, eri, w.V, w.vsize);
+  CASPT2_CUDA_TRY(cudaGetLastError());
+
+  const int nsec = w.dc.pair0 < 0 ? 1 : 2;
+  for (int sec = 0; sec < nsec; ++sec) {
+    const long ntup = sector_tuples(w, sec);
+    if (ntup == 0) continue;
+    const double sgn = w.dc.pair0 < 0 ? 0.0 : (sec == 0 ? 1.0 : -1.0);
+    const int nsel = scheme == CASPT2_SSSR ? n : 1;
+    for (int is = 0; is < nsel; ++is) {
+      const int Lsel = scheme == CASPT2_SSSR ? is : -1;
+      const int msec = scheme == CASPT2_SSSR ? m / n : m;
+      const long ms2 = (long)msec * msec;
+      ++launch_counter();
+      k_sector<<<launch_blocks(ms2), 256, 0, s>>>(w.Sact, m, n, sgn, Lsel, sw.Ssec, msec);
+      ++launch_counter();
+      k_sector<<<launch_blocks(ms2), 256, 0, s>>>(w.Fact, m, n, sgn, Lsel, sw.Fsec, msec);
+      CASPT2_CUDA_TRY(cudaGetLastError());
+      int st = sym_eig_jacobi(sw.Ssec, msec, sw.s, sw.Qs, sw.jac, s);
+      if (st != CASPT2_OK) return st;
+      ++launch_counter();
+      k_range_basis<<<launch_blocks(ms2), 256, 0, s>>>(sw.Qs, sw.s, msec, thresh, sw.X, sw.mask);
+      CASPT2_CUDA_TRY(cudaGetLastError());
+      CASPT2_CUDA_TRY(dgemm(msec, msec, msec, 1.0, sw.Fsec, msec, false, sw.X, msec, false, 0.0,
+                            sw.FX, msec, s));
+      CASPT2_CUDA_TRY(dgemm(msec, msec, msec, 1.0, sw.X, msec, true, sw.FX, msec, false, 0.0,
+                            sw.Ft, msec, s));
+      st = sym_eig_jacobi(sw.Ft, msec, sw.omega, sw.Qf, sw.jac, s);
+      if (st != CASPT2_OK) return st;
+      CASPT2_CUDA_TRY(dgemm(msec, msec, msec, 1.0, sw.X, msec, false, sw.Qf, msec, false, 0.0,
+                            sw.Y, msec, s));
+      const long ncol = ntup * n;
+      ++launch_counter();
+      k_sector_src<<<launch_blocks((long)msec * ncol), 256, 0, s>>>(w.V, w.dc, w.ed, d.a, n, sec,
+                                                                    Lsel, ntup, msec, sw.W);
+      CASPT2_CUDA_TRY(cudaGetLastError());
+      CASPT2_CUDA_TRY(dgemm(msec, (int)ncol, msec, 1.0, sw.Y, msec, true, sw.W, (int)ncol, false,
+                            0.0, sw.Vt, (int)ncol, s));
+      const int nL = Lsel < 0 ? n : 1;
+      const long ne = ntup * nL * n;
+      ++launch_counter();
+      k_sector_energy<<<launch_blocks(ne), 256, 0, s>>>(sw.Vt, sw.omega, sw.mask, E0, eps_cv, w.dc,
+                                                        w.ed, d.c, n, sec, Lsel, ntup, msec, shift,
+                                                        sw.part, sw.partn, mindenom);
+      ++launch_counter();
+      k_colsum_acc<<<nL * n, 256, 0, s>>>(sw.part, ntup, nL * n, ecls, 1, Lsel < 0 ? 0 : Lsel * n);
+      ++launch_counter();
+      k_colsum_acc<<<nL, 256, 0, s>>>(sw.partn, ntup, nL, ncls, 1, Lsel < 0 ? 0 : Lsel);
+      CASPT2_CUDA_TRY(cudaGetLastError());
+    }
+  }
+  return CASPT2_OK;
+}
+
+}  // namespace caspt2

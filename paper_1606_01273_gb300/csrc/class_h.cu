@@ -11,8 +11,8 @@
 // with K = (ai|bj) = sum_P B_Pai B_Pbj, K' = (aj|bi).  Under SS-SR (Eq. wfp2) only
 // nu = L survives and D = e_a + e_b - e_i - e_j + E_s.
 //
-// The amplitudes are never stored: one CTA forms a 64x64 tile of K_ij and of
-// K_ji (= K_ij transposed) over the DF index, and the epilogue applies every
+// The amplitudes are never stored: one CTA forms a 64x64 tile of K_ij (and the
+// mirrored tile) over the DF index, and the epilogue applies every
 // denominator shift and reduces the energy and norm sums.  Per-CTA partial
 // sums are reduced afterwards in a fixed order, so results are bitwise
 // reproducible run to run.
@@ -57,22 +57,37 @@ __global__ void k_classH_shifts(const double* __restrict__ omega, const double* 
   if (k < n * n) shifts[k] = omega[k / n] - E0[k % n] + shift;
 }
 
+// One CTA = (pair i <= j, tile pair ta <= tb).  It forms T1[a][b] = K_ij^ab over
+// a in tile ta, b in tile tb and, when ta < tb, T2[a][b] = K_ij^ba = sum_P B_ib B_ja,
+// so each thread holds both K_ij^ab and K_ij^ba for its elements and the K_ij block
+// is computed exactly once.  On a diagonal tile (ta == tb) K_ij^ba is read from the
+// transposed tile staged in shared memory.  Block (j, i) equals block (i, j) with a
+// and b swapped, so i < j carries weight 2; for i == j, K_ii^ba = K_ii^ab.
 __global__ void __launch_bounds__(kHThreads)
 k_classH(const double* __restrict__ Bp, const double* __restrict__ eps,
          const double* __restrict__ shifts, int nshift, int c, int v, int X, int ntile,
          double* __restrict__ partial) {
-  __shared__ double sAi[kHK][kHT], sBj[kHK][kHT], sAj[kHK][kHT], sBi[kHK][kHT];
+  __shared__ double sbuf[4 * kHK * kHT];   // operand tiles; reused for the diagonal transpose
   __shared__ double sEa[kHT], sEb[kHT];
   __shared__ double sShift[kMaxShift];
   __shared__ double red[32];
+  double (*sAi)[kHT] = reinterpret_cast<double (*)[kHT]>(sbuf);
+  double (*sBj)[kHT] = reinterpret_cast<double (*)[kHT]>(sbuf + kHK * kHT);
+  double (*sAj)[kHT] = reinterpret_cast<double (*)[kHT]>(sbuf + 2 * kHK * kHT);
+  double (*sBi)[kHT] = reinterpret_cast<double (*)[kHT]>(sbuf + 3 * kHK * kHT);
 
+  const int ntp = ntile * (ntile + 1) / 2;
   long bid = blockIdx.x;
-  const int tb = bid % ntile; bid /= ntile;
-  const int ta = bid % ntile; bid /= ntile;
-  int pair = (int)bid, i = 0;
+  int tp = bid % ntp;
+  int pair = (int)(bid / ntp), i = 0;
   while (pair >= c - i) { pair -= c - i; ++i; }
   const int j = i + pair;
+  int ta = 0;
+  while (tp >= ntile - ta) { tp -= ntile - ta; ++ta; }
+  const int tb = ta + tp;
   const bool same = (i == j);
+  const bool diag = (ta == tb);
+  const bool need_t2 = !same && !diag;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int a0 = ta * kHT, b0 = tb * kHT;
   const double* bi = Bp + (long)i * X * v;
@@ -99,7 +114,7 @@ k_classH(const double* __restrict__ Bp, const double* __restrict__ eps,
       const int a = a0 + col, b = b0 + col;
       sAi[kk][col] = (okP && a < v) ? bi[(long)P * v + a] : 0.0;
       sBj[kk][col] = (okP && b < v) ? bj[(long)P * v + b] : 0.0;
-      if (!same) {
+      if (need_t2) {
         sAj[kk][col] = (okP && a < v) ? bj[(long)P * v + a] : 0.0;
         sBi[kk][col] = (okP && b < v) ? bi[(long)P * v + b] : 0.0;
       }
@@ -116,7 +131,7 @@ k_classH(const double* __restrict__ Bp, const double* __restrict__ eps,
       for (int ii = 0; ii < 4; ++ii)
 #pragma unroll
         for (int jj = 0; jj < 4; ++jj) t1[ii][jj] = fma(ra[ii], rb[jj], t1[ii][jj]);
-      if (!same) {
+      if (need_t2) {
 #pragma unroll
         for (int ii = 0; ii < 4; ++ii) ra[ii] = sAj[kk][ty + 16 * ii];
 #pragma unroll
@@ -130,7 +145,27 @@ k_classH(const double* __restrict__ Bp, const double* __restrict__ eps,
     __syncthreads();
   }
 
+  if (same) {
+#pragma unroll
+    for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) t2[ii][jj] = t1[ii][jj];
+  } else if (diag) {
+    // K_ij^ba of this thread's (a, b) is T1 at (b, a): stage T1 (64 x 64) and read it transposed
+    double* sT = sbuf;
+#pragma unroll
+    for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) sT[(ty + 16 * ii) * kHT + tx + 16 * jj] = t1[ii][jj];
+    __syncthreads();
+#pragma unroll
+    for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) t2[ii][jj] = sT[(tx + 16 * jj) * kHT + ty + 16 * ii];
+  }
+
   // epilogue: numerators and shift-free denominators of this thread's 16 (a, b)
+  const double wij = same ? 1.0 : 2.0;
   const double ei = eps[i], ej = eps[j];
   double num[16], d0[16];
 #pragma unroll
@@ -139,12 +174,12 @@ k_classH(const double* __restrict__ Bp, const double* __restrict__ eps,
     for (int jj = 0; jj < 4; ++jj) {
       const int la = ty + 16 * ii, lb = tx + 16 * jj;
       const bool ok = (a0 + la < v) && (b0 + lb < v);
-      const double k1 = t1[ii][jj];
-      const double k2 = same ? k1 : t2[ii][jj];
-      // K_ij^ab (2K_ij^ab - K_ij^ba) + (i != j) K_ji^ab (2K_ji^ab - K_ji^ba)
+      const double k1 = t1[ii][jj];          // K_ij^ab
+      const double k2 = t2[ii][jj];          // K_ij^ba
+      // element (a, b); when ta < tb also element (b, a), which lives in no other CTA
       double nm = k1 * (2.0 * k1 - k2);
-      if (!same) nm += k2 * (2.0 * k2 - k1);
-      num[ii * 4 + jj] = ok ? nm : 0.0;
+      if (!diag) nm += k2 * (2.0 * k2 - k1);
+      num[ii * 4 + jj] = ok ? wij * nm : 0.0;
       d0[ii * 4 + jj] = ok ? (sEa[la] + sEb[lb] - ei - ej) : 1.0;
     }
   double* out = partial + blockIdx.x * (long)(2 * nshift + 1);
@@ -215,10 +250,17 @@ __global__ void k_classH_combine(const double* __restrict__ sums, const double* 
   }
 }
 
+cudaError_t launch_eps_cv(const double* f, const Dims& d, double* eps, cudaStream_t s) {
+  if (d.c + d.v == 0) return cudaSuccess;
+  ++launch_counter();
+  k_eps_cv<<<(d.c + d.v + 127) / 128, 128, 0, s>>>(f, d.nmo(), d.c, d.a, d.v, eps);
+  return cudaGetLastError();
+}
+
 long classH_blocks(const Dims& d) {
   long ntile = (d.v + kHT - 1) / kHT;
   long npair = (long)d.c * (d.c + 1) / 2;
-  return npair * ntile * ntile;
+  return npair * (ntile * (ntile + 1) / 2);
 }
 
 int classH_nshift(const Dims& d, int scheme) { return scheme == CASPT2_SSSR ? 1 : d.n * d.n; }

@@ -6,7 +6,7 @@ namespace caspt2 {
 
 struct Dims {
   int c, a, v, X, n;
-  int nmo() const { return c + a + v; }
+  __host__ __device__ int nmo() const { return c + a + v; }
 };
 
 // ---- setup (setup.cu) --------------------------------------------------------
@@ -55,6 +55,10 @@ struct ClassHWork {
   cudaEvent_t ev_gemm0 = nullptr, ev_gemm1 = nullptr;  // optional: bracket the GEMM kernel
 };
 long classH_blocks(const Dims& d);
+// eps[0..c) closed and eps[c..c+v) virtual orbital energies (diagonal of f)
+cudaError_t launch_eps_cv(const double* f, const Dims& d, double* eps, cudaStream_t s);
+// out[r][s] = f[c + r][c + s] (active block, compact)
+cudaError_t launch_active_block(const double* f, const Dims& d, double* out, cudaStream_t s);
 int  classH_nshift(const Dims& d, int scheme);
 cudaError_t launch_classH(const double* f, const double* B, const double* Ftil, const double* E0,
                           double shift, int scheme, const Dims& d, ClassHWork& w, int* status,

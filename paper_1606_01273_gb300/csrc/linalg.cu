@@ -1,0 +1,235 @@
+// FP64 dense building blocks: a tiled GEMM and a parallel cyclic Jacobi
+// eigensolver for symmetric matrices (used for the per-class overlap and Fock
+// eigenproblems, Sec. II.B: truncation of the overlap eigenvalues).
+#include "linalg.cuh"
+
+namespace caspt2 {
+
+// C[i][j] = alpha * sum_k A(i,k) B(k,j) + beta * C[i][j]
+// A(i,k) = ta ? A[k*lda + i] : A[i*lda + k]; B(k,j) = tb ? B[j*ldb + k] : B[k*ldb + j]
+constexpr int kGT = 64, kGK = 16;
+__global__ void __launch_bounds__(256)
+k_dgemm(int M, int N, int K, double alpha, const double* __restrict__ A, int lda, int ta,
+        const double* __restrict__ B, int ldb, int tb, double beta, double* __restrict__ C, int ldc,
+        long sA, long sB, long sC) {
+  __shared__ double sa[kGK][kGT + 1], sb[kGK][kGT + 1];
+  A += blockIdx.z * sA;
+  B += blockIdx.z * sB;
+  C += blockIdx.z * sC;
+  const int i0 = blockIdx.y * kGT, j0 = blockIdx.x * kGT;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double acc[4][4] = {};
+  for (int k0 = 0; k0 < K; k0 += kGK) {
+    for (int l = threadIdx.x; l < kGK * kGT; l += 256) {
+      int kk, ii;
+      if (ta) { ii = l % kGT; kk = l / kGT; } else { kk = l % kGK; ii = l / kGK; }
+      const int gi = i0 + ii, gk = k0 + kk;
+      double v = 0.0;
+      if (gi < M && gk < K) v = ta ? A[(long)gk * lda + gi] : A[(long)gi * lda + gk];
+      sa[kk][ii] = v;
+    }
+    for (int l = threadIdx.x; l < kGK * kGT; l += 256) {
+      int kk, jj;
+      if (tb) { kk = l % kGK; jj = l / kGK; } else { jj = l % kGT; kk = l / kGT; }
+      const int gj = j0 + jj, gk = k0 + kk;
+      double v = 0.0;
+      if (gj < N && gk < K) v = tb ? B[(long)gj * ldb + gk] : B[(long)gk * ldb + gj];
+      sb[kk][jj] = v;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < kGK; ++kk) {
+      double ra[4], rb[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) { ra[q] = sa[kk][ty + 16 * q]; rb[q] = sb[kk][tx + 16 * q]; }
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[p][q] = fma(ra[p], rb[q], acc[p][q]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int gi = i0 + ty + 16 * p, gj = j0 + tx + 16 * q;
+      if (gi < M && gj < N) {
+        double* c = C + (long)gi * ldc + gj;
+        *c = alpha * acc[p][q] + (beta == 0.0 ? 0.0 : beta * *c);
+      }
+    }
+}
+
+cudaError_t dgemm(int M, int N, int K, double alpha, const double* A, int lda, bool ta,
+                  const double* B, int ldb, bool tb, double beta, double* C, int ldc,
+                  cudaStream_t s, int batch, long sA, long sB, long sC) {
+  if (M <= 0 || N <= 0 || batch <= 0) return cudaSuccess;
+  dim3 grid((N + kGT - 1) / kGT, (M + kGT - 1) / kGT, batch);
+  ++launch_counter();
+  k_dgemm<<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, ta ? 1 : 0, B, ldb, tb ? 1 : 0, beta, C, ldc,
+                               sA, sB, sC);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- Jacobi
+// Round-robin ("circle") pairing over mp = m rounded up to even positions: in round r
+// position 0 is fixed and positions 1..mp-1 rotate; pair k joins positions k and
+// mp-1-k.  Indices >= m are padding (zero rows/columns, never rotated).
+__device__ __forceinline__ int jac_index(int pos, int r, int mp) {
+  return pos == 0 ? 0 : ((pos - 1 + r) % (mp - 1)) + 1;
+}
+
+__device__ __forceinline__ void jac_pair(int k, int r, int mp, int& p, int& q) {
+  int a = jac_index(k, r, mp), b = jac_index(mp - 1 - k, r, mp);
+  p = a < b ? a : b;
+  q = a < b ? b : a;
+}
+
+__device__ __forceinline__ void jac_rot(const double* A, int m, int p, int q, double& c, double& s) {
+  c = 1.0;
+  s = 0.0;
+  if (q >= m) return;
+  const double apq = A[(long)p * m + q];
+  if (apq == 0.0) return;
+  const double app = A[(long)p * m + p], aqq = A[(long)q * m + q];
+  const double theta = (aqq - app) / (2.0 * apq);
+  double t;
+  if (fabs(theta) > 1e150) t = 0.5 / theta;
+  else t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+  c = 1.0 / sqrt(t * t + 1.0);
+  s = t * c;
+}
+
+// A' = J^T A J for the disjoint rotations of round r (one thread per 2x2 block of pairs),
+// V' = V J.  Reads A, V; writes A2, V2 (ping-pong buffers).
+__global__ void k_jacobi_round(const double* __restrict__ A, double* __restrict__ A2,
+                               const double* __restrict__ V, double* __restrict__ V2, int m,
+                               int mp, int r) {
+  const int npair = mp / 2;
+  const long nblk = (long)npair * npair;
+  const long total = nblk + (long)m * npair;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total;
+       t += (long)gridDim.x * blockDim.x) {
+    if (t < nblk) {
+      const int I = t / npair, J = t % npair;
+      int pI, qI, pJ, qJ;
+      jac_pair(I, r, mp, pI, qI);
+      jac_pair(J, r, mp, pJ, qJ);
+      double cI, sI, cJ, sJ;
+      jac_rot(A, m, pI, qI, cI, sI);
+      jac_rot(A, m, pJ, qJ, cJ, sJ);
+      const bool vq_I = qI < m, vq_J = qJ < m;
+      const double a00 = A[(long)pI * m + pJ];
+      const double a01 = vq_J ? A[(long)pI * m + qJ] : 0.0;
+      const double a10 = vq_I ? A[(long)qI * m + pJ] : 0.0;
+      const double a11 = (vq_I && vq_J) ? A[(long)qI * m + qJ] : 0.0;
+      // rows: [c -s; s c] * A_sub ; columns: * [c s; -s c]
+      const double r00 = cI * a00 - sI * a10, r01 = cI * a01 - sI * a11;
+      const double r10 = sI * a00 + cI * a10, r11 = sI * a01 + cI * a11;
+      double n00 = r00 * cJ - r01 * sJ, n01 = r00 * sJ + r01 * cJ;
+      double n10 = r10 * cJ - r11 * sJ, n11 = r10 * sJ + r11 * cJ;
+      if (I == J && vq_I) { n01 = 0.0; n10 = 0.0; }   // the rotated pair is annihilated
+      A2[(long)pI * m + pJ] = n00;
+      if (vq_J) A2[(long)pI * m + qJ] = n01;
+      if (vq_I) A2[(long)qI * m + pJ] = n10;
+      if (vq_I && vq_J) A2[(long)qI * m + qJ] = n11;
+    } else {
+      const long u = t - nblk;
+      const int row = u / npair, J = u % npair;
+      int pJ, qJ;
+      jac_pair(J, r, mp, pJ, qJ);
+      double cJ, sJ;
+      jac_rot(A, m, pJ, qJ, cJ, sJ);
+      const double vp = V[(long)row * m + pJ];
+      if (qJ < m) {
+        const double vq = V[(long)row * m + qJ];
+        V2[(long)row * m + pJ] = cJ * vp - sJ * vq;
+        V2[(long)row * m + qJ] = sJ * vp + cJ * vq;
+      } else {
+        V2[(long)row * m + pJ] = vp;
+      }
+    }
+  }
+}
+
+__global__ void k_eye(double* V, int m) {
+  long total = (long)m * m;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total;
+       t += (long)gridDim.x * blockDim.x)
+    V[t] = (t / m == t % m) ? 1.0 : 0.0;
+}
+
+// off = sum_{i != j} A_ij^2, dia = sum_i A_ii^2 (fixed-order block reduction)
+__global__ void k_offnorm(const double* __restrict__ A, int m, double* out) {
+  __shared__ double red[32];
+  double off = 0.0, dia = 0.0;
+  const long total = (long)m * m;
+  for (long t = threadIdx.x; t < total; t += blockDim.x) {
+    const double x = A[t];
+    if (t / m == t % m) dia += x * x; else off += x * x;
+  }
+  off = block_sum(off, red);
+  if (threadIdx.x == 0) out[0] = off;
+  dia = block_sum(dia, red);
+  if (threadIdx.x == 0) out[1] = dia;
+}
+
+__global__ void k_diag_out(const double* __restrict__ A, int m, double* w) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) w[i] = A[(long)i * m + i];
+}
+
+// Eigenpairs of symmetric A (m x m, row-major, overwritten): w[m], V[m][m] (columns).
+// work: 2*m*m doubles + 2.  Unsorted.  Synchronises the stream once per sweep.
+int sym_eig_jacobi(double* A, int m, double* w, double* V, double* work, cudaStream_t s) {
+  if (m <= 0) return CASPT2_OK;
+  double* A2 = work;
+  double* V2 = work + (long)m * m;
+  double* nrm = work + 2L * m * m;
+  const int mp = m + (m & 1);
+  const long total = (long)(mp / 2) * (mp / 2) + (long)m * (mp / 2);
+  const int threads = 256;
+  const int blocks = (int)std::min<long>((total + threads - 1) / threads, 152L * 16);
+  ++launch_counter();
+  k_eye<<<(int)std::min<long>(((long)m * m + 255) / 256, 152L * 16), 256, 0, s>>>(V, m);
+  CASPT2_CUDA_TRY(cudaGetLastError());
+  CASPT2_CUDA_TRY(cudaMemcpyAsync(A2, A, sizeof(double) * m * m, cudaMemcpyDeviceToDevice, s));
+  CASPT2_CUDA_TRY(cudaMemcpyAsync(V2, V, sizeof(double) * m * m, cudaMemcpyDeviceToDevice, s));
+  double* cur = A;
+  double* nxt = A2;
+  double* vc = V;
+  double* vn = V2;
+  bool conv = (m == 1);
+  double prev = -1.0;
+  // Sweep until the off-diagonal norm reaches the rounding floor: it is exactly zero,
+  // below 1e-34 of the diagonal, or (once below 1e-20) it no longer drops by 4x.
+  for (int sweep = 0; sweep < 60 && !conv; ++sweep) {
+    for (int r = 0; r < mp - 1; ++r) {
+      ++launch_counter();
+      k_jacobi_round<<<blocks, threads, 0, s>>>(cur, nxt, vc, vn, m, mp, r);
+      std::swap(cur, nxt);
+      std::swap(vc, vn);
+    }
+    CASPT2_CUDA_TRY(cudaGetLastError());
+    ++launch_counter();
+    k_offnorm<<<1, 1024, 0, s>>>(cur, m, nrm);
+    double h[2];
+    CASPT2_CUDA_TRY(cudaMemcpyAsync(h, nrm, sizeof(h), cudaMemcpyDeviceToHost, s));
+    CASPT2_CUDA_TRY(cudaStreamSynchronize(s));
+    if (!(h[0] == h[0])) return CASPT2_ENAN;
+    if (h[0] == 0.0 || h[0] <= 1e-34 * h[1]) conv = true;
+    else if (h[0] <= 1e-20 * h[1] && prev >= 0.0 && h[0] > 0.25 * prev) conv = true;
+    prev = h[0];
+  }
+  if (cur != A) {
+    CASPT2_CUDA_TRY(cudaMemcpyAsync(A, cur, sizeof(double) * m * m, cudaMemcpyDeviceToDevice, s));
+    CASPT2_CUDA_TRY(cudaMemcpyAsync(V, vc, sizeof(double) * m * m, cudaMemcpyDeviceToDevice, s));
+  }
+  ++launch_counter();
+  k_diag_out<<<(m + 127) / 128, 128, 0, s>>>(A, m, w);
+  CASPT2_CUDA_TRY(cudaGetLastError());
+  return conv ? CASPT2_OK : CASPT2_ENOTCONV;
+}
+
+}  // namespace caspt2

@@ -358,6 +358,18 @@ cudaError_t launch_href(const double* f, const double* g, const double* rdm1r, c
   return cudaGetLastError();
 }
 
+__global__ void k_active_block(const double* __restrict__ f, int nmo, int c, int a, double* out) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < a * a) out[idx] = f[(long)(c + idx / a) * nmo + c + idx % a];
+}
+
+cudaError_t launch_active_block(const double* f, const Dims& d, double* out, cudaStream_t s) {
+  if (d.a == 0) return cudaSuccess;
+  ++launch_counter();
+  k_active_block<<<(d.a * d.a + 127) / 128, 128, 0, s>>>(f, d.nmo(), d.c, d.a, out);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- H^eff
 __global__ void k_heff(const double* __restrict__ href, const double* __restrict__ ecls,
                        const double* __restrict__ ncls, unsigned mask, double shift, int n,

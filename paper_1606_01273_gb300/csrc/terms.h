@@ -1,0 +1,61 @@
+// Contraction terms of the excitation classes (host-side generator; not part of the C ABI).
+//
+// The overlap, active-Fock and source matrix elements of every class in Eq. (class)
+// are products of spin-free generators between reference states whose closed
+// orbitals are doubly occupied and whose virtual orbitals are empty.  The generator
+// reduces each product to active-space RDMs and emits "access plans": for every term,
+// which RDM rank and which output / loop index feeds each RDM index, which integral
+// block and indices multiply it, and which index equalities it requires.  The device
+// kernels in class_ag.cu evaluate these plans.
+#pragma once
+#include <cstdint>
+#include <vector>
+
+namespace caspt2 {
+
+enum Space : int8_t { SP_C = 0, SP_A = 1, SP_V = 2 };
+
+// An index reference in a plan: output bra slot k (k < 8), output ket slot (8 + k),
+// or loop variable (16 + k).
+constexpr int kRefBra = 0, kRefKet = 8, kRefLoop = 16;
+
+struct ClassDef {
+  int nfam;            // operator families (class D has two)
+  int fam[2][4];       // slot ids of p, q, r, s in E_{pq,rs}
+  int nslot;
+  Space slot_space[4];
+  int next, ext[3];    // external slots in output order
+  int nact, act[3];    // active slots in output order
+  int pair0, pair1;    // external slots that can be swapped (-1 if none)
+};
+
+const ClassDef& class_def(int cls);   // cls = 0..6 for classes A..G
+
+// Term of S / F_act: coeff * [prod eq] * sum_{loops} f[l0][l1]^{has_f} * Gamma_rank[idx...]
+// indices refer to bra active slots, ket active slots or loop variables (all active).
+struct ActPlan {
+  double coeff;
+  int8_t fb, fk, pi, rank, has_f, nloop, neq;
+  int8_t idx[8];       // RDM indices p1 q1 p2 q2 ... (refs)
+  int8_t fidx[2];      // f indices (refs) when has_f
+  int8_t eq[4][2];     // pairs of output refs that must be equal
+};
+
+// Term of the sources V[fam][ext...][act...][M][L] = <M|E_Omega^dag H|L>:
+// coeff * integral[iidx...] * Gamma_rank[idx...] summed over loop variables.
+struct SrcPlan {
+  double coeff;        // includes the 1/2 of the two-body part
+  int8_t fb, kind;     // kind 0: h_pq, 1: (pq|rt)
+  int8_t ispace[4];    // spaces of the integral indices
+  int8_t iidx[4];      // integral indices (refs: bra slot = ext/act slot id, loops)
+  int8_t rank, nloop, neq;
+  int8_t idx[8];
+  int8_t loop_space[4];
+  int8_t eq[4][2];
+};
+
+// Build the plans of class cls (0..6).  Deterministic; a few hundred terms.
+void build_act_plans(int cls, bool with_fock, std::vector<ActPlan>& out);
+void build_src_plans(int cls, std::vector<SrcPlan>& out);
+
+}  // namespace caspt2

@@ -17,8 +17,9 @@ CASES = {
     "nact0_c6v50x40": dict(nclosed=6, nact=0, nvirt=50, naux=40, nstate=1, seed=22),
     "c20a8v200x700n3": WORKLOADS["c20a8v200x700n3"],
 }
-OPTS = [dict(xms=1, scheme=0, shift=0.0), dict(xms=1, scheme=0, shift=0.2),
-        dict(xms=0, scheme=0, shift=0.2), dict(xms=1, scheme=1, shift=0.2)]
+H_ONLY = 1 << 7
+OPTS = [dict(xms=1, scheme=0, shift=0.0, class_mask=H_ONLY), dict(xms=1, scheme=0, shift=0.2, class_mask=H_ONLY),
+        dict(xms=0, scheme=0, shift=0.2, class_mask=H_ONLY), dict(xms=1, scheme=1, shift=0.2, class_mask=H_ONLY)]
 
 ETOL = 1e-8   # |dE| bound on energies (Eh)
 
@@ -68,8 +69,8 @@ def test_class_h_parity(cp, name, opt):
 
 def test_bitwise_reproducible(cp):
     p = _prob("ragged_c5a3v70x37n3")
-    a = cp.solve_problem(p, shift=0.2)
-    b = cp.solve_problem(p, shift=0.2)
+    a = cp.solve_problem(p, shift=0.2, class_mask=H_ONLY)
+    b = cp.solve_problem(p, shift=0.2, class_mask=H_ONLY)
     assert np.array_equal(a.Ems, b.Ems) and np.array_equal(a.e_class["H"], b.e_class["H"])
 
 
@@ -77,15 +78,15 @@ def test_device_resident_inputs_and_stream(cp):
     """Inputs passed as device pointers and a caller stream give the host-path result."""
     import torch
     p = _prob("c4a4v20x84n2")
-    host = cp.problem_inputs(p)
+    host = cp.problem_inputs(p, kmax=2)[:4]
     dev = [torch.from_numpy(x).cuda() for x in host]
-    ctx = cp.Context(p.nclosed, p.nact, p.nvirt, p.naux, p.nstate, shift=0.1)
+    ctx = cp.Context(p.nclosed, p.nact, p.nvirt, p.naux, p.nstate, shift=0.1, class_mask=H_ONLY)
     s = torch.cuda.Stream()
     ctx.set_inputs(*dev)
     ctx.solve(stream=s.cuda_stream)
     r_dev = ctx.result()
     ctx.close()
-    r_host = cp.solve_problem(p, shift=0.1)
+    r_host = cp.solve_problem(p, shift=0.1, class_mask=H_ONLY)
     assert np.array_equal(r_dev.Ems, r_host.Ems)
 
 
@@ -95,9 +96,9 @@ def test_errors_are_status_codes(cp):
     h = C.c_void_p()
     bad = cp.Dims(2, 2, 2, 4, 0)
     assert L.caspt2_create(C.byref(h), C.byref(bad), None) == cp.EINVAL
-    ctx = cp.Context(2, 2, 2, 4, 1)
+    ctx = cp.Context(2, 2, 2, 4, 1, class_mask=H_ONLY)
     assert L.caspt2_solve(ctx._h, None) == cp.ESTATE
     assert L.caspt2_get_energies(ctx._h, None, None, None, None, None, None) == cp.ESTATE
     with pytest.raises(cp.CASPT2Error):
-        cp.Context(2, 2, 2, 4, 1, class_mask=1)   # class A is not in this build
+        cp.Context(2, 2, 2, 4, 1, class_mask=1 << 9)   # no such class
     ctx.close()

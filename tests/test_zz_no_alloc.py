@@ -34,9 +34,9 @@ def cp():
 def test_noalloc_matches_solve_twice(cp, opt):
     import torch
     p = make_problem(nclosed=5, nact=3, nvirt=70, naux=37, nstate=3, seed=21, nelact=2, kmax=2)
-    ref = cp.solve_problem(p, **opt)
+    ref = cp.solve_problem(p, class_mask=1 << 7, **opt)
     e_ref, n_ref = ref.e_class["H"], ref.norm_class["H"]
-    f, B, rdm1, _ = cp.problem_inputs(p)
+    f, B, rdm1 = cp.problem_inputs(p, kmax=1)[:3]
     dev = torch.device("cuda", 0)
     f_d, B_d, r_d = (torch.from_numpy(x).to(dev) for x in (f, B, rdm1))
     n = p.nstate
