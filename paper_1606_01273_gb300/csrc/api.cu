@@ -230,7 +230,7 @@ int caspt2_create(caspt2_ctx** out, const caspt2_dims* dims, const caspt2_option
       const long mx = (long)std::sqrt((double)m2max) + 1;
       ALLOC(q.Ssec, m2max); ALLOC(q.Fsec, m2max); ALLOC(q.s, mx); ALLOC(q.Qs, m2max);
       ALLOC(q.X, m2max); ALLOC(q.FX, m2max); ALLOC(q.Ft, m2max); ALLOC(q.omega, mx);
-      ALLOC(q.Qf, m2max); ALLOC(q.Y, m2max); ALLOC(q.mask, mx); ALLOC(q.jac, 2 * m2max + 2);
+      ALLOC(q.Qf, m2max); ALLOC(q.Y, m2max); ALLOC(q.mask, mx); ALLOC(q.jac, sym_eig_work((int)mx));
       ALLOC(q.W, wmax); ALLOC(q.Vt, wmax); ALLOC(q.part, pmax); ALLOC(q.partn, pmax);
       ALLOC(c->h, nmo * nmo);
       ALLOC(c->fact, a2);

@@ -179,16 +179,15 @@ __global__ void k_sector(const double* __restrict__ in, int m, int n, double sgn
   }
 }
 
-// X[:, k] = Q[:, k] / sqrt(s_k) for s_k >= thresh, else 0; mask[k] = kept
+// Eigenvalues ascending: the kept overlap directions are the last nk columns.
+// X[i][c] = Q[i][m - nk + c] / sqrt(s[m - nk + c])   (m x nk, row-major)
 __global__ void k_range_basis(const double* __restrict__ Q, const double* __restrict__ s, int m,
-                              double thresh, double* __restrict__ X, double* __restrict__ mask) {
-  const long total = (long)m * m;
+                              int nk, double* __restrict__ X) {
+  const long total = (long)m * nk;
   for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
        e += (long)gridDim.x * blockDim.x) {
-    const int k = e % m;
-    const bool keep = s[k] >= thresh;
-    X[e] = keep ? Q[e] / sqrt(s[k]) : 0.0;
-    if (e < m) mask[e] = s[e] >= thresh ? 1.0 : 0.0;
+    const int i = e / nk, c = e % nk, k = m - nk + c;
+    X[e] = Q[(long)i * m + k] / sqrt(s[k]);
   }
 }
 
@@ -278,7 +277,7 @@ __global__ void k_sector_src(const double* __restrict__ V, DevClass C, ExtDims e
 // Per (tuple, L, L'): sum_mu -Vt[mu][t,L] Vt[mu][t,L'] / D and, for L == L', sum (Vt/D)^2,
 // D = e_ext(t) + omega_mu - E0_L + E_s over kept mu.  Written to part[t][L][L'], partn[t][L].
 __global__ void k_sector_energy(const double* __restrict__ Vt, const double* __restrict__ omega,
-                                const double* __restrict__ mask, const double* __restrict__ E0,
+                                const double* __restrict__ E0,
                                 const double* __restrict__ eps, DevClass C, ExtDims ed, int c,
                                 int n, int sector, int Lsel, long ntup, int msec, double shift,
                                 double* __restrict__ part, double* __restrict__ partn,
@@ -300,7 +299,6 @@ __global__ void k_sector_energy(const double* __restrict__ Vt, const double* __r
       ee += (C.slot_space[C.ext[k]] == SP_V) ? eps[c + co[k]] : -eps[co[k]];
     double se = 0.0, sn = 0.0;
     for (int mu = 0; mu < msec; ++mu) {
-      if (mask[mu] == 0.0) continue;
       const double D = ee + omega[mu] - E0[L] + shift;
       const double vl = Vt[(long)mu * ncol + t * n + L];
       const double amp = -vl / D;
@@ -483,31 +481,37 @@ int class_solve(ClassWork& w, SectorWork& sw, const Dims& d, int scheme, double 
       ++launch_counter();
       k_sector<<<launch_blocks(ms2), 256, 0, s>>>(w.Fact, m, n, sgn, Lsel, sw.Fsec, msec);
       CASPT2_CUDA_TRY(cudaGetLastError());
-      int st = sym_eig_jacobi(sw.Ssec, msec, sw.s, sw.Qs, sw.jac, s);
+      int st = sym_eig(sw.Ssec, msec, sw.s, sw.Qs, sw.jac, s);
       if (st != CASPT2_OK) return st;
+      // number of overlap eigenvalues at or above the threshold (ascending order)
+      std::vector<double> hs(msec);
+      CASPT2_CUDA_TRY(cudaMemcpyAsync(hs.data(), sw.s, sizeof(double) * msec,
+                                      cudaMemcpyDeviceToHost, s));
+      CASPT2_CUDA_TRY(cudaStreamSynchronize(s));
+      int nk = 0;
+      for (int k = 0; k < msec; ++k) nk += hs[k] >= thresh ? 1 : 0;
+      if (nk == 0) continue;
       ++launch_counter();
-      k_range_basis<<<launch_blocks(ms2), 256, 0, s>>>(sw.Qs, sw.s, msec, thresh, sw.X, sw.mask);
+      k_range_basis<<<launch_blocks((long)msec * nk), 256, 0, s>>>(sw.Qs, sw.s, msec, nk, sw.X);
       CASPT2_CUDA_TRY(cudaGetLastError());
-      CASPT2_CUDA_TRY(dgemm(msec, msec, msec, 1.0, sw.Fsec, msec, false, sw.X, msec, false, 0.0,
-                            sw.FX, msec, s));
-      CASPT2_CUDA_TRY(dgemm(msec, msec, msec, 1.0, sw.X, msec, true, sw.FX, msec, false, 0.0,
-                            sw.Ft, msec, s));
-      st = sym_eig_jacobi(sw.Ft, msec, sw.omega, sw.Qf, sw.jac, s);
+      CASPT2_CUDA_TRY(dgemm(msec, nk, msec, 1.0, sw.Fsec, msec, false, sw.X, nk, false, 0.0,
+                            sw.FX, nk, s));
+      CASPT2_CUDA_TRY(dgemm(nk, nk, msec, 1.0, sw.X, nk, true, sw.FX, nk, false, 0.0, sw.Ft, nk, s));
+      st = sym_eig(sw.Ft, nk, sw.omega, sw.Qf, sw.jac, s);
       if (st != CASPT2_OK) return st;
-      CASPT2_CUDA_TRY(dgemm(msec, msec, msec, 1.0, sw.X, msec, false, sw.Qf, msec, false, 0.0,
-                            sw.Y, msec, s));
+      CASPT2_CUDA_TRY(dgemm(msec, nk, nk, 1.0, sw.X, nk, false, sw.Qf, nk, false, 0.0, sw.Y, nk, s));
       const long ncol = ntup * n;
       ++launch_counter();
       k_sector_src<<<launch_blocks((long)msec * ncol), 256, 0, s>>>(w.V, w.dc, w.ed, d.a, n, sec,
                                                                     Lsel, ntup, msec, sw.W);
       CASPT2_CUDA_TRY(cudaGetLastError());
-      CASPT2_CUDA_TRY(dgemm(msec, (int)ncol, msec, 1.0, sw.Y, msec, true, sw.W, (int)ncol, false,
+      CASPT2_CUDA_TRY(dgemm(nk, (int)ncol, msec, 1.0, sw.Y, nk, true, sw.W, (int)ncol, false,
                             0.0, sw.Vt, (int)ncol, s));
       const int nL = Lsel < 0 ? n : 1;
       const long ne = ntup * nL * n;
       ++launch_counter();
-      k_sector_energy<<<launch_blocks(ne), 256, 0, s>>>(sw.Vt, sw.omega, sw.mask, E0, eps_cv, w.dc,
-                                                        w.ed, d.c, n, sec, Lsel, ntup, msec, shift,
+      k_sector_energy<<<launch_blocks(ne), 256, 0, s>>>(sw.Vt, sw.omega, E0, eps_cv, w.dc, w.ed,
+                                                        d.c, n, sec, Lsel, ntup, nk, shift,
                                                         sw.part, sw.partn, mindenom);
       ++launch_counter();
       k_colsum_acc<<<nL * n, 256, 0, s>>>(sw.part, ntup, nL * n, ecls, 1, Lsel < 0 ? 0 : Lsel * n);

@@ -1,0 +1,378 @@
+// FP64 symmetric eigensolver for the per-class overlap and Fock matrices
+// (Sec. II.B: eigenvalues of the overlap below the threshold are truncated):
+//   1. Householder reduction to tridiagonal form, T = Q^T A Q (one reflector per step:
+//      p = tau A22 v, w = p - (tau/2)(p.v) v, A22 -= v w^T + w v^T);
+//   2. every eigenvalue of T by bisection on Sturm counts (one thread per eigenvalue,
+//      absolute accuracy ~ eps ||T||);
+//   3. every eigenvector of T by inverse iteration on the pivoted tridiagonal LU
+//      (one thread per eigenvalue), Gram-Schmidt inside clusters of equal eigenvalues;
+//   4. one Newton-Schulz step Z <- Z (3 - Z^T Z) / 2 to restore orthogonality to
+//      rounding level;
+//   5. back-transformation V = Q Z by applying the reflectors in reverse order.
+#include <vector>
+
+#include "linalg.cuh"
+
+namespace caspt2 {
+
+namespace {
+
+constexpr int kT = 256;
+
+int nblocks(long total, int threads = kT) {
+  long b = (total + threads - 1) / threads;
+  return (int)std::max<long>(1, std::min<long>(b, 152L * 32));
+}
+
+}  // namespace
+
+// Reflector for column k: x = A[k][k+1..m-1] (row k, symmetric storage).
+// v is stored in vbuf[k*m + k+1 ..] with v[k+1] = 1; tau[k]; d[k] = A[k][k]; e[k] = beta.
+__global__ void k_house(double* __restrict__ A, int m, int k, double* __restrict__ vbuf,
+                        double* __restrict__ tau, double* __restrict__ d, double* __restrict__ e) {
+  __shared__ double red[32];
+  __shared__ double sh[2];
+  const double* x = A + (long)k * m + k + 1;
+  const int n1 = m - k - 1;
+  double s = 0.0;
+  for (int i = 1 + threadIdx.x; i < n1; i += blockDim.x) s += x[i] * x[i];
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) {
+    const double alpha = x[0];
+    double beta, t, scale;
+    if (s == 0.0) {
+      beta = alpha;
+      t = 0.0;
+      scale = 0.0;
+    } else {
+      beta = -copysign(sqrt(alpha * alpha + s), alpha);
+      t = (beta - alpha) / beta;
+      scale = 1.0 / (alpha - beta);
+    }
+    sh[0] = t;
+    sh[1] = scale;
+    tau[k] = t;
+    d[k] = A[(long)k * m + k];
+    e[k] = beta;
+  }
+  __syncthreads();
+  const double scale = sh[1];
+  double* v = vbuf + (long)k * m + k + 1;
+  for (int i = threadIdx.x; i < n1; i += blockDim.x) v[i] = (i == 0) ? 1.0 : x[i] * scale;
+}
+
+// p[i] = tau * sum_j A22[i][j] v[j], one warp per row of the trailing block
+__global__ void k_symv(const double* __restrict__ A, int m, int k, const double* __restrict__ vbuf,
+                       const double* __restrict__ tau, double* __restrict__ p) {
+  const int n1 = m - k - 1;
+  const double* v = vbuf + (long)k * m + k + 1;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  const double t = tau[k];
+  for (int i = warp; i < n1; i += nw) {
+    const double* row = A + (long)(k + 1 + i) * m + k + 1;
+    double s = 0.0;
+    for (int j = lane; j < n1; j += 32) s += row[j] * v[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) p[i] = t * s;
+  }
+}
+
+// A22 -= v w^T + w v^T with w = p - (tau/2)(p.v) v  (each block recomputes p.v)
+__global__ void k_rank2(double* __restrict__ A, int m, int k, const double* __restrict__ vbuf,
+                        const double* __restrict__ tau, const double* __restrict__ p) {
+  __shared__ double red[32];
+  __shared__ double sg;
+  const int n1 = m - k - 1;
+  const double* v = vbuf + (long)k * m + k + 1;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n1; i += blockDim.x) s += p[i] * v[i];
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) sg = 0.5 * tau[k] * s;
+  __syncthreads();
+  const double g = sg;
+  const long total = (long)n1 * n1;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total;
+       t += (long)gridDim.x * blockDim.x) {
+    const int i = t / n1, j = t % n1;
+    const double wi = p[i] - g * v[i], wj = p[j] - g * v[j];
+    A[(long)(k + 1 + i) * m + k + 1 + j] -= v[i] * wj + wi * v[j];
+  }
+}
+
+__global__ void k_tail(const double* __restrict__ A, int m, double* d, double* e) {
+  if (threadIdx.x != 0) return;
+  if (m >= 2) {
+    d[m - 2] = A[(long)(m - 2) * m + m - 2];
+    e[m - 2] = A[(long)(m - 2) * m + m - 1];
+  }
+  d[m - 1] = A[(long)(m - 1) * m + m - 1];
+  e[m - 1] = 0.0;
+}
+
+// Sturm count: number of eigenvalues of T below x
+__device__ int sturm(const double* __restrict__ d, const double* __restrict__ e2, int m, double x,
+                     double pivmin) {
+  int cnt = 0;
+  double q = d[0] - x;
+  if (fabs(q) < pivmin) q = -pivmin;
+  if (q < 0.0) ++cnt;
+  for (int i = 1; i < m; ++i) {
+    q = d[i] - x - e2[i - 1] / q;
+    if (fabs(q) < pivmin) q = -pivmin;
+    if (q < 0.0) ++cnt;
+  }
+  return cnt;
+}
+
+__global__ void k_e2(const double* __restrict__ e, int m, double* __restrict__ e2) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) e2[i] = (i < m - 1) ? e[i] * e[i] : 0.0;
+}
+
+// j-th smallest eigenvalue by bisection inside the Gershgorin interval [glo, ghi]
+__global__ void k_bisect(const double* __restrict__ d, const double* __restrict__ e,
+                         const double* __restrict__ e2, int m, double glo, double ghi,
+                         double pivmin, double* __restrict__ w) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= m) return;
+  double lo = glo, hi = ghi;
+  for (int it = 0; it < 120; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (sturm(d, e2, m, mid, pivmin) > j) hi = mid; else lo = mid;
+  }
+  w[j] = 0.5 * (lo + hi);
+}
+
+__device__ __forceinline__ double hash_unit(unsigned a, unsigned b) {
+  unsigned h = a * 0x9E3779B1u ^ (b + 0x7F4A7C15u) * 0x85EBCA77u;
+  h ^= h >> 15; h *= 0x2C1B3C6Du; h ^= h >> 12; h *= 0x297A2D39u; h ^= h >> 15;
+  return (double)(h & 0xFFFFFF) / 16777216.0 + 0.5;   // in [0.5, 1.5)
+}
+
+// Inverse iteration for eigenvalue j (thread j).  Scratch arrays are laid out
+// [i][j] so that threads access consecutive addresses.  Z[i][j] = component i of vector j.
+__global__ void k_inviter(const double* __restrict__ d, const double* __restrict__ e,
+                          const double* __restrict__ w, int m, double tnorm,
+                          double* __restrict__ u0, double* __restrict__ u1,
+                          double* __restrict__ u2, double* __restrict__ lm,
+                          double* __restrict__ pv, double* __restrict__ Z) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= m) return;
+  const double lam = w[j];
+  const double tiny = 2.2e-16 * (tnorm > 0 ? tnorm : 1.0);
+#define IX(i) ((long)(i) * m + j)
+  // factor T - lam I = P L U, U with two superdiagonals
+  for (int i = 0; i < m; ++i) {
+    u0[IX(i)] = d[i] - lam;
+    u1[IX(i)] = (i < m - 1) ? e[i] : 0.0;
+    u2[IX(i)] = 0.0;
+  }
+  for (int i = 0; i < m - 1; ++i) {
+    const double c = e[i];          // subdiagonal element of row i+1
+    const double a = u0[IX(i)];
+    if (fabs(a) >= fabs(c)) {
+      const double piv = (a == 0.0) ? tiny : a;
+      u0[IX(i)] = piv;
+      const double l = c / piv;
+      lm[IX(i)] = l;
+      pv[IX(i)] = 0.0;
+      u0[IX(i + 1)] -= l * u1[IX(i)];
+    } else {
+      const double l = a / c;
+      lm[IX(i)] = l;
+      pv[IX(i)] = 1.0;
+      const double b_i = u1[IX(i)];
+      const double a_n = u0[IX(i + 1)], b_n = u1[IX(i + 1)];
+      u0[IX(i)] = c;
+      u1[IX(i)] = a_n;
+      u2[IX(i)] = b_n;
+      u0[IX(i + 1)] = b_i - l * a_n;
+      u1[IX(i + 1)] = -l * b_n;
+    }
+  }
+  if (u0[IX(m - 1)] == 0.0) u0[IX(m - 1)] = tiny;
+  // start vector
+  for (int i = 0; i < m; ++i) Z[IX(i)] = hash_unit(i, j);
+  for (int iter = 0; iter < 3; ++iter) {
+    // apply L^-1 with the row interchanges
+    for (int i = 0; i < m - 1; ++i) {
+      double yi = Z[IX(i)], yn = Z[IX(i + 1)];
+      if (pv[IX(i)] != 0.0) {
+        const double t = yi; yi = yn; yn = t;
+      }
+      Z[IX(i)] = yi;
+      Z[IX(i + 1)] = yn - lm[IX(i)] * yi;
+    }
+    // U^-1 with overflow guard
+    double big = 0.0;
+    for (int i = m - 1; i >= 0; --i) {
+      double x = Z[IX(i)];
+      if (i + 1 < m) x -= u1[IX(i)] * Z[IX(i + 1)];
+      if (i + 2 < m) x -= u2[IX(i)] * Z[IX(i + 2)];
+      double piv = u0[IX(i)];
+      if (fabs(piv) < tiny) piv = copysign(tiny, piv == 0.0 ? 1.0 : piv);
+      x /= piv;
+      Z[IX(i)] = x;
+      big = fmax(big, fabs(x));
+      if (big > 1e100) {  // rescale the partial solution
+        for (int k2 = i; k2 < m; ++k2) Z[IX(k2)] *= 1e-100;
+        big *= 1e-100;
+      }
+    }
+    double nrm = 0.0;
+    for (int i = 0; i < m; ++i) nrm += Z[IX(i)] * Z[IX(i)];
+    nrm = 1.0 / sqrt(nrm);
+    for (int i = 0; i < m; ++i) Z[IX(i)] *= nrm;
+  }
+#undef IX
+}
+
+// Modified Gram-Schmidt inside each cluster of (numerically) equal eigenvalues.
+// One block per eigenvalue index; only cluster starts do work.
+__global__ void k_cluster_mgs(const double* __restrict__ w, int m, double tol,
+                              double* __restrict__ Z) {
+  __shared__ double red[32];
+  __shared__ double sc;
+  const int j0 = blockIdx.x;
+  if (j0 > 0 && w[j0] - w[j0 - 1] <= tol) return;            // not a start
+  if (j0 + 1 >= m || w[j0 + 1] - w[j0] > tol) return;         // singleton
+  int j1 = j0 + 1;
+  while (j1 + 1 < m && w[j1 + 1] - w[j1] <= tol) ++j1;
+  for (int j = j0; j <= j1; ++j) {
+    for (int k = j0; k < j; ++k) {
+      double s = 0.0;
+      for (int i = threadIdx.x; i < m; i += blockDim.x) s += Z[(long)i * m + k] * Z[(long)i * m + j];
+      s = block_sum(s, red);
+      if (threadIdx.x == 0) sc = s;
+      __syncthreads();
+      const double proj = sc;
+      for (int i = threadIdx.x; i < m; i += blockDim.x) Z[(long)i * m + j] -= proj * Z[(long)i * m + k];
+      __syncthreads();
+    }
+    double s = 0.0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) s += Z[(long)i * m + j] * Z[(long)i * m + j];
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) sc = (s > 0.0) ? 1.0 / sqrt(s) : 0.0;
+    __syncthreads();
+    const double nr = sc;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) Z[(long)i * m + j] *= nr;
+    __syncthreads();
+  }
+}
+
+// G = 1.5 I - 0.5 G (in place)
+__global__ void k_ns_coef(double* __restrict__ G, int m) {
+  const long total = (long)m * m;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total;
+       t += (long)gridDim.x * blockDim.x)
+    G[t] = ((t / m == t % m) ? 1.5 : 0.0) - 0.5 * G[t];
+}
+
+// r[c] = sum_i v[i] Z[k+1+i][c]  (one thread per column)
+__global__ void k_vtz(const double* __restrict__ vbuf, int m, int k, const double* __restrict__ Z,
+                      double* __restrict__ r) {
+  const int n1 = m - k - 1;
+  const double* v = vbuf + (long)k * m + k + 1;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int i = 0; i < n1; ++i) s += v[i] * Z[(long)(k + 1 + i) * m + c];
+    r[c] = s;
+  }
+}
+
+// Z[k+1+i][c] -= tau v[i] r[c]
+__global__ void k_zupd(const double* __restrict__ vbuf, int m, int k,
+                       const double* __restrict__ tau, const double* __restrict__ r,
+                       double* __restrict__ Z) {
+  const int n1 = m - k - 1;
+  const double* v = vbuf + (long)k * m + k + 1;
+  const double t = tau[k];
+  const long total = (long)n1 * m;
+  for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < total;
+       q += (long)gridDim.x * blockDim.x) {
+    const int i = q / m, c = q % m;
+    Z[(long)(k + 1 + i) * m + c] -= t * v[i] * r[c];
+  }
+}
+
+size_t sym_eig_tridiag_work(int m) { return (size_t)m * m * 9 + (size_t)m * 8 + 64; }
+
+int sym_eig_tridiag(double* A, int m, double* w, double* V, double* work, cudaStream_t s) {
+  if (m <= 0) return CASPT2_OK;
+  const long mm = (long)m * m;
+  double* vbuf = work;            // m*m reflectors
+  double* Z = vbuf + mm;          // m*m eigenvectors of T
+  double* G = Z + mm;             // m*m Gram / scratch
+  double* u0 = G + mm;            // 5*m*m inverse-iteration scratch
+  double* u1 = u0 + mm;
+  double* u2 = u1 + mm;
+  double* lm = u2 + mm;
+  double* pv = lm + mm;
+  double* d = pv + mm;
+  double* e = d + m;
+  double* e2 = e + m;
+  double* tau = e2 + m;
+  double* p = tau + m;
+  double* r = p + m;
+  // 1. tridiagonalise
+  for (int k = 0; k + 2 < m; ++k) {
+    const int n1 = m - k - 1;
+    ++launch_counter();
+    k_house<<<1, 256, 0, s>>>(A, m, k, vbuf, tau, d, e);
+    ++launch_counter();
+    k_symv<<<std::max(1, std::min((n1 + 7) / 8, 152 * 8)), 256, 0, s>>>(A, m, k, vbuf, tau, p);
+    ++launch_counter();
+    k_rank2<<<nblocks((long)n1 * n1), kT, 0, s>>>(A, m, k, vbuf, tau, p);
+  }
+  ++launch_counter();
+  k_tail<<<1, 32, 0, s>>>(A, m, d, e);
+  CASPT2_CUDA_TRY(cudaGetLastError());
+  // Gershgorin interval and pivmin on the host (small vectors)
+  std::vector<double> hd(m), he(m);
+  CASPT2_CUDA_TRY(cudaMemcpyAsync(hd.data(), d, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
+  CASPT2_CUDA_TRY(cudaMemcpyAsync(he.data(), e, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
+  CASPT2_CUDA_TRY(cudaStreamSynchronize(s));
+  double glo = 1e300, ghi = -1e300, emax2 = 0.0, tnorm = 0.0;
+  for (int i = 0; i < m; ++i) {
+    const double r0 = (i > 0 ? fabs(he[i - 1]) : 0.0) + (i < m - 1 ? fabs(he[i]) : 0.0);
+    glo = std::min(glo, hd[i] - r0);
+    ghi = std::max(ghi, hd[i] + r0);
+    if (i < m - 1) emax2 = std::max(emax2, he[i] * he[i]);
+    tnorm = std::max(tnorm, fabs(hd[i]) + r0);
+    if (!(hd[i] == hd[i]) || !(he[i] == he[i])) return CASPT2_ENAN;
+  }
+  const double pad = 2.2e-16 * std::max(1.0, tnorm) * 4.0 + 1e-300;
+  glo -= pad;
+  ghi += pad;
+  const double pivmin = std::max(1e-300, 1e-290 * std::max(1.0, emax2));
+  // 2. eigenvalues
+  ++launch_counter();
+  k_e2<<<(m + 255) / 256, 256, 0, s>>>(e, m, e2);
+  ++launch_counter();
+  k_bisect<<<(m + 127) / 128, 128, 0, s>>>(d, e, e2, m, glo, ghi, pivmin, w);
+  // 3. eigenvectors of T
+  ++launch_counter();
+  k_inviter<<<(m + 127) / 128, 128, 0, s>>>(d, e, w, m, tnorm, u0, u1, u2, lm, pv, Z);
+  ++launch_counter();
+  k_cluster_mgs<<<m, 256, 0, s>>>(w, m, 1e-12 * std::max(1.0, tnorm), Z);
+  CASPT2_CUDA_TRY(cudaGetLastError());
+  // 4. Newton-Schulz: Z <- Z (1.5 I - 0.5 Z^T Z)
+  CASPT2_CUDA_TRY(dgemm(m, m, m, 1.0, Z, m, true, Z, m, false, 0.0, G, m, s));
+  ++launch_counter();
+  k_ns_coef<<<nblocks(mm), kT, 0, s>>>(G, m);
+  CASPT2_CUDA_TRY(dgemm(m, m, m, 1.0, Z, m, false, G, m, false, 0.0, V, m, s));
+  // 5. back-transformation V = H_0 ... H_{m-3} Z
+  for (int k = m - 3; k >= 0; --k) {
+    ++launch_counter();
+    k_vtz<<<(m + 127) / 128, 128, 0, s>>>(vbuf, m, k, V, r);
+    ++launch_counter();
+    k_zupd<<<nblocks((long)(m - k - 1) * m), kT, 0, s>>>(vbuf, m, k, tau, r, V);
+  }
+  CASPT2_CUDA_TRY(cudaGetLastError());
+  return CASPT2_OK;
+}
+
+}  // namespace caspt2

@@ -180,8 +180,19 @@ __global__ void k_diag_out(const double* __restrict__ A, int m, double* w) {
   if (i < m) w[i] = A[(long)i * m + i];
 }
 
+// Sort eigenpairs ascending (one block; rank by counting, ties by index): w2, V2 from w, V.
+__global__ void k_sort_pairs(const double* __restrict__ w, const double* __restrict__ V, int m,
+                             double* __restrict__ w2, double* __restrict__ V2) {
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    int r = 0;
+    for (int k = 0; k < m; ++k) r += (w[k] < w[j] || (w[k] == w[j] && k < j)) ? 1 : 0;
+    w2[r] = w[j];
+    for (int i = 0; i < m; ++i) V2[(long)i * m + r] = V[(long)i * m + j];
+  }
+}
+
 // Eigenpairs of symmetric A (m x m, row-major, overwritten): w[m], V[m][m] (columns).
-// work: 2*m*m doubles + 2.  Unsorted.  Synchronises the stream once per sweep.
+// work: 2*m*m doubles + 2.  Ascending.  Synchronises the stream once per sweep.
 int sym_eig_jacobi(double* A, int m, double* w, double* V, double* work, cudaStream_t s) {
   if (m <= 0) return CASPT2_OK;
   double* A2 = work;
@@ -226,8 +237,12 @@ int sym_eig_jacobi(double* A, int m, double* w, double* V, double* work, cudaStr
     CASPT2_CUDA_TRY(cudaMemcpyAsync(A, cur, sizeof(double) * m * m, cudaMemcpyDeviceToDevice, s));
     CASPT2_CUDA_TRY(cudaMemcpyAsync(V, vc, sizeof(double) * m * m, cudaMemcpyDeviceToDevice, s));
   }
+  // eigenvalues into A2's first row, sorted pairs back into w and V
   ++launch_counter();
-  k_diag_out<<<(m + 127) / 128, 128, 0, s>>>(A, m, w);
+  k_diag_out<<<(m + 127) / 128, 128, 0, s>>>(A, m, A2);
+  CASPT2_CUDA_TRY(cudaMemcpyAsync(V2, V, sizeof(double) * m * m, cudaMemcpyDeviceToDevice, s));
+  ++launch_counter();
+  k_sort_pairs<<<1, 256, 0, s>>>(A2, V2, m, w, V);
   CASPT2_CUDA_TRY(cudaGetLastError());
   return conv ? CASPT2_OK : CASPT2_ENOTCONV;
 }

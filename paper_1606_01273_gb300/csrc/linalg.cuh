@@ -13,9 +13,23 @@ cudaError_t dgemm(int M, int N, int K, double alpha, const double* A, int lda, b
                   cudaStream_t s, int batch = 1, long sA = 0, long sB = 0, long sC = 0);
 
 // Eigenpairs of a symmetric m x m matrix by parallel cyclic Jacobi.  A is destroyed
-// (left holding the diagonalised matrix); w[m] eigenvalues (unsorted), V[m][m] with
+// (left holding the diagonalised matrix); w[m] eigenvalues (ascending), V[m][m] with
 // eigenvectors as columns; work >= 2*m*m + 2 doubles.  Returns CASPT2_OK, ENOTCONV,
 // ENAN or ECUDA.  Synchronises the stream once per sweep.
 int sym_eig_jacobi(double* A, int m, double* w, double* V, double* work, cudaStream_t s);
+
+// Eigenpairs of a symmetric m x m matrix by Householder tridiagonalisation, bisection,
+// inverse iteration and back-transformation (eig_tridiag.cu).  A is destroyed; w[m]
+// ascending; V[m][m] eigenvectors as columns.  work >= sym_eig_tridiag_work(m) doubles.
+size_t sym_eig_tridiag_work(int m);
+int sym_eig_tridiag(double* A, int m, double* w, double* V, double* work, cudaStream_t s);
+
+// Dispatch: Jacobi for small matrices, tridiagonal method otherwise.
+inline int sym_eig(double* A, int m, double* w, double* V, double* work, cudaStream_t s) {
+  return m <= 32 ? sym_eig_jacobi(A, m, w, V, work, s) : sym_eig_tridiag(A, m, w, V, work, s);
+}
+inline size_t sym_eig_work(int m) {
+  return std::max<size_t>((size_t)2 * m * m + 2, sym_eig_tridiag_work(m));
+}
 
 }  // namespace caspt2
