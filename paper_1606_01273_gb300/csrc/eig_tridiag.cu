@@ -101,6 +101,109 @@ __global__ void k_rank2(double* __restrict__ A, int m, int k, const double* __re
   }
 }
 
+// Grid-wide barrier for a cooperative launch, bounded: after kSpinLimit polls it sets
+// *err and returns false so that every block can leave the kernel.
+constexpr long kSpinLimit = 1L << 24;
+
+__device__ bool grid_sync_bounded(unsigned* count, volatile unsigned* gen, int* err) {
+  __syncthreads();
+  __shared__ int ok;
+  if (threadIdx.x == 0) {
+    const unsigned g = *gen;
+    __threadfence();
+    if (atomicAdd(count, 1u) == gridDim.x - 1) {
+      *count = 0;
+      __threadfence();
+      atomicAdd((unsigned*)gen, 1u);
+      ok = 1;
+    } else {
+      long it = 0;
+      while (*gen == g && *(volatile int*)err == 0) {
+        if (++it > kSpinLimit) {
+          atomicExch(err, 1);
+          break;
+        }
+        __nanosleep(64);
+      }
+      ok = (*(volatile int*)err == 0);
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// Householder reduction in one cooperative launch.  Per step k: (block 0) reflector of
+// row k, barrier, p = tau A22 v by warps over rows, barrier, A22 -= v w^T + w v^T,
+// barrier.  sync[0..1] barrier state (zeroed by the host), sync[2] error flag.
+__global__ void __launch_bounds__(512)
+k_tridiag(double* __restrict__ A, int m, double* __restrict__ vbuf, double* __restrict__ tau,
+          double* __restrict__ d, double* __restrict__ e, double* __restrict__ p,
+          unsigned* sync) {
+  __shared__ double red[32];
+  __shared__ double sh[2];
+  int* err = reinterpret_cast<int*>(sync + 2);
+  for (int k = 0; k + 2 < m; ++k) {
+    const int n1 = m - k - 1;
+    double* v = vbuf + (long)k * m + k + 1;
+    if (blockIdx.x == 0) {
+      const double* x = A + (long)k * m + k + 1;
+      double s = 0.0;
+      for (int i = 1 + threadIdx.x; i < n1; i += blockDim.x) s += __ldcg(x + i) * __ldcg(x + i);
+      s = block_sum(s, red);
+      if (threadIdx.x == 0) {
+        const double alpha = __ldcg(x);
+        double beta, t, scale;
+        if (s == 0.0) { beta = alpha; t = 0.0; scale = 0.0; }
+        else {
+          beta = -copysign(sqrt(alpha * alpha + s), alpha);
+          t = (beta - alpha) / beta;
+          scale = 1.0 / (alpha - beta);
+        }
+        sh[0] = t;
+        sh[1] = scale;
+        tau[k] = t;
+        d[k] = __ldcg(A + (long)k * m + k);
+        e[k] = beta;
+      }
+      __syncthreads();
+      const double scale = sh[1];
+      for (int i = threadIdx.x; i < n1; i += blockDim.x) v[i] = (i == 0) ? 1.0 : __ldcg(x + i) * scale;
+    }
+    if (!grid_sync_bounded(sync, sync + 1, err)) return;
+    const double t = __ldcg(tau + k);
+    {
+      const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+      const int nw = (gridDim.x * blockDim.x) >> 5;
+      for (int i = warp; i < n1; i += nw) {
+        const double* row = A + (long)(k + 1 + i) * m + k + 1;
+        double s = 0.0;
+        for (int j = lane; j < n1; j += 32) s += __ldcg(row + j) * __ldcg(v + j);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) p[i] = t * s;
+      }
+    }
+    if (!grid_sync_bounded(sync, sync + 1, err)) return;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n1; i += blockDim.x) s += __ldcg(p + i) * __ldcg(v + i);
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) sh[0] = 0.5 * t * s;
+    __syncthreads();
+    const double g = sh[0];
+    const long total = (long)n1 * n1;
+    for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < total;
+         q += (long)gridDim.x * blockDim.x) {
+      const int i = q / n1, j = q % n1;
+      const double vi = __ldcg(v + i), vj = __ldcg(v + j);
+      const double wi = __ldcg(p + i) - g * vi, wj = __ldcg(p + j) - g * vj;
+      double* a = A + (long)(k + 1 + i) * m + k + 1 + j;
+      *a = __ldcg(a) - (vi * wj + wi * vj);
+    }
+    if (!grid_sync_bounded(sync, sync + 1, err)) return;
+  }
+}
+
 __global__ void k_tail(const double* __restrict__ A, int m, double* d, double* e) {
   if (threadIdx.x != 0) return;
   if (m >= 2) {
@@ -131,19 +234,30 @@ __global__ void k_e2(const double* __restrict__ e, int m, double* __restrict__ e
   if (i < m) e2[i] = (i < m - 1) ? e[i] * e[i] : 0.0;
 }
 
-// j-th smallest eigenvalue by bisection inside the Gershgorin interval [glo, ghi]
+// j-th smallest eigenvalue by multisection inside the Gershgorin interval [glo, ghi]:
+// one warp per eigenvalue, each lane evaluates the Sturm count at one of 31 interior
+// points, so every iteration shrinks the bracket 32-fold.
 __global__ void k_bisect(const double* __restrict__ d, const double* __restrict__ e,
                          const double* __restrict__ e2, int m, double glo, double ghi,
                          double pivmin, double* __restrict__ w) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (j >= m) return;
   double lo = glo, hi = ghi;
-  for (int it = 0; it < 120; ++it) {
-    const double mid = 0.5 * (lo + hi);
-    if (mid <= lo || mid >= hi) break;
-    if (sturm(d, e2, m, mid, pivmin) > j) hi = mid; else lo = mid;
+  for (int it = 0; it < 40; ++it) {
+    const double h = (hi - lo) / 32.0;
+    const double x = lo + h * (lane + 1);          // lane 31 -> hi (not evaluated)
+    const bool above = (lane < 31) && (x > lo) && (x < hi) && (sturm(d, e2, m, x, pivmin) > j);
+    const unsigned mask = __ballot_sync(0xffffffffu, above);
+    // points with count > j form a suffix; the first one is the new upper bound
+    const int first = mask ? (__ffs(mask) - 1) : 31;
+    const double nhi = (first < 31) ? lo + h * (first + 1) : hi;
+    const double nlo = (first > 0) ? lo + h * first : lo;
+    if (!(nhi < hi || nlo > lo)) break;            // no progress: bracket at rounding level
+    lo = nlo;
+    hi = nhi;
   }
-  w[j] = 0.5 * (lo + hi);
+  if (lane == 0) w[j] = 0.5 * (lo + hi);
 }
 
 __device__ __forceinline__ double hash_unit(unsigned a, unsigned b) {
@@ -271,15 +385,61 @@ __global__ void k_ns_coef(double* __restrict__ G, int m) {
     G[t] = ((t / m == t % m) ? 1.5 : 0.0) - 0.5 * G[t];
 }
 
-// r[c] = sum_i v[i] Z[k+1+i][c]  (one thread per column)
-__global__ void k_vtz(const double* __restrict__ vbuf, int m, int k, const double* __restrict__ Z,
-                      double* __restrict__ r) {
+// r[c] = sum_i v[i] Z[k+1+i][c]: 32 columns x 8 row groups per block (coalesced rows),
+// fixed-order reduction over the row groups in shared memory.
+__global__ void __launch_bounds__(256)
+k_vtz(const double* __restrict__ vbuf, int m, int k, const double* __restrict__ Z,
+      double* __restrict__ r) {
+  __shared__ double part[8][33];
   const int n1 = m - k - 1;
   const double* v = vbuf + (long)k * m + k + 1;
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) {
+  const int cx = threadIdx.x & 31, ry = threadIdx.x >> 5;
+  const int c = blockIdx.x * 32 + cx;
+  double s = 0.0;
+  if (c < m) {
+#pragma unroll 4
+    for (int i = ry; i < n1; i += 8) s += v[i] * Z[(long)(k + 1 + i) * m + c];
+  }
+  part[ry][cx] = s;
+  __syncthreads();
+  if (ry == 0 && c < m) {
+    double t = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) t += part[q][cx];
+    r[c] = t;
+  }
+}
+
+// Back-transformation V = H_0 ... H_{m-3} Z with each block owning 8 columns: for every
+// reflector (in reverse order) the block forms r_c = v . Z[k+1.., c] for its columns and
+// applies Z[k+1+i][c] -= tau v_i r_c.  Columns are independent, so no grid-wide
+// synchronisation is needed.
+__global__ void __launch_bounds__(256)
+k_backtransform(const double* __restrict__ vbuf, const double* __restrict__ tau, int m,
+                double* __restrict__ Z) {
+  __shared__ double part[32][9];
+  __shared__ double rc[8];
+  const int cx = threadIdx.x & 7, ry = threadIdx.x >> 3;       // 8 columns x 32 row groups
+  const int c = blockIdx.x * 8 + cx;
+  for (int k = m - 3; k >= 0; --k) {
+    const int n1 = m - k - 1;
+    const double* v = vbuf + (long)k * m + k + 1;
     double s = 0.0;
-    for (int i = 0; i < n1; ++i) s += v[i] * Z[(long)(k + 1 + i) * m + c];
-    r[c] = s;
+    if (c < m)
+      for (int i = ry; i < n1; i += 32) s += v[i] * Z[(long)(k + 1 + i) * m + c];
+    part[ry][cx] = s;
+    __syncthreads();
+    if (threadIdx.x < 8) {
+      double t = 0.0;
+      for (int q = 0; q < 32; ++q) t += part[q][threadIdx.x];
+      rc[threadIdx.x] = t * tau[k];
+    }
+    __syncthreads();
+    if (c < m) {
+      const double r = rc[cx];
+      for (int i = ry; i < n1; i += 32) Z[(long)(k + 1 + i) * m + c] -= v[i] * r;
+    }
+    __syncthreads();
   }
 }
 
@@ -317,15 +477,32 @@ int sym_eig_tridiag(double* A, int m, double* w, double* V, double* work, cudaSt
   double* tau = e2 + m;
   double* p = tau + m;
   double* r = p + m;
-  // 1. tridiagonalise
-  for (int k = 0; k + 2 < m; ++k) {
-    const int n1 = m - k - 1;
+  // 1. tridiagonalise (one cooperative launch for large matrices)
+  if (m > 64) {
+    int dev = 0, nsm = 0, per = 0;
+    CASPT2_CUDA_TRY(cudaGetDevice(&dev));
+    CASPT2_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    CASPT2_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_tridiag, 512, 0));
+    const int grid = std::max(1, std::min(nsm * std::max(per, 1), nsm));
+    unsigned* sync = reinterpret_cast<unsigned*>(r);   // r is free until the back-transform
+    CASPT2_CUDA_TRY(cudaMemsetAsync(sync, 0, 4 * sizeof(unsigned), s));
+    void* args[] = {&A, (void*)&m, &vbuf, &tau, &d, &e, &p, &sync};
     ++launch_counter();
-    k_house<<<1, 256, 0, s>>>(A, m, k, vbuf, tau, d, e);
-    ++launch_counter();
-    k_symv<<<std::max(1, std::min((n1 + 7) / 8, 152 * 8)), 256, 0, s>>>(A, m, k, vbuf, tau, p);
-    ++launch_counter();
-    k_rank2<<<nblocks((long)n1 * n1), kT, 0, s>>>(A, m, k, vbuf, tau, p);
+    CASPT2_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_tridiag, grid, 512, args, 0, s));
+    int herr = 0;
+    CASPT2_CUDA_TRY(cudaMemcpyAsync(&herr, sync + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CASPT2_CUDA_TRY(cudaStreamSynchronize(s));
+    if (herr != 0) return CASPT2_ETIMEOUT;
+  } else {
+    for (int k = 0; k + 2 < m; ++k) {
+      const int n1 = m - k - 1;
+      ++launch_counter();
+      k_house<<<1, 256, 0, s>>>(A, m, k, vbuf, tau, d, e);
+      ++launch_counter();
+      k_symv<<<std::max(1, std::min((n1 + 7) / 8, 152 * 8)), 256, 0, s>>>(A, m, k, vbuf, tau, p);
+      ++launch_counter();
+      k_rank2<<<nblocks((long)n1 * n1), kT, 0, s>>>(A, m, k, vbuf, tau, p);
+    }
   }
   ++launch_counter();
   k_tail<<<1, 32, 0, s>>>(A, m, d, e);
@@ -352,7 +529,7 @@ int sym_eig_tridiag(double* A, int m, double* w, double* V, double* work, cudaSt
   ++launch_counter();
   k_e2<<<(m + 255) / 256, 256, 0, s>>>(e, m, e2);
   ++launch_counter();
-  k_bisect<<<(m + 127) / 128, 128, 0, s>>>(d, e, e2, m, glo, ghi, pivmin, w);
+  k_bisect<<<(m * 32 + 255) / 256, 256, 0, s>>>(d, e, e2, m, glo, ghi, pivmin, w);
   // 3. eigenvectors of T
   ++launch_counter();
   k_inviter<<<(m + 127) / 128, 128, 0, s>>>(d, e, w, m, tnorm, u0, u1, u2, lm, pv, Z);
@@ -364,12 +541,10 @@ int sym_eig_tridiag(double* A, int m, double* w, double* V, double* work, cudaSt
   ++launch_counter();
   k_ns_coef<<<nblocks(mm), kT, 0, s>>>(G, m);
   CASPT2_CUDA_TRY(dgemm(m, m, m, 1.0, Z, m, false, G, m, false, 0.0, V, m, s));
-  // 5. back-transformation V = H_0 ... H_{m-3} Z
-  for (int k = m - 3; k >= 0; --k) {
+  // 5. back-transformation V = H_0 ... H_{m-3} Z (column-owned, one launch)
+  if (m >= 3) {
     ++launch_counter();
-    k_vtz<<<(m + 127) / 128, 128, 0, s>>>(vbuf, m, k, V, r);
-    ++launch_counter();
-    k_zupd<<<nblocks((long)(m - k - 1) * m), kT, 0, s>>>(vbuf, m, k, tau, r, V);
+    k_backtransform<<<(m + 7) / 8, 256, 0, s>>>(vbuf, tau, m, V);
   }
   CASPT2_CUDA_TRY(cudaGetLastError());
   return CASPT2_OK;
