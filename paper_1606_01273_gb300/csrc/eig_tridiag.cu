@@ -133,9 +133,41 @@ __device__ bool grid_sync_bounded(unsigned* count, volatile unsigned* gen, int* 
   return ok != 0;
 }
 
-// Householder reduction in one cooperative launch.  Per step k: (block 0) reflector of
-// row k, barrier, p = tau A22 v by warps over rows, barrier, A22 -= v w^T + w v^T,
-// barrier.  sync[0..1] barrier state (zeroed by the host), sync[2] error flag.
+// Reflector of row k from its trailing part (one block): tau, d[k], e[k] = beta, v.
+__device__ void house_row(double* __restrict__ A, int m, int k, double* __restrict__ vbuf,
+                          double* __restrict__ tau, double* __restrict__ d,
+                          double* __restrict__ e, double* red, double* sh) {
+  const int n1 = m - k - 1;
+  const double* x = A + (long)k * m + k + 1;
+  double s = 0.0;
+  for (int i = 1 + threadIdx.x; i < n1; i += blockDim.x) s += __ldcg(x + i) * __ldcg(x + i);
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) {
+    const double alpha = __ldcg(x);
+    double beta, t, scale;
+    if (s == 0.0) { beta = alpha; t = 0.0; scale = 0.0; }
+    else {
+      beta = -copysign(sqrt(alpha * alpha + s), alpha);
+      t = (beta - alpha) / beta;
+      scale = 1.0 / (alpha - beta);
+    }
+    sh[1] = scale;
+    tau[k] = t;
+    d[k] = __ldcg(A + (long)k * m + k);
+    e[k] = beta;
+  }
+  __syncthreads();
+  const double scale = sh[1];
+  double* v = vbuf + (long)k * m + k + 1;
+  for (int i = threadIdx.x; i < n1; i += blockDim.x) v[i] = (i == 0) ? 1.0 : __ldcg(x + i) * scale;
+  __syncthreads();
+}
+
+// Householder reduction in one cooperative launch, two bounded grid barriers per step:
+//   p = tau A22 v (warps over rows)                              | barrier
+//   A22 -= v w^T + w v^T; block 0 then forms the next reflector   | barrier
+// from row k+1, which its warp 0 has just finished updating.
+// sync[0..1] barrier state (zeroed by the host), sync[2] error flag.
 __global__ void __launch_bounds__(512)
 k_tridiag(double* __restrict__ A, int m, double* __restrict__ vbuf, double* __restrict__ tau,
           double* __restrict__ d, double* __restrict__ e, double* __restrict__ p,
@@ -143,46 +175,21 @@ k_tridiag(double* __restrict__ A, int m, double* __restrict__ vbuf, double* __re
   __shared__ double red[32];
   __shared__ double sh[2];
   int* err = reinterpret_cast<int*>(sync + 2);
+  if (blockIdx.x == 0) house_row(A, m, 0, vbuf, tau, d, e, red, sh);
+  if (!grid_sync_bounded(sync, sync + 1, err)) return;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
   for (int k = 0; k + 2 < m; ++k) {
     const int n1 = m - k - 1;
-    double* v = vbuf + (long)k * m + k + 1;
-    if (blockIdx.x == 0) {
-      const double* x = A + (long)k * m + k + 1;
-      double s = 0.0;
-      for (int i = 1 + threadIdx.x; i < n1; i += blockDim.x) s += __ldcg(x + i) * __ldcg(x + i);
-      s = block_sum(s, red);
-      if (threadIdx.x == 0) {
-        const double alpha = __ldcg(x);
-        double beta, t, scale;
-        if (s == 0.0) { beta = alpha; t = 0.0; scale = 0.0; }
-        else {
-          beta = -copysign(sqrt(alpha * alpha + s), alpha);
-          t = (beta - alpha) / beta;
-          scale = 1.0 / (alpha - beta);
-        }
-        sh[0] = t;
-        sh[1] = scale;
-        tau[k] = t;
-        d[k] = __ldcg(A + (long)k * m + k);
-        e[k] = beta;
-      }
-      __syncthreads();
-      const double scale = sh[1];
-      for (int i = threadIdx.x; i < n1; i += blockDim.x) v[i] = (i == 0) ? 1.0 : __ldcg(x + i) * scale;
-    }
-    if (!grid_sync_bounded(sync, sync + 1, err)) return;
+    const double* v = vbuf + (long)k * m + k + 1;
     const double t = __ldcg(tau + k);
-    {
-      const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-      const int nw = (gridDim.x * blockDim.x) >> 5;
-      for (int i = warp; i < n1; i += nw) {
-        const double* row = A + (long)(k + 1 + i) * m + k + 1;
-        double s = 0.0;
-        for (int j = lane; j < n1; j += 32) s += __ldcg(row + j) * __ldcg(v + j);
+    for (int i = warp; i < n1; i += nw) {
+      const double* row = A + (long)(k + 1 + i) * m + k + 1;
+      double s = 0.0;
+      for (int j = lane; j < n1; j += 32) s += __ldcg(row + j) * __ldcg(v + j);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-        if (lane == 0) p[i] = t * s;
-      }
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+      if (lane == 0) p[i] = t * s;
     }
     if (!grid_sync_bounded(sync, sync + 1, err)) return;
     double s = 0.0;
@@ -191,14 +198,17 @@ k_tridiag(double* __restrict__ A, int m, double* __restrict__ vbuf, double* __re
     if (threadIdx.x == 0) sh[0] = 0.5 * t * s;
     __syncthreads();
     const double g = sh[0];
-    const long total = (long)n1 * n1;
-    for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < total;
-         q += (long)gridDim.x * blockDim.x) {
-      const int i = q / n1, j = q % n1;
-      const double vi = __ldcg(v + i), vj = __ldcg(v + j);
-      const double wi = __ldcg(p + i) - g * vi, wj = __ldcg(p + j) - g * vj;
-      double* a = A + (long)(k + 1 + i) * m + k + 1 + j;
-      *a = __ldcg(a) - (vi * wj + wi * vj);
+    for (int i = warp; i < n1; i += nw) {
+      const double vi = __ldcg(v + i), wi = __ldcg(p + i) - g * vi;
+      double* row = A + (long)(k + 1 + i) * m + k + 1;
+      for (int j = lane; j < n1; j += 32) {
+        const double vj = __ldcg(v + j), wj = __ldcg(p + j) - g * vj;
+        row[j] = __ldcg(row + j) - (vi * wj + wi * vj);
+      }
+    }
+    if (blockIdx.x == 0 && k + 3 < m) {
+      __syncthreads();
+      house_row(A, m, k + 1, vbuf, tau, d, e, red, sh);
     }
     if (!grid_sync_bounded(sync, sync + 1, err)) return;
   }
@@ -234,30 +244,54 @@ __global__ void k_e2(const double* __restrict__ e, int m, double* __restrict__ e
   if (i < m) e2[i] = (i < m - 1) ? e[i] * e[i] : 0.0;
 }
 
-// j-th smallest eigenvalue by multisection inside the Gershgorin interval [glo, ghi]:
-// one warp per eigenvalue, each lane evaluates the Sturm count at one of 31 interior
-// points, so every iteration shrinks the bracket 32-fold.
+// Number of eigenvalues of T below x from the sign changes of the leading principal
+// minors p_i = (d_i - x) p_{i-1} - e_{i-1}^2 p_{i-2} (p_{-1} = 1): two multiply-adds per
+// step and no division; the pair (p_i, p_{i-1}) is rescaled by powers of two to stay in
+// range, and an exact zero takes the sign opposite to its predecessor.
+__device__ int sturm_nodiv(const double* __restrict__ d, const double* __restrict__ e2, int m,
+                           double x) {
+  double pm = 1.0, pc = d[0] - x;
+  if (pc == 0.0) pc = -1e-300;
+  int cnt = pc < 0.0 ? 1 : 0;
+  for (int i = 1; i < m; ++i) {
+    double pn = (d[i] - x) * pc - e2[i - 1] * pm;
+    if (pn == 0.0) pn = pc > 0.0 ? -1e-300 : 1e-300;
+    cnt += ((pn < 0.0) != (pc < 0.0)) ? 1 : 0;
+    pm = pc;
+    pc = pn;
+    const double a = fabs(pc);
+    if (a > 1e150) { pc *= 0x1p-500; pm *= 0x1p-500; }
+    else if (a < 1e-150 && fabs(pm) < 1e-150) { pc *= 0x1p500; pm *= 0x1p500; }
+  }
+  return cnt;
+}
+
+// j-th smallest eigenvalue by 4-way multisection inside the Gershgorin interval: four
+// lanes per eigenvalue evaluate the Sturm count at the three interior quarter points
+// (lane 3 idles), so each step removes two bits; stop at an absolute width of tol.
 __global__ void k_bisect(const double* __restrict__ d, const double* __restrict__ e,
-                         const double* __restrict__ e2, int m, double glo, double ghi,
-                         double pivmin, double* __restrict__ w) {
-  const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (j >= m) return;
+                         const double* __restrict__ e2, int m, double glo, double ghi, double tol,
+                         double* __restrict__ w) {
+  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = gid >> 2, q = gid & 3;
+  const unsigned grp = 0xFu << (threadIdx.x & 28);
+  if ((gid & ~3) >= ((m + 0) << 2)) return;          // whole group beyond m
+  const bool live = j < m;
   double lo = glo, hi = ghi;
-  for (int it = 0; it < 40; ++it) {
-    const double h = (hi - lo) / 32.0;
-    const double x = lo + h * (lane + 1);          // lane 31 -> hi (not evaluated)
-    const bool above = (lane < 31) && (x > lo) && (x < hi) && (sturm(d, e2, m, x, pivmin) > j);
-    const unsigned mask = __ballot_sync(0xffffffffu, above);
-    // points with count > j form a suffix; the first one is the new upper bound
-    const int first = mask ? (__ffs(mask) - 1) : 31;
-    const double nhi = (first < 31) ? lo + h * (first + 1) : hi;
-    const double nlo = (first > 0) ? lo + h * first : lo;
-    if (!(nhi < hi || nlo > lo)) break;            // no progress: bracket at rounding level
+  for (int it = 0; it < 80; ++it) {
+    if (hi - lo <= tol) break;
+    const double h = 0.25 * (hi - lo);
+    const double x = lo + h * (q + 1);
+    const bool above = live && q < 3 && x > lo && x < hi && sturm_nodiv(d, e2, m, x) > j;
+    const unsigned b = (__ballot_sync(grp, above) >> (threadIdx.x & 28)) & 0x7u;
+    const int first = b ? (__ffs(b) - 1) : 3;           // first quarter point above j
+    const double nhi = first < 3 ? lo + h * (first + 1) : hi;
+    const double nlo = first > 0 ? lo + h * first : lo;
+    if (!(nhi < hi || nlo > lo)) break;
     lo = nlo;
     hi = nhi;
   }
-  if (lane == 0) w[j] = 0.5 * (lo + hi);
+  if (live && q == 0) w[j] = 0.5 * (lo + hi);
 }
 
 __device__ __forceinline__ double hash_unit(unsigned a, unsigned b) {
@@ -529,7 +563,8 @@ int sym_eig_tridiag(double* A, int m, double* w, double* V, double* work, cudaSt
   ++launch_counter();
   k_e2<<<(m + 255) / 256, 256, 0, s>>>(e, m, e2);
   ++launch_counter();
-  k_bisect<<<(m * 32 + 255) / 256, 256, 0, s>>>(d, e, e2, m, glo, ghi, pivmin, w);
+  k_bisect<<<(4 * m + 31) / 32, 32, 0, s>>>(d, e, e2, m, glo, ghi,
+                                            4.0 * 2.2e-16 * std::max(1.0, tnorm), w);
   // 3. eigenvectors of T
   ++launch_counter();
   k_inviter<<<(m + 127) / 128, 128, 0, s>>>(d, e, w, m, tnorm, u0, u1, u2, lm, pv, Z);
