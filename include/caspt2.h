@@ -107,6 +107,14 @@ int caspt2_get_energies(caspt2_ctx* ctx, double* U, double* E0, double* Href, do
  * Either pointer may be NULL.  Errors: EINVAL (class not enabled / out of range). */
 int caspt2_get_class_energy(caspt2_ctx* ctx, int cls, double* e, double* norm);
 
+/* lambda of the last solve for target state P = opt.target_state (the Lagrange multipliers
+ * of Eq. lambdaeq, solution of the lambda equation obtained by differentiating the
+ * Lagrangian with respect to T), per class, in gauge-invariant form:
+ *   NL[L]     = <lambda_L|T_L> in the overlap metric (the class's share of N_L, Sec. II.D)
+ *   lv[L][L'] = <Psi_lambda_L|H|L'~>, Psi_lambda_L = sum_N lambda_LN |N~>
+ * Either pointer may be NULL.  Errors: EINVAL (class not enabled, or target_state < 0). */
+int caspt2_get_class_lambda(caspt2_ctx* ctx, int cls, double* NL, double* lv);
+
 /* Core energy E_core = <core|H|core> (closed orbitals doubly occupied) of the last solve. */
 int caspt2_get_core_energy(caspt2_ctx* ctx, double* ecore);
 

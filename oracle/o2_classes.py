@@ -225,16 +225,50 @@ def all_classes(prob, st, shift=0.0, scheme="msmr", thresh=1e-9):
     return out
 
 
+def all_moments(prob, st, shift=0.0, scheme="msmr", thresh=1e-9):
+    """{class: (M1, M2, M3)} for all eight classes."""
+    from .o2_rdm import class_h_moments
+    out = {cls: class_moments(prob, st, cls, shift, scheme, thresh) for cls in "ABCDEFG"}
+    out["H"] = class_h_moments(prob, st, shift=shift, scheme=scheme)
+    return out
+
+
 def class_energy(prob, st, cls, shift=0.0, scheme="msmr", thresh=1e-9, h=None):
-    """Per-class pieces e[L, L'] = <Psi1_L|H|L'~>_X and norm[L] = <Psi1_L|Psi1_L>_X for
-    block-diagonal f, from the rotated RDMs of `st` (an o2_rdm.Setup with kmax >= 4)."""
+    """(e, norm) of a class; see class_moments for the definitions."""
+    M1, M2, M3 = class_moments(prob, st, cls, shift, scheme, thresh, h)
+    n = prob.nstate
+    e = -np.array([[M1[L, L, Lp] for Lp in range(n)] for L in range(n)])
+    nr = np.array([M2[L, L] for L in range(n)])
+    return e, nr
+
+
+def lambda_pieces(M1, M2, M3, R, P, shift):
+    """lambda of the Lagrangian (Eq. lambdaeq differentiated with respect to T) in each
+    sector's orthonormal basis: lam_L = -[R_LP sum_N R_NP Vt_N - 2 E_s R_LP^2 amp_L] / D_L
+    with amp_L = -Vt_L / D_L.  Returns NL[L] = <lam_L|S|T_L> and
+    lv[L, L'] = <Psi_lam_L|H|L'~> of the class."""
+    n = R.shape[0]
+    r = R[:, P]
+    NL = np.array([r[L] * np.sum(r * M2[L]) + 2.0 * shift * r[L] ** 2 * M3[L] for L in range(n)])
+    lv = np.array([[-r[L] * np.sum(r * M1[L, :, Lp]) - 2.0 * shift * r[L] ** 2 * M2[L, Lp]
+                    for Lp in range(n)] for L in range(n)])
+    return NL, lv
+
+
+def class_moments(prob, st, cls, shift=0.0, scheme="msmr", thresh=1e-9, h=None):
+    """Moment sums over the external tuples and sector eigenvectors mu of a class:
+      M1[L, N, L'] = sum Vt_N Vt_L' / D_L,  M2[L, N] = sum Vt_N Vt_L / D_L^2,
+      M3[L] = sum Vt_L^2 / D_L^3,   D_L = e_ext + omega_mu - E0_L + E_s,
+    with Vt = Y^T V the sources in the orthonormal eigenbasis of the sector.  Then
+    <Psi1_L|H|L'~> = -M1[L, L, L'] and <Psi1_L|Psi1_L> = M2[L, L].  For block-diagonal f,
+    from the rotated RDMs of `st` (an o2_rdm.Setup with kmax >= 4)."""
     from .o2_rdm import g_of
     c, a, v, n = prob.nclosed, prob.nact, prob.nvirt, prob.nstate
     fams, ext, pair, act = CLASS_DEF[cls]
     sp = _space_of_slot(cls)
     dims = {"c": c, "a": a, "v": v}
     if any(dims[sp[e]] == 0 for e in ext) or a == 0:
-        return np.zeros((n, n)), np.zeros(n)
+        return np.zeros((n, n, n)), np.zeros((n, n)), np.zeros(n)
     if h is None:
         nmo = prob.nmo
         d = np.zeros((nmo, nmo))
@@ -254,8 +288,9 @@ def class_energy(prob, st, cls, shift=0.0, scheme="msmr", thresh=1e-9, h=None):
     F = {k: x.reshape(m, m) for k, x in mats["F"].items()}
     # external tuples and their energies
     ranges = [range(dims[sp[e]]) for e in ext]
-    e_out = np.zeros((n, n))
-    n_out = np.zeros(n)
+    M1 = np.zeros((n, n, n))
+    M2 = np.zeros((n, n))
+    M3 = np.zeros(n)
     Vr = V.reshape((nf,) + V.shape[1:1 + len(ext)] + (a ** len(act), n, n))
 
     sp_list = [sp[e] for e in ext]
@@ -307,7 +342,7 @@ def class_energy(prob, st, cls, shift=0.0, scheme="msmr", thresh=1e-9, h=None):
             Ls = range(n) if Lsel is None else [Lsel]
             for L in Ls:
                 D = ee_sel[None, :] + om[:, None] - st.E0[L] + shift      # [mu, tuple]
-                amp = -Vt[:, :, L] / D
-                e_out[L, :] += np.einsum("ut,utl->l", amp, Vt)
-                n_out[L] += np.sum(amp * amp)
-    return e_out, n_out
+                M1[L] += np.einsum("utn,utl->nl", Vt / D[:, :, None], Vt)
+                M2[L] += np.einsum("utn,ut->n", Vt, Vt[:, :, L] / D ** 2)
+                M3[L] += np.sum(Vt[:, :, L] ** 2 / D ** 3)
+    return M1, M2, M3

@@ -114,6 +114,42 @@ def class_h(prob, st: Setup, shift: float = 0.0, scheme: str = "msmr"):
     return e, nr
 
 
+def class_h_moments(prob, st: Setup, shift: float = 0.0, scheme: str = "msmr"):
+    """Moment sums (M1, M2, M3) of class E_ai,bj in the eigenbasis nu of U^T Fref U, where the
+    sources are Vt_N(nu) = W_N nu k and sum_tuples k^2 = sum_ijab K(2K - K'):
+      M1[L,N,L'] = sum_nu W_Nnu W_L'nu S1[nu,L],  M2[L,N] = sum_nu W_Nnu W_Lnu S2[nu,L],
+      M3[L] = sum_nu W_Lnu^2 S3[nu,L],  Sk[nu,L] = sum_ijab K(2K - K') / D^k."""
+    c, a, v, n = prob.nclosed, prob.nact, prob.nvirt, prob.nstate
+    M1, M2, M3 = np.zeros((n, n, n)), np.zeros((n, n)), np.zeros(n)
+    if c == 0 or v == 0:
+        return M1, M2, M3
+    vo = c + a
+    eps = np.diag(prob.f)
+    ec, ev = eps[:c], eps[vo:]
+    X = prob.B.shape[0]
+    Bcv = np.ascontiguousarray(prob.B[:, :c, vo:]).reshape(X, c * v)
+    K = (Bcv.T @ Bcv).reshape(c, v, c, v)
+    num = K * (2.0 * K - K.transpose(0, 3, 2, 1))
+    D = (ev[None, :, None, None] + ev[None, None, None, :]
+         - ec[:, None, None, None] - ec[None, None, :, None])
+    if scheme == "sssr":
+        for L in range(n):
+            dd = D + shift
+            M1[L, L, L] = np.sum(num / dd)
+            M2[L, L] = np.sum(num / dd ** 2)
+            M3[L] = np.sum(num / dd ** 3)
+        return M1, M2, M3
+    omega, W = np.linalg.eigh(0.5 * (st.Ftil + st.Ftil.T))
+    for L in range(n):
+        for nu in range(n):
+            dd = D + omega[nu] - st.E0[L] + shift
+            s1, s2, s3 = np.sum(num / dd), np.sum(num / dd ** 2), np.sum(num / dd ** 3)
+            M1[L] += np.outer(W[:, nu], W[:, nu]) * s1
+            M2[L] += W[:, nu] * W[L, nu] * s2
+            M3[L] += W[L, nu] ** 2 * s3
+    return M1, M2, M3
+
+
 def heff(st: Setup, parts: dict, shift: float):
     """H^eff = H^ref + 1/2 (e + e^T) - E_s diag(norm), summed over the given classes
     (Sec. II.B); returns (Heff, Ems ascending, R with canonical column signs)."""

@@ -55,6 +55,7 @@ def lib():
         L.caspt2_get_energies.argtypes = [P, dp, dp, dp, dp, dp, dp]
         L.caspt2_get_class_energy.argtypes = [P, C.c_int, dp, dp]
         L.caspt2_get_core_energy.argtypes = [P, dp]
+        L.caspt2_get_class_lambda.argtypes = [P, C.c_int, dp, dp]
         L.caspt2_get_timings.argtypes = [P, dp, C.POINTER(C.c_int)]
         L.caspt2_get_kernel_launches.argtypes = [P]
         L.caspt2_get_kernel_launches.restype = C.c_long
@@ -124,6 +125,8 @@ class Result:
     status: int
     timings_ms: list
     launches: int
+    lam_NL: dict = None
+    lam_lv: dict = None
 
 
 class Context:
@@ -173,11 +176,20 @@ class Context:
                 _check(lib().caspt2_get_class_energy(self._h, k, _dp(e), _dp(nr)),
                        "caspt2_get_class_energy")
                 e_cls[name], n_cls[name] = e, nr
+        lam_NL, lam_lv = {}, {}
+        if self.opts.target_state >= 0:
+            for k, name in enumerate(CLASSES):
+                if self.opts.class_mask >> k & 1:
+                    a_, b_ = np.zeros(n), np.zeros((n, n))
+                    _check(lib().caspt2_get_class_lambda(self._h, k, _dp(a_), _dp(b_)),
+                           "caspt2_get_class_lambda")
+                    lam_NL[name], lam_lv[name] = a_, b_
         t = np.zeros(8)
         cnt = C.c_int(8)
         _check(lib().caspt2_get_timings(self._h, _dp(t), C.byref(cnt)), "caspt2_get_timings")
         return Result(U, E0, Href, Heff, Ems, R, ec.value, e_cls, n_cls, status,
-                      list(t[: cnt.value]), int(lib().caspt2_get_kernel_launches(self._h)))
+                      list(t[: cnt.value]), int(lib().caspt2_get_kernel_launches(self._h)),
+                      lam_NL, lam_lv)
 
 
 def classH_noalloc(dims: Dims, opts: Options, fock, dfB, rdm1, e, norm, stream=None) -> int:

@@ -42,6 +42,7 @@ struct caspt2_ctx {
          *href = nullptr;
   // classes
   double *ecls = nullptr, *ncls = nullptr, *mindenom = nullptr;
+  double *mom = nullptr, *lamNL = nullptr, *lamLV = nullptr;   // per class moments, lambda
   ClassHWork hw{};
   // classes A-G
   int kmax = 2;                       // highest RDM rank the enabled classes read
@@ -58,7 +59,7 @@ struct caspt2_ctx {
   cudaEvent_t ev[kNumStages + 1] = {};
 
   // host copies of the last results
-  std::vector<double> hU, hE0, hHref, hHeff, hEms, hR, hEcls, hNcls;
+  std::vector<double> hU, hE0, hHref, hHeff, hEms, hR, hEcls, hNcls, hLamNL, hLamLV;
   double hEcore = 0.0, hMinDenom = 0.0;
   double times[kNumTimes] = {};
   long launches = 0;
@@ -182,8 +183,11 @@ int caspt2_create(caspt2_ctx** out, const caspt2_dims* dims, const caspt2_option
   ALLOC(c->hw.W, n * n);
   ALLOC(c->hw.omega, n);
   ALLOC(c->hw.shifts, nshift);
-  ALLOC(c->hw.partial, (size_t)c->hw.nblocks * (2 * nshift + 1));
-  ALLOC(c->hw.sums, 2 * nshift + 1);
+  ALLOC(c->hw.partial, (size_t)c->hw.nblocks * (3 * nshift + 1));
+  ALLOC(c->hw.sums, 3 * nshift + 1);
+  ALLOC(c->mom, (size_t)CASPT2_NCLASS * (n * n * n + n * n + n));
+  ALLOC(c->lamNL, (size_t)CASPT2_NCLASS * n);
+  ALLOC(c->lamLV, (size_t)CASPT2_NCLASS * n * n);
   // classes A-G: plans, class matrices, sources, sector work space, integral blocks
   {
     long m2max = 0, wmax = 0, pmax = 0;
@@ -273,6 +277,8 @@ int caspt2_create(caspt2_ctx** out, const caspt2_dims* dims, const caspt2_option
   c->hR.assign(n * n, 0.0);
   c->hEcls.assign((size_t)CASPT2_NCLASS * n * n, 0.0);
   c->hNcls.assign((size_t)CASPT2_NCLASS * n, 0.0);
+  c->hLamNL.assign((size_t)CASPT2_NCLASS * n, 0.0);
+  c->hLamLV.assign((size_t)CASPT2_NCLASS * n * n, 0.0);
   *out = c;
   return CASPT2_OK;
 }
@@ -317,6 +323,10 @@ int caspt2_solve(caspt2_ctx* c, void* stream) {
   CASPT2_CUDA_TRY(cudaMemcpyAsync(c->mindenom, &big, sizeof(double), cudaMemcpyHostToDevice, s));
   CASPT2_CUDA_TRY(cudaMemsetAsync(c->ecls, 0, sizeof(double) * CASPT2_NCLASS * n * n, s));
   CASPT2_CUDA_TRY(cudaMemsetAsync(c->ncls, 0, sizeof(double) * CASPT2_NCLASS * n, s));
+  const long msz = (long)n * n * n + n * n + n;
+  CASPT2_CUDA_TRY(cudaMemsetAsync(c->mom, 0, sizeof(double) * CASPT2_NCLASS * msz, s));
+  CASPT2_CUDA_TRY(cudaMemsetAsync(c->lamNL, 0, sizeof(double) * CASPT2_NCLASS * n, s));
+  CASPT2_CUDA_TRY(cudaMemsetAsync(c->lamLV, 0, sizeof(double) * CASPT2_NCLASS * n * n, s));
 
   // ---- stage 0: setup (Sec. II.A, II.B)
   CASPT2_CUDA_TRY(cudaEventRecord(c->ev[0], s));
@@ -338,7 +348,8 @@ int caspt2_solve(caspt2_ctx* c, void* stream) {
   if (o.class_mask >> CASPT2_CLASS_H & 1u) {
     CASPT2_CUDA_TRY(launch_classH(c->f, c->B, c->Ftil, c->E0, o.shift, o.scheme, d, c->hw,
                                   c->status, c->ecls + (long)CASPT2_CLASS_H * n * n,
-                                  c->ncls + (long)CASPT2_CLASS_H * n, c->mindenom, s));
+                                  c->ncls + (long)CASPT2_CLASS_H * n,
+                                  c->mom + (long)CASPT2_CLASS_H * msz, c->mindenom, s));
   }
   CASPT2_CUDA_TRY(cudaEventRecord(c->ev[2], s));
   // ---- stage 2: classes A-G
@@ -361,9 +372,10 @@ int caspt2_solve(caspt2_ctx* c, void* stream) {
       for (int k = 0; k < 7; ++k) {
         if (!c->cw_on[k]) continue;
         int st = class_solve(c->cw[k], c->sw, d, o.scheme, o.shift, o.ovl_thresh, g, c->fact, c->h,
-                             c->eri_tab, c->E0, c->eps, c->ecls + (long)k * n * n,
-                             c->ncls + (long)k * n, c->mindenom, s);
+                             c->eri_tab, c->E0, c->eps, c->mom + (long)k * msz, c->mindenom, s);
         if (st != CASPT2_OK) return st;
+        CASPT2_CUDA_TRY(launch_moments_to_e(c->mom + (long)k * msz, n, c->ecls + (long)k * n * n,
+                                            c->ncls + (long)k * n, s));
       }
     }
   }
@@ -371,6 +383,14 @@ int caspt2_solve(caspt2_ctx* c, void* stream) {
   // ---- stage 3: effective Hamiltonian and its eigenpairs (Sec. II.B)
   CASPT2_CUDA_TRY(launch_heff(c->href, c->ecls, c->ncls, o.class_mask, o.shift, n, c->heff, s));
   CASPT2_CUDA_TRY(launch_sym_eig(c->heff, n, c->R, c->ems, 0, c->status, s));
+  // lambda of the target state from the class moments (Eq. lambdaeq)
+  if (o.target_state >= 0) {
+    for (int k = 0; k < CASPT2_NCLASS; ++k) {
+      if (!(o.class_mask >> k & 1u)) continue;
+      CASPT2_CUDA_TRY(launch_lambda(c->mom + (long)k * msz, c->R, n, o.target_state, o.shift,
+                                    c->lamNL + (long)k * n, c->lamLV + (long)k * n * n, s));
+    }
+  }
   CASPT2_CUDA_TRY(cudaEventRecord(c->ev[4], s));
 
   // results back to the host copies
@@ -383,6 +403,8 @@ int caspt2_solve(caspt2_ctx* c, void* stream) {
   CASPT2_CUDA_TRY(cudaMemcpyAsync(c->hR.data(), c->R, sizeof(double) * n * n, cudaMemcpyDeviceToHost, s));
   CASPT2_CUDA_TRY(cudaMemcpyAsync(c->hEcls.data(), c->ecls, sizeof(double) * CASPT2_NCLASS * n * n, cudaMemcpyDeviceToHost, s));
   CASPT2_CUDA_TRY(cudaMemcpyAsync(c->hNcls.data(), c->ncls, sizeof(double) * CASPT2_NCLASS * n, cudaMemcpyDeviceToHost, s));
+  CASPT2_CUDA_TRY(cudaMemcpyAsync(c->hLamNL.data(), c->lamNL, sizeof(double) * CASPT2_NCLASS * n, cudaMemcpyDeviceToHost, s));
+  CASPT2_CUDA_TRY(cudaMemcpyAsync(c->hLamLV.data(), c->lamLV, sizeof(double) * CASPT2_NCLASS * n * n, cudaMemcpyDeviceToHost, s));
   CASPT2_CUDA_TRY(cudaMemcpyAsync(&c->hEcore, c->ecore, sizeof(double), cudaMemcpyDeviceToHost, s));
   CASPT2_CUDA_TRY(cudaMemcpyAsync(&c->hMinDenom, c->mindenom, sizeof(double), cudaMemcpyDeviceToHost, s));
   CASPT2_CUDA_TRY(cudaMemcpyAsync(&hst, c->status, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -428,6 +450,16 @@ int caspt2_get_class_energy(caspt2_ctx* c, int cls, double* e, double* norm) {
   const size_t n = c->d.n;
   if (e) std::memcpy(e, c->hEcls.data() + cls * n * n, sizeof(double) * n * n);
   if (norm) std::memcpy(norm, c->hNcls.data() + cls * n, sizeof(double) * n);
+  return CASPT2_OK;
+}
+
+int caspt2_get_class_lambda(caspt2_ctx* c, int cls, double* NL, double* lv) {
+  if (!c || cls < 0 || cls >= CASPT2_NCLASS) return CASPT2_EINVAL;
+  if (!(c->opt.class_mask >> cls & 1u) || c->opt.target_state < 0) return CASPT2_EINVAL;
+  if (!c->solved) return CASPT2_ESTATE;
+  const size_t n = c->d.n;
+  if (NL) std::memcpy(NL, c->hLamNL.data() + cls * n, sizeof(double) * n);
+  if (lv) std::memcpy(lv, c->hLamLV.data() + cls * n * n, sizeof(double) * n * n);
   return CASPT2_OK;
 }
 

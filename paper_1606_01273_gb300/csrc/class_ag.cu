@@ -274,21 +274,23 @@ __global__ void k_sector_src(const double* __restrict__ V, DevClass C, ExtDims e
   }
 }
 
-// Per (tuple, L, L'): sum_mu -Vt[mu][t,L] Vt[mu][t,L'] / D and, for L == L', sum (Vt/D)^2,
-// D = e_ext(t) + omega_mu - E0_L + E_s over kept mu.  Written to part[t][L][L'], partn[t][L].
+// Moment sums of the sector for each (tuple t, L, N) over the kept eigenvectors mu:
+//   M1[L][N][L'] += Vt_N Vt_L' / D_L (all L'),  M2[L][N] += Vt_N Vt_L / D_L^2,
+//   M3[L] += Vt_L^2 / D_L^3 (N == L),   D_L = e_ext(t) + omega_mu - E0_L + E_s.
+// part[t][Li][N][n + 2] (Li = L, or 0 under SS-SR where L = Lsel).
 __global__ void k_sector_energy(const double* __restrict__ Vt, const double* __restrict__ omega,
                                 const double* __restrict__ E0,
                                 const double* __restrict__ eps, DevClass C, ExtDims ed, int c,
                                 int n, int sector, int Lsel, long ntup, int msec, double shift,
-                                double* __restrict__ part, double* __restrict__ partn,
-                                double* __restrict__ mindenom) {
+                                double* __restrict__ part, double* __restrict__ mindenom) {
   const long ncol = ntup * n;
   const int nL = Lsel < 0 ? n : 1;
   const long total = ntup * nL * n;
+  const int w = n + 2;
   double dmin = 1e300;
   for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
        e += (long)gridDim.x * blockDim.x) {
-    const int Lp = e % n;
+    const int N = e % n;
     const int Li = (e / n) % nL;
     const long t = e / ((long)n * nL);
     const int L = Lsel < 0 ? Li : Lsel;
@@ -297,23 +299,46 @@ __global__ void k_sector_energy(const double* __restrict__ Vt, const double* __r
     double ee = 0.0;
     for (int k = 0; k < C.next; ++k)
       ee += (C.slot_space[C.ext[k]] == SP_V) ? eps[c + co[k]] : -eps[co[k]];
-    double se = 0.0, sn = 0.0;
+    double m1[kMaxStates], m2 = 0.0, m3 = 0.0;
+    for (int q = 0; q < n; ++q) m1[q] = 0.0;
     for (int mu = 0; mu < msec; ++mu) {
       const double D = ee + omega[mu] - E0[L] + shift;
-      const double vl = Vt[(long)mu * ncol + t * n + L];
-      const double amp = -vl / D;
-      se += amp * Vt[(long)mu * ncol + t * n + Lp];
-      if (Lp == L) sn += amp * amp;
+      const double inv = 1.0 / D;
+      const double* row = Vt + (long)mu * ncol + t * n;
+      const double vn = row[N] * inv;
+      for (int q = 0; q < n; ++q) m1[q] += vn * row[q];
+      m2 += vn * row[L] * inv;
+      if (N == L) m3 += row[L] * row[L] * inv * inv * inv;
       dmin = fmin(dmin, fabs(D));
     }
-    part[(t * nL + Li) * n + Lp] = se;
-    if (Lp == L) partn[t * nL + Li] = sn;
+    double* o = part + (((t * nL + Li) * n) + N) * w;
+    for (int q = 0; q < n; ++q) o[q] = m1[q];
+    o[n] = m2;
+    o[n + 1] = m3;
   }
-  // per-thread minimum -> one slot per thread block (fixed reduction later is not needed
-  // for a minimum: fmin is order independent)
   __shared__ double red[32];
   dmin = block_min(dmin, red);
   if (threadIdx.x == 0) atomicMin_double(mindenom, dmin);
+}
+
+// Fixed-order column sums of part[rows][nL][n][n+2] accumulated into the class moments
+// mom = [M1: n^3][M2: n^2][M3: n].
+__global__ void k_moment_colsum(const double* __restrict__ part, long rows, int n, int nL, int Lsel,
+                                double* __restrict__ mom) {
+  __shared__ double red[32];
+  const int w = n + 2;
+  const int col = blockIdx.x;          // (Li, N, q)
+  const int ncol = nL * n * w;
+  const int q = col % w, N = (col / w) % n, Li = col / (w * n);
+  const int L = Lsel < 0 ? Li : Lsel;
+  double acc = 0.0;
+  for (long r = threadIdx.x; r < rows; r += blockDim.x) acc += part[r * ncol + col];
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) {
+    if (q < n) mom[(L * n + N) * n + q] += acc;
+    else if (q == n) mom[n * n * n + L * n + N] += acc;
+    else if (N == L) mom[n * n * n + n * n + L] += acc;
+  }
 }
 
 // column sums of part[rows][ncol] in fixed order -> out[ncol] (accumulated: out += sum)
@@ -374,6 +399,51 @@ __global__ void k_hcore(const double* __restrict__ f, const double* __restrict__
   }
 }
 
+// e[L][L'] = -M1[L][L][L'], norm[L] = M2[L][L] of one class
+__global__ void k_moments_to_e(const double* __restrict__ mom, int n, double* e, double* nr) {
+  const int idx = threadIdx.x;
+  if (idx < n * n) {
+    const int L = idx / n, Lp = idx % n;
+    e[idx] = -mom[(L * n + L) * n + Lp];
+  }
+  if (idx < n) nr[idx] = mom[n * n * n + idx * n + idx];
+}
+
+cudaError_t launch_moments_to_e(const double* mom, int n, double* e, double* nr, cudaStream_t s) {
+  ++launch_counter();
+  k_moments_to_e<<<1, kMaxStates * kMaxStates, 0, s>>>(mom, n, e, nr);
+  return cudaGetLastError();
+}
+
+// lambda of the target state P from the moments (Eq. lambdaeq differentiated w.r.t. T):
+//   NL[L] = R_LP sum_N R_NP M2[L][N] + 2 E_s R_LP^2 M3[L]
+//   lv[L][L'] = -R_LP sum_N R_NP M1[L][N][L'] - 2 E_s R_LP^2 M2[L][L']
+__global__ void k_lambda_from_moments(const double* __restrict__ mom, const double* __restrict__ R,
+                                      int n, int P, double shift, double* NL, double* lv) {
+  const int idx = threadIdx.x;
+  if (idx < n * n) {
+    const int L = idx / n, Lp = idx % n;
+    const double rl = R[L * n + P];
+    double acc = 0.0;
+    for (int N = 0; N < n; ++N) acc += R[N * n + P] * mom[(L * n + N) * n + Lp];
+    lv[idx] = -rl * acc - 2.0 * shift * rl * rl * mom[n * n * n + L * n + Lp];
+  }
+  if (idx < n) {
+    const int L = idx;
+    const double rl = R[L * n + P];
+    double acc = 0.0;
+    for (int N = 0; N < n; ++N) acc += R[N * n + P] * mom[n * n * n + L * n + N];
+    NL[L] = rl * acc + 2.0 * shift * rl * rl * mom[n * n * n + n * n + L];
+  }
+}
+
+cudaError_t launch_lambda(const double* mom, const double* R, int n, int P, double shift, double* NL,
+                          double* lv, cudaStream_t s) {
+  ++launch_counter();
+  k_lambda_from_moments<<<1, kMaxStates * kMaxStates, 0, s>>>(mom, R, n, P, shift, NL, lv);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_hcore(const double* f, const double* g_act, const double* B, const double* bsum,
                          const Dims& d, double* h, cudaStream_t s) {
   const long tot = (long)d.nmo() * d.nmo();
@@ -432,7 +502,7 @@ long class_sector_wsize(const ClassWork& w, const Dims& d, int scheme, long* par
     const long nt = sector_tuples(w, sec);
     const long msec = scheme == CASPT2_SSSR ? w.m / d.n : w.m;
     wmax = std::max(wmax, msec * nt * d.n);
-    pmax = std::max(pmax, nt * (long)d.n * d.n);
+    pmax = std::max(pmax, nt * (long)d.n * d.n * (d.n + 2));
   }
   if (partsize) *partsize = pmax;
   return wmax;
@@ -452,8 +522,8 @@ cudaError_t class_upload_plans(ClassWork& w, const std::vector<ActPlan>& S,
 
 int class_solve(ClassWork& w, SectorWork& sw, const Dims& d, int scheme, double shift,
                 double thresh, RdmPtrs rdm, const double* f_act, const double* h,
-                const EriBlocks& eri, const double* E0, const double* eps_cv, double* ecls,
-                double* ncls, double* mindenom, cudaStream_t s) {
+                const EriBlocks& eri, const double* E0, const double* eps_cv, double* mom,
+                double* mindenom, cudaStream_t s) {
   const int m = w.m, n = d.n;
   if (w.vsize == 0 || m == 0) return CASPT2_OK;
   const long mm = (long)m * m;
@@ -512,11 +582,9 @@ int class_solve(ClassWork& w, SectorWork& sw, const Dims& d, int scheme, double 
       ++launch_counter();
       k_sector_energy<<<launch_blocks(ne), 256, 0, s>>>(sw.Vt, sw.omega, E0, eps_cv, w.dc, w.ed,
                                                         d.c, n, sec, Lsel, ntup, nk, shift,
-                                                        sw.part, sw.partn, mindenom);
+                                                        sw.part, mindenom);
       ++launch_counter();
-      k_colsum_acc<<<nL * n, 256, 0, s>>>(sw.part, ntup, nL * n, ecls, 1, Lsel < 0 ? 0 : Lsel * n);
-      ++launch_counter();
-      k_colsum_acc<<<nL, 256, 0, s>>>(sw.partn, ntup, nL, ncls, 1, Lsel < 0 ? 0 : Lsel);
+      k_moment_colsum<<<nL * n * (n + 2), 256, 0, s>>>(sw.part, ntup, n, nL, Lsel, mom);
       CASPT2_CUDA_TRY(cudaGetLastError());
     }
   }

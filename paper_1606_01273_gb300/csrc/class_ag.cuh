@@ -57,11 +57,17 @@ long class_sector_wsize(const ClassWork& w, const Dims& d, int scheme, long* par
 cudaError_t class_upload_plans(ClassWork& w, const std::vector<ActPlan>& S,
                                const std::vector<ActPlan>& F, const std::vector<SrcPlan>& V);
 
-// Evaluate S, F_act, V of a class and solve it; accumulates e[L][L'] and norm[L].
+// Evaluate S, F_act, V of a class and solve it; accumulates the moment sums
+// mom = [M1: n^3][M2: n^2][M3: n] (see k_sector_energy).
 int class_solve(ClassWork& w, SectorWork& sw, const Dims& d, int scheme, double shift,
                 double thresh, RdmPtrs rdm, const double* f, const double* h, const EriBlocks& eri,
-                const double* E0, const double* eps_cv, double* ecls, double* ncls,
-                double* mindenom, cudaStream_t s);
+                const double* E0, const double* eps_cv, double* mom, double* mindenom,
+                cudaStream_t s);
+// e = -M1[L][L][.], norm = M2[L][L] of one class
+cudaError_t launch_moments_to_e(const double* mom, int n, double* e, double* nr, cudaStream_t s);
+// lambda pieces of the target state P of one class from its moments and R
+cudaError_t launch_lambda(const double* mom, const double* R, int n, int P, double shift, double* NL,
+                          double* lv, cudaStream_t s);
 
 // DF integral block out[p][q][r][t] = sum_P B[P][p][q] B[P][r][t] for the given spaces.
 cudaError_t eri_block(const double* B, const Dims& d, const int sp[4], double* pack0, double* pack1,

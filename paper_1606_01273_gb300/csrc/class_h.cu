@@ -182,25 +182,29 @@ k_classH(const double* __restrict__ Bp, const double* __restrict__ eps,
       num[ii * 4 + jj] = ok ? wij * nm : 0.0;
       d0[ii * 4 + jj] = ok ? (sEa[la] + sEb[lb] - ei - ej) : 1.0;
     }
-  double* out = partial + blockIdx.x * (long)(2 * nshift + 1);
+  double* out = partial + blockIdx.x * (long)(3 * nshift + 1);
   double dmin = 1e300;
   for (int k = 0; k < nshift; ++k) {
     const double sh = sShift[k];
-    double e = 0.0, nr = 0.0;
+    double e = 0.0, nr = 0.0, n3 = 0.0;
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
       const double inv = 1.0 / (d0[q] + sh);
-      e = fma(num[q], inv, e);
-      nr = fma(num[q] * inv, inv, nr);
+      const double x = num[q] * inv;
+      e += x;
+      nr = fma(x, inv, nr);
+      n3 = fma(x * inv, inv, n3);
       if (num[q] != 0.0) dmin = fmin(dmin, fabs(d0[q] + sh));
     }
     e = block_sum(e, red);
     if (threadIdx.x == 0) out[k] = e;
     nr = block_sum(nr, red);
     if (threadIdx.x == 0) out[nshift + k] = nr;
+    n3 = block_sum(n3, red);
+    if (threadIdx.x == 0) out[2 * nshift + k] = n3;
   }
   dmin = block_min(dmin, red);
-  if (threadIdx.x == 0) out[2 * nshift] = dmin;
+  if (threadIdx.x == 0) out[3 * nshift] = dmin;
 }
 
 // sums[col] = fixed-order reduction of partial[.][col]; the last column is a min.
@@ -218,33 +222,44 @@ __global__ void k_reduce_cols(const double* __restrict__ partial, long nblocks, 
   if (threadIdx.x == 0) sums[col] = acc;
 }
 
-// e[L][L'] = -sum_nu W_Lnu W_L'nu S_e[nu,L]; norm[L] = sum_nu W_Lnu^2 S_n[nu,L]
+// Moments of class H from the sums Sk[nu,L] = sum num / D^k (k = 1, 2, 3):
+//   M1[L][N][L'] = sum_nu W_Nnu W_L'nu S1[nu,L], M2[L][N] = sum_nu W_Nnu W_Lnu S2[nu,L],
+//   M3[L] = sum_nu W_Lnu^2 S3[nu,L]; under SS-SR only N = L' = L with S_k[0].
+// e[L][L'] = -M1[L][L][L'], norm[L] = M2[L][L].
 __global__ void k_classH_combine(const double* __restrict__ sums, const double* __restrict__ W,
-                                 int n, int scheme, double* ecls, double* ncls, double* mindenom,
-                                 int* status) {
-  int idx = threadIdx.x;
+                                 int n, int scheme, double* ecls, double* ncls, double* mom,
+                                 double* mindenom, int* status) {
   const int nshift = (scheme == CASPT2_SSSR) ? 1 : n * n;
-  if (idx < n * n) {
-    int L = idx / n, Lp = idx % n;
-    double e = 0.0;
-    if (scheme == CASPT2_SSSR) {
-      e = (L == Lp) ? -sums[0] : 0.0;
-    } else {
-      for (int nu = 0; nu < n; ++nu) e -= W[L * n + nu] * W[Lp * n + nu] * sums[nu * n + L];
-    }
-    ecls[idx] = e;
+  const double* S1 = sums;
+  const double* S2 = sums + nshift;
+  const double* S3 = sums + 2 * nshift;
+  for (int idx = threadIdx.x; idx < n * n * n; idx += blockDim.x) {
+    const int L = idx / (n * n), N = (idx / n) % n, Lp = idx % n;
+    double v = 0.0;
+    if (scheme == CASPT2_SSSR) v = (N == L && Lp == L) ? S1[0] : 0.0;
+    else
+      for (int nu = 0; nu < n; ++nu) v += W[N * n + nu] * W[Lp * n + nu] * S1[nu * n + L];
+    mom[idx] = v;
+    if (N == L) ecls[L * n + Lp] = -v;
   }
-  if (idx < n) {
-    double nr = 0.0;
-    if (scheme == CASPT2_SSSR) {
-      nr = sums[nshift];
-    } else {
-      for (int nu = 0; nu < n; ++nu) nr += W[idx * n + nu] * W[idx * n + nu] * sums[nshift + nu * n + idx];
-    }
-    ncls[idx] = nr;
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int L = idx / n, N = idx % n;
+    double v = 0.0;
+    if (scheme == CASPT2_SSSR) v = (N == L) ? S2[0] : 0.0;
+    else
+      for (int nu = 0; nu < n; ++nu) v += W[N * n + nu] * W[L * n + nu] * S2[nu * n + L];
+    mom[n * n * n + idx] = v;
+    if (N == L) ncls[L] = v;
   }
-  if (idx == 0) {
-    double dm = sums[2 * nshift];
+  for (int L = threadIdx.x; L < n; L += blockDim.x) {
+    double v = 0.0;
+    if (scheme == CASPT2_SSSR) v = S3[0];
+    else
+      for (int nu = 0; nu < n; ++nu) v += W[L * n + nu] * W[L * n + nu] * S3[nu * n + L];
+    mom[n * n * n + n * n + L] = v;
+  }
+  if (threadIdx.x == 0) {
+    const double dm = sums[3 * nshift];
     *mindenom = fmin(*mindenom, dm);
     if (!(dm == dm)) atomicExch(status, CASPT2_ENAN);
   }
@@ -267,7 +282,8 @@ int classH_nshift(const Dims& d, int scheme) { return scheme == CASPT2_SSSR ? 1 
 
 cudaError_t launch_classH(const double* f, const double* B, const double* Ftil, const double* E0,
                           double shift, int scheme, const Dims& d, ClassHWork& w, int* status,
-                          double* ecls, double* ncls, double* mindenom, cudaStream_t s) {
+                          double* ecls, double* ncls, double* mom, double* mindenom,
+                          cudaStream_t s) {
   const int n = d.n, nmo = d.nmo();
   const int nshift = classH_nshift(d, scheme);
   cudaError_t e;
@@ -293,11 +309,11 @@ cudaError_t launch_classH(const double* f, const double* B, const double* Ftil, 
   k_classH<<<(unsigned)nb, kHThreads, 0, s>>>(w.Bp, w.eps, w.shifts, nshift, d.c, d.v, d.X, ntile,
                                              w.partial);
   if (w.ev_gemm1) cudaEventRecord(w.ev_gemm1, s);
-  const int ncol = 2 * nshift + 1;
+  const int ncol = 3 * nshift + 1;
   ++launch_counter();
   k_reduce_cols<<<ncol, 256, 0, s>>>(w.partial, nb, ncol, w.sums);
   ++launch_counter();
-  k_classH_combine<<<1, kMaxShift, 0, s>>>(w.sums, w.W, n, scheme, ecls, ncls, mindenom, status);
+  k_classH_combine<<<1, 256, 0, s>>>(w.sums, w.W, n, scheme, ecls, ncls, mom, mindenom, status);
   return cudaGetLastError();
 }
 

@@ -49,8 +49,8 @@ struct ClassHWork {
   double* W;         // [n][n]      eigenvectors of U^T Fref U
   double* omega;     // [n]
   double* shifts;    // [nshift]    omega_nu - E0_L + E_s
-  double* partial;   // [nblocks][2*nshift + 1]
-  double* sums;      // [2*nshift + 1]
+  double* partial;   // [nblocks][3*nshift + 1]
+  double* sums;      // [3*nshift + 1]
   long    nblocks;
   cudaEvent_t ev_gemm0 = nullptr, ev_gemm1 = nullptr;  // optional: bracket the GEMM kernel
 };
@@ -62,6 +62,7 @@ cudaError_t launch_active_block(const double* f, const Dims& d, double* out, cud
 int  classH_nshift(const Dims& d, int scheme);
 cudaError_t launch_classH(const double* f, const double* B, const double* Ftil, const double* E0,
                           double shift, int scheme, const Dims& d, ClassHWork& w, int* status,
-                          double* ecls, double* ncls, double* mindenom, cudaStream_t s);
+                          double* ecls, double* ncls, double* mom, double* mindenom,
+                          cudaStream_t s);
 
 }  // namespace caspt2

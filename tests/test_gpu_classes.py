@@ -57,8 +57,15 @@ def test_all_classes_vs_rdm_oracle(cp, name, opt):
     r = cp.solve_problem(p, **opt)
     st = o2.setup(p, xms=bool(opt["xms"]), kmax=4)
     sch = "sssr" if opt["scheme"] == 1 else "msmr"
-    parts = oc.all_classes(p, st, shift=opt["shift"], scheme=sch)
+    mom = oc.all_moments(p, st, shift=opt["shift"], scheme=sch)
+    parts = {c: (-np.einsum("llk->lk", M1), np.diagonal(M2).copy()) for c, (M1, M2, M3) in mom.items()}
     _check(r, parts, st, opt["shift"])
+    # lambda of target state 0 (Eq. lambdaeq), per class
+    H, w, R = o2.heff(st, parts, opt["shift"])
+    for cls in "ABCDEFGH":
+        NL, lv = oc.lambda_pieces(*mom[cls], R, 0, opt["shift"])
+        assert np.abs(r.lam_NL[cls] - NL).max() <= 1e-9 * max(1.0, np.abs(NL).max()), cls
+        assert np.abs(r.lam_lv[cls] - lv).max() <= 1e-9 * max(1.0, np.abs(lv).max()), cls
 
 
 @pytest.mark.parametrize("opt", OPTS, ids=lambda o: f"xms{o['xms']}_sch{o['scheme']}_s{o['shift']}")
@@ -72,6 +79,18 @@ def test_all_classes_vs_brute_force(cp, opt):
         scale = max(1.0, np.abs(ref.e_class[cls]).max())
         assert np.abs(r.e_class[cls] - ref.e_class[cls]).max() <= 1e-10 * scale, cls
         assert np.abs(r.norm_class[cls] - ref.norm_class[cls]).max() <= 1e-10, cls
+        # lambda against the explicit determinant-space vectors
+        n = p.nstate
+        for L in range(n):
+            idx = [k for k, c in enumerate(ref.cols[L]) if c[0] == cls]
+            if not idx:
+                continue
+            lam, t = ref.lam[L][idx], ref.t[L][idx]
+            nl = lam @ ref.S[L][np.ix_(idx, idx)] @ t
+            assert abs(r.lam_NL[cls][L] - nl) <= 1e-9 * max(1.0, abs(nl)), cls
+            for Lp in range(n):
+                lv = lam @ ref.b_src[L][Lp][idx]
+                assert abs(r.lam_lv[cls][L, Lp] - lv) <= 1e-9 * max(1.0, abs(lv)), cls
     assert np.abs(r.Heff - ref.Heff).max() <= ETOL
     assert np.abs(r.Ems - ref.Ems).max() <= ETOL
 

@@ -81,3 +81,30 @@ def test_wick_engine_identities():
     assert got == {(1, (), (("r", "s"), ("t", "u"))), (1, (("s", "t"),), (("r", "u"),))}
     got = {(x.coeff, x.deltas, x.rdm) for x in expect(b.E("i", "r") + b.E("s", "j"), sp)}
     assert got == {(2, (("i", "j"), ("r", "s")), ()), (-1, (("i", "j"),), (("s", "r"),))}
+
+
+@pytest.mark.parametrize("xms,scheme,shift", [(True, "msmr", 0.2), (False, "msmr", 0.0),
+                                              (True, "sssr", 0.1), (False, "msmr", 0.3)])
+def test_lambda_pieces_match_o1(cprob, xms, scheme, shift):
+    """lambda per class from the moment sums equals O1's explicit lambda vectors:
+    NL[L] = lam_L . S_L t_L and lv[L, L'] = lam_L . V_L^T H |L'~> over the class columns."""
+    from oracle import o2_classes as oc
+    r = o1.solve_problem(cprob, xms=xms, scheme=scheme, shift=shift, densities=False)
+    st = o2.setup(cprob, xms=xms, kmax=4)
+    mom = oc.all_moments(cprob, st, shift=shift, scheme=scheme)
+    parts = {c: (-np.einsum("llk->lk", M1), np.diagonal(M2).copy()) for c, (M1, M2, M3) in mom.items()}
+    H, w, R = o2.heff(st, parts, shift)
+    assert np.abs(R - r.R).max() < 1e-9
+    n = cprob.nstate
+    for cls in "ABCDEFGH":
+        NL, lv = oc.lambda_pieces(*mom[cls], R, 0, shift)
+        for L in range(n):
+            idx = [k for k, c in enumerate(r.cols[L]) if c[0] == cls]
+            if not idx:
+                continue
+            lam, t = r.lam[L][idx], r.t[L][idx]
+            S = r.S[L][np.ix_(idx, idx)]
+            assert abs(NL[L] - lam @ S @ t) <= 1e-10 * max(1.0, abs(NL[L])), cls
+            for Lp in range(n):
+                ref = lam @ r.b_src[L][Lp][idx]
+                assert abs(lv[L, Lp] - ref) <= 1e-10 * max(1.0, abs(ref)), cls
