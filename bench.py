@@ -110,12 +110,15 @@ def make_inputs():
 
 
 def oracle_solve(p):
-    """The CPU oracle for the same step (setup, classes A-H, H^eff)."""
+    """The CPU oracle for the same step (setup, classes A-H, H^eff, lambda of state 0)."""
     from oracle import o2_rdm as o2
     from oracle import o2_classes as oc
     st = o2.setup(p, xms=bool(OPTS["xms"]), kmax=4)
-    parts = oc.all_classes(p, st, shift=OPTS["shift"], scheme="msmr")
-    return o2.heff(st, parts, OPTS["shift"])
+    mom = oc.all_moments(p, st, shift=OPTS["shift"], scheme="msmr")
+    parts = {c: (-np.einsum("llk->lk", M1), np.diagonal(M2).copy()) for c, (M1, M2, M3) in mom.items()}
+    H, w, R = o2.heff(st, parts, OPTS["shift"])
+    lam = {c: oc.lambda_pieces(*mom[c], R, 0, OPTS["shift"]) for c in mom}
+    return H, w, R, lam
 
 
 def cpu_cores():
@@ -196,7 +199,7 @@ def run_ours(args):
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
-    kern_ms, launches = [], 0
+    kern_ms, launches, tri = [], 0, []
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize(dev)
@@ -209,6 +212,7 @@ def run_ours(args):
                 ev[k][1].record(stream)
             r = ctx.result()
             kern_ms.append(r.timings_ms[4])
+            tri.append((r.timings_ms[5], r.timings_ms[6], r.timings_ms[7]))
             launches += r.launches
         torch.cuda.synchronize(dev)
     if ws > 1:
@@ -253,6 +257,11 @@ def run_ours(args):
     kavg = statistics.mean(kern_ms)
     flops = classh_flops(p.nclosed, p.nvirt, p.naux)
     achieved = flops / (kavg * 1e-3) / 1e12
+    tri_ms = sum(t[0] for t in tri)
+    tri_fl = sum(t[1] for t in tri)
+    tri_n = sum(t[2] for t in tri)
+    tri_avg_ms = tri_ms / max(tri_n, 1)
+    tri_achieved = tri_fl / max(tri_ms * 1e-3, 1e-12) / 1e12
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
@@ -262,21 +271,28 @@ def run_ours(args):
                    "form": "plain FP64", "parallelism": f"{ws} independent solve(s)",
                    "l2": "256 MB write between steps; B (291 MB) larger than L2"},
         "tflops_classH_kernel": achieved,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                     "traffic": CLASSH_TRAFFIC_BYTES, "kernel": "k_classH",
-                     "kernel_ms": kavg, "flops_per_launch": flops,
+        # dominant kernel by device time (see profiles/): the Householder tridiagonalisation
+        # of the class overlap / Fock matrices; FP64, 4/3 m^3 algorithmic flops per launch
+        "roofline": {"bound": "alu", "achieved": tri_achieved, "peak": FP64_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": tri_achieved / FP64_PEAK_TFLOPS,
+                     "traffic": None, "kernel": "k_tridiag", "kernel_ms": tri_avg_ms,
+                     "launches_per_step": tri_n / max(len(tri), 1),
+                     "flops_per_launch": tri_fl / max(tri_n, 1),
                      "peak_kind": "nominal FP64 (no measured FP64 peak in MEASURED_PEAKS)"},
+        "roofline_classH": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                            "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                            "traffic": CLASSH_TRAFFIC_BYTES, "kernel": "k_classH",
+                            "kernel_ms": kavg, "flops_per_launch": flops},
         "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": clk.summary(),
-        "stage_ms_last": dict(zip(["setup", "classH", "classesAG", "heff", "classH_kernel"],
-                                  last.timings_ms)),
+        "stage_ms_last": dict(zip(["setup", "classH", "classesAG", "heff_lambda", "classH_kernel",
+                                   "tridiag_kernel_total"], last.timings_ms[:6])),
     }
     if ws == 1 and not args.no_cpu_baseline:
         ts, ref = time_oracle(p)
-        _, w, _ = ref
+        w = ref[1]
         line["cpu_baseline"] = {"value": len(ts) / sum(ts), "unit": "solves/s",
                                 "cores": cpu_cores(), "kind": "oracle",
                                 "sample": f"{len(ts)} whole solve(s) of the workload, numpy FP64"}

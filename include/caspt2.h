@@ -119,8 +119,10 @@ int caspt2_get_class_lambda(caspt2_ctx* ctx, int cls, double* NL, double* lv);
 int caspt2_get_core_energy(caspt2_ctx* ctx, double* ecore);
 
 /* Device time in milliseconds of the last solve, measured with CUDA events on the
- * solve stream: times[0] setup, [1] class H stage, [2] other classes, [3] effective
- * Hamiltonian, [4] the class-H DF-GEMM kernel alone (0 if class H is off).
+ * solve stream: times[0] setup, [1] class H stage, [2] classes A-G, [3] effective
+ * Hamiltonian and lambda, [4] the class-H DF-GEMM kernel alone (0 if class H is off),
+ * [5] the Householder tridiagonalisation kernel summed over its launches, [6] its
+ * algorithmic flops (4/3 m^3 per launch), [7] its number of launches.
  *   times[k] is written for k < *count on input; *count = number of entries on output. */
 int caspt2_get_timings(caspt2_ctx* ctx, double* times, int* count);
 

@@ -19,7 +19,7 @@ using namespace caspt2;
 namespace {
 
 constexpr int kNumStages = 4;  // setup, class H, classes A-G, H^eff
-constexpr int kNumTimes = kNumStages + 1;  // + the class-H GEMM kernel alone
+constexpr int kNumTimes = kNumStages + 4;  // + class-H kernel, tridiagonalisation ms/flops/launches
 
 }  // namespace
 
@@ -63,6 +63,7 @@ struct caspt2_ctx {
   double hEcore = 0.0, hMinDenom = 0.0;
   double times[kNumTimes] = {};
   long launches = 0;
+  KernelTimer tri{};
 
   template <class T>
   int alloc(T** p, size_t count) {
@@ -118,6 +119,8 @@ void caspt2_destroy(caspt2_ctx* ctx) {
     if (e) cudaEventDestroy(e);
   if (ctx->hw.ev_gemm0) cudaEventDestroy(ctx->hw.ev_gemm0);
   if (ctx->hw.ev_gemm1) cudaEventDestroy(ctx->hw.ev_gemm1);
+  if (ctx->tri.e0) cudaEventDestroy(ctx->tri.e0);
+  if (ctx->tri.e1) cudaEventDestroy(ctx->tri.e1);
   cudaSetDevice(cur);
   delete ctx;
 }
@@ -263,7 +266,9 @@ int caspt2_create(caspt2_ctx** out, const caspt2_dims* dims, const caspt2_option
   for (auto& e : c->ev)
     if (st == CASPT2_OK && cudaEventCreate(&e) != cudaSuccess) st = CASPT2_ECUDA;
   if (st == CASPT2_OK && (cudaEventCreate(&c->hw.ev_gemm0) != cudaSuccess ||
-                          cudaEventCreate(&c->hw.ev_gemm1) != cudaSuccess))
+                          cudaEventCreate(&c->hw.ev_gemm1) != cudaSuccess ||
+                          cudaEventCreate(&c->tri.e0) != cudaSuccess ||
+                          cudaEventCreate(&c->tri.e1) != cudaSuccess))
     st = CASPT2_ECUDA;
   if (st != CASPT2_OK) {
     caspt2_destroy(c);
@@ -319,6 +324,8 @@ int caspt2_solve(caspt2_ctx* c, void* stream) {
   const long a2 = (long)d.a * d.a;
   const double big = 1e300;
   const long launches0 = launch_counter();
+  c->tri.ms = c->tri.flops = 0.0;
+  c->tri.launches = 0;
   CASPT2_CUDA_TRY(cudaMemsetAsync(c->status, 0, sizeof(int), s));
   CASPT2_CUDA_TRY(cudaMemcpyAsync(c->mindenom, &big, sizeof(double), cudaMemcpyHostToDevice, s));
   CASPT2_CUDA_TRY(cudaMemsetAsync(c->ecls, 0, sizeof(double) * CASPT2_NCLASS * n * n, s));
@@ -372,7 +379,8 @@ int caspt2_solve(caspt2_ctx* c, void* stream) {
       for (int k = 0; k < 7; ++k) {
         if (!c->cw_on[k]) continue;
         int st = class_solve(c->cw[k], c->sw, d, o.scheme, o.shift, o.ovl_thresh, g, c->fact, c->h,
-                             c->eri_tab, c->E0, c->eps, c->mom + (long)k * msz, c->mindenom, s);
+                             c->eri_tab, c->E0, c->eps, c->mom + (long)k * msz, c->mindenom, s,
+                             &c->tri);
         if (st != CASPT2_OK) return st;
         CASPT2_CUDA_TRY(launch_moments_to_e(c->mom + (long)k * msz, n, c->ecls + (long)k * n * n,
                                             c->ncls + (long)k * n, s));
@@ -420,6 +428,9 @@ int caspt2_solve(caspt2_ctx* c, void* stream) {
     CASPT2_CUDA_TRY(cudaEventElapsedTime(&ms, c->hw.ev_gemm0, c->hw.ev_gemm1));
     c->times[kNumStages] = ms;
   }
+  c->times[kNumStages + 1] = c->tri.ms;
+  c->times[kNumStages + 2] = c->tri.flops;
+  c->times[kNumStages + 3] = (double)c->tri.launches;
   c->launches = launch_counter() - launches0;
   c->solved = true;
   if (hst != 0) return hst;

@@ -523,7 +523,7 @@ cudaError_t class_upload_plans(ClassWork& w, const std::vector<ActPlan>& S,
 int class_solve(ClassWork& w, SectorWork& sw, const Dims& d, int scheme, double shift,
                 double thresh, RdmPtrs rdm, const double* f_act, const double* h,
                 const EriBlocks& eri, const double* E0, const double* eps_cv, double* mom,
-                double* mindenom, cudaStream_t s) {
+                double* mindenom, cudaStream_t s, KernelTimer* tm) {
   const int m = w.m, n = d.n;
   if (w.vsize == 0 || m == 0) return CASPT2_OK;
   const long mm = (long)m * m;
@@ -551,7 +551,7 @@ int class_solve(ClassWork& w, SectorWork& sw, const Dims& d, int scheme, double 
       ++launch_counter();
       k_sector<<<launch_blocks(ms2), 256, 0, s>>>(w.Fact, m, n, sgn, Lsel, sw.Fsec, msec);
       CASPT2_CUDA_TRY(cudaGetLastError());
-      int st = sym_eig(sw.Ssec, msec, sw.s, sw.Qs, sw.jac, s);
+      int st = sym_eig(sw.Ssec, msec, sw.s, sw.Qs, sw.jac, s, tm);
       if (st != CASPT2_OK) return st;
       // number of overlap eigenvalues at or above the threshold (ascending order)
       std::vector<double> hs(msec);
@@ -567,7 +567,7 @@ int class_solve(ClassWork& w, SectorWork& sw, const Dims& d, int scheme, double 
       CASPT2_CUDA_TRY(dgemm(msec, nk, msec, 1.0, sw.Fsec, msec, false, sw.X, nk, false, 0.0,
                             sw.FX, nk, s));
       CASPT2_CUDA_TRY(dgemm(nk, nk, msec, 1.0, sw.X, nk, true, sw.FX, nk, false, 0.0, sw.Ft, nk, s));
-      st = sym_eig(sw.Ft, nk, sw.omega, sw.Qf, sw.jac, s);
+      st = sym_eig(sw.Ft, nk, sw.omega, sw.Qf, sw.jac, s, tm);
       if (st != CASPT2_OK) return st;
       CASPT2_CUDA_TRY(dgemm(msec, nk, nk, 1.0, sw.X, nk, false, sw.Qf, nk, false, 0.0, sw.Y, nk, s));
       const long ncol = ntup * n;

@@ -3,6 +3,7 @@
 #include <vector>
 
 #include "kernels.cuh"
+#include "linalg.cuh"
 #include "terms.h"
 
 namespace caspt2 {
@@ -62,7 +63,7 @@ cudaError_t class_upload_plans(ClassWork& w, const std::vector<ActPlan>& S,
 int class_solve(ClassWork& w, SectorWork& sw, const Dims& d, int scheme, double shift,
                 double thresh, RdmPtrs rdm, const double* f, const double* h, const EriBlocks& eri,
                 const double* E0, const double* eps_cv, double* mom, double* mindenom,
-                cudaStream_t s);
+                cudaStream_t s, KernelTimer* tm = nullptr);
 // e = -M1[L][L][.], norm = M2[L][L] of one class
 cudaError_t launch_moments_to_e(const double* mom, int n, double* e, double* nr, cudaStream_t s);
 // lambda pieces of the target state P of one class from its moments and R

@@ -494,7 +494,8 @@ __global__ void k_zupd(const double* __restrict__ vbuf, int m, int k,
 
 size_t sym_eig_tridiag_work(int m) { return (size_t)m * m * 9 + (size_t)m * 8 + 64; }
 
-int sym_eig_tridiag(double* A, int m, double* w, double* V, double* work, cudaStream_t s) {
+int sym_eig_tridiag(double* A, int m, double* w, double* V, double* work, cudaStream_t s,
+                    KernelTimer* tm) {
   if (m <= 0) return CASPT2_OK;
   const long mm = (long)m * m;
   double* vbuf = work;            // m*m reflectors
@@ -522,11 +523,20 @@ int sym_eig_tridiag(double* A, int m, double* w, double* V, double* work, cudaSt
     CASPT2_CUDA_TRY(cudaMemsetAsync(sync, 0, 4 * sizeof(unsigned), s));
     void* args[] = {&A, (void*)&m, &vbuf, &tau, &d, &e, &p, &sync};
     ++launch_counter();
+    if (tm && tm->e0) CASPT2_CUDA_TRY(cudaEventRecord(tm->e0, s));
     CASPT2_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_tridiag, grid, 512, args, 0, s));
+    if (tm && tm->e1) CASPT2_CUDA_TRY(cudaEventRecord(tm->e1, s));
     int herr = 0;
     CASPT2_CUDA_TRY(cudaMemcpyAsync(&herr, sync + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
     CASPT2_CUDA_TRY(cudaStreamSynchronize(s));
     if (herr != 0) return CASPT2_ETIMEOUT;
+    if (tm && tm->e0) {
+      float ms = 0.f;
+      CASPT2_CUDA_TRY(cudaEventElapsedTime(&ms, tm->e0, tm->e1));
+      tm->ms += ms;
+      tm->flops += 4.0 / 3.0 * (double)m * m * m;   // Householder tridiagonalisation
+      ++tm->launches;
+    }
   } else {
     for (int k = 0; k + 2 < m; ++k) {
       const int n1 = m - k - 1;

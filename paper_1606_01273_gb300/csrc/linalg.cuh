@@ -6,6 +6,14 @@
 
 namespace caspt2 {
 
+// Optional device-time accounting for one kernel (CUDA events on the launching stream).
+struct KernelTimer {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  double ms = 0.0;       // summed device time
+  double flops = 0.0;    // summed algorithmic flops
+  long launches = 0;
+};
+
 // Row-major C = alpha * op(A) op(B) + beta * C, op = transpose when the flag is set.
 // Batched over `batch` with element strides sA, sB, sC.
 cudaError_t dgemm(int M, int N, int K, double alpha, const double* A, int lda, bool ta,
@@ -22,11 +30,13 @@ int sym_eig_jacobi(double* A, int m, double* w, double* V, double* work, cudaStr
 // inverse iteration and back-transformation (eig_tridiag.cu).  A is destroyed; w[m]
 // ascending; V[m][m] eigenvectors as columns.  work >= sym_eig_tridiag_work(m) doubles.
 size_t sym_eig_tridiag_work(int m);
-int sym_eig_tridiag(double* A, int m, double* w, double* V, double* work, cudaStream_t s);
+int sym_eig_tridiag(double* A, int m, double* w, double* V, double* work, cudaStream_t s,
+                    KernelTimer* tm = nullptr);
 
 // Dispatch: Jacobi for small matrices, tridiagonal method otherwise.
-inline int sym_eig(double* A, int m, double* w, double* V, double* work, cudaStream_t s) {
-  return m <= 32 ? sym_eig_jacobi(A, m, w, V, work, s) : sym_eig_tridiag(A, m, w, V, work, s);
+inline int sym_eig(double* A, int m, double* w, double* V, double* work, cudaStream_t s,
+                   KernelTimer* tm = nullptr) {
+  return m <= 32 ? sym_eig_jacobi(A, m, w, V, work, s) : sym_eig_tridiag(A, m, w, V, work, s, tm);
 }
 inline size_t sym_eig_work(int m) {
   return std::max<size_t>((size_t)2 * m * m + 2, sym_eig_tridiag_work(m));
