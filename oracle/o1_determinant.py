@@ -197,6 +197,7 @@ class O1Result:
     b_src: list            # per L: [L'] -> V_L^T H |L'~>
     d1: np.ndarray = None
     D1: np.ndarray = None
+    D1df: np.ndarray = None     # sum_zw D1[x,y,z,w] B[P,z,w]
     d2: np.ndarray = None
     dbar2: np.ndarray = None
     NL: np.ndarray = None
@@ -207,8 +208,8 @@ class O1Result:
 def solve(nclosed: int, nact: int, nvirt: int, nelact: int, f: np.ndarray, B: np.ndarray,
           ci: np.ndarray, det_alpha, det_beta, *, xms: bool = True, scheme: str = "msmr",
           shift: float = 0.0, thresh: float = 1e-9, target: int = 0, enuc: float = 0.0,
-          h: np.ndarray | None = None, densities: bool = True, space: FullSpace | None = None
-          ) -> O1Result:
+          h: np.ndarray | None = None, densities: bool = True, space: FullSpace | None = None,
+          density_classes: str = "ABCDEFGH") -> O1Result:
     nmo = nclosed + nact + nvirt
     n = ci.shape[1]
     eri = np.einsum("Ppq,Prs->pqrs", B, B)
@@ -338,14 +339,21 @@ def solve(nclosed: int, nact: int, nvirt: int, nelact: int, f: np.ndarray, B: np
         sel = [k for k, c in enumerate(cols_all) if scheme == "msmr" or c[2] == L]
         return Vall[:, sel] @ vec
 
-    psi1 = [full(ts[L], L) for L in range(n)]
-    psil = [full(lams[L], L) for L in range(n)]
+    def only(vec, L):
+        # restrict an amplitude vector to the columns of the requested classes
+        sel = [k for k, c in enumerate(cols_all) if scheme == "msmr" or c[2] == L]
+        mask = np.array([cols_all[k][0] in density_classes for k in sel], dtype=float)
+        return vec * mask
+
+    psi1 = [full(only(ts[L], L), L) for L in range(n)]
+    psil = [full(only(lams[L], L), L) for L in range(n)]
     mixP = rot @ R[:, P]                                  # |P>
     psiT = sum(R[L, P] * psi1[L] for L in range(n))       # sum_M T_PM |M~> (mixed amplitudes)
     d1 = space.tdm1(psiT, mixP) + sum(space.tdm1(psil[N], rot[:, N]) for N in range(n))
     D1 = space.tdm2(psiT, mixP) + sum(space.tdm2(psil[N], rot[:, N]) for N in range(n))
     dbar2 = sum(space.tdm1(psil[L], psi1[L]) for L in range(n))
     NL = np.array([psil[L] @ psi1[L] for L in range(n)])
+    res.D1df = np.einsum("xyzw,Pzw->Pxy", D1, B)
     d2 = dbar2.copy()
     act = slice(nclosed, nclosed + nact)
     for L in range(n):

@@ -346,3 +346,251 @@ def class_moments(prob, st, cls, shift=0.0, scheme="msmr", thresh=1e-9, h=None):
                 M2[L] += np.einsum("utn,ut->n", Vt, Vt[:, :, L] / D ** 2)
                 M3[L] += np.sum(Vt[:, :, L] ** 2 / D ** 3)
     return M1, M2, M3
+
+
+def class_amplitudes(prob, st, cls, shift, scheme, R, P, thresh=1e-9, h=None):
+    """T_L and lambda_L (target state P) of class cls in the basis of all index tuples:
+    arrays [L][fam, ext..., act..., M].  Each sector is solved as in class_moments; the
+    sector amplitudes Y amp and Y lam are mapped back to the tuples (a pair (x, y), x < y,
+    takes (T+ + T-)/sqrt2 and its swap (T+ - T-)/sqrt2; x = y takes T+)."""
+    from .o2_rdm import g_of
+    c, a, v, n = prob.nclosed, prob.nact, prob.nvirt, prob.nstate
+    fams, ext, pair, act = CLASS_DEF[cls]
+    sp = _space_of_slot(cls)
+    dims = {"c": c, "a": a, "v": v}
+    nf = len(fams)
+    ext_shape = [dims[sp[e]] for e in ext]
+    T = np.zeros((n, nf) + tuple(ext_shape) + (a,) * len(act) + (n,))
+    Lam = np.zeros_like(T)
+    if any(d_ == 0 for d_ in ext_shape) or a == 0:
+        return T, Lam
+    if h is None:
+        nmo = prob.nmo
+        d = np.zeros((nmo, nmo))
+        d[np.arange(c), np.arange(c)] = 2.0
+        g1 = prob.rdm[1].reshape(n, n, a, a)
+        d[c:c + a, c:c + a] = sum(g1[m, m] for m in range(n)) / n
+        h = prob.f - g_of(prob.B, d)
+    mats = active_matrices(cls, st.rdm, n, a, prob.f[c:c + a, c:c + a])
+    V = sources(cls, st.rdm, n, a, integral_blocks(prob, h))
+    eps = np.diag(prob.f)
+    ec, ev = eps[:c], eps[c + a:]
+    m = nf * a ** len(act) * n
+    S = {k: x_.reshape(m, m) for k, x_ in mats["S"].items()}
+    F = {k: x_.reshape(m, m) for k, x_ in mats["F"].items()}
+    ntot = int(np.prod(ext_shape))
+    grids = np.meshgrid(*[np.arange(r_) for r_ in ext_shape], indexing="ij")
+    tup_all = np.stack([g_.ravel() for g_ in grids], axis=1)
+    eext_all = np.zeros(len(tup_all))
+    for k, e_ in enumerate(ext):
+        eext_all += ev[tup_all[:, k]] if sp[e_] == "v" else -ec[tup_all[:, k]]
+    Vflat = V.reshape((nf, ntot, a ** len(act), n, n))
+    Tf = np.zeros((n, nf, ntot, a ** len(act), n))
+    Lf = np.zeros_like(Tf)
+    r = R[:, P]
+    sectors = [("+", 1.0), ("-", -1.0)] if pair is not None else [("id", 0.0)]
+    for name, sgn in sectors:
+        if pair is None:
+            Ssec, Fsec = S["id"], F["id"]
+            sel = np.arange(ntot)
+            partner = sel
+            vmat = Vflat[:, sel]
+        else:
+            Ssec, Fsec = S["id"] + sgn * S["sw"], F["id"] + sgn * F["sw"]
+            pi_, pj_ = ext.index(pair[0]), ext.index(pair[1])
+            ti, tj = tup_all[:, pi_], tup_all[:, pj_]
+            sel = np.nonzero((ti < tj) if name == "-" else (ti <= tj))[0]
+            swp = tup_all[sel].copy()
+            swp[:, [pi_, pj_]] = swp[:, [pj_, pi_]]
+            partner = np.ravel_multi_index(tuple(swp.T), ext_shape)
+            v1, v2 = Vflat[:, sel], Vflat[:, partner]
+            diag = (ti[sel] == tj[sel])[None, :, None, None, None]
+            vmat = np.where(diag, v1, (v1 + sgn * v2) / np.sqrt(2.0))
+        Ssec = 0.5 * (Ssec + Ssec.T)
+        Fsec = 0.5 * (Fsec + Fsec.T)
+        ee = eext_all[sel]
+        Vm = np.moveaxis(vmat, 1, 3).reshape(m, len(sel), n)
+        isdiag = np.zeros(len(sel), dtype=bool) if pair is None else (partner == sel)
+        for Lsel in (range(n) if scheme == "sssr" else [None]):
+            keep_idx = np.arange(m) if Lsel is None else np.arange(Lsel, m, n)
+            Ss = Ssec[np.ix_(keep_idx, keep_idx)]
+            Fs = Fsec[np.ix_(keep_idx, keep_idx)]
+            s_, q_ = np.linalg.eigh(Ss)
+            keep = s_ >= thresh
+            if not keep.any() or len(sel) == 0:
+                continue
+            X = q_[:, keep] / np.sqrt(s_[keep])
+            om, Q = np.linalg.eigh(X.T @ Fs @ X)
+            Y = X @ Q
+            Vt = np.einsum("ku,ktl->utl", Y, Vm[keep_idx])
+            for L in (range(n) if Lsel is None else [Lsel]):
+                D = ee[None, :] + om[:, None] - st.E0[L] + shift
+                amp = -Vt[:, :, L] / D
+                src = r[L] * np.einsum("n,utn->ut", r, Vt) - 2.0 * shift * r[L] ** 2 * amp
+                lam = -src / D
+                tsec, lsec = Y @ amp, Y @ lam          # [rows(keep_idx), sel]
+                full_t = np.zeros((m, len(sel)))
+                full_l = np.zeros((m, len(sel)))
+                full_t[keep_idx], full_l[keep_idx] = tsec, lsec
+                # rows (fam, act, M) -> [fam, act, M]
+                ft = full_t.reshape(nf, a ** len(act), n, len(sel))
+                fl = full_l.reshape(nf, a ** len(act), n, len(sel))
+                if pair is None:
+                    Tf[L][:, sel] += np.moveaxis(ft, 3, 1)
+                    Lf[L][:, sel] += np.moveaxis(fl, 3, 1)
+                else:
+                    w1 = np.where(isdiag, 1.0, 1.0 / np.sqrt(2.0))
+                    w2 = np.where(isdiag, 0.0, sgn / np.sqrt(2.0))
+                    for arr, src_ in ((Tf, ft), (Lf, fl)):
+                        arr[L][:, sel] += np.moveaxis(src_ * w1, 3, 1)
+                        np.add.at(arr[L], (slice(None), partner),
+                                  np.moveaxis(src_ * w2, 3, 1))
+    T = Tf.reshape((n, nf) + tuple(ext_shape) + (a,) * len(act) + (n,))
+    Lam = Lf.reshape(T.shape)
+    return T, Lam
+
+
+def class_densities(prob, st, cls, shift, scheme, R, P, thresh=1e-9):
+    """Class cls's share of the correlated densities of target state P (Sec. II.D):
+      d1[x, y]     = sum W <M~|E_Omega^dag E_xy|L'~>,  W = R_L'P sum_L R_LP T_L + lambda_L'
+      GDF[Q, x, y] = d/dB_Qxy of sum W <M~|E_Omega^dag H_2|L'~>  (= sum_zw D1_xy,zw B_Qzw)
+      d2[x, y]     = d L_PT2 / d f_xy on the closed-closed, active-active and virtual-virtual
+                     blocks (the closed-vacuum normal-ordered f^), with the E0 term
+      NL[L]        = <lambda_L|S|T_L>."""
+    from .o2_rdm import g_of
+    c, a, v, n, nmo = prob.nclosed, prob.nact, prob.nvirt, prob.nstate, prob.nmo
+    fams, ext, pair, act = CLASS_DEF[cls]
+    sp = _space_of_slot(cls)
+    d1 = np.zeros((nmo, nmo))
+    GDF = np.zeros_like(prob.B)
+    d2 = np.zeros((nmo, nmo))
+    NL = np.zeros(n)
+    dims = {"c": c, "a": a, "v": v}
+    if any(dims[sp[e]] == 0 for e in ext) or a == 0:
+        return d1, GDF, d2, NL
+    d = np.zeros((nmo, nmo))
+    d[np.arange(c), np.arange(c)] = 2.0
+    g1 = prob.rdm[1].reshape(n, n, a, a)
+    d[c:c + a, c:c + a] = sum(g1[m_, m_] for m_ in range(n)) / n
+    h = prob.f - g_of(prob.B, d)
+    T, Lam = class_amplitudes(prob, st, cls, shift, scheme, R, P, thresh, h)
+    r = R[:, P]
+    nf = len(fams)
+    # W[fam, ext..., act..., M, L'] (the source contraction pairs M with the bra and L' with the ket)
+    W = (np.einsum("l,k,l...->...k", r, r, T) + np.moveaxis(Lam, 0, -1))
+    off = {"c": 0, "a": c, "v": c + a}
+    rng = {s_: slice(off[s_], off[s_] + dims[s_]) for s_ in "cav"}
+    blocks = integral_blocks(prob, h)
+    for fb in range(nf):
+        for kind, spc, w, t in source_terms(cls, fb):
+            L_ = _Letters()
+            subs, opnds = [], []
+            subs.append("".join(L_(e_ + "_b") for e_ in ext) + "".join(L_(s_ + "_b") for s_ in act) + "MN")
+            opnds.append(W[fb])
+            k = len(t.rdm)
+            if k == 0:
+                subs.append("MN")
+                opnds.append(np.eye(n))
+            else:
+                subs.append("MN" + "".join(L_(p_) + L_(q_) for p_, q_ in t.rdm))
+                opnds.append(st.rdm[k])
+            lab_space = {"p": spc[0], "q": spc[1]} if kind == "h" else dict(zip("pqrt", spc))
+            for s_ in sp:
+                lab_space[s_ + "_b"] = sp[s_]
+            for x_, y_ in t.deltas:
+                subs.append(L_(x_) + L_(y_))
+                opnds.append(np.eye(dims[lab_space[x_]]))
+            if kind == "h":
+                out = L_("p") + L_("q")
+                val = np.einsum(",".join(subs) + "->" + out, *opnds, optimize=True)
+                d1[rng[spc[0]], rng[spc[1]]] += w * t.coeff * val
+            else:
+                out = L_("p") + L_("q") + L_("r") + L_("t")
+                G = w * t.coeff * np.einsum(",".join(subs) + "->" + out, *opnds, optimize=True)
+                B1 = prob.B[:, rng[spc[0]], rng[spc[1]]]
+                B2 = prob.B[:, rng[spc[2]], rng[spc[3]]]
+                GDF[:, rng[spc[0]], rng[spc[1]]] += np.einsum("pqrt,Qrt->Qpq", G, B2)
+                GDF[:, rng[spc[2]], rng[spc[3]]] += np.einsum("pqrt,Qpq->Qrt", G, B1)
+    # overlap-metric contractions
+    mats = active_matrices(cls, st.rdm, n, a, None)["S"]
+    m = nf * a ** len(act) * n
+    next_ = len(ext)
+    ax_ext = list(range(2, 2 + next_))                 # ext axes of T[L] arrays (after L, fam)
+
+    def apply_S(Spi, arr):   # arr [L][fam, ext..., act..., M] -> S applied over (fam, act, M)
+        Sm = Spi.reshape(m, m)
+        ext_axes = list(range(2, 2 + next_))
+        x_ = np.moveaxis(arr, ext_axes, list(range(1, 1 + next_)))   # [L, ext..., fam, act..., M]
+        shp = x_.shape
+        y_ = (x_.reshape(shp[:1 + next_] + (m,)) @ Sm.T).reshape(shp)
+        return np.moveaxis(y_, list(range(1, 1 + next_)), ext_axes)
+
+    def swap_pair(arr):
+        if pair is None:
+            return arr
+        i_, j_ = ext.index(pair[0]), ext.index(pair[1])
+        return np.swapaxes(arr, 2 + i_, 2 + j_)
+
+    U = {"id": apply_S(mats["id"], T), "sw": apply_S(mats["sw"], T)}
+    ax = tuple(range(1, T.ndim))
+    NL = np.sum(Lam * U["id"], axis=ax)
+    if pair is not None:
+        NL = NL + np.sum(Lam * swap_pair(U["sw"]), axis=ax)
+    # external blocks: one slot of the ket tuple moves (hole for closed, particle for virtual)
+    letters = "abcdefghijk"
+    for si, s_ in enumerate(ext):
+        blk = sp[s_]
+        for pi_name, Lm in (("id", Lam), ("sw", swap_pair(Lam) if pair is not None else None)):
+            if Lm is None:
+                continue
+            rank = Lm.ndim
+            sl = list(letters[:rank])
+            su = list(sl)
+            sl[2 + si] = "x"
+            su[2 + si] = "y"
+            X = np.einsum("".join(sl) + "," + "".join(su) + "->xy", Lm, U[pi_name])
+            if blk == "c":
+                d2[rng["c"], rng["c"]] -= X.T        # d2[i][j] = -sum lam(s=j) S T(s=i)
+            else:
+                d2[rng["v"], rng["v"]] += X          # d2[a][b] = +sum lam(s=a) S T(s=b)
+    # active block: lambda x T contracted with the Fock-type terms (E_uw between IC functions)
+    Dm = {}
+    for pi_name in ("id", "sw"):
+        Tp = T if pi_name == "id" else swap_pair(T)
+        if pi_name == "sw" and pair is None:
+            continue
+        nb = 2 + next_
+        sl = "L" + "f" + "".join("e" + str(k) for k in range(next_))
+        # einsum over L and ext: rows (fam_b, act_b, M), cols (fam_k, act_k, N)
+        A_ = Lam.reshape((n, nf, -1, a ** len(act) * n))
+        B_ = Tp.reshape((n, nf, -1, a ** len(act) * n))
+        Dm[pi_name] = np.einsum("lfer,lgec->frgc", A_, B_).reshape(
+            (nf,) + (a,) * len(act) + (n,) + (nf,) + (a,) * len(act) + (n,))
+    for fb in range(nf):
+        for fk in range(nf):
+            for t in overlap_terms(cls, fb, fk, True):
+                pi = _ext_perm(cls, t.deltas)
+                if pi not in Dm:
+                    continue
+                L_ = _Letters()
+                subs, opnds = [], []
+                subs.append("".join(L_(s_ + "_b") for s_ in act) + "M" + "".join(L_(s_ + "_k") for s_ in act) + "N")
+                opnds.append(Dm[pi][(fb,) + (slice(None),) * (len(act) + 1) + (fk,)])
+                k = len(t.rdm)
+                if k == 0:
+                    subs.append("MN")
+                    opnds.append(np.eye(n))
+                else:
+                    subs.append("MN" + "".join(L_(p_) + L_(q_) for p_, q_ in t.rdm))
+                    opnds.append(st.rdm[k])
+                for x_, y_ in t.deltas:
+                    if x_[:-2] in ext and (x_.endswith("_b") or x_.endswith("_k")):
+                        continue
+                    subs.append(L_(x_) + L_(y_))
+                    opnds.append(np.eye(a))
+                val = np.einsum(",".join(subs) + "->" + L_("u") + L_("w"), *opnds, optimize=True)
+                d2[rng["a"], rng["a"]] += t.coeff * val
+    g1r = st.rdm[1]
+    for L in range(n):
+        d2[rng["a"], rng["a"]] -= NL[L] * g1r[L, L]
+    return d1, GDF, d2, NL

@@ -158,3 +158,78 @@ def heff(st: Setup, parts: dict, shift: float):
         H += 0.5 * (e + e.T) - shift * np.diag(nr)
     w, R = np.linalg.eigh(0.5 * (H + H.T))
     return H, w, _canon(R)
+
+
+def class_h_densities(prob, st: Setup, R: np.ndarray, P: int, shift: float = 0.0,
+                      scheme: str = "msmr"):
+    """Class E_ai,bj share of the densities of target state P (Sec. II.D).
+
+    In the eigenbasis nu of U^T Fref U the first-order functions of state L are closed-shell
+    pair functions |Psi(t)> = 1/2 sum t_ij^ab E_ai E_bj |0> times |nu> = sum_N W_Nnu |N~>, with
+      t(L, nu)   = -W_Lnu K / D,                      D = e_a + e_b - e_i - e_j + omega_nu - E0_L + E_s
+      lam(L, nu) = -[R_LP c_nu + 2 E_s R_LP^2 W_Lnu / D] K / D,   c_nu = sum_N R_NP W_Nnu
+    (under SS-SR only nu = L with W = 1 and D = e_a + e_b - e_i - e_j + E_s).  For two pair
+    functions <Psi(l)|E_ab|Psi(t)> = 2 sum_ijc l_ij^ac (2 t_ij^bc - t_ij^cb),
+    <Psi(l)|E_ij - 2 delta_ij|Psi(t)> = -2 sum_kab l_jk^ab (2 t_ik^ab - t_ik^ba),
+    <Psi(l)|Psi(t)> = sum l (2t - t'), and the source functional sum w (2K - K') gives
+    GDF[Q][a][i] = 2 sum_jb (2 w_ij^ab - w_ij^ba) B_Qbj with w the reference-projected
+    combination R_L'P sum_L R_LP t + lam over the component along |L'~>.
+    The active block of d2 pairs nu and nu' through <nu|E_rs|nu'> and carries -N_L <L~|E_rs|L~>.
+    Returns (d2 closed, active and virtual blocks, GDF, NL)."""
+    c, a, v, n, nmo = prob.nclosed, prob.nact, prob.nvirt, prob.nstate, prob.nmo
+    d2 = np.zeros((nmo, nmo))
+    GDF = np.zeros_like(prob.B)
+    NL = np.zeros(n)
+    if c == 0 or v == 0:
+        return d2, GDF, NL
+    vo = c + a
+    eps = np.diag(prob.f)
+    ec, ev = eps[:c], eps[vo:]
+    X = prob.B.shape[0]
+    Bcv = np.ascontiguousarray(prob.B[:, :c, vo:])          # [Q, i, a] = B_Q,ia = B_Q,ai
+    K = np.einsum("Qia,Qjb->ijab", Bcv, Bcv)                  # (ai|bj)
+    D0 = (ev[None, None, :, None] + ev[None, None, None, :]
+          - ec[:, None, None, None] - ec[None, :, None, None])
+    r = R[:, P]
+    if scheme == "sssr":
+        W = np.eye(n)
+        shifts = lambda nu, L: shift
+        pairs = [(L, L) for L in range(n)]
+    else:
+        omega, W = np.linalg.eigh(0.5 * (st.Ftil + st.Ftil.T))
+        shifts = lambda nu, L: omega[nu] - st.E0[L] + shift
+        pairs = [(L, nu) for L in range(n) for nu in range(n)]
+    cnu = W.T @ r
+    wsum = np.zeros_like(K)
+    # active block: E_rs acts on |nu>, coupling nu and nu' of the same state L
+    g1nu = np.einsum("mu,nw,mnrs->uwrs", W, W, st.rdm[1])      # <nu|E_rs|nu'>
+    if scheme != "sssr":
+        for L in range(n):
+            for nu in range(n):
+                Dl = D0 + shifts(nu, L)
+                lam = (r[L] * cnu[nu] + 2.0 * shift * r[L] ** 2 * W[L, nu] / Dl) * (-K / Dl)
+                for nu2 in range(n):
+                    Dt = D0 + shifts(nu2, L)
+                    t = W[L, nu2] * (-K / Dt)
+                    ov = np.sum(lam * (2.0 * t - t.transpose(0, 1, 3, 2)))
+                    d2[c:vo, c:vo] += ov * g1nu[nu, nu2]
+    for L, nu in pairs:
+        D = D0 + shifts(nu, L)
+        u = -K / D
+        t = W[L, nu] * u
+        lam = (r[L] * cnu[nu] + 2.0 * shift * r[L] ** 2 * W[L, nu] / D) * u
+        tt = 2.0 * t - t.transpose(0, 1, 3, 2)
+        NL[L] += np.sum(lam * tt)
+        d2[vo:, vo:] += 2.0 * np.einsum("ijac,ijbc->ab", lam, tt)
+        d2[:c, :c] -= 2.0 * np.einsum("jkab,ikab->ij", lam, tt)
+        # component along |L'~> of the IC amplitude: sum_nu W_L'nu (amplitude at nu)
+        for Lp in range(n):
+            if scheme == "sssr" and Lp != L:
+                continue
+            wsum += W[Lp, nu] * (r[Lp] * r[L] * t + (lam if Lp == L else 0.0))
+    if scheme != "sssr":   # under SS-SR <lam_L|E_rs|T_L> = N_L <L~|E_rs|L~> cancels the E0 term
+        for L in range(n):
+            d2[c:vo, c:vo] -= NL[L] * st.rdm[1][L, L]
+    # the lambda term pairs lambda_L' with reference L' only (Sec. II.D d(1)/D(1) definition)
+    GDF[:, vo:, :c] = 2.0 * np.einsum("ijab,Qjb->Qai", 2.0 * wsum - wsum.transpose(0, 1, 3, 2), Bcv)
+    return d2, GDF, NL

@@ -108,3 +108,64 @@ def test_lambda_pieces_match_o1(cprob, xms, scheme, shift):
             for Lp in range(n):
                 ref = lam @ r.b_src[L][Lp][idx]
                 assert abs(lv[L, Lp] - ref) <= 1e-10 * max(1.0, abs(ref)), cls
+
+
+def _o2_state(p, xms, scheme, shift):
+    from oracle import o2_classes as oc
+    st = o2.setup(p, xms=xms, kmax=4)
+    mom = oc.all_moments(p, st, shift=shift, scheme=scheme)
+    parts = {c: (-np.einsum("llk->lk", M1), np.diagonal(M2).copy()) for c, (M1, M2, M3) in mom.items()}
+    H, w, R = o2.heff(st, parts, shift)
+    return st, R
+
+
+def _o2_densities(p, st, R, shift, scheme, classes="ABCDEFGH"):
+    from oracle import o2_classes as oc
+    nmo = p.nmo
+    d1, G, d2, NL = np.zeros((nmo, nmo)), np.zeros_like(p.B), np.zeros((nmo, nmo)), np.zeros(p.nstate)
+    for cls in classes:
+        if cls == "H":
+            a2, b2, c2 = o2.class_h_densities(p, st, R, 0, shift, scheme)
+            d2 += a2; G += b2; NL += c2
+        else:
+            a1, b1, c1, e1 = oc.class_densities(p, st, cls, shift, scheme, R, 0)
+            d1 += a1; G += b1; d2 += c1; NL += e1
+    return d1, G, d2, NL
+
+
+def _diag_blocks(p, x):
+    c, a = p.nclosed, p.nact
+    m = np.zeros_like(x)
+    m[:c, :c] = 1
+    m[c:c + a, c:c + a] = 1
+    m[c + a:, c + a:] = 1
+    return x * m
+
+
+@pytest.mark.parametrize("xms,scheme,shift", [(True, "msmr", 0.2), (False, "sssr", 0.1)])
+def test_class_densities_match_o1(xms, scheme, shift):
+    """Each class's share of d(1), D(1).B, N_L and the closed/active/virtual blocks of d(2)
+    (Sec. II.D) equals O1's densities built from that class's amplitudes alone."""
+    p = make_problem(**CLASS_CASES[0])
+    st, R = _o2_state(p, xms, scheme, shift)
+    for cls in "ABCDEFGH":
+        r = o1.solve_problem(p, xms=xms, scheme=scheme, shift=shift, density_classes=cls)
+        d1, G, d2, NL = _o2_densities(p, st, R, shift, scheme, cls)
+        assert np.abs(d1 - r.d1).max() < 1e-12, cls
+        assert np.abs(G - r.D1df).max() < 1e-12, cls
+        assert np.abs(_diag_blocks(p, d2 - r.d2)).max() < 1e-12, cls
+        assert np.abs(NL - r.NL).max() < 1e-12, cls
+
+
+@pytest.mark.parametrize("xms,scheme,shift", [(True, "msmr", 0.2), (False, "msmr", 0.0),
+                                              (True, "sssr", 0.1)])
+def test_total_densities_match_o1(cprob, xms, scheme, shift):
+    """Sum over classes: d(1), D(1).B and N_L equal O1 (FD-validated) exactly; d(2) on its
+    closed, active and virtual blocks."""
+    st, R = _o2_state(cprob, xms, scheme, shift)
+    r = o1.solve_problem(cprob, xms=xms, scheme=scheme, shift=shift)
+    d1, G, d2, NL = _o2_densities(cprob, st, R, shift, scheme)
+    assert np.abs(d1 - r.d1).max() < 1e-11
+    assert np.abs(G - r.D1df).max() < 1e-11
+    assert np.abs(_diag_blocks(cprob, d2 - r.d2)).max() < 1e-11
+    assert np.abs(NL - r.NL).max() < 1e-11
