@@ -122,9 +122,38 @@ int caspt2_get_core_energy(caspt2_ctx* ctx, double* ecore);
  * solve stream: times[0] setup, [1] class H stage, [2] classes A-G, [3] effective
  * Hamiltonian and lambda, [4] the class-H DF-GEMM kernel alone (0 if class H is off),
  * [5] the Householder tridiagonalisation kernel summed over its launches, [6] its
- * algorithmic flops (4/3 m^3 per launch), [7] its number of launches.
+ * algorithmic flops (4/3 m^3 per launch), [7] its number of launches, [8] the last
+ * caspt2_densities call (0 before one).
  *   times[k] is written for k < *count on input; *count = number of entries on output. */
 int caspt2_get_timings(caspt2_ctx* ctx, double* times, int* count);
+
+/* Correlated densities of the target state P = opt.target_state (Sec. II.D: the
+ * derivatives of the Lagrangian L = sum_LL' R_LP R_L'P Heff_LL' + sum <lambda|..> at the
+ * converged amplitudes and lambda), computed on the device for the classes in
+ * class_mask (a subset of the solved classes; CASPT2_CLASS_* bits), summed over them:
+ *   d1[p][q]      derivative of the source terms <Omega|H|L'~> with respect to the
+ *                 one-electron operator h (h = f minus the core and state-averaged active
+ *                 mean fields, Sec. II.F) — classes A-G;
+ *   d2[p][q]      derivative with respect to the Fock matrix f on the closed-closed,
+ *                 active-active and virtual-virtual blocks (the blocks that the
+ *                 block-diagonal f of the solve carries; other blocks are zero), including
+ *                 the E0 dependence of the denominators (-N_L <L~|E_pq|L~>);
+ *   gdf[Q][p][q]  derivative with respect to the DF factors B[Q][p][q] of the two-electron
+ *                 source terms (D(1) contracted with B, Sec. II.D DF form).
+ * All three are returned symmetrised (x + x^T)/2 per matrix: the integrals are
+ * symmetric, so only the symmetric part enters a gradient.
+ * Call after a successful (or WINTRUDER) caspt2_solve with target_state >= 0; runs on
+ * cuda_stream (NULL = default stream) and synchronises it.  The first call allocates
+ * the density work space (about 6 x the largest class's amplitude array plus 3 (c v)^2
+ * doubles for class H).  Errors: EINVAL (mask outside the solved classes, target_state
+ * < 0, nact > 16), ESTATE (no solve), ENOMEM, ECUDA. */
+int caspt2_densities(caspt2_ctx* ctx, unsigned class_mask, void* cuda_stream);
+
+/* Copy the densities of the last caspt2_densities call: d1 and d2 [nmo][nmo], gdf
+ * [naux][nmo][nmo] (the layout of the dfB input), to host (mem = CASPT2_MEM_HOST) or
+ * device (CASPT2_MEM_DEVICE) buffers owned by the caller.  Any pointer may be NULL.
+ * Errors: EINVAL, ESTATE (no densities computed since the last solve). */
+int caspt2_get_densities(caspt2_ctx* ctx, int mem, double* d1, double* d2, double* gdf);
 
 /* Number of CUDA kernels the library launched during the last solve (-1 if ctx is NULL). */
 long caspt2_get_kernel_launches(caspt2_ctx* ctx);

@@ -63,6 +63,8 @@ def lib():
         L.caspt2_supported_classes.restype = C.c_uint
         L.caspt2_destroy.argtypes = [P]
         L.caspt2_destroy.restype = None
+        L.caspt2_densities.argtypes = [P, C.c_uint, P]
+        L.caspt2_get_densities.argtypes = [P, C.c_int, P, P, P]
         L.caspt2_classH_noalloc.argtypes = [C.POINTER(Dims), C.POINTER(Options), P, P, P, P, P, P]
         L.caspt2_strerror.argtypes = [C.c_int]
         L.caspt2_strerror.restype = C.c_char_p
@@ -127,6 +129,9 @@ class Result:
     launches: int
     lam_NL: dict = None
     lam_lv: dict = None
+    d1: np.ndarray = None
+    d2: np.ndarray = None
+    gdf: np.ndarray = None
 
 
 class Context:
@@ -184,12 +189,27 @@ class Context:
                     _check(lib().caspt2_get_class_lambda(self._h, k, _dp(a_), _dp(b_)),
                            "caspt2_get_class_lambda")
                     lam_NL[name], lam_lv[name] = a_, b_
-        t = np.zeros(8)
-        cnt = C.c_int(8)
+        t = np.zeros(9)
+        cnt = C.c_int(9)
         _check(lib().caspt2_get_timings(self._h, _dp(t), C.byref(cnt)), "caspt2_get_timings")
         return Result(U, E0, Href, Heff, Ems, R, ec.value, e_cls, n_cls, status,
                       list(t[: cnt.value]), int(lib().caspt2_get_kernel_launches(self._h)),
                       lam_NL, lam_lv)
+
+
+    def densities(self, class_mask=None, stream=None):
+        """caspt2_densities for the classes in class_mask (default: all solved classes);
+        returns host copies (d1, d2, gdf), each symmetrised."""
+        mask = self.opts.class_mask if class_mask is None else class_mask
+        s = C.c_void_p(stream) if stream is not None else None
+        _check(lib().caspt2_densities(self._h, mask, s), "caspt2_densities")
+        nmo = self.dims.nclosed + self.dims.nact + self.dims.nvirt
+        d1, d2 = np.zeros((nmo, nmo)), np.zeros((nmo, nmo))
+        gdf = np.zeros((self.dims.naux, nmo, nmo))
+        _check(lib().caspt2_get_densities(self._h, MEM_HOST, C.c_void_p(d1.ctypes.data),
+                                          C.c_void_p(d2.ctypes.data), C.c_void_p(gdf.ctypes.data)),
+               "caspt2_get_densities")
+        return d1, d2, gdf
 
 
 def classH_noalloc(dims: Dims, opts: Options, fock, dfB, rdm1, e, norm, stream=None) -> int:
@@ -214,12 +234,19 @@ def problem_inputs(prob, kmax: int = 4):
     return (np.ascontiguousarray(prob.f), np.ascontiguousarray(prob.B), *r)
 
 
-def solve_problem(prob, **opts) -> Result:
-    """Create a context, copy a synth.Problem from host memory, solve, fetch results."""
+def solve_problem(prob, densities=None, **opts) -> Result:
+    """Create a context, copy a synth.Problem from host memory, solve, fetch results.
+    densities: a class mask (or True for all solved classes) to also compute the
+    densities of opts' target_state."""
     ctx = Context(prob.nclosed, prob.nact, prob.nvirt, prob.naux, prob.nstate, **opts)
     try:
         ctx.set_inputs(*problem_inputs(prob))
         st = ctx.solve()
-        return ctx.result(st)
+        r = ctx.result(st)
+        if densities is not None and densities is not False:
+            mask = None if densities is True else int(densities)
+            r.d1, r.d2, r.gdf = ctx.densities(mask)
+            r.timings_ms = ctx.result(st).timings_ms
+        return r
     finally:
         ctx.close()

@@ -19,7 +19,8 @@ using namespace caspt2;
 namespace {
 
 constexpr int kNumStages = 4;  // setup, class H, classes A-G, H^eff
-constexpr int kNumTimes = kNumStages + 4;  // + class-H kernel, tridiagonalisation ms/flops/launches
+constexpr int kNumTimes = kNumStages + 5;  // + class-H kernel, tridiagonalisation ms/flops/launches,
+                                           //   densities
 
 }  // namespace
 
@@ -53,6 +54,15 @@ struct caspt2_ctx {
   double *pack0 = nullptr, *pack1 = nullptr;
   std::map<int, double*> eri_blk;     // canonical space key -> (pq|rt) block
   EriBlocks eri_tab{};
+  long wmax = 0, m2max = 0, packmax = 0;
+  // densities (allocated on the first caspt2_densities call)
+  bool dens_alloc = false, dens_done = false;
+  DensWork dw{};
+  HDensWork hd{};
+  std::map<int, double*> gblk;        // adjoint (pq|rt) blocks, keys of eri_blk
+  EriBlocks g_tab{};
+  double *dd1 = nullptr, *dd2 = nullptr, *dgdf = nullptr, *gtmp = nullptr;
+  cudaEvent_t dev0 = nullptr, dev1 = nullptr;
   // results
   double *heff = nullptr, *ems = nullptr, *R = nullptr;
   int* status = nullptr;
@@ -120,6 +130,8 @@ void caspt2_destroy(caspt2_ctx* ctx) {
   if (ctx->hw.ev_gemm0) cudaEventDestroy(ctx->hw.ev_gemm0);
   if (ctx->hw.ev_gemm1) cudaEventDestroy(ctx->hw.ev_gemm1);
   if (ctx->tri.e0) cudaEventDestroy(ctx->tri.e0);
+  if (ctx->dev0) cudaEventDestroy(ctx->dev0);
+  if (ctx->dev1) cudaEventDestroy(ctx->dev1);
   if (ctx->tri.e1) cudaEventDestroy(ctx->tri.e1);
   cudaSetDevice(cur);
   delete ctx;
@@ -227,18 +239,29 @@ int caspt2_create(caspt2_ctx** out, const caspt2_dims* dims, const caspt2_option
       ALLOC(w.Sact, 2 * (size_t)w.m * w.m);
       ALLOC(w.Fact, 2 * (size_t)w.m * w.m);
       ALLOC(w.V, (size_t)w.vsize);
+      // sector bases kept for the densities
+      class_keep_layout(w, d, o.scheme);
+      for (SectorKeep& K : w.keep) {
+        if (K.ntup == 0) continue;
+        ALLOC(K.Y, (size_t)K.msec * K.msec);
+        ALLOC(K.omega, (size_t)K.msec);
+        ALLOC(K.Vt, (size_t)K.msec * K.ntup * n);
+      }
       m2max = std::max(m2max, (long)w.m * w.m);
       long ps = 0;
       wmax = std::max(wmax, class_sector_wsize(w, d, o.scheme, &ps));
       pmax = std::max(pmax, ps);
     }
+    c->wmax = wmax;
+    c->m2max = m2max;
+    c->packmax = packmax;
     if (m2max > 0) {
       SectorWork& q = c->sw;
       const long mx = (long)std::sqrt((double)m2max) + 1;
       ALLOC(q.Ssec, m2max); ALLOC(q.Fsec, m2max); ALLOC(q.s, mx); ALLOC(q.Qs, m2max);
-      ALLOC(q.X, m2max); ALLOC(q.FX, m2max); ALLOC(q.Ft, m2max); ALLOC(q.omega, mx);
-      ALLOC(q.Qf, m2max); ALLOC(q.Y, m2max); ALLOC(q.mask, mx); ALLOC(q.jac, sym_eig_work((int)mx));
-      ALLOC(q.W, wmax); ALLOC(q.Vt, wmax); ALLOC(q.part, pmax); ALLOC(q.partn, pmax);
+      ALLOC(q.X, m2max); ALLOC(q.FX, m2max); ALLOC(q.Ft, m2max);
+      ALLOC(q.Qf, m2max); ALLOC(q.jac, sym_eig_work((int)mx));
+      ALLOC(q.W, wmax); ALLOC(q.part, pmax);
       ALLOC(c->h, nmo * nmo);
       ALLOC(c->fact, a2);
       ALLOC(c->eps, nmo);
@@ -268,7 +291,9 @@ int caspt2_create(caspt2_ctx** out, const caspt2_dims* dims, const caspt2_option
   if (st == CASPT2_OK && (cudaEventCreate(&c->hw.ev_gemm0) != cudaSuccess ||
                           cudaEventCreate(&c->hw.ev_gemm1) != cudaSuccess ||
                           cudaEventCreate(&c->tri.e0) != cudaSuccess ||
-                          cudaEventCreate(&c->tri.e1) != cudaSuccess))
+                          cudaEventCreate(&c->tri.e1) != cudaSuccess ||
+                          cudaEventCreate(&c->dev0) != cudaSuccess ||
+                          cudaEventCreate(&c->dev1) != cudaSuccess))
     st = CASPT2_ECUDA;
   if (st != CASPT2_OK) {
     caspt2_destroy(c);
@@ -431,8 +456,10 @@ int caspt2_solve(caspt2_ctx* c, void* stream) {
   c->times[kNumStages + 1] = c->tri.ms;
   c->times[kNumStages + 2] = c->tri.flops;
   c->times[kNumStages + 3] = (double)c->tri.launches;
+  c->times[kNumStages + 4] = 0.0;
   c->launches = launch_counter() - launches0;
   c->solved = true;
+  c->dens_done = false;
   if (hst != 0) return hst;
   for (double x : c->hEms)
     if (!(x == x) || x > 1e300 || x < -1e300) return CASPT2_ENAN;
@@ -490,5 +517,150 @@ int caspt2_get_timings(caspt2_ctx* c, double* times, int* count) {
 }
 
 long caspt2_get_kernel_launches(caspt2_ctx* c) { return c ? c->launches : -1; }
+
+}  // extern "C"
+
+namespace {
+
+// Device work space of the densities, sized from the solved classes.
+int alloc_densities(caspt2_ctx* c) {
+  const Dims& d = c->d;
+  const size_t nmo = d.nmo(), n = d.n;
+  int st = CASPT2_OK;
+#define ALLOC(ptr, cnt) \
+  if (st == CASPT2_OK) st = c->alloc(&(ptr), (cnt))
+  ALLOC(c->dd1, nmo * nmo);
+  ALLOC(c->dd2, nmo * nmo);
+  ALLOC(c->dgdf, (size_t)d.X * nmo * nmo);
+  long tall = 0;
+  for (int k = 0; k < 7; ++k)
+    if (c->cw_on[k]) tall = std::max(tall, class_dens_tall(c->cw[k], d));
+  const bool h_on = (c->opt.class_mask >> CASPT2_CLASS_H & 1u) && d.c > 0 && d.v > 0;
+  long partmax = std::max<long>(kDensPartMax, 4 * c->m2max);
+  if (h_on) {
+    partmax = std::max<long>(partmax, (long)d.v * d.v);
+    partmax = std::max<long>(partmax, 2L * 64 * (long)n * n * n);
+  }
+  partmax = std::max<long>(partmax, 152L * 4 * 256);
+  ALLOC(c->dw.part, (size_t)partmax);
+  c->dw.partmax = partmax;
+  if (tall > 0) {
+    DensWork& w = c->dw;
+    w.tall = tall;
+    w.secmax = std::max<long>(c->wmax, 1);
+    ALLOC(w.T, (size_t)tall);
+    ALLOC(w.Lam, (size_t)tall);
+    ALLOC(w.U1, (size_t)tall);
+    ALLOC(w.U2, (size_t)tall);
+    ALLOC(w.Tsw, (size_t)tall);
+    ALLOC(w.sec, 2 * (size_t)w.secmax);
+    ALLOC(w.tmp, 2 * (size_t)w.secmax);
+    ALLOC(w.Dm, 2 * (size_t)std::max<long>(c->m2max, 1));
+    ALLOC(c->gtmp, (size_t)std::max<long>(c->packmax, 1));
+    for (auto& kv : c->eri_blk) {
+      const int dims3[3] = {d.c, d.a, d.v};
+      const int sp4[4] = {kv.first / 27, (kv.first / 9) % 3, (kv.first / 3) % 3, kv.first % 3};
+      const long sz = (long)dims3[sp4[0]] * dims3[sp4[1]] * dims3[sp4[2]] * dims3[sp4[3]];
+      double* p = nullptr;
+      ALLOC(p, (size_t)std::max<long>(sz, 1));
+      c->gblk[kv.first] = p;
+      c->g_tab.p[kv.first] = p;
+    }
+  }
+  if (h_on) {
+    HDensWork& h = c->hd;
+    const long cv = (long)d.c * d.v;
+    h.size = cv * cv;
+    ALLOC(h.K, (size_t)h.size);
+    ALLOC(h.B1, (size_t)h.size);
+    ALLOC(h.B2, (size_t)h.size);
+    ALLOC(h.pack, (size_t)d.X * cv);
+    ALLOC(h.tmp, (size_t)d.X * cv);
+    ALLOC(h.coef, 6 * n * n);
+    h.part = c->dw.part;
+    h.partmax = partmax;
+  }
+#undef ALLOC
+  if (st == CASPT2_OK) c->dens_alloc = true;
+  return st;
+}
+
+long block_size(const Dims& d, int key) {
+  const int dims3[3] = {d.c, d.a, d.v};
+  return (long)dims3[key / 27] * dims3[(key / 9) % 3] * dims3[(key / 3) % 3] * dims3[key % 3];
+}
+
+}  // namespace
+
+extern "C" {
+
+int caspt2_densities(caspt2_ctx* c, unsigned class_mask, void* stream) {
+  if (!c) return CASPT2_EINVAL;
+  if (!c->solved) return CASPT2_ESTATE;
+  const caspt2_options& o = c->opt;
+  if (o.target_state < 0 || (class_mask & ~o.class_mask) || c->d.a > 16) return CASPT2_EINVAL;
+  CASPT2_CUDA_TRY(cudaSetDevice(c->device));
+  if (!c->dens_alloc) {
+    const int st = alloc_densities(c);
+    if (st != CASPT2_OK) return st;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const Dims& d = c->d;
+  const int n = d.n, P = o.target_state;
+  const size_t nmo = d.nmo();
+  const long launches0 = launch_counter();
+  CASPT2_CUDA_TRY(cudaEventRecord(c->dev0, s));
+  CASPT2_CUDA_TRY(cudaMemsetAsync(c->dd1, 0, sizeof(double) * nmo * nmo, s));
+  CASPT2_CUDA_TRY(cudaMemsetAsync(c->dd2, 0, sizeof(double) * nmo * nmo, s));
+  CASPT2_CUDA_TRY(cudaMemsetAsync(c->dgdf, 0, sizeof(double) * d.X * nmo * nmo, s));
+  bool any_ag = false;
+  for (int k = 0; k < 7; ++k) any_ag = any_ag || ((class_mask >> k & 1u) && c->cw_on[k]);
+  if (any_ag) {
+    for (auto& kv : c->gblk)
+      CASPT2_CUDA_TRY(cudaMemsetAsync(kv.second, 0, sizeof(double) * block_size(d, kv.first), s));
+    RdmPtrs g{{nullptr, c->rdm1r, c->rdm2r, c->rdm3r, c->rdm4r}};
+    for (int k = 0; k < 7; ++k) {
+      if (!(class_mask >> k & 1u) || !c->cw_on[k]) continue;
+      const int st = class_densities(c->cw[k], c->dw, d, o.scheme, o.shift, g, c->E0, c->eps, c->R,
+                                     P, c->lamNL + (long)k * n, c->g_tab, c->dd1, c->dd2, s);
+      if (st != CASPT2_OK) return st;
+    }
+    for (auto& kv : c->gblk) {
+      const int sp4[4] = {kv.first / 27, (kv.first / 9) % 3, (kv.first / 3) % 3, kv.first % 3};
+      CASPT2_CUDA_TRY(gdf_from_block(c->B, d, sp4, kv.second, c->pack0, c->pack1, c->gtmp,
+                                     c->dgdf, s));
+    }
+  }
+  if ((class_mask >> CASPT2_CLASS_H & 1u) && d.c > 0 && d.v > 0) {
+    const int st = classH_densities(c->B, d, c->hw, o.scheme, o.shift, c->R, P,
+                                    c->lamNL + (long)CASPT2_CLASS_H * n, c->rdm1r, c->hd, c->dd2,
+                                    c->dgdf, s);
+    if (st != CASPT2_OK) return st;
+  }
+  CASPT2_CUDA_TRY(launch_symmetrize(c->dd1, (int)nmo, 1, s));
+  CASPT2_CUDA_TRY(launch_symmetrize(c->dd2, (int)nmo, 1, s));
+  CASPT2_CUDA_TRY(launch_symmetrize(c->dgdf, (int)nmo, d.X, s));
+  CASPT2_CUDA_TRY(cudaEventRecord(c->dev1, s));
+  CASPT2_CUDA_TRY(cudaStreamSynchronize(s));
+  float ms = 0.f;
+  CASPT2_CUDA_TRY(cudaEventElapsedTime(&ms, c->dev0, c->dev1));
+  c->times[kNumStages + 4] = ms;
+  c->launches += launch_counter() - launches0;
+  c->dens_done = true;
+  return CASPT2_OK;
+}
+
+int caspt2_get_densities(caspt2_ctx* c, int mem, double* d1, double* d2, double* gdf) {
+  if (!c) return CASPT2_EINVAL;
+  if (mem != CASPT2_MEM_HOST && mem != CASPT2_MEM_DEVICE) return CASPT2_EINVAL;
+  if (!c->dens_done) return CASPT2_ESTATE;
+  CASPT2_CUDA_TRY(cudaSetDevice(c->device));
+  const cudaMemcpyKind k = mem == CASPT2_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  const size_t nmo = c->d.nmo();
+  if (d1) CASPT2_CUDA_TRY(cudaMemcpy(d1, c->dd1, sizeof(double) * nmo * nmo, k));
+  if (d2) CASPT2_CUDA_TRY(cudaMemcpy(d2, c->dd2, sizeof(double) * nmo * nmo, k));
+  if (gdf) CASPT2_CUDA_TRY(cudaMemcpy(gdf, c->dgdf, sizeof(double) * c->d.X * nmo * nmo, k));
+  return CASPT2_OK;
+}
 
 }  // extern "C"

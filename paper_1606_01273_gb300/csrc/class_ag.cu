@@ -14,27 +14,11 @@
 #include <vector>
 
 #include "class_ag.cuh"
+#include "class_dev.cuh"
 #include "linalg.cuh"
 
 namespace caspt2 {
 
-namespace {
-
-__device__ __forceinline__ long ipow(int a, int k) {
-  long r = 1;
-  for (int i = 0; i < k; ++i) r *= a;
-  return r;
-}
-
-__device__ __forceinline__ double rdm_at(const double* const* g, int rank, int n, int a, int M,
-                                         int N, const int* vals, const int8_t* idx) {
-  if (rank == 0) return M == N ? 1.0 : 0.0;
-  long off = 0;
-  for (int j = 0; j < 2 * rank; ++j) off = off * a + vals[idx[j]];
-  return g[rank][((long)M * n + N) * ipow(a, 2 * rank) + off];
-}
-
-}  // namespace
 
 // S or F_act for all (row, col) of the m x m class matrix; out[pi][row][col].
 // row = ((fam * a^nact + act) * n + M), act digits in slot order (first slot slowest).
@@ -191,55 +175,6 @@ __global__ void k_range_basis(const double* __restrict__ Q, const double* __rest
   }
 }
 
-__device__ __forceinline__ void tri_decode(long t, int R, bool strict, int& x, int& y) {
-  // enumerate x <= y (or x < y) row-major by x over [0, R)
-  const int w = strict ? R - 1 : R;
-  double b = 2.0 * w + 1.0;
-  int xx = (int)floor((b - sqrt(b * b - 8.0 * (double)t)) * 0.5);
-  if (xx < 0) xx = 0;
-  auto start = [&](int q) { return (long)q * w - (long)q * (q - 1) / 2; };
-  while (xx > 0 && start(xx) > t) --xx;
-  while (start(xx + 1) <= t) ++xx;
-  x = xx;
-  y = (int)(t - start(xx)) + xx + (strict ? 1 : 0);
-}
-
-// Sector tuple -> coordinates of the external slots (output order of C.ext) and the
-// partner tuple with the pair swapped.
-__device__ void sector_tuple(const DevClass& C, const int* extdim, int sector, long t, int* co,
-                             int* co_sw) {
-  if (C.pair0 < 0) {
-    for (int k = C.next - 1; k >= 0; --k) {
-      co[k] = t % extdim[k];
-      t /= extdim[k];
-      co_sw[k] = co[k];
-    }
-    return;
-  }
-  int ip = -1, jp = -1;
-  for (int k = 0; k < C.next; ++k) {
-    if (C.ext[k] == C.pair0) ip = k;
-    if (C.ext[k] == C.pair1) jp = k;
-  }
-  const int R = extdim[ip];
-  const bool strict = sector == 1;
-  const long npairs = strict ? (long)R * (R - 1) / 2 : (long)R * (R + 1) / 2;
-  const long pidx = t % npairs;
-  t /= npairs;
-  for (int k = C.next - 1; k >= 0; --k) {
-    if (k == ip || k == jp) continue;
-    co[k] = t % extdim[k];
-    t /= extdim[k];
-  }
-  int x, y;
-  tri_decode(pidx, R, strict, x, y);
-  co[ip] = x;
-  co[jp] = y;
-  for (int k = 0; k < C.next; ++k) co_sw[k] = co[k];
-  co_sw[ip] = y;
-  co_sw[jp] = x;
-}
-
 // W[row][(tuple, L')] for the sector: rows (fam, act, M) (M == Lsel under SS-SR)
 __global__ void k_sector_src(const double* __restrict__ V, DevClass C, ExtDims ed, int a, int n,
                              int sector, int Lsel, long ntup, int msec, double* __restrict__ W) {
@@ -357,29 +292,6 @@ __global__ void k_colsum_acc(const double* __restrict__ part, long rows, int nco
 // ============================================================== host side
 namespace caspt2 {
 
-namespace {
-int launch_blocks(long total, int threads = 256) {
-  long b = (total + threads - 1) / threads;
-  return (int)std::max<long>(1, std::min<long>(b, 152L * 32));
-}
-int space_dim(const Dims& d, int sp) { return sp == SP_C ? d.c : (sp == SP_A ? d.a : d.v); }
-int space_off(const Dims& d, int sp) { return sp == SP_C ? 0 : (sp == SP_A ? d.c : d.c + d.a); }
-
-long sector_tuples(const ClassWork& w, int sector) {
-  const DevClass& C = w.dc;
-  if (C.pair0 < 0) {
-    long t = 1;
-    for (int k = 0; k < C.next; ++k) t *= w.ed.d[k];
-    return sector == 0 ? t : 0;
-  }
-  long t = 1, R = 0;
-  for (int k = 0; k < C.next; ++k) {
-    if (C.ext[k] == C.pair0) R = w.ed.d[k];
-    else if (C.ext[k] != C.pair1) t *= w.ed.d[k];
-  }
-  return t * (sector == 0 ? R * (R + 1) / 2 : R * (R - 1) / 2);
-}
-}  // namespace
 
 // g(d_core)_xy = sum_P B_Pxy bsum_P * 2 - sum_P sum_j B_Pxj B_Pjy; h = f - g_act - g_core
 __global__ void k_hcore(const double* __restrict__ f, const double* __restrict__ gact,
@@ -452,6 +364,72 @@ cudaError_t launch_hcore(const double* f, const double* g_act, const double* B, 
   return cudaGetLastError();
 }
 
+// gdf[Q][off0 + x][off1 + y] += tmp[Q][x][y]
+__global__ void k_unpack_add(const double* __restrict__ tmp, int X, int nmo, int off0, int n0,
+                             int off1, int n1, double* __restrict__ gdf) {
+  const long total = (long)X * n0 * n1;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    const int y = e % n1;
+    const long r = e / n1;
+    const int x = r % n0;
+    const long P = r / n0;
+    gdf[(P * nmo + off0 + x) * nmo + off1 + y] += tmp[e];
+  }
+}
+
+cudaError_t launch_pack_block(const double* B, const Dims& d, int sp0, int sp1, double* out,
+                              cudaStream_t s) {
+  const int n0 = space_dim(d, sp0), n1 = space_dim(d, sp1);
+  const long t = (long)d.X * n0 * n1;
+  if (t == 0) return cudaSuccess;
+  ++launch_counter();
+  k_pack_block<<<launch_blocks(t), 256, 0, s>>>(B, d.X, d.nmo(), space_off(d, sp0), n0,
+                                               space_off(d, sp1), n1, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpack_add(const double* tmp, const Dims& d, int sp0, int sp1, double* gdf,
+                              cudaStream_t s) {
+  const int n0 = space_dim(d, sp0), n1 = space_dim(d, sp1);
+  const long t = (long)d.X * n0 * n1;
+  if (t == 0) return cudaSuccess;
+  ++launch_counter();
+  k_unpack_add<<<launch_blocks(t), 256, 0, s>>>(tmp, d.X, d.nmo(), space_off(d, sp0), n0,
+                                               space_off(d, sp1), n1, gdf);
+  return cudaGetLastError();
+}
+
+cudaError_t gdf_from_block(const double* B, const Dims& d, const int sp[4], const double* G,
+                           double* pack0, double* pack1, double* tmp, double* gdf, cudaStream_t s) {
+  const int n0 = space_dim(d, sp[0]), n1 = space_dim(d, sp[1]);
+  const int n2 = space_dim(d, sp[2]), n3 = space_dim(d, sp[3]);
+  if ((long)n0 * n1 * n2 * n3 == 0) return cudaSuccess;
+  const int n01 = n0 * n1, n23 = n2 * n3;
+  const long t0 = (long)d.X * n01, t1 = (long)d.X * n23;
+  ++launch_counter();
+  k_pack_block<<<launch_blocks(t0), 256, 0, s>>>(B, d.X, d.nmo(), space_off(d, sp[0]), n0,
+                                                space_off(d, sp[1]), n1, pack0);
+  ++launch_counter();
+  k_pack_block<<<launch_blocks(t1), 256, 0, s>>>(B, d.X, d.nmo(), space_off(d, sp[2]), n2,
+                                                space_off(d, sp[3]), n3, pack1);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // d/dB[Q][pq] = sum_rt G[pq][rt] B[Q][rt]
+  e = dgemm(d.X, n01, n23, 1.0, pack1, n23, false, G, n23, true, 0.0, tmp, n01, s);
+  if (e != cudaSuccess) return e;
+  ++launch_counter();
+  k_unpack_add<<<launch_blocks(t0), 256, 0, s>>>(tmp, d.X, d.nmo(), space_off(d, sp[0]), n0,
+                                                space_off(d, sp[1]), n1, gdf);
+  // d/dB[Q][rt] = sum_pq G[pq][rt] B[Q][pq]
+  e = dgemm(d.X, n23, n01, 1.0, pack0, n01, false, G, n23, false, 0.0, tmp, n23, s);
+  if (e != cudaSuccess) return e;
+  ++launch_counter();
+  k_unpack_add<<<launch_blocks(t1), 256, 0, s>>>(tmp, d.X, d.nmo(), space_off(d, sp[2]), n2,
+                                                space_off(d, sp[3]), n3, gdf);
+  return cudaGetLastError();
+}
+
 cudaError_t eri_block(const double* B, const Dims& d, const int sp[4], double* pack0, double* pack1,
                       double* out, cudaStream_t s) {
   const int n0 = space_dim(d, sp[0]), n1 = space_dim(d, sp[1]);
@@ -508,6 +486,20 @@ long class_sector_wsize(const ClassWork& w, const Dims& d, int scheme, long* par
   return wmax;
 }
 
+void class_keep_layout(ClassWork& w, const Dims& d, int scheme) {
+  const int nsec = w.dc.pair0 < 0 ? 1 : 2;
+  const int nsel = scheme == CASPT2_SSSR ? d.n : 1;
+  w.keep.assign((size_t)nsec * nsel, SectorKeep{});
+  for (int sec = 0; sec < nsec; ++sec)
+    for (int is = 0; is < nsel; ++is) {
+      SectorKeep& K = w.keep[sec * nsel + is];
+      K.sec = sec;
+      K.Lsel = scheme == CASPT2_SSSR ? is : -1;
+      K.msec = scheme == CASPT2_SSSR ? w.m / d.n : w.m;
+      K.ntup = sector_tuples(w, sec);
+    }
+}
+
 cudaError_t class_upload_plans(ClassWork& w, const std::vector<ActPlan>& S,
                                const std::vector<ActPlan>& F, const std::vector<SrcPlan>& V) {
   cudaError_t e;
@@ -551,6 +543,8 @@ int class_solve(ClassWork& w, SectorWork& sw, const Dims& d, int scheme, double 
       ++launch_counter();
       k_sector<<<launch_blocks(ms2), 256, 0, s>>>(w.Fact, m, n, sgn, Lsel, sw.Fsec, msec);
       CASPT2_CUDA_TRY(cudaGetLastError());
+      SectorKeep& K = w.keep[sec * nsel + is];
+      K.nk = 0;
       int st = sym_eig(sw.Ssec, msec, sw.s, sw.Qs, sw.jac, s, tm);
       if (st != CASPT2_OK) return st;
       // number of overlap eigenvalues at or above the threshold (ascending order)
@@ -561,26 +555,27 @@ int class_solve(ClassWork& w, SectorWork& sw, const Dims& d, int scheme, double 
       int nk = 0;
       for (int k = 0; k < msec; ++k) nk += hs[k] >= thresh ? 1 : 0;
       if (nk == 0) continue;
+      K.nk = nk;
       ++launch_counter();
       k_range_basis<<<launch_blocks((long)msec * nk), 256, 0, s>>>(sw.Qs, sw.s, msec, nk, sw.X);
       CASPT2_CUDA_TRY(cudaGetLastError());
       CASPT2_CUDA_TRY(dgemm(msec, nk, msec, 1.0, sw.Fsec, msec, false, sw.X, nk, false, 0.0,
                             sw.FX, nk, s));
       CASPT2_CUDA_TRY(dgemm(nk, nk, msec, 1.0, sw.X, nk, true, sw.FX, nk, false, 0.0, sw.Ft, nk, s));
-      st = sym_eig(sw.Ft, nk, sw.omega, sw.Qf, sw.jac, s, tm);
+      st = sym_eig(sw.Ft, nk, K.omega, sw.Qf, sw.jac, s, tm);
       if (st != CASPT2_OK) return st;
-      CASPT2_CUDA_TRY(dgemm(msec, nk, nk, 1.0, sw.X, nk, false, sw.Qf, nk, false, 0.0, sw.Y, nk, s));
+      CASPT2_CUDA_TRY(dgemm(msec, nk, nk, 1.0, sw.X, nk, false, sw.Qf, nk, false, 0.0, K.Y, nk, s));
       const long ncol = ntup * n;
       ++launch_counter();
       k_sector_src<<<launch_blocks((long)msec * ncol), 256, 0, s>>>(w.V, w.dc, w.ed, d.a, n, sec,
                                                                     Lsel, ntup, msec, sw.W);
       CASPT2_CUDA_TRY(cudaGetLastError());
-      CASPT2_CUDA_TRY(dgemm(nk, (int)ncol, msec, 1.0, sw.Y, nk, true, sw.W, (int)ncol, false,
-                            0.0, sw.Vt, (int)ncol, s));
+      CASPT2_CUDA_TRY(dgemm(nk, (int)ncol, msec, 1.0, K.Y, nk, true, sw.W, (int)ncol, false,
+                            0.0, K.Vt, (int)ncol, s));
       const int nL = Lsel < 0 ? n : 1;
       const long ne = ntup * nL * n;
       ++launch_counter();
-      k_sector_energy<<<launch_blocks(ne), 256, 0, s>>>(sw.Vt, sw.omega, E0, eps_cv, w.dc, w.ed,
+      k_sector_energy<<<launch_blocks(ne), 256, 0, s>>>(K.Vt, K.omega, E0, eps_cv, w.dc, w.ed,
                                                         d.c, n, sec, Lsel, ntup, nk, shift,
                                                         sw.part, mindenom);
       ++launch_counter();

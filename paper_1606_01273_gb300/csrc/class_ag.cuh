@@ -25,6 +25,14 @@ __device__ __forceinline__ void atomicMin_double(double* addr, double v) {
             static_cast<unsigned long long>(__double_as_longlong(v)));
 }
 
+// Sector eigenbasis kept from the energy pass for the densities: Y (msec x nk, the
+// first nk columns used), omega (nk) and the sources Vt = Y^T V (nk x ntup * n).
+struct SectorKeep {
+  int sec = 0, Lsel = -1, msec = 0, nk = 0;
+  long ntup = 0;
+  double *Y = nullptr, *omega = nullptr, *Vt = nullptr;
+};
+
 struct ClassWork {
   int cls = -1;
   DevClass dc{};
@@ -36,14 +44,30 @@ struct ClassWork {
   ActPlan* dF = nullptr; int nF = 0;
   SrcPlan* dV = nullptr; int nV = 0;
   double *Sact = nullptr, *Fact = nullptr, *V = nullptr;
+  std::vector<SectorKeep> keep;   // one per (sector, SS-SR state), see class_keep_layout
 };
 
 struct SectorWork {
   double *Ssec = nullptr, *Fsec = nullptr, *s = nullptr, *Qs = nullptr, *X = nullptr,
-         *FX = nullptr, *Ft = nullptr, *omega = nullptr, *Qf = nullptr, *Y = nullptr,
-         *mask = nullptr, *jac = nullptr, *W = nullptr, *Vt = nullptr, *part = nullptr,
-         *partn = nullptr;
+         *FX = nullptr, *Ft = nullptr, *Qf = nullptr, *jac = nullptr, *W = nullptr,
+         *part = nullptr;
 };
+
+// Work space of the class densities (sized by the caller, see density_ag.cu).
+struct DensWork {
+  double *T = nullptr, *Lam = nullptr;   // all-tuple amplitudes [tuple][L][row], tall each
+  double *U1 = nullptr, *U2 = nullptr;   // S^id T, S^sw T (U1 later holds W)
+  double *Tsw = nullptr;                 // a tuple-swapped copy
+  double *sec = nullptr;                 // sector amplitudes and lambda [2][secmax]
+  double *tmp = nullptr;                 // back-transformed sector rows [2][secmax]
+  double *Dm = nullptr;                  // D^id, D^sw [2][m^2]
+  double *part = nullptr;                // split-K / block partial sums, partmax
+  long tall = 0, secmax = 0, partmax = 0;
+};
+constexpr long kDensPartMax = 152L * 4 * 64 * 64;
+
+// Device doubles a class needs in DensWork (all-tuple arrays).
+long class_dens_tall(const ClassWork& w, const Dims& d);
 
 // Sizes the context must allocate (doubles).
 struct ClassSizes {
@@ -53,6 +77,8 @@ struct ClassSizes {
 };
 
 void class_setup(int cls, const Dims& d, ClassWork& w);   // host-only: sizes and plans
+// Fill w.keep with the sectors of the scheme (device pointers left to the caller).
+void class_keep_layout(ClassWork& w, const Dims& d, int scheme);
 long class_sector_wsize(const ClassWork& w, const Dims& d, int scheme, long* partsize);
 // Upload plans (allocated by the caller with cudaMalloc into w.dS/dF/dV).
 cudaError_t class_upload_plans(ClassWork& w, const std::vector<ActPlan>& S,
@@ -69,6 +95,36 @@ cudaError_t launch_moments_to_e(const double* mom, int n, double* e, double* nr,
 // lambda pieces of the target state P of one class from its moments and R
 cudaError_t launch_lambda(const double* mom, const double* R, int n, int P, double shift, double* NL,
                           double* lv, cudaStream_t s);
+
+// Class share of the densities of target state P (Sec. II.D) accumulated into
+// d1[nmo][nmo] (source derivative w.r.t. h), d2[nmo][nmo] (closed, active and
+// virtual blocks of dL/df) and the adjoint integral blocks G (same keys and layout
+// as the (pq|rt) blocks of the solve).  Uses the sector bases kept by class_solve;
+// NL = this class's <lambda_L|S|T_L>.
+int class_densities(ClassWork& w, DensWork& dw, const Dims& d, int scheme, double shift,
+                    RdmPtrs rdm, const double* E0, const double* eps_cv, const double* R, int P,
+                    const double* NL, const EriBlocks& G, double* d1, double* d2, cudaStream_t s);
+
+// GDF[Q][p][q] += sum_rt G[pq][rt] B[Q][rt] and GDF[Q][r][t] += sum_pq G[pq][rt] B[Q][pq]
+// for one adjoint block with spaces sp; pack0/pack1/tmp hold X * (block pair) doubles.
+cudaError_t gdf_from_block(const double* B, const Dims& d, const int sp[4], const double* G,
+                           double* pack0, double* pack1, double* tmp, double* gdf, cudaStream_t s);
+
+// Split-K FP64 Gram product over [pre][Ns][post] tensors:
+//   X[x][y] = sum_(p, q) A[(p Ns + x) post + q] B[(p Ns + y) post + q],
+// finished into out by mode: 0 out[x][y] = X; 1 out[off+y][off+x] -= X; 2 out[off+x][off+y] += X.
+// part holds the split partials (partmax doubles, >= Ns^2).
+int gram_product(const double* A, const double* B, long pre, long Ns, long post, int mode,
+                 double* out, long ld, long off, double* part, long partmax, cudaStream_t s);
+
+// out[Q][x][y] = B[Q][off(sp0) + x][off(sp1) + y];  gdf[Q][off(sp0) + x][off(sp1) + y] += tmp[Q][x][y]
+cudaError_t launch_pack_block(const double* B, const Dims& d, int sp0, int sp1, double* out,
+                              cudaStream_t s);
+cudaError_t launch_unpack_add(const double* tmp, const Dims& d, int sp0, int sp1, double* gdf,
+                              cudaStream_t s);
+
+// x <- (x + x^T) / 2 for `batch` square nmo x nmo matrices.
+cudaError_t launch_symmetrize(double* x, int nmo, long batch, cudaStream_t s);
 
 // DF integral block out[p][q][r][t] = sum_P B[P][p][q] B[P][r][t] for the given spaces.
 cudaError_t eri_block(const double* B, const Dims& d, const int sp[4], double* pack0, double* pack1,

@@ -1,0 +1,540 @@
+// Classes A-G: the class share of the correlated densities of a target state P
+// (Sec. II.D) from the sector bases kept by the energy pass.
+//
+// With R the eigenvectors of H^eff, r = R[:, P], and T_L, lambda_L the first-order
+// amplitudes and the lambda amplitudes (Eq. lambdaeq) over all index tuples,
+//   W_L'   = r_L' sum_L r_L T_L + lambda_L'                (source multiplier)
+//   d1_pq  = sum W <M~|E_Omega^dag E_pq|L'~>                (d/dh of the sources)
+//   G_pqrt = sum W <M~|E_Omega^dag 1/2 E_pq,rt|L'~>         (d/d(pq|rt))
+//   d2     = d L / d f on the closed, active and virtual blocks:
+//            closed/virtual: one external slot of T moves (hole or particle line of
+//            f), contracted through the overlap (identity or pair swap);
+//            active: lambda x T contracted with the d/df_uw of F_act, minus
+//            N_L <L~|E_uw|L~> from the E0 dependence of the denominators.
+// All contractions reuse the access plans of the solve (transposed), so the device
+// path shares the solve's normal ordering and index conventions.
+#include <cmath>
+#include <vector>
+
+#include "class_ag.cuh"
+#include "class_dev.cuh"
+#include "linalg.cuh"
+
+namespace caspt2 {
+
+namespace {
+
+constexpr double kInvSqrt2 = 0.70710678118654752440;
+
+// Sector amplitudes and lambda in the eigenbasis mu of the sector, for every
+// (tuple t, state L): amp = -Vt_L / D_L, lam = -(r_L sum_N r_N Vt_N - 2 E_s r_L^2 amp) / D_L,
+// D_L = e_ext(t) + omega_mu - E0_L + E_s.  Layout [mu][t][Li] (Li = L, or 0 for SS-SR).
+__global__ void k_sector_amp(const double* __restrict__ Vt, const double* __restrict__ omega,
+                             const double* __restrict__ E0, const double* __restrict__ eps,
+                             const double* __restrict__ R, int P, DevClass C, ExtDims ed, int c,
+                             int n, int sector, int Lsel, long ntup, int nk, double shift,
+                             double* __restrict__ amp, double* __restrict__ lam) {
+  const int nL = Lsel < 0 ? n : 1;
+  const long ncolV = ntup * n;
+  const long total = (long)nk * ntup * nL;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    const int Li = e % nL;
+    const long t = (e / nL) % ntup;
+    const long mu = e / (nL * ntup);
+    const int L = Lsel < 0 ? Li : Lsel;
+    int co[3], cs[3];
+    sector_tuple(C, ed.d, sector, t, co, cs);
+    double ee = 0.0;
+    for (int k = 0; k < C.next; ++k)
+      ee += (C.slot_space[C.ext[k]] == SP_V) ? eps[c + co[k]] : -eps[co[k]];
+    const double D = ee + omega[mu] - E0[L] + shift;
+    const double* row = Vt + mu * ncolV + t * n;
+    const double am = -row[L] / D;
+    double acc = 0.0;
+    for (int N = 0; N < n; ++N) acc += R[N * n + P] * row[N];
+    const double rl = R[L * n + P];
+    amp[e] = am;
+    lam[e] = -(rl * acc - 2.0 * shift * rl * rl * am) / D;
+  }
+}
+
+// Sector rows src[i][(t, Li)] (i over the sector rows) -> all-tuple arrays
+// dst[tuple][L][row]; pair classes: a pair (x, y), x < y, receives (T+ + T-)/sqrt2 and its
+// swap (T+ - T-)/sqrt2, x = y receives T+.  Two arrays (T and lambda) per launch.
+__global__ void k_tuple_scatter(const double* __restrict__ src0, const double* __restrict__ src1,
+                                DevClass C, ExtDims ed, int n, int m, int sector, int Lsel,
+                                long ntup, int msec, double* __restrict__ dst0,
+                                double* __restrict__ dst1) {
+  const int nL = Lsel < 0 ? n : 1;
+  const long ncol = ntup * nL;
+  const long total = (long)msec * ncol;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    const long i = e / ncol, col = e % ncol;
+    const long t = col / nL;
+    const int Li = col % nL;
+    const int L = Lsel < 0 ? Li : Lsel;
+    const long row = Lsel < 0 ? i : i * n + Lsel;
+    int co[3], cs[3];
+    sector_tuple(C, ed.d, sector, t, co, cs);
+    const long ia = (tuple_index(C, ed.d, co) * n + L) * m + row;
+    const long ib = (tuple_index(C, ed.d, cs) * n + L) * m + row;
+    const double x0 = src0[e], x1 = src1[e];
+    if (C.pair0 < 0) {
+      dst0[ia] = x0;
+      dst1[ia] = x1;
+    } else if (ia == ib) {
+      dst0[ia] += x0;
+      dst1[ia] += x1;
+    } else {
+      const double sg = sector == 0 ? kInvSqrt2 : -kInvSqrt2;
+      dst0[ia] += kInvSqrt2 * x0;
+      dst1[ia] += kInvSqrt2 * x1;
+      dst0[ib] += sg * x0;
+      dst1[ib] += sg * x1;
+    }
+  }
+}
+
+// dst[t][inner] = src[swap(t)][inner], swap exchanging the pair slots of the tuple.
+__global__ void k_swap_tuples(const double* __restrict__ src, DevClass C, ExtDims ed, long ntot,
+                              long inner, double* __restrict__ dst) {
+  int ip = 0, jp = 0;
+  for (int k = 0; k < C.next; ++k) {
+    if (C.ext[k] == C.pair0) ip = k;
+    if (C.ext[k] == C.pair1) jp = k;
+  }
+  const long total = ntot * inner;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    long t = e / inner;
+    const long r = e % inner;
+    int co[3];
+    for (int k = C.next - 1; k >= 0; --k) {
+      co[k] = t % ed.d[k];
+      t /= ed.d[k];
+    }
+    const int x = co[ip];
+    co[ip] = co[jp];
+    co[jp] = x;
+    dst[e] = src[tuple_index(C, ed.d, co) * inner + r];
+  }
+}
+
+// Split-K Gram product over a tensor viewed as [pre][Ns][post]:
+//   part[z][x][y] = sum_{k in chunk z} A(x, k) B(y, k),  k = (p, q) over pre x post,
+//   A(x, (p, q)) = A[(p * Ns + x) * post + q].
+// 64 x 64 output tile per block, 4 x 4 per thread, FP64 FMA.
+constexpr int kGT = 64, kGK = 16;
+__global__ void __launch_bounds__(256)
+k_gram(const double* __restrict__ A, const double* __restrict__ B, long Ns, unsigned post,
+       unsigned K, unsigned chunk, double* __restrict__ part) {
+  __shared__ double sa[kGK][kGT + 1], sb[kGK][kGT + 1];
+  const long x0 = (long)blockIdx.y * kGT, y0 = (long)blockIdx.x * kGT;
+  const unsigned kbeg = blockIdx.z * chunk;
+  const unsigned kend = min(K, kbeg + chunk);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const bool xfast = post == 1u;
+  double acc[4][4] = {};
+  for (unsigned k0 = kbeg; k0 < kend; k0 += kGK) {
+    for (int l = threadIdx.x; l < kGK * kGT; l += 256) {
+      int kk, ii;
+      if (xfast) { ii = l % kGT; kk = l / kGT; } else { kk = l % kGK; ii = l / kGK; }
+      const unsigned gk = k0 + kk;
+      const long gx = x0 + ii, gy = y0 + ii;
+      double va = 0.0, vb = 0.0;
+      if (gk < kend) {
+        const unsigned p = gk / post, q = gk - p * post;
+        const long base = (long)p * Ns * post + q;
+        if (gx < Ns) va = A[base + gx * post];
+        if (gy < Ns) vb = B[base + gy * post];
+      }
+      sa[kk][ii] = va;
+      sb[kk][ii] = vb;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < kGK; ++kk) {
+      double ra[4], rb[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) { ra[q] = sa[kk][ty + 16 * q]; rb[q] = sb[kk][tx + 16 * q]; }
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[p][q] = fma(ra[p], rb[q], acc[p][q]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const long gx = x0 + ty + 16 * p, gy = y0 + tx + 16 * q;
+      if (gx < Ns && gy < Ns) part[((long)blockIdx.z * Ns + gx) * Ns + gy] = acc[p][q];
+    }
+}
+
+// Fixed-order sum of the split-K partials.  mode 0: out[x][y] = X; mode 1 (closed
+// block): out[off + y][off + x] -= X; mode 2 (virtual block): out[off + x][off + y] += X.
+__global__ void k_gram_finish(const double* __restrict__ part, int nsplit, long Ns, int mode,
+                              double* __restrict__ out, long ld, long off) {
+  const long total = Ns * Ns;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int z = 0; z < nsplit; ++z) s += part[(long)z * total + e];
+    const long x = e / Ns, y = e % Ns;
+    if (mode == 0) out[x * ld + y] = s;
+    else if (mode == 1) out[(off + y) * ld + off + x] -= s;
+    else out[(off + x) * ld + off + y] += s;
+  }
+}
+
+// Active block of d2: partial sums over (row, col) of D^pi[row][col] dF_act^pi/df_uw.
+// Thread layout: uw = tid % a^2 (one output per thread), sub = tid / a^2 strides over the
+// m x m elements; a loop variable that carries an f index is bound to u or w, so every
+// (plan, loop) term is evaluated once across the block.  part[block][a^2].
+__global__ void k_act_adj(const ActPlan* __restrict__ plans, int nplan, DevClass C, int a, int n,
+                          RdmPtrs g, const double* __restrict__ Dm, int m,
+                          double* __restrict__ part) {
+  __shared__ double red[256];
+  const int a2 = a * a;
+  const int nsub = blockDim.x / a2;
+  const int uw = threadIdx.x % a2, sub = threadIdx.x / a2;
+  const int u = uw / a, w = uw % a;
+  const long total = (long)m * m;
+  const long A = ipow(a, C.nact);
+  double acc = 0.0;
+  if (sub < nsub) {
+    for (long e = (long)blockIdx.x * nsub + sub; e < total; e += (long)gridDim.x * nsub) {
+      const double D0 = Dm[e], D1 = Dm[total + e];
+      if (D0 == 0.0 && D1 == 0.0) continue;
+      const int row = e / m, col = e % m;
+      int vals[24];
+      const int M = row % n, N = col % n;
+      long ab = row / n, ak = col / n;
+      const int fb = ab / A, fk = ak / A;
+      ab %= A;
+      ak %= A;
+      for (int k = C.nact - 1; k >= 0; --k) {
+        vals[kRefBra + k] = ab % a;
+        ab /= a;
+        vals[kRefKet + k] = ak % a;
+        ak /= a;
+      }
+      for (int t = 0; t < nplan; ++t) {
+        const ActPlan& P = plans[t];
+        if (!P.has_f || P.fb != fb || P.fk != fk) continue;
+        const double Dv = P.pi == 0 ? D0 : D1;
+        if (Dv == 0.0) continue;
+        bool ok = true;
+        for (int q = 0; q < P.neq; ++q)
+          if (vals[P.eq[q][0]] != vals[P.eq[q][1]]) ok = false;
+        int fix[2] = {-1, -1};
+        for (int j = 0; j < 2 && ok; ++j) {
+          const int ref = P.fidx[j], v = j == 0 ? u : w;
+          if (ref >= kRefLoop) {
+            const int k = ref - kRefLoop;
+            if (k > 1) { ok = false; break; }
+            if (fix[k] >= 0 && fix[k] != v) ok = false;
+            fix[k] = v;
+          } else if (vals[ref] != v) {
+            ok = false;
+          }
+        }
+        if (!ok) continue;
+        const int nl = P.nloop;
+        const int n0 = (nl >= 1 && fix[0] < 0) ? a : 1;
+        const int n1 = (nl >= 2 && fix[1] < 0) ? a : 1;
+        double s = 0.0;
+        for (int i0 = 0; i0 < n0; ++i0) {
+          if (nl >= 1) vals[kRefLoop] = fix[0] >= 0 ? fix[0] : i0;
+          for (int i1 = 0; i1 < n1; ++i1) {
+            if (nl >= 2) vals[kRefLoop + 1] = fix[1] >= 0 ? fix[1] : i1;
+            s += rdm_at(g.p, P.rank, n, a, M, N, vals, P.idx);
+          }
+        }
+        acc += P.coeff * Dv * s;
+      }
+    }
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x < a2) {
+    double t = 0.0;
+    for (int q = 0; q < nsub; ++q) t += red[q * a2 + threadIdx.x];
+    part[(long)blockIdx.x * a2 + threadIdx.x] = t;
+  }
+}
+
+// d2[c + u][c + w] += sum_blocks part[b][uw] - sum_L NL[L] Gamma1[L][L][u][w]
+__global__ void k_act_finish(const double* __restrict__ part, int nblk, int a, int c, int nmo,
+                             const double* __restrict__ NL, const double* __restrict__ g1, int n,
+                             double* __restrict__ d2) {
+  const int a2 = a * a;
+  for (int uw = threadIdx.x; uw < a2; uw += blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += part[(long)b * a2 + uw];
+    for (int L = 0; L < n; ++L) s -= NL[L] * g1[((long)L * n + L) * a2 + uw];
+    d2[(long)(c + uw / a) * nmo + c + uw % a] += s;
+  }
+}
+
+// W[t][L'][row] = r_L' sum_L r_L T[t][L][row] + Lam[t][L'][row]
+__global__ void k_wsrc(const double* __restrict__ T, const double* __restrict__ Lam,
+                       const double* __restrict__ R, int P, int n, long m, long total,
+                       double* __restrict__ W) {
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    const long row = e % m;
+    const int Lp = (e / m) % n;
+    const long t = e / (m * n);
+    double acc = 0.0;
+    for (int L = 0; L < n; ++L) acc += R[L * n + P] * T[(t * n + L) * m + row];
+    W[e] = R[Lp * n + P] * acc + Lam[e];
+  }
+}
+
+__device__ __forceinline__ void flush_add(double* p, double v) {
+  if (p != nullptr && v != 0.0) atomicAdd(p, v);
+}
+
+// Adjoint of the sources: for every V element (fam, ext, act, M, L') with multiplier
+// W, each plan term coeff * I[...] * Gamma adds coeff * W * Gamma to dI[...] (d1 for the
+// one-electron part, G blocks for (pq|rt)).  Runs of equal targets are summed before
+// the atomic add.
+__global__ void k_src_adj(const SrcPlan* __restrict__ plans, int nplan, DevClass C, Dims d,
+                          RdmPtrs g, const double* __restrict__ W, long m, long vtotal,
+                          double* __restrict__ d1, EriBlocks G) {
+  const int n = d.n, a = d.a, nmo = d.nmo();
+  const int dimsp[3] = {d.c, d.a, d.v};
+  const int offsp[3] = {0, d.c, d.c + d.a};
+  const long A = ipow(a, C.nact);
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < vtotal;
+       e += (long)gridDim.x * blockDim.x) {
+    long r = e;
+    const int L = r % n; r /= n;
+    const int M = r % n; r /= n;
+    const long actlin = r % A; r /= A;
+    int vals[24];
+    long q = actlin;
+    for (int k = C.nact - 1; k >= 0; --k) {
+      vals[kRefBra + C.act[k]] = q % a;
+      q /= a;
+    }
+    int co[3];
+    for (int k = C.next - 1; k >= 0; --k) {
+      const int dm = dimsp[C.slot_space[C.ext[k]]];
+      co[k] = r % dm;
+      vals[kRefBra + C.ext[k]] = co[k];
+      r /= dm;
+    }
+    const int fam = (int)r;
+    long t = 0;
+    for (int k = 0; k < C.next; ++k) t = t * dimsp[C.slot_space[C.ext[k]]] + co[k];
+    const double Wv = W[(t * n + L) * m + (fam * A + actlin) * n + M];
+    if (Wv == 0.0) continue;
+    double* last = nullptr;
+    double run = 0.0;
+    for (int tp = 0; tp < nplan; ++tp) {
+      const SrcPlan& P = plans[tp];
+      if (P.fb != fam) continue;
+      bool ok = true;
+      for (int qq = 0; qq < P.neq; ++qq)
+        if (vals[P.eq[qq][0]] != vals[P.eq[qq][1]]) ok = false;
+      if (!ok) continue;
+      long niter = 1;
+      for (int j = 0; j < P.nloop; ++j) niter *= dimsp[P.loop_space[j]];
+      double* blk = nullptr;
+      long bd[4] = {1, 1, 1, 1};
+      if (P.kind == 1) {
+        const int key = ((P.ispace[0] * 3 + P.ispace[1]) * 3 + P.ispace[2]) * 3 + P.ispace[3];
+        blk = const_cast<double*>(G.p[key]);
+        for (int j = 0; j < 4; ++j) bd[j] = dimsp[P.ispace[j]];
+      }
+      const double cw = P.coeff * Wv;
+      for (long it = 0; it < niter; ++it) {
+        long qi = it;
+        for (int j = 0; j < P.nloop; ++j) {
+          const int dm = dimsp[P.loop_space[j]];
+          vals[kRefLoop + j] = qi % dm;
+          qi /= dm;
+        }
+        const double x = rdm_at(g.p, P.rank, n, a, M, L, vals, P.idx);
+        if (x == 0.0) continue;
+        double* tgt;
+        if (P.kind == 0) {
+          tgt = d1 + (long)(offsp[P.ispace[0]] + vals[P.iidx[0]]) * nmo + offsp[P.ispace[1]] +
+                vals[P.iidx[1]];
+        } else {
+          tgt = blk + ((vals[P.iidx[0]] * bd[1] + vals[P.iidx[1]]) * bd[2] + vals[P.iidx[2]]) *
+                          bd[3] + vals[P.iidx[3]];
+        }
+        if (tgt != last) {
+          flush_add(last, run);
+          last = tgt;
+          run = 0.0;
+        }
+        run += cw * x;
+      }
+    }
+    flush_add(last, run);
+  }
+}
+
+__global__ void k_symmetrize(double* __restrict__ x, int nmo, long batch) {
+  const long nn = (long)nmo * nmo;
+  const long total = batch * nn;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    const long r = e % nn;
+    const int i = r / nmo, j = r % nmo;
+    if (i >= j) continue;
+    double* m = x + (e - r);
+    const double s = 0.5 * (m[(long)i * nmo + j] + m[(long)j * nmo + i]);
+    m[(long)i * nmo + j] = s;
+    m[(long)j * nmo + i] = s;
+  }
+}
+
+}  // namespace
+
+// X = sum over (pre, post) of A(x, .) B(y, .) for [pre][Ns][post] tensors, finished
+// into `out` according to `mode` (see k_gram_finish).
+int gram_product(const double* A, const double* B, long pre, long Ns, long post, int mode,
+                 double* out, long ld, long off, double* part, long partmax, cudaStream_t s) {
+  if (pre * Ns * post == 0) return CASPT2_OK;
+  const long K = pre * post;
+  if (K >= (1L << 31) || Ns * Ns > partmax) return CASPT2_EINVAL;
+  const long tiles = ((Ns + kGT - 1) / kGT) * ((Ns + kGT - 1) / kGT);
+  long nsplit = std::max<long>(1, (152L * 4 + tiles - 1) / tiles);
+  nsplit = std::min(nsplit, std::max<long>(1, K / 256));
+  nsplit = std::min(nsplit, partmax / (Ns * Ns));
+  long chunk = (K + nsplit - 1) / nsplit;
+  chunk = (chunk + kGK - 1) / kGK * kGK;
+  nsplit = (K + chunk - 1) / chunk;
+  dim3 grid((unsigned)((Ns + kGT - 1) / kGT), (unsigned)((Ns + kGT - 1) / kGT), (unsigned)nsplit);
+  ++launch_counter();
+  k_gram<<<grid, 256, 0, s>>>(A, B, Ns, (unsigned)post, (unsigned)K, (unsigned)chunk, part);
+  ++launch_counter();
+  k_gram_finish<<<launch_blocks(Ns * Ns), 256, 0, s>>>(part, (int)nsplit, Ns, mode, out, ld, off);
+  CASPT2_CUDA_TRY(cudaGetLastError());
+  return CASPT2_OK;
+}
+
+long class_dens_tall(const ClassWork& w, const Dims& d) {
+  if (w.vsize == 0 || w.m == 0) return 0;
+  return all_tuples(w) * d.n * w.m;
+}
+
+cudaError_t launch_symmetrize(double* x, int nmo, long batch, cudaStream_t s) {
+  const long total = batch * (long)nmo * nmo;
+  if (total == 0) return cudaSuccess;
+  ++launch_counter();
+  k_symmetrize<<<launch_blocks(total), 256, 0, s>>>(x, nmo, batch);
+  return cudaGetLastError();
+}
+
+int class_densities(ClassWork& w, DensWork& dw, const Dims& d, int scheme, double shift,
+                    RdmPtrs rdm, const double* E0, const double* eps_cv, const double* R, int P,
+                    const double* NL, const EriBlocks& G, double* d1, double* d2,
+                    cudaStream_t s) {
+  (void)scheme;
+  const int m = w.m, n = d.n, a = d.a, nmo = d.nmo();
+  if (w.vsize == 0 || m == 0) return CASPT2_OK;
+  const DevClass& C = w.dc;
+  const long ntot = all_tuples(w);
+  const long tall = ntot * n * m;
+  if (tall > dw.tall || a * a > 256) return CASPT2_EINVAL;
+  CASPT2_CUDA_TRY(cudaMemsetAsync(dw.T, 0, sizeof(double) * tall, s));
+  CASPT2_CUDA_TRY(cudaMemsetAsync(dw.Lam, 0, sizeof(double) * tall, s));
+
+  // ---- amplitudes and lambda of every sector, back-transformed to all tuples
+  for (const SectorKeep& K : w.keep) {
+    if (K.nk == 0 || K.ntup == 0) continue;
+    const int nL = K.Lsel < 0 ? n : 1;
+    const long ncol = K.ntup * nL;
+    if ((long)K.nk * ncol > dw.secmax || (long)K.msec * ncol > dw.secmax) return CASPT2_EINVAL;
+    double* amp = dw.sec;
+    double* lam = dw.sec + dw.secmax;
+    ++launch_counter();
+    k_sector_amp<<<launch_blocks((long)K.nk * ncol), 256, 0, s>>>(
+        K.Vt, K.omega, E0, eps_cv, R, P, C, w.ed, d.c, n, K.sec, K.Lsel, K.ntup, K.nk, shift, amp,
+        lam);
+    CASPT2_CUDA_TRY(cudaGetLastError());
+    // rows = Y (msec x nk) times sector columns, for amp and lam together
+    CASPT2_CUDA_TRY(dgemm(K.msec, (int)ncol, K.nk, 1.0, K.Y, K.nk, false, dw.sec, (int)ncol, false,
+                          0.0, dw.tmp, (int)ncol, s, 2, 0, dw.secmax, dw.secmax));
+    ++launch_counter();
+    k_tuple_scatter<<<launch_blocks((long)K.msec * ncol), 256, 0, s>>>(
+        dw.tmp, dw.tmp + dw.secmax, C, w.ed, n, m, K.sec, K.Lsel, K.ntup, K.msec, dw.T, dw.Lam);
+    CASPT2_CUDA_TRY(cudaGetLastError());
+  }
+  const bool pair = C.pair0 >= 0;
+  const long mm = (long)m * m;
+  // ---- overlap applied to T: U1 = S^id T, U2 = S^sw T (rows of T are (tuple, L))
+  CASPT2_CUDA_TRY(dgemm((int)(ntot * n), m, m, 1.0, dw.T, m, false, w.Sact, m, true, 0.0, dw.U1, m,
+                        s));
+  if (pair)
+    CASPT2_CUDA_TRY(dgemm((int)(ntot * n), m, m, 1.0, dw.T, m, false, w.Sact + mm, m, true, 0.0,
+                          dw.U2, m, s));
+  // ---- closed and virtual blocks: one external slot moves
+  auto slot_blocks = [&](const double* Lm, const double* U) -> int {
+    long pre = 1;
+    for (int k = 0; k < C.next; ++k) {
+      const long Ns = w.ed.d[k];
+      long post = (long)n * m;
+      for (int k2 = k + 1; k2 < C.next; ++k2) post *= w.ed.d[k2];
+      const int sp = C.slot_space[C.ext[k]];
+      const int st = gram_product(Lm, U, pre, Ns, post, sp == SP_C ? 1 : 2, d2, nmo,
+                                  space_off(d, sp), dw.part, dw.partmax, s);
+      if (st != CASPT2_OK) return st;
+      pre *= Ns;
+    }
+    return CASPT2_OK;
+  };
+  int st = slot_blocks(dw.Lam, dw.U1);
+  if (st != CASPT2_OK) return st;
+  if (pair) {
+    ++launch_counter();
+    k_swap_tuples<<<launch_blocks(tall), 256, 0, s>>>(dw.Lam, C, w.ed, ntot, (long)n * m, dw.Tsw);
+    CASPT2_CUDA_TRY(cudaGetLastError());
+    st = slot_blocks(dw.Tsw, dw.U2);
+    if (st != CASPT2_OK) return st;
+  }
+  // ---- active block: D^pi = sum_(tuple, L) lambda x T^pi, contracted with dF_act/df
+  st = gram_product(dw.Lam, dw.T, ntot * n, m, 1, 0, dw.Dm, m, 0, dw.part, dw.partmax, s);
+  if (st != CASPT2_OK) return st;
+  if (pair) {
+    ++launch_counter();
+    k_swap_tuples<<<launch_blocks(tall), 256, 0, s>>>(dw.T, C, w.ed, ntot, (long)n * m, dw.Tsw);
+    CASPT2_CUDA_TRY(cudaGetLastError());
+    st = gram_product(dw.Lam, dw.Tsw, ntot * n, m, 1, 0, dw.Dm + mm, m, 0, dw.part, dw.partmax,
+                      s);
+    if (st != CASPT2_OK) return st;
+  } else {
+    CASPT2_CUDA_TRY(cudaMemsetAsync(dw.Dm + mm, 0, sizeof(double) * mm, s));
+  }
+  if (a > 0) {
+    const int a2 = a * a;
+    const int nsub = 256 / a2;
+    const long nblk = std::max<long>(1, std::min<long>(152L * 4, (mm + nsub - 1) / nsub));
+    if (nblk * a2 > dw.partmax) return CASPT2_EINVAL;
+    ++launch_counter();
+    k_act_adj<<<(unsigned)nblk, 256, 0, s>>>(w.dF, w.nF, C, a, n, rdm, dw.Dm, m, dw.part);
+    ++launch_counter();
+    k_act_finish<<<1, 256, 0, s>>>(dw.part, (int)nblk, a, d.c, nmo, NL, rdm.p[1], n, d2);
+    CASPT2_CUDA_TRY(cudaGetLastError());
+  }
+  // ---- sources: d1 and the adjoint integral blocks
+  ++launch_counter();
+  k_wsrc<<<launch_blocks(tall), 256, 0, s>>>(dw.T, dw.Lam, R, P, n, m, tall, dw.U1);
+  ++launch_counter();
+  k_src_adj<<<launch_blocks(w.vsize), 256, 0, s>>>(w.dV, w.nV, C, d, rdm, dw.U1, m, w.vsize, d1,
+                                                   G);
+  CASPT2_CUDA_TRY(cudaGetLastError());
+  return CASPT2_OK;
+}
+
+}  // namespace caspt2

@@ -55,6 +55,19 @@ struct ClassHWork {
   cudaEvent_t ev_gemm0 = nullptr, ev_gemm1 = nullptr;  // optional: bracket the GEMM kernel
 };
 long classH_blocks(const Dims& d);
+
+// Work space of the class-H densities: K, B1, B2 hold (c v)^2 doubles each (size),
+// pack and tmp X c v, coef 6 n^2, part partmax.
+struct HDensWork {
+  double *K = nullptr, *B1 = nullptr, *B2 = nullptr, *pack = nullptr, *tmp = nullptr,
+         *coef = nullptr, *part = nullptr;
+  long size = 0, partmax = 0;
+};
+// Class-H share of d2 (closed, active, virtual blocks) and GDF of target state P
+// (Sec. II.D), accumulated; needs the W, shifts and eps left by launch_classH.
+int classH_densities(const double* B, const Dims& d, const ClassHWork& hw, int scheme,
+                     double shift, const double* R, int P, const double* NL, const double* g1,
+                     const HDensWork& hd, double* d2, double* gdf, cudaStream_t s);
 // eps[0..c) closed and eps[c..c+v) virtual orbital energies (diagonal of f)
 cudaError_t launch_eps_cv(const double* f, const Dims& d, double* eps, cudaStream_t s);
 // out[r][s] = f[c + r][c + s] (active block, compact)

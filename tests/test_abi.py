@@ -41,6 +41,10 @@ def test_host_only_entry_points(so):
     so.caspt2_get_kernel_launches.restype = C.c_long
     so.caspt2_get_kernel_launches.argtypes = [C.c_void_p]
     assert so.caspt2_get_kernel_launches(None) == -1
+    so.caspt2_densities.argtypes = [C.c_void_p, C.c_uint, C.c_void_p]
+    assert so.caspt2_densities(None, 0xFF, None) == -1
+    so.caspt2_get_densities.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
+    assert so.caspt2_get_densities(None, 0, None, None, None) == -1
 
 
 def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):

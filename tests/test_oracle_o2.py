@@ -169,3 +169,47 @@ def test_total_densities_match_o1(cprob, xms, scheme, shift):
     assert np.abs(G - r.D1df).max() < 1e-11
     assert np.abs(_diag_blocks(cprob, d2 - r.d2)).max() < 1e-11
     assert np.abs(NL - r.NL).max() < 1e-11
+
+
+# (closed, active, virtual) change of the orbital-space occupation made by each class's
+# excitation operator (Eq. class): e.g. class A moves one electron closed -> active.
+OCC_CHANGE = {"A": (-1, 1, 0), "B": (-2, 2, 0), "C": (0, -1, 1), "D": (-1, 0, 1),
+              "E": (-2, 1, 1), "F": (0, -2, 2), "G": (-1, -1, 2), "H": (-2, 0, 2)}
+
+
+def _h_of(p):
+    c, a, n = p.nclosed, p.nact, p.nstate
+    d = np.zeros((p.nmo, p.nmo))
+    d[np.arange(c), np.arange(c)] = 2.0
+    g1 = p.rdm[1].reshape(n, n, a, a)
+    d[c:c + a, c:c + a] = sum(g1[m, m] for m in range(n)) / n
+    return p.f - o2.g_of(p.B, d)
+
+
+@pytest.mark.parametrize("xms,scheme,shift", [(True, "msmr", 0.2), (False, "sssr", 0.1),
+                                              (False, "msmr", 0.0)])
+def test_density_identities(xms, scheme, shift):
+    """Two exact identities per class, independent of the density algebra:
+    (1) particle-number conservation: shifting every f_pp of one orbital space by delta
+        shifts each denominator by delta times the class's occupation change there, so
+        tr d2(space) = change(space) * sum_L N_L (the E0 term cancels the reference part);
+    (2) Euler's theorem: the sources are linear in h and bilinear in B, so
+        sum d1 h + 1/2 sum GDF B = sum_LL' r_L r_L' e[L][L'] + sum_L lv[L][L]
+        with e and lv from the moment path (Eq. lambdaeq)."""
+    from oracle import o2_classes as oc
+    p = make_problem(nclosed=2, nact=4, nvirt=3, naux=24, nstate=2, seed=5)
+    st = o2.setup(p, xms=xms, kmax=4)
+    mom = oc.all_moments(p, st, shift=shift, scheme=scheme)
+    parts = {c: (-np.einsum("llk->lk", M1), np.diagonal(M2).copy()) for c, (M1, M2, M3) in mom.items()}
+    _, _, R = o2.heff(st, parts, shift)
+    h = _h_of(p)
+    c, a = p.nclosed, p.nact
+    r = R[:, 0]
+    for cls in "ABCDEFGH":
+        NL, lv = oc.lambda_pieces(*mom[cls], R, 0, shift)
+        d1, G, d2, _ = _o2_densities(p, st, R, shift, scheme, cls)
+        tr = [np.trace(d2[:c, :c]), np.trace(d2[c:c + a, c:c + a]), np.trace(d2[c + a:, c + a:])]
+        for k in range(3):
+            assert abs(tr[k] - OCC_CHANGE[cls][k] * NL.sum()) < 1e-12, (cls, k)
+        src = r @ parts[cls][0] @ r + np.trace(lv)
+        assert abs(np.sum(d1 * h) + 0.5 * np.sum(G * p.B) - src) < 1e-12 * max(1.0, abs(src)), cls
