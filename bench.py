@@ -1,11 +1,12 @@
 #!/usr/bin/env python
 """Throughput of the (X)MS-CASPT2 amplitude / effective-Hamiltonian path on GB300.
 
-One step = one caspt2_solve of the synthetic benzophenone-like XMS-CASPT2 workload
-(nclosed 20, nact 8 with 8 electrons, nvirt 200, naux 700, 3 states, shift 0.2,
-MS-MR): setup (SA density, mean field, core energy, XMS rotation, rotated RDMs,
-H^ref), every class this build implements, H^eff and its eigenpairs.  Inputs are
-resident in HBM before the timed region; L2 is flushed between steps.
+One step = one caspt2_solve + caspt2_densities of the synthetic benzophenone-like
+XMS-CASPT2 workload (nclosed 20, nact 8 with 8 electrons, nvirt 200, naux 700, 3 states,
+shift 0.2, MS-MR): setup (SA density, mean field, core energy, XMS rotation, rotated
+RDMs, H^ref), the amplitude solves of all eight classes, H^eff and its eigenpairs, lambda
+of state 0, and the densities d1, d2 and D1 in DF form of state 0.  Inputs are resident
+in HBM before the timed region; L2 is flushed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -160,7 +161,10 @@ def run_reference(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD_DESC, "classes": "ABCDEFGH", "form": "oracle (numpy FP64)"},
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cpu_cores(),
-                         "kind": "oracle", "sample": f"{args.steps} whole solves of the workload"},
+                         "kind": "oracle",
+                         "sample": (f"{args.steps} whole amplitude + lambda solves of the workload "
+                                    "(densities not included: the oracle's density pass alone "
+                                    "takes about 190 s on 8 cores)")},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -185,7 +189,9 @@ def run_ours(args):
     host = cp.problem_inputs(p)
     h2d = sum(x.nbytes for x in host if x is not None)
     n = p.nstate
-    d2h = 8 * (4 * n * n + 2 * n + 1 + 8 * (n * n + n))
+    # energies, per-class pieces and lambda, plus d1 and d2 (GDF stays in HBM for the
+    # gradient contraction with the derivative integrals)
+    d2h = 8 * (4 * n * n + 2 * n + 1 + 8 * (n * n + n)) + 2 * 8 * p.nmo * p.nmo
     dev_in = [torch.from_numpy(x).to(dev) for x in host]   # f, B, rdm1-4
     ctx = cp.Context(p.nclosed, p.nact, p.nvirt, p.naux, p.nstate, **OPTS)
     ctx.set_inputs(*dev_in)
@@ -195,11 +201,12 @@ def run_ours(args):
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             ctx.solve(stream.cuda_stream)
+            ctx.compute_densities(stream=stream.cuda_stream)
     torch.cuda.synchronize(dev)
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
-    kern_ms, launches, tri = [], 0, []
+    kern_ms, launches, tri, dens_ms = [], 0, [], []
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize(dev)
@@ -209,8 +216,10 @@ def run_ours(args):
                 flush.fill_(float(k))                # L2 flush outside the timed events
                 ev[k][0].record(stream)
                 ctx.solve(stream.cuda_stream)
+                ctx.compute_densities(stream=stream.cuda_stream)
                 ev[k][1].record(stream)
             r = ctx.result()
+            dens_ms.append(r.timings_ms[8])
             kern_ms.append(r.timings_ms[4])
             tri.append((r.timings_ms[5], r.timings_ms[6], r.timings_ms[7]))
             launches += r.launches
@@ -232,13 +241,17 @@ def run_ours(args):
     for _ in range(max(1, args.warmup)):
         ctx_h.set_inputs(*pinned)
         ctx_h.solve()
+        ctx_h.compute_densities()
         ctx_h.result()
+        ctx_h.get_densities(with_gdf=False)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     for _ in range(args.steps):
         ctx_h.set_inputs(*pinned)
         ctx_h.solve()
+        ctx_h.compute_densities()
         ctx_h.result()
+        ctx_h.get_densities(with_gdf=False)
     torch.cuda.synchronize(dev)
     e2e_s = time.perf_counter() - t0
     if ws > 1:
@@ -288,14 +301,19 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clk.summary(),
         "stage_ms_last": dict(zip(["setup", "classH", "classesAG", "heff_lambda", "classH_kernel",
-                                   "tridiag_kernel_total"], last.timings_ms[:6])),
+                                   "tridiag_kernel_total"], last.timings_ms[:6]),
+                              densities=statistics.mean(dens_ms)),
     }
     if ws == 1 and not args.no_cpu_baseline:
         ts, ref = time_oracle(p)
         w = ref[1]
         line["cpu_baseline"] = {"value": len(ts) / sum(ts), "unit": "solves/s",
                                 "cores": cpu_cores(), "kind": "oracle",
-                                "sample": f"{len(ts)} whole solve(s) of the workload, numpy FP64"}
+                                "sample": (f"{len(ts)} whole amplitude + lambda solve(s) of the "
+                                           "workload (setup, classes A-H, H^eff, lambda), numpy "
+                                           "FP64; the oracle's density pass is not in the sample "
+                                           "(about 190 s on 8 cores), so this rate is an upper "
+                                           "bound for the oracle's full step")}
         line["parity"] = {"max_abs_dE_Eh": float(np.abs(last.Ems - w).max()), "tol_Eh": 1e-8}
     print(json.dumps(line))
     ctx.close()

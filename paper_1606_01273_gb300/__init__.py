@@ -197,19 +197,28 @@ class Context:
                       lam_NL, lam_lv)
 
 
-    def densities(self, class_mask=None, stream=None):
+    def compute_densities(self, class_mask=None, stream=None):
         """caspt2_densities for the classes in class_mask (default: all solved classes);
-        returns host copies (d1, d2, gdf), each symmetrised."""
+        the results stay on the device until get_densities."""
         mask = self.opts.class_mask if class_mask is None else class_mask
         s = C.c_void_p(stream) if stream is not None else None
         _check(lib().caspt2_densities(self._h, mask, s), "caspt2_densities")
+
+    def get_densities(self, with_gdf: bool = True):
+        """Host copies (d1, d2, gdf) of the last densities (gdf None if not requested)."""
         nmo = self.dims.nclosed + self.dims.nact + self.dims.nvirt
         d1, d2 = np.zeros((nmo, nmo)), np.zeros((nmo, nmo))
-        gdf = np.zeros((self.dims.naux, nmo, nmo))
+        gdf = np.zeros((self.dims.naux, nmo, nmo)) if with_gdf else None
+        gp = C.c_void_p(gdf.ctypes.data) if with_gdf else None
         _check(lib().caspt2_get_densities(self._h, MEM_HOST, C.c_void_p(d1.ctypes.data),
-                                          C.c_void_p(d2.ctypes.data), C.c_void_p(gdf.ctypes.data)),
+                                          C.c_void_p(d2.ctypes.data), gp),
                "caspt2_get_densities")
         return d1, d2, gdf
+
+    def densities(self, class_mask=None, stream=None):
+        """compute_densities + get_densities: host copies (d1, d2, gdf), each symmetrised."""
+        self.compute_densities(class_mask, stream)
+        return self.get_densities()
 
 
 def classH_noalloc(dims: Dims, opts: Options, fock, dfB, rdm1, e, norm, stream=None) -> int:
