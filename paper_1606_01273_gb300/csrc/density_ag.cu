@@ -25,6 +25,7 @@ namespace caspt2 {
 namespace {
 
 constexpr double kInvSqrt2 = 0.70710678118654752440;
+constexpr long kActAdjSmem = 96L * 1024;
 
 // Sector amplitudes and lambda in the eigenbasis mu of the sector, for every
 // (tuple t, state L): amp = -Vt_L / D_L, lam = -(r_L sum_N r_N Vt_N - 2 E_s r_L^2 amp) / D_L,
@@ -125,22 +126,30 @@ __global__ void k_swap_tuples(const double* __restrict__ src, DevClass C, ExtDim
 // Split-K Gram product over a tensor viewed as [pre][Ns][post]:
 //   part[z][x][y] = sum_{k in chunk z} A(x, k) B(y, k),  k = (p, q) over pre x post,
 //   A(x, (p, q)) = A[(p * Ns + x) * post + q].
-// 64 x 64 output tile per block, 4 x 4 per thread, FP64 FMA.
-constexpr int kGT = 64, kGK = 16;
+// Output tile TS x TS per block (TS <= 32 fitted to Ns), up to 4 outputs per thread,
+// K staged in chunks of 16 through shared memory; FP64 FMA.
+constexpr int kGS = 32, kGK = 16;
 __global__ void __launch_bounds__(256)
 k_gram(const double* __restrict__ A, const double* __restrict__ B, long Ns, unsigned post,
-       unsigned K, unsigned chunk, double* __restrict__ part) {
-  __shared__ double sa[kGK][kGT + 1], sb[kGK][kGT + 1];
-  const long x0 = (long)blockIdx.y * kGT, y0 = (long)blockIdx.x * kGT;
+       unsigned K, unsigned chunk, int TS, double* __restrict__ part) {
+  __shared__ double sa[kGK][kGS + 1], sb[kGK][kGS + 1];
+  const long x0 = (long)blockIdx.y * TS, y0 = (long)blockIdx.x * TS;
   const unsigned kbeg = blockIdx.z * chunk;
   const unsigned kend = min(K, kbeg + chunk);
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const bool xfast = post == 1u;
-  double acc[4][4] = {};
+  const int nout = TS * TS;
+  int ox[4], oy[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int q = threadIdx.x + 256 * r;
+    ox[r] = q < nout ? q / TS : 0;
+    oy[r] = q < nout ? q % TS : 0;
+  }
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
   for (unsigned k0 = kbeg; k0 < kend; k0 += kGK) {
-    for (int l = threadIdx.x; l < kGK * kGT; l += 256) {
+    for (int l = threadIdx.x; l < kGK * TS; l += 256) {
       int kk, ii;
-      if (xfast) { ii = l % kGT; kk = l / kGT; } else { kk = l % kGK; ii = l / kGK; }
+      if (xfast) { ii = l % TS; kk = l / TS; } else { kk = l % kGK; ii = l / kGK; }
       const unsigned gk = k0 + kk;
       const long gx = x0 + ii, gy = y0 + ii;
       double va = 0.0, vb = 0.0;
@@ -156,23 +165,17 @@ k_gram(const double* __restrict__ A, const double* __restrict__ B, long Ns, unsi
     __syncthreads();
 #pragma unroll 4
     for (int kk = 0; kk < kGK; ++kk) {
-      double ra[4], rb[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) { ra[q] = sa[kk][ty + 16 * q]; rb[q] = sb[kk][tx + 16 * q]; }
-#pragma unroll
-      for (int p = 0; p < 4; ++p)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc[p][q] = fma(ra[p], rb[q], acc[p][q]);
+      for (int r = 0; r < 4; ++r) acc[r] = fma(sa[kk][ox[r]], sb[kk][oy[r]], acc[r]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int p = 0; p < 4; ++p)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const long gx = x0 + ty + 16 * p, gy = y0 + tx + 16 * q;
-      if (gx < Ns && gy < Ns) part[((long)blockIdx.z * Ns + gx) * Ns + gy] = acc[p][q];
-    }
+  for (int r = 0; r < 4; ++r) {
+    const int q = threadIdx.x + 256 * r;
+    const long gx = x0 + ox[r], gy = y0 + oy[r];
+    if (q < nout && gx < Ns && gy < Ns) part[((long)blockIdx.z * Ns + gx) * Ns + gy] = acc[r];
+  }
 }
 
 // Fixed-order sum of the split-K partials.  mode 0: out[x][y] = X; mode 1 (closed
@@ -192,79 +195,60 @@ __global__ void k_gram_finish(const double* __restrict__ part, int nsplit, long 
 }
 
 // Active block of d2: partial sums over (row, col) of D^pi[row][col] dF_act^pi/df_uw.
-// Thread layout: uw = tid % a^2 (one output per thread), sub = tid / a^2 strides over the
-// m x m elements; a loop variable that carries an f index is bound to u or w, so every
-// (plan, loop) term is evaluated once across the block.  part[block][a^2].
+// Each thread takes its own (row, col) elements, evaluates every plan term once (as the
+// forward evaluation does) and adds coeff * D * Gamma into its private column of
+// acc[uw][thread] in shared memory at uw = (f index 0, f index 1); a fixed-order sum over
+// the threads gives part[block][a^2].
 __global__ void k_act_adj(const ActPlan* __restrict__ plans, int nplan, DevClass C, int a, int n,
                           RdmPtrs g, const double* __restrict__ Dm, int m,
                           double* __restrict__ part) {
-  __shared__ double red[256];
-  const int a2 = a * a;
-  const int nsub = blockDim.x / a2;
-  const int uw = threadIdx.x % a2, sub = threadIdx.x / a2;
-  const int u = uw / a, w = uw % a;
+  extern __shared__ double acc[];   // [a^2][blockDim.x]
+  const int a2 = a * a, nt = blockDim.x, tid = threadIdx.x;
+  for (int q = 0; q < a2; ++q) acc[q * nt + tid] = 0.0;
   const long total = (long)m * m;
   const long A = ipow(a, C.nact);
-  double acc = 0.0;
-  if (sub < nsub) {
-    for (long e = (long)blockIdx.x * nsub + sub; e < total; e += (long)gridDim.x * nsub) {
-      const double D0 = Dm[e], D1 = Dm[total + e];
-      if (D0 == 0.0 && D1 == 0.0) continue;
-      const int row = e / m, col = e % m;
-      int vals[24];
-      const int M = row % n, N = col % n;
-      long ab = row / n, ak = col / n;
-      const int fb = ab / A, fk = ak / A;
-      ab %= A;
-      ak %= A;
-      for (int k = C.nact - 1; k >= 0; --k) {
-        vals[kRefBra + k] = ab % a;
-        ab /= a;
-        vals[kRefKet + k] = ak % a;
-        ak /= a;
-      }
-      for (int t = 0; t < nplan; ++t) {
-        const ActPlan& P = plans[t];
-        if (!P.has_f || P.fb != fb || P.fk != fk) continue;
-        const double Dv = P.pi == 0 ? D0 : D1;
-        if (Dv == 0.0) continue;
-        bool ok = true;
-        for (int q = 0; q < P.neq; ++q)
-          if (vals[P.eq[q][0]] != vals[P.eq[q][1]]) ok = false;
-        int fix[2] = {-1, -1};
-        for (int j = 0; j < 2 && ok; ++j) {
-          const int ref = P.fidx[j], v = j == 0 ? u : w;
-          if (ref >= kRefLoop) {
-            const int k = ref - kRefLoop;
-            if (k > 1) { ok = false; break; }
-            if (fix[k] >= 0 && fix[k] != v) ok = false;
-            fix[k] = v;
-          } else if (vals[ref] != v) {
-            ok = false;
-          }
-        }
-        if (!ok) continue;
-        const int nl = P.nloop;
-        const int n0 = (nl >= 1 && fix[0] < 0) ? a : 1;
-        const int n1 = (nl >= 2 && fix[1] < 0) ? a : 1;
-        double s = 0.0;
-        for (int i0 = 0; i0 < n0; ++i0) {
-          if (nl >= 1) vals[kRefLoop] = fix[0] >= 0 ? fix[0] : i0;
-          for (int i1 = 0; i1 < n1; ++i1) {
-            if (nl >= 2) vals[kRefLoop + 1] = fix[1] >= 0 ? fix[1] : i1;
-            s += rdm_at(g.p, P.rank, n, a, M, N, vals, P.idx);
-          }
-        }
-        acc += P.coeff * Dv * s;
+  for (long e = (long)blockIdx.x * nt + tid; e < total; e += (long)gridDim.x * nt) {
+    const double D0 = Dm[e], D1 = Dm[total + e];
+    if (D0 == 0.0 && D1 == 0.0) continue;
+    const int row = e / m, col = e % m;
+    int vals[24];
+    const int M = row % n, N = col % n;
+    long ab = row / n, ak = col / n;
+    const int fb = ab / A, fk = ak / A;
+    ab %= A;
+    ak %= A;
+    for (int k = C.nact - 1; k >= 0; --k) {
+      vals[kRefBra + k] = ab % a;
+      ab /= a;
+      vals[kRefKet + k] = ak % a;
+      ak /= a;
+    }
+    for (int t = 0; t < nplan; ++t) {
+      const ActPlan& P = plans[t];
+      if (!P.has_f || P.fb != fb || P.fk != fk) continue;
+      const double Dv = P.pi == 0 ? D0 : D1;
+      if (Dv == 0.0) continue;
+      bool ok = true;
+      for (int q = 0; q < P.neq; ++q)
+        if (vals[P.eq[q][0]] != vals[P.eq[q][1]]) ok = false;
+      if (!ok) continue;
+      const int nl = P.nloop;
+      const int niter = nl == 0 ? 1 : (nl == 1 ? a : a * a);
+      const double cd = P.coeff * Dv;
+      for (int it = 0; it < niter; ++it) {
+        if (nl >= 1) vals[kRefLoop] = it % a;
+        if (nl >= 2) vals[kRefLoop + 1] = it / a;
+        const double x = rdm_at(g.p, P.rank, n, a, M, N, vals, P.idx);
+        const int uw = vals[P.fidx[0]] * a + vals[P.fidx[1]];
+        acc[uw * nt + tid] += cd * x;
       }
     }
   }
-  red[threadIdx.x] = acc;
   __syncthreads();
-  if (threadIdx.x < a2) {
+  for (int q = tid; q < a2; q += nt) {
     double t = 0.0;
-    for (int q = 0; q < nsub; ++q) t += red[q * a2 + threadIdx.x];
-    part[(long)blockIdx.x * a2 + threadIdx.x] = t;
+    for (int j = 0; j < nt; ++j) t += acc[q * nt + j];
+    part[(long)blockIdx.x * a2 + q] = t;
   }
 }
 
@@ -407,16 +391,18 @@ int gram_product(const double* A, const double* B, long pre, long Ns, long post,
   if (pre * Ns * post == 0) return CASPT2_OK;
   const long K = pre * post;
   if (K >= (1L << 31) || Ns * Ns > partmax) return CASPT2_EINVAL;
-  const long tiles = ((Ns + kGT - 1) / kGT) * ((Ns + kGT - 1) / kGT);
+  const long ntile = (Ns + kGS - 1) / kGS;
+  const int TS = (int)((Ns + ntile - 1) / ntile);        // tile edge fitted to Ns
+  const long tiles = ntile * ntile;
   long nsplit = std::max<long>(1, (152L * 4 + tiles - 1) / tiles);
   nsplit = std::min(nsplit, std::max<long>(1, K / 256));
   nsplit = std::min(nsplit, partmax / (Ns * Ns));
   long chunk = (K + nsplit - 1) / nsplit;
   chunk = (chunk + kGK - 1) / kGK * kGK;
   nsplit = (K + chunk - 1) / chunk;
-  dim3 grid((unsigned)((Ns + kGT - 1) / kGT), (unsigned)((Ns + kGT - 1) / kGT), (unsigned)nsplit);
+  dim3 grid((unsigned)ntile, (unsigned)ntile, (unsigned)nsplit);
   ++launch_counter();
-  k_gram<<<grid, 256, 0, s>>>(A, B, Ns, (unsigned)post, (unsigned)K, (unsigned)chunk, part);
+  k_gram<<<grid, 256, 0, s>>>(A, B, Ns, (unsigned)post, (unsigned)K, (unsigned)chunk, TS, part);
   ++launch_counter();
   k_gram_finish<<<launch_blocks(Ns * Ns), 256, 0, s>>>(part, (int)nsplit, Ns, mode, out, ld, off);
   CASPT2_CUDA_TRY(cudaGetLastError());
@@ -518,11 +504,16 @@ int class_densities(ClassWork& w, DensWork& dw, const Dims& d, int scheme, doubl
   }
   if (a > 0) {
     const int a2 = a * a;
-    const int nsub = 256 / a2;
-    const long nblk = std::max<long>(1, std::min<long>(152L * 4, (mm + nsub - 1) / nsub));
+    // per-thread accumulator columns: at most 96 KB of shared memory per block
+    const int nt = std::max(32, std::min(256, (int)(kActAdjSmem / (8L * a2)) / 32 * 32));
+    const size_t smem = 8ull * a2 * nt;
+    if (smem > (size_t)kActAdjSmem) return CASPT2_EINVAL;
+    const long nblk = std::max<long>(1, std::min<long>(152L * 4, (mm + nt - 1) / nt));
     if (nblk * a2 > dw.partmax) return CASPT2_EINVAL;
+    CASPT2_CUDA_TRY(cudaFuncSetAttribute(k_act_adj, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kActAdjSmem));
     ++launch_counter();
-    k_act_adj<<<(unsigned)nblk, 256, 0, s>>>(w.dF, w.nF, C, a, n, rdm, dw.Dm, m, dw.part);
+    k_act_adj<<<(unsigned)nblk, nt, smem, s>>>(w.dF, w.nF, C, a, n, rdm, dw.Dm, m, dw.part);
     ++launch_counter();
     k_act_finish<<<1, 256, 0, s>>>(dw.part, (int)nblk, a, d.c, nmo, NL, rdm.p[1], n, d2);
     CASPT2_CUDA_TRY(cudaGetLastError());

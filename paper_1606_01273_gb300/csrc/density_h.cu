@@ -132,6 +132,60 @@ __global__ void k_h_ov(const double* __restrict__ KK, const double* __restrict__
   }
 }
 
+// Same sums for n <= NM with one division per (element, shift): grid = (blocks, n), block
+// y = L; every thread holds 1 / (D0 + sigma_(L,nu)) for all nu and accumulates the 2 n^2
+// pair sums in registers.  part[(L, nu, nu')][block][2] as above.
+template <int NM>
+__global__ void k_h_ov_reg(const double* __restrict__ KK, const double* __restrict__ eps, int c,
+                           int v, const double* __restrict__ coef, int n,
+                           double* __restrict__ part) {
+  __shared__ double red[32];
+  const int L = blockIdx.y;
+  double sig[NM];
+#pragma unroll
+  for (int q = 0; q < NM; ++q) sig[q] = q < n ? coef[6 * (L * n + q)] : 0.0;
+  double sa[NM][NM], sb[NM][NM];
+#pragma unroll
+  for (int p = 0; p < NM; ++p)
+#pragma unroll
+    for (int q = 0; q < NM; ++q) sa[p][q] = sb[p][q] = 0.0;
+  const long cv = (long)c * v;
+  const long total = cv * cv;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    const long ia = e / cv, jb = e % cv;
+    const int i = ia / v, a = ia % v, j = jb / v, b = jb % v;
+    const double D0 = eps[c + a] + eps[c + b] - eps[i] - eps[j];
+    const double kk = KK[e];
+    double inv[NM];
+#pragma unroll
+    for (int q = 0; q < NM; ++q) inv[q] = q < n ? 1.0 / (D0 + sig[q]) : 0.0;
+#pragma unroll
+    for (int p = 0; p < NM; ++p) {
+      const double x1 = kk * inv[p];
+#pragma unroll
+      for (int q = 0; q < NM; ++q) {
+        const double x = x1 * inv[q];
+        sa[p][q] += x;
+        sb[p][q] += x * inv[p];
+      }
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < NM; ++p)
+#pragma unroll
+    for (int q = 0; q < NM; ++q) {
+      if (p >= n || q >= n) continue;
+      const double ta = block_sum(sa[p][q], red);
+      const double tb = block_sum(sb[p][q], red);
+      if (threadIdx.x == 0) {
+        double* o = part + ((long)((L * n + p) * n + q) * gridDim.x + blockIdx.x) * 2;
+        o[0] = ta;
+        o[1] = tb;
+      }
+    }
+}
+
 // Active block: d2[c + r][c + s] += sum_(L,nu,nu') W_Lnu' (gamma Sa + delta Sb)_(L,nu)
 // g1nu[nu][nu'][rs] - sum_L NL[L] Gamma1[L][L][rs],  g1nu = W^T Gamma1 W.
 __global__ void k_h_act_finish(const double* __restrict__ part, int nblk,
@@ -193,11 +247,14 @@ int classH_densities(const double* B, const Dims& d, const ClassHWork& hw, int s
   CASPT2_CUDA_TRY(launch_unpack_add(hd.tmp, d, SP_C, SP_V, gdf, s));
   // active block (MS-MR): pairs nu, nu' of the same state through <nu|E_rs|nu'>
   if (scheme != CASPT2_SSSR && a > 0) {
-    const int nblk = (int)std::min<long>(64, (total + 255) / 256);
+    const int nblk = (int)std::min<long>(n <= 4 ? 152L * 2 : 64L, (total + 255) / 256);
     const int n3 = n * n * n;
     if ((long)n3 * nblk * 2 > hd.partmax) return CASPT2_EINVAL;
     ++launch_counter();
-    k_h_ov<<<dim3(nblk, n3), 256, 0, s>>>(hd.B2, hw.eps, c, v, hd.coef, n, hd.part);
+    if (n <= 4)
+      k_h_ov_reg<4><<<dim3(nblk, n), 256, 0, s>>>(hd.B2, hw.eps, c, v, hd.coef, n, hd.part);
+    else
+      k_h_ov<<<dim3(nblk, n3), 256, 0, s>>>(hd.B2, hw.eps, c, v, hd.coef, n, hd.part);
     ++launch_counter();
     k_h_act_finish<<<1, 256, 0, s>>>(hd.part, nblk, hd.coef, hw.W, g1, NL, n, a, c, nmo, d2);
     CASPT2_CUDA_TRY(cudaGetLastError());

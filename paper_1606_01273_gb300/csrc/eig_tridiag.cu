@@ -214,6 +214,142 @@ k_tridiag(double* __restrict__ A, int m, double* __restrict__ vbuf, double* __re
   }
 }
 
+// Householder reflector of x[0..n1) (x[0] = alpha): tau, beta and v (v[0] = 1) written
+// by every calling block; the reduction order is fixed, so all blocks obtain bitwise
+// identical results from identical x.
+__device__ void house_vec(const double* __restrict__ x, int n1, double* __restrict__ v,
+                          double* red, double* sh) {
+  double s = 0.0;
+  for (int i = 1 + threadIdx.x; i < n1; i += blockDim.x) s += x[i] * x[i];
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) {
+    const double alpha = x[0];
+    double beta, t, scale;
+    if (s == 0.0) { beta = alpha; t = 0.0; scale = 0.0; }
+    else {
+      beta = -copysign(sqrt(alpha * alpha + s), alpha);
+      t = (beta - alpha) / beta;
+      scale = 1.0 / (alpha - beta);
+    }
+    sh[0] = t;
+    sh[1] = scale;
+    sh[2] = beta;
+  }
+  __syncthreads();
+  const double scale = sh[1];
+  for (int i = threadIdx.x; i < n1; i += blockDim.x) v[i] = (i == 0) ? 1.0 : x[i] * scale;
+  __syncthreads();
+}
+
+// Householder reduction with the matrix resident in shared memory: block b owns the
+// rows r = b (mod gridDim.x).  One bounded grid barrier per step:
+//   p_i = tau sum_j A_ij v_j for owned rows (published)                | barrier
+//   every block: w = p - (tau/2)(p.v) v, update of its rows, and — redundantly — the
+//   update of row k+1 (published by its owner after the previous step) and the next
+//   reflector, so no second barrier is needed; the owner of row k+2 publishes it.
+// Shared layout: rows [nloc][m], v[m], w[m], r[m] (all indexed by absolute column).
+// pbuf[2][m], rowbuf[2][m] are double-buffered by step parity; sync[0..1] barrier state,
+// sync[2] error flag.
+__global__ void __launch_bounds__(512)
+k_tridiag_smem(const double* __restrict__ A, int m, double* __restrict__ vbuf,
+               double* __restrict__ tau, double* __restrict__ d, double* __restrict__ e,
+               double* __restrict__ pbuf, double* __restrict__ rowbuf, unsigned* sync) {
+  extern __shared__ double smem[];
+  __shared__ double red[32];
+  __shared__ double sh[4];
+  int* err = reinterpret_cast<int*>(sync + 2);
+  const int G = gridDim.x, b = blockIdx.x;
+  const int nloc = (m - b + G - 1) / G;            // rows b, b+G, ...
+  double* rows = smem;
+  double* v = rows + (long)((m + G - 1) / G) * m;
+  double* w = v + m;
+  double* r = w + m;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  for (long q = threadIdx.x; q < (long)nloc * m; q += blockDim.x) {
+    const int li = q / m, j = q % m;
+    rows[q] = A[(long)(b + li * G) * m + j];
+  }
+  // reflector of row 0 (every block from the input)
+  for (int j = threadIdx.x; j < m; j += blockDim.x) r[j] = A[j];
+  __syncthreads();
+  house_vec(r + 1, m - 1, v + 1, red, sh);
+  double t = sh[0];
+  if (b == 0) {
+    for (int i = threadIdx.x; i < m - 1; i += blockDim.x) vbuf[1 + i] = v[1 + i];
+    if (threadIdx.x == 0) { tau[0] = t; d[0] = r[0]; e[0] = sh[2]; }
+  }
+  for (int k = 0; k + 2 < m; ++k) {
+    const int k1 = k + 1;
+    // p for the owned trailing rows
+    const int lfirst = (k1 - b + G - 1) / G;       // first owned row index >= k+1
+    for (int li = lfirst + warp; li < nloc; li += nwarp) {
+      const double* row = rows + (long)li * m;
+      double s = 0.0;
+      for (int j = k1 + lane; j < m; j += 32) s += row[j] * v[j];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+      if (lane == 0) pbuf[(long)(k & 1) * m + b + li * G] = t * s;
+    }
+    if (!grid_sync_bounded(sync, sync + 1, err)) return;
+    // w = p - (tau/2)(p.v) v
+    double s = 0.0;
+    for (int j = k1 + threadIdx.x; j < m; j += blockDim.x) {
+      const double pj = __ldcg(pbuf + (long)(k & 1) * m + j);
+      w[j] = pj;
+      s += pj * v[j];
+    }
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) sh[3] = 0.5 * t * s;
+    __syncthreads();
+    const double g = sh[3];
+    for (int j = k1 + threadIdx.x; j < m; j += blockDim.x) w[j] -= g * v[j];
+    __syncthreads();
+    // update of the owned rows
+    const long nq = (long)(nloc - lfirst) * (m - k1);
+    for (long q = threadIdx.x; q < nq; q += blockDim.x) {
+      const int li = lfirst + (int)(q / (m - k1));
+      const int j = k1 + (int)(q % (m - k1));
+      const int i = b + li * G;
+      rows[(long)li * m + j] -= v[i] * w[j] + w[i] * v[j];
+    }
+    // row k+1 after this step (every block, from the copy published before the barrier)
+    const double* old = (k == 0) ? A + (long)k1 * m : rowbuf + (long)(k1 & 1) * m;
+    for (int j = k1 + threadIdx.x; j < m; j += blockDim.x)
+      r[j] = __ldcg(old + j) - (v[k1] * w[j] + w[k1] * v[j]);
+    __syncthreads();
+    // the owner of row k+2 publishes it for the next step
+    const int k2 = k + 2;
+    if (k2 < m && (k2 % G) == b) {
+      const double* row = rows + (long)(k2 / G) * m;
+      for (int j = k2 + threadIdx.x; j < m; j += blockDim.x)
+        rowbuf[(long)(k2 & 1) * m + j] = row[j];
+    }
+    if (k + 3 < m) {
+      // next reflector from row k+1's trailing part (v is free again)
+      house_vec(r + k2, m - k2, v + k2, red, sh);
+      t = sh[0];
+      if (b == 0) {
+        for (int i = threadIdx.x; i < m - k2; i += blockDim.x)
+          vbuf[(long)k1 * m + k2 + i] = v[k2 + i];
+        if (threadIdx.x == 0) { tau[k1] = t; d[k1] = r[k1]; e[k1] = sh[2]; }
+      }
+    } else if (b == 0 && threadIdx.x == 0) {
+      d[m - 2] = r[m - 2];
+      e[m - 2] = r[m - 1];
+    }
+    __syncthreads();
+  }
+  // last diagonal element from its owner
+  if (m >= 2 && ((m - 1) % G) == b && threadIdx.x == 0)
+    d[m - 1] = rows[(long)((m - 1) / G) * m + m - 1];
+}
+
+// Shared memory of k_tridiag_smem for m columns on G blocks (0 if it does not fit).
+size_t tridiag_smem_bytes(int m, int G) {
+  const size_t b = 8ull * ((size_t)((m + G - 1) / G) * m + 3ull * m);
+  return b <= 200ull * 1024 ? b : 0;
+}
+
 __global__ void k_tail(const double* __restrict__ A, int m, double* d, double* e) {
   if (threadIdx.x != 0) return;
   if (m >= 2) {
@@ -444,34 +580,37 @@ k_vtz(const double* __restrict__ vbuf, int m, int k, const double* __restrict__ 
   }
 }
 
-// Back-transformation V = H_0 ... H_{m-3} Z with each block owning 8 columns: for every
-// reflector (in reverse order) the block forms r_c = v . Z[k+1.., c] for its columns and
+// Back-transformation V = H_0 ... H_{m-3} Z with each block owning cb consecutive columns
+// (cb = ceil(m / #SMs), one block per SM): for every reflector (in reverse order) the block
+// forms r_c = v . Z[k+1.., c] for its columns over rg = blockDim / cb row groups and
 // applies Z[k+1+i][c] -= tau v_i r_c.  Columns are independent, so no grid-wide
 // synchronisation is needed.
 __global__ void __launch_bounds__(256)
-k_backtransform(const double* __restrict__ vbuf, const double* __restrict__ tau, int m,
+k_backtransform(const double* __restrict__ vbuf, const double* __restrict__ tau, int m, int cb,
                 double* __restrict__ Z) {
-  __shared__ double part[32][9];
-  __shared__ double rc[8];
-  const int cx = threadIdx.x & 7, ry = threadIdx.x >> 3;       // 8 columns x 32 row groups
-  const int c = blockIdx.x * 8 + cx;
+  __shared__ double part[256];
+  __shared__ double rc[32];
+  const int rg = blockDim.x / cb;
+  const int cx = threadIdx.x % cb, ry = threadIdx.x / cb;
+  const bool act = ry < rg;
+  const int c = blockIdx.x * cb + cx;
   for (int k = m - 3; k >= 0; --k) {
     const int n1 = m - k - 1;
     const double* v = vbuf + (long)k * m + k + 1;
     double s = 0.0;
-    if (c < m)
-      for (int i = ry; i < n1; i += 32) s += v[i] * Z[(long)(k + 1 + i) * m + c];
-    part[ry][cx] = s;
+    if (act && c < m)
+      for (int i = ry; i < n1; i += rg) s += v[i] * Z[(long)(k + 1 + i) * m + c];
+    part[threadIdx.x] = s;
     __syncthreads();
-    if (threadIdx.x < 8) {
+    if (threadIdx.x < cb) {
       double t = 0.0;
-      for (int q = 0; q < 32; ++q) t += part[q][threadIdx.x];
+      for (int q = 0; q < rg; ++q) t += part[q * cb + threadIdx.x];
       rc[threadIdx.x] = t * tau[k];
     }
     __syncthreads();
-    if (c < m) {
+    if (act && c < m) {
       const double r = rc[cx];
-      for (int i = ry; i < n1; i += 32) Z[(long)(k + 1 + i) * m + c] -= v[i] * r;
+      for (int i = ry; i < n1; i += rg) Z[(long)(k + 1 + i) * m + c] -= v[i] * r;
     }
     __syncthreads();
   }
@@ -512,11 +651,40 @@ int sym_eig_tridiag(double* A, int m, double* w, double* V, double* work, cudaSt
   double* tau = e2 + m;
   double* p = tau + m;
   double* r = p + m;
-  // 1. tridiagonalise (one cooperative launch for large matrices)
-  if (m > 64) {
-    int dev = 0, nsm = 0, per = 0;
-    CASPT2_CUDA_TRY(cudaGetDevice(&dev));
-    CASPT2_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  // 1. tridiagonalise (one cooperative launch for large matrices: rows resident in
+  //    shared memory when they fit, else streamed through L2)
+  int dev = 0, nsm = 0;
+  CASPT2_CUDA_TRY(cudaGetDevice(&dev));
+  CASPT2_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const int Gs = std::max(1, std::min(nsm, m));
+  const size_t smem_b = m > 64 ? tridiag_smem_bytes(m, Gs) : 0;
+  if (smem_b > 0) {
+    unsigned* sync = reinterpret_cast<unsigned*>(r);   // r is free until the back-transform
+    double* pbuf = u0;                                 // u0.. are free until inverse iteration
+    double* rowbuf = u0 + 2 * (long)m;
+    CASPT2_CUDA_TRY(cudaFuncSetAttribute(k_tridiag_smem,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem_b));
+    CASPT2_CUDA_TRY(cudaMemsetAsync(sync, 0, 4 * sizeof(unsigned), s));
+    const double* Ac = A;
+    void* args[] = {&Ac, (void*)&m, &vbuf, &tau, &d, &e, &pbuf, &rowbuf, &sync};
+    ++launch_counter();
+    if (tm && tm->e0) CASPT2_CUDA_TRY(cudaEventRecord(tm->e0, s));
+    CASPT2_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_tridiag_smem, Gs, 512, args, smem_b, s));
+    if (tm && tm->e1) CASPT2_CUDA_TRY(cudaEventRecord(tm->e1, s));
+    int herr = 0;
+    CASPT2_CUDA_TRY(cudaMemcpyAsync(&herr, sync + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CASPT2_CUDA_TRY(cudaStreamSynchronize(s));
+    if (herr != 0) return CASPT2_ETIMEOUT;
+    if (tm && tm->e0) {
+      float ms = 0.f;
+      CASPT2_CUDA_TRY(cudaEventElapsedTime(&ms, tm->e0, tm->e1));
+      tm->ms += ms;
+      tm->flops += 4.0 / 3.0 * (double)m * m * m;   // Householder tridiagonalisation
+      ++tm->launches;
+    }
+  } else if (m > 64) {
+    int per = 0;
     CASPT2_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_tridiag, 512, 0));
     const int grid = std::max(1, std::min(nsm * std::max(per, 1), nsm));
     unsigned* sync = reinterpret_cast<unsigned*>(r);   // r is free until the back-transform
@@ -548,8 +716,10 @@ int sym_eig_tridiag(double* A, int m, double* w, double* V, double* work, cudaSt
       k_rank2<<<nblocks((long)n1 * n1), kT, 0, s>>>(A, m, k, vbuf, tau, p);
     }
   }
-  ++launch_counter();
-  k_tail<<<1, 32, 0, s>>>(A, m, d, e);
+  if (smem_b == 0) {
+    ++launch_counter();
+    k_tail<<<1, 32, 0, s>>>(A, m, d, e);
+  }
   CASPT2_CUDA_TRY(cudaGetLastError());
   // Gershgorin interval and pivmin on the host (small vectors)
   std::vector<double> hd(m), he(m);
@@ -589,7 +759,8 @@ int sym_eig_tridiag(double* A, int m, double* w, double* V, double* work, cudaSt
   // 5. back-transformation V = H_0 ... H_{m-3} Z (column-owned, one launch)
   if (m >= 3) {
     ++launch_counter();
-    k_backtransform<<<(m + 7) / 8, 256, 0, s>>>(vbuf, tau, m, V);
+    const int cb = std::max(1, std::min(32, (m + nsm - 1) / nsm));
+    k_backtransform<<<(m + cb - 1) / cb, 256, 0, s>>>(vbuf, tau, m, cb, V);
   }
   CASPT2_CUDA_TRY(cudaGetLastError());
   return CASPT2_OK;

@@ -61,14 +61,82 @@ k_dgemm(int M, int N, int K, double alpha, const double* __restrict__ A, int lda
     }
 }
 
+// Small-tile variant for products with a short edge: a TM x TN tile (each <= 32,
+// fitted to M and N) per block, up to 4 outputs per thread, K in chunks of 8.
+constexpr int kST = 32, kSK = 8;
+__global__ void __launch_bounds__(256)
+k_dgemm_s(int M, int N, int K, double alpha, const double* __restrict__ A, int lda, int ta,
+          const double* __restrict__ B, int ldb, int tb, double beta, double* __restrict__ C,
+          int ldc, int TM, int TN, int tn, long sA, long sB, long sC) {
+  __shared__ double sa[kSK][kST + 1], sb[kSK][kST + 1];
+  A += blockIdx.y * sA;
+  B += blockIdx.y * sB;
+  C += blockIdx.y * sC;
+  const int i0 = (int)(blockIdx.x / tn) * TM, j0 = (int)(blockIdx.x % tn) * TN;
+  const int nout = TM * TN;
+  int oi[4], oj[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int q = threadIdx.x + 256 * r;
+    oi[r] = q < nout ? q / TN : 0;
+    oj[r] = q < nout ? q % TN : 0;
+  }
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int k0 = 0; k0 < K; k0 += kSK) {
+    for (int l = threadIdx.x; l < kSK * TM; l += 256) {
+      int kk, ii;
+      if (ta) { ii = l % TM; kk = l / TM; } else { kk = l % kSK; ii = l / kSK; }
+      const int gi = i0 + ii, gk = k0 + kk;
+      double v = 0.0;
+      if (gi < M && gk < K) v = ta ? A[(long)gk * lda + gi] : A[(long)gi * lda + gk];
+      sa[kk][ii] = v;
+    }
+    for (int l = threadIdx.x; l < kSK * TN; l += 256) {
+      int kk, jj;
+      if (tb) { kk = l % kSK; jj = l / kSK; } else { jj = l % TN; kk = l / TN; }
+      const int gj = j0 + jj, gk = k0 + kk;
+      double v = 0.0;
+      if (gj < N && gk < K) v = tb ? B[(long)gj * ldb + gk] : B[(long)gk * ldb + gj];
+      sb[kk][jj] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kSK; ++kk) {
+#pragma unroll
+      for (int r = 0; r < 4; ++r) acc[r] = fma(sa[kk][oi[r]], sb[kk][oj[r]], acc[r]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int q = threadIdx.x + 256 * r;
+    const int gi = i0 + oi[r], gj = j0 + oj[r];
+    if (q < nout && gi < M && gj < N) {
+      double* c = C + (long)gi * ldc + gj;
+      *c = alpha * acc[r] + (beta == 0.0 ? 0.0 : beta * *c);
+    }
+  }
+}
+
 cudaError_t dgemm(int M, int N, int K, double alpha, const double* A, int lda, bool ta,
                   const double* B, int ldb, bool tb, double beta, double* C, int ldc,
                   cudaStream_t s, int batch, long sA, long sB, long sC) {
   if (M <= 0 || N <= 0 || batch <= 0) return cudaSuccess;
-  dim3 grid((N + kGT - 1) / kGT, (M + kGT - 1) / kGT, batch);
+  // padded work of the 64 x 64 tiles against tiles fitted to M and N (<= 32)
+  const double pad64 = (double)((M + kGT - 1) / kGT * kGT) * ((N + kGT - 1) / kGT * kGT) /
+                       ((double)M * N);
   ++launch_counter();
-  k_dgemm<<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, ta ? 1 : 0, B, ldb, tb ? 1 : 0, beta, C, ldc,
-                               sA, sB, sC);
+  if (pad64 > 1.3 || (M + kGT - 1) / kGT > 65535) {
+    const int tm = (M + kST - 1) / kST, tn = (N + kST - 1) / kST;
+    const int TM = (M + tm - 1) / tm, TN = (N + tn - 1) / tn;
+    dim3 grid((unsigned)((long)tm * tn), batch);
+    k_dgemm_s<<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, ta ? 1 : 0, B, ldb, tb ? 1 : 0, beta, C,
+                                   ldc, TM, TN, tn, sA, sB, sC);
+  } else {
+    dim3 grid((N + kGT - 1) / kGT, (M + kGT - 1) / kGT, batch);
+    k_dgemm<<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, ta ? 1 : 0, B, ldb, tb ? 1 : 0, beta, C,
+                                 ldc, sA, sB, sC);
+  }
   return cudaGetLastError();
 }
 
