@@ -193,7 +193,9 @@ def run_ours(args):
     # gradient contraction with the derivative integrals)
     d2h = 8 * (4 * n * n + 2 * n + 1 + 8 * (n * n + n)) + 2 * 8 * p.nmo * p.nmo
     dev_in = [torch.from_numpy(x).to(dev) for x in host]   # f, B, rdm1-4
-    ctx = cp.Context(p.nclosed, p.nact, p.nvirt, p.naux, p.nstate, **OPTS)
+    popt = dict(OPTS, precision=cp.BF16X if args.precision == "bf16x" else cp.FP64,
+                slices=args.slices)
+    ctx = cp.Context(p.nclosed, p.nact, p.nvirt, p.naux, p.nstate, **popt)
     ctx.set_inputs(*dev_in)
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -237,7 +239,7 @@ def run_ours(args):
 
     # end to end through the C ABI with host buffers (pinned), H2D + D2H inside the timing
     pinned = [torch.from_numpy(x).pin_memory() for x in host]
-    ctx_h = cp.Context(p.nclosed, p.nact, p.nvirt, p.naux, p.nstate, **OPTS)
+    ctx_h = cp.Context(p.nclosed, p.nact, p.nvirt, p.naux, p.nstate, **popt)
     for _ in range(max(1, args.warmup)):
         ctx_h.set_inputs(*pinned)
         ctx_h.solve()
@@ -329,6 +331,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", choices=["fp64", "bf16x"], default="fp64")
+    ap.add_argument("--slices", type=int, default=7)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

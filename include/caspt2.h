@@ -46,6 +46,13 @@ extern "C" {
 /* contraction schemes (Sec. II.B, Eq. wfp and Eq. wfp2) */
 #define CASPT2_MSMR          0
 #define CASPT2_SSSR          1
+/* precision forms */
+#define CASPT2_FP64          0   /* plain FP64 on the FP64 pipe                              */
+#define CASPT2_BF16X         1   /* exact BF16 splitting on the tcgen05 tensor cores: the DF  */
+                                 /* integral contractions, the class-H pair integrals and the */
+                                 /* density Gram products run as S-slice split GEMMs (see    */
+                                 /* options.slices); eigensolvers, H^eff and reductions stay  */
+                                 /* FP64                                                      */
 
 /* excitation classes (Eq. class): A E_ri,st  B E_ri,sj  C E_ar,st  D E_ai,rs + E_ar,si
  *                                  E E_ai,rj  F E_ar,bs  G E_ar,bi  H E_ai,bj        */
@@ -66,9 +73,14 @@ typedef struct {
     double enuc;         /* constant added to the diagonal of H^ref                            */
     int    target_state; /* P for lambda and densities; -1 = energies only                     */
     unsigned class_mask; /* bit k set = class k is included (default: all supported)           */
+    int    precision;    /* CASPT2_FP64 (default) or CASPT2_BF16X                               */
+    int    slices;       /* BF16 slices per operand for CASPT2_BF16X, 1..7 (default 7: every   */
+                         /* product within FP64 rounding of the plain form; 5: ~2e-12 of the   */
+                         /* row x column scale)                                                */
 } caspt2_options;
 
-/* Fill *opt with defaults: XMS, MS-MR, shift 0, 1e-9, enuc 0, target 0, all classes. */
+/* Fill *opt with defaults: XMS, MS-MR, shift 0, 1e-9, enuc 0, target 0, all classes,
+ * plain FP64, 7 slices. */
 void caspt2_default_options(caspt2_options* opt);
 
 /* Create a context for the given sizes.  Allocates its device buffers

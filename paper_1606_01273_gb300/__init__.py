@@ -20,6 +20,7 @@ OK, EINVAL, ENOMEM, ENOTCONV, ENAN, ETIMEOUT, ECUDA, ESTATE, ESCRATCH = 0, -1, -
 WINTRUDER = 1
 MEM_HOST, MEM_DEVICE = 0, 1
 MSMR, SSSR = 0, 1
+FP64, BF16X = 0, 1
 CLASSES = "ABCDEFGH"
 
 
@@ -31,7 +32,7 @@ class Dims(C.Structure):
 class Options(C.Structure):
     _fields_ = [("xms", C.c_int), ("scheme", C.c_int), ("shift", C.c_double),
                 ("ovl_thresh", C.c_double), ("enuc", C.c_double), ("target_state", C.c_int),
-                ("class_mask", C.c_uint)]
+                ("class_mask", C.c_uint), ("precision", C.c_int), ("slices", C.c_int)]
 
 
 _lib = None

@@ -13,6 +13,7 @@
 #include "class_ag.cuh"
 #include "kernels.cuh"
 #include "linalg.cuh"
+#include "ozaki.cuh"
 
 using namespace caspt2;
 
@@ -62,6 +63,9 @@ struct caspt2_ctx {
   std::map<int, double*> gblk;        // adjoint (pq|rt) blocks, keys of eri_blk
   EriBlocks g_tab{};
   double *dd1 = nullptr, *dd2 = nullptr, *dgdf = nullptr, *gtmp = nullptr;
+  // precision form: split BF16 tensor-core GEMMs, class-H pair integrals kept for the densities
+  OzWork oz{};
+  double *hK = nullptr, *hKK = nullptr, *hpack = nullptr;
   cudaEvent_t dev0 = nullptr, dev1 = nullptr;
   // results
   double *heff = nullptr, *ems = nullptr, *R = nullptr;
@@ -98,6 +102,8 @@ void caspt2_default_options(caspt2_options* o) {
   o->enuc = 0.0;
   o->target_state = 0;
   o->class_mask = caspt2_supported_classes();
+  o->precision = CASPT2_FP64;
+  o->slices = 7;
 }
 
 unsigned caspt2_supported_classes(void) { return (1u << CASPT2_NCLASS) - 1u; }
@@ -131,6 +137,7 @@ void caspt2_destroy(caspt2_ctx* ctx) {
   if (ctx->hw.ev_gemm1) cudaEventDestroy(ctx->hw.ev_gemm1);
   if (ctx->tri.e0) cudaEventDestroy(ctx->tri.e0);
   if (ctx->dev0) cudaEventDestroy(ctx->dev0);
+  oz_release(ctx->oz);
   if (ctx->dev1) cudaEventDestroy(ctx->dev1);
   if (ctx->tri.e1) cudaEventDestroy(ctx->tri.e1);
   cudaSetDevice(cur);
@@ -151,6 +158,8 @@ int caspt2_create(caspt2_ctx** out, const caspt2_dims* dims, const caspt2_option
   if (!(o.shift >= 0.0) || !(o.ovl_thresh > 0.0)) return CASPT2_EINVAL;
   if (o.class_mask & ~caspt2_supported_classes()) return CASPT2_EINVAL;
   if (o.target_state >= q.nstate) return CASPT2_EINVAL;
+  if (o.precision != CASPT2_FP64 && o.precision != CASPT2_BF16X) return CASPT2_EINVAL;
+  if (o.precision == CASPT2_BF16X && (o.slices < 1 || o.slices > 7)) return CASPT2_EINVAL;
 
   caspt2_ctx* c = new (std::nothrow) caspt2_ctx();
   if (!c) return CASPT2_ENOMEM;
@@ -201,6 +210,16 @@ int caspt2_create(caspt2_ctx** out, const caspt2_dims* dims, const caspt2_option
   ALLOC(c->hw.partial, (size_t)c->hw.nblocks * (3 * nshift + 1));
   ALLOC(c->hw.sums, 3 * nshift + 1);
   ALLOC(c->mom, (size_t)CASPT2_NCLASS * (n * n * n + n * n + n));
+  if (o.precision == CASPT2_BF16X) {
+    c->oz.on = true;
+    c->oz.S = o.slices;
+    if ((o.class_mask >> CASPT2_CLASS_H & 1u) && d.c > 0 && d.v > 0) {
+      const size_t cv = (size_t)d.c * d.v;
+      ALLOC(c->hK, cv * cv);
+      ALLOC(c->hKK, cv * cv);
+      ALLOC(c->hpack, (size_t)d.X * cv);
+    }
+  }
   ALLOC(c->lamNL, (size_t)CASPT2_NCLASS * n);
   ALLOC(c->lamLV, (size_t)CASPT2_NCLASS * n * n);
   // classes A-G: plans, class matrices, sources, sector work space, integral blocks
@@ -377,7 +396,13 @@ int caspt2_solve(caspt2_ctx* c, void* stream) {
   CASPT2_CUDA_TRY(cudaEventRecord(c->ev[1], s));
 
   // ---- stage 1: class H (direct)
-  if (o.class_mask >> CASPT2_CLASS_H & 1u) {
+  if ((o.class_mask >> CASPT2_CLASS_H & 1u) && c->oz.on) {
+    CASPT2_CUDA_TRY(launch_classH_split(c->f, c->B, c->Ftil, c->E0, o.shift, o.scheme, d, c->hw,
+                                        c->status, c->ecls + (long)CASPT2_CLASS_H * n * n,
+                                        c->ncls + (long)CASPT2_CLASS_H * n,
+                                        c->mom + (long)CASPT2_CLASS_H * msz, c->mindenom, c->oz,
+                                        c->hpack, c->hK, c->hKK, s));
+  } else if (o.class_mask >> CASPT2_CLASS_H & 1u) {
     CASPT2_CUDA_TRY(launch_classH(c->f, c->B, c->Ftil, c->E0, o.shift, o.scheme, d, c->hw,
                                   c->status, c->ecls + (long)CASPT2_CLASS_H * n * n,
                                   c->ncls + (long)CASPT2_CLASS_H * n,
@@ -398,7 +423,7 @@ int caspt2_solve(caspt2_ctx* c, void* stream) {
         CASPT2_CUDA_TRY(launch_rotate_rdm(c->rdm4, c->U, n, a2 * a2 * a2 * a2, c->rdm4r, s));
       for (auto& kv : c->eri_blk) {
         int sp4[4] = {kv.first / 27, (kv.first / 9) % 3, (kv.first / 3) % 3, kv.first % 3};
-        CASPT2_CUDA_TRY(eri_block(c->B, d, sp4, c->pack0, c->pack1, kv.second, s));
+        CASPT2_CUDA_TRY(eri_block(c->B, d, sp4, c->pack0, c->pack1, kv.second, s, &c->oz));
       }
       RdmPtrs g{{nullptr, c->rdm1r, c->rdm2r, c->rdm3r, c->rdm4r}};
       for (int k = 0; k < 7; ++k) {
@@ -441,7 +466,11 @@ int caspt2_solve(caspt2_ctx* c, void* stream) {
   CASPT2_CUDA_TRY(cudaMemcpyAsync(&c->hEcore, c->ecore, sizeof(double), cudaMemcpyDeviceToHost, s));
   CASPT2_CUDA_TRY(cudaMemcpyAsync(&c->hMinDenom, c->mindenom, sizeof(double), cudaMemcpyDeviceToHost, s));
   CASPT2_CUDA_TRY(cudaMemcpyAsync(&hst, c->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  int ozerr = 0;
+  if (c->oz.err)
+    CASPT2_CUDA_TRY(cudaMemcpyAsync(&ozerr, c->oz.err, sizeof(int), cudaMemcpyDeviceToHost, s));
   CASPT2_CUDA_TRY(cudaStreamSynchronize(s));
+  if (ozerr != 0) return CASPT2_ETIMEOUT;
   for (int k = 0; k < kNumStages; ++k) {
     float ms = 0.f;
     CASPT2_CUDA_TRY(cudaEventElapsedTime(&ms, c->ev[k], c->ev[k + 1]));
@@ -571,7 +600,8 @@ int alloc_densities(caspt2_ctx* c) {
     HDensWork& h = c->hd;
     const long cv = (long)d.c * d.v;
     h.size = cv * cv;
-    ALLOC(h.K, (size_t)h.size);
+    if (c->hK) h.K = c->hK;          // the split energy path keeps K for the densities
+    else ALLOC(h.K, (size_t)h.size);
     ALLOC(h.B1, (size_t)h.size);
     ALLOC(h.B2, (size_t)h.size);
     ALLOC(h.pack, (size_t)d.X * cv);
@@ -622,7 +652,8 @@ int caspt2_densities(caspt2_ctx* c, unsigned class_mask, void* stream) {
     for (int k = 0; k < 7; ++k) {
       if (!(class_mask >> k & 1u) || !c->cw_on[k]) continue;
       const int st = class_densities(c->cw[k], c->dw, d, o.scheme, o.shift, g, c->E0, c->eps, c->R,
-                                     P, c->lamNL + (long)k * n, c->g_tab, c->dd1, c->dd2, s);
+                                     P, c->lamNL + (long)k * n, c->g_tab, c->dd1, c->dd2, &c->oz,
+                                     s);
       if (st != CASPT2_OK) return st;
     }
     for (auto& kv : c->gblk) {
@@ -634,14 +665,18 @@ int caspt2_densities(caspt2_ctx* c, unsigned class_mask, void* stream) {
   if ((class_mask >> CASPT2_CLASS_H & 1u) && d.c > 0 && d.v > 0) {
     const int st = classH_densities(c->B, d, c->hw, o.scheme, o.shift, c->R, P,
                                     c->lamNL + (long)CASPT2_CLASS_H * n, c->rdm1r, c->hd, c->dd2,
-                                    c->dgdf, s);
+                                    c->dgdf, &c->oz, c->hK != nullptr && c->hd.K == c->hK, s);
     if (st != CASPT2_OK) return st;
   }
   CASPT2_CUDA_TRY(launch_symmetrize(c->dd1, (int)nmo, 1, s));
   CASPT2_CUDA_TRY(launch_symmetrize(c->dd2, (int)nmo, 1, s));
   CASPT2_CUDA_TRY(launch_symmetrize(c->dgdf, (int)nmo, d.X, s));
   CASPT2_CUDA_TRY(cudaEventRecord(c->dev1, s));
+  int ozerr = 0;
+  if (c->oz.err)
+    CASPT2_CUDA_TRY(cudaMemcpyAsync(&ozerr, c->oz.err, sizeof(int), cudaMemcpyDeviceToHost, s));
   CASPT2_CUDA_TRY(cudaStreamSynchronize(s));
+  if (ozerr != 0) return CASPT2_ETIMEOUT;
   float ms = 0.f;
   CASPT2_CUDA_TRY(cudaEventElapsedTime(&ms, c->dev0, c->dev1));
   c->times[kNumStages + 4] = ms;

@@ -431,7 +431,7 @@ cudaError_t gdf_from_block(const double* B, const Dims& d, const int sp[4], cons
 }
 
 cudaError_t eri_block(const double* B, const Dims& d, const int sp[4], double* pack0, double* pack1,
-                      double* out, cudaStream_t s) {
+                      double* out, cudaStream_t s, OzWork* oz) {
   const int n0 = space_dim(d, sp[0]), n1 = space_dim(d, sp[1]);
   const int n2 = space_dim(d, sp[2]), n3 = space_dim(d, sp[3]);
   if ((long)n0 * n1 * n2 * n3 == 0) return cudaSuccess;
@@ -444,6 +444,11 @@ cudaError_t eri_block(const double* B, const Dims& d, const int sp[4], double* p
                                                 space_off(d, sp[3]), n3, pack1);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  if (oz && oz->on) {
+    // rows pq (K = P): pack0[P][pq]; rows rt: pack1[P][rt]
+    const OzView va{pack0, 1, (long)n0 * n1, (long)d.X, 0}, vb{pack1, 1, (long)n2 * n3, (long)d.X, 0};
+    return oz_matmul(*oz, va, vb, false, n0 * n1, n2 * n3, d.X, 1.0, 0.0, out, (long)n2 * n3, s);
+  }
   return dgemm(n0 * n1, n2 * n3, d.X, 1.0, pack0, n0 * n1, true, pack1, n2 * n3, false, 0.0, out,
                n2 * n3, s);
 }

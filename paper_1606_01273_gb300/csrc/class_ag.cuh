@@ -4,6 +4,7 @@
 
 #include "kernels.cuh"
 #include "linalg.cuh"
+#include "ozaki.cuh"
 #include "terms.h"
 
 namespace caspt2 {
@@ -103,7 +104,8 @@ cudaError_t launch_lambda(const double* mom, const double* R, int n, int P, doub
 // NL = this class's <lambda_L|S|T_L>.
 int class_densities(ClassWork& w, DensWork& dw, const Dims& d, int scheme, double shift,
                     RdmPtrs rdm, const double* E0, const double* eps_cv, const double* R, int P,
-                    const double* NL, const EriBlocks& G, double* d1, double* d2, cudaStream_t s);
+                    const double* NL, const EriBlocks& G, double* d1, double* d2, OzWork* oz,
+                    cudaStream_t s);
 
 // GDF[Q][p][q] += sum_rt G[pq][rt] B[Q][rt] and GDF[Q][r][t] += sum_pq G[pq][rt] B[Q][pq]
 // for one adjoint block with spaces sp; pack0/pack1/tmp hold X * (block pair) doubles.
@@ -114,8 +116,10 @@ cudaError_t gdf_from_block(const double* B, const Dims& d, const int sp[4], cons
 //   X[x][y] = sum_(p, q) A[(p Ns + x) post + q] B[(p Ns + y) post + q],
 // finished into out by mode: 0 out[x][y] = X; 1 out[off+y][off+x] -= X; 2 out[off+x][off+y] += X.
 // part holds the split partials (partmax doubles, >= Ns^2).
+// oz (optional, on): the product runs as a split BF16 GEMM on the tensor cores.
 int gram_product(const double* A, const double* B, long pre, long Ns, long post, int mode,
-                 double* out, long ld, long off, double* part, long partmax, cudaStream_t s);
+                 double* out, long ld, long off, double* part, long partmax, cudaStream_t s,
+                 OzWork* oz = nullptr);
 
 // out[Q][x][y] = B[Q][off(sp0) + x][off(sp1) + y];  gdf[Q][off(sp0) + x][off(sp1) + y] += tmp[Q][x][y]
 cudaError_t launch_pack_block(const double* B, const Dims& d, int sp0, int sp1, double* out,
@@ -128,7 +132,7 @@ cudaError_t launch_symmetrize(double* x, int nmo, long batch, cudaStream_t s);
 
 // DF integral block out[p][q][r][t] = sum_P B[P][p][q] B[P][r][t] for the given spaces.
 cudaError_t eri_block(const double* B, const Dims& d, const int sp[4], double* pack0, double* pack1,
-                      double* out, cudaStream_t s);
+                      double* out, cudaStream_t s, OzWork* oz = nullptr);
 
 // h = f - g(d_core) - g(d_act), g(d_core)_xy = sum_j [2 (xy|jj) - (xj|jy)]
 cudaError_t launch_hcore(const double* f, const double* g_act, const double* B, const double* bsum,

@@ -17,6 +17,8 @@
 // sums are reduced afterwards in a fixed order, so results are bitwise
 // reproducible run to run.
 #include "kernels.cuh"
+#include "class_ag.cuh"
+#include "ozaki.cuh"
 
 namespace caspt2 {
 
@@ -265,6 +267,57 @@ __global__ void k_classH_combine(const double* __restrict__ sums, const double* 
   }
 }
 
+// Split form: KK[(ia)][(jb)] = K_ij^ab (2 K_ij^ab - K_ij^ba) from the full K matrix.
+__global__ void k_classH_num(const double* __restrict__ K, int c, int v, double* __restrict__ KK) {
+  const long cv = (long)c * v, total = cv * cv;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    const long ia = e / cv, jb = e % cv;
+    const int i = ia / v, a = ia % v, j = jb / v, b = jb % v;
+    const double k1 = K[e];
+    KK[e] = k1 * (2.0 * k1 - K[((long)i * v + b) * cv + (long)j * v + a]);
+  }
+}
+
+// Split form: per-shift sums over all (i, j, a, b) of KK / D, KK / D^2, KK / D^3 and the
+// smallest |D| with KK != 0; grid (nblk, nshift), one row of partial per block with only
+// its own shift's columns set (the others zero, the min column +inf for no element), so the
+// fixed-order column reduction of the fused kernel applies unchanged.
+__global__ void k_classH_sums(const double* __restrict__ KK, const double* __restrict__ eps,
+                              const double* __restrict__ shifts, int nshift, int c, int v,
+                              double* __restrict__ partial) {
+  __shared__ double red[32];
+  const int k = blockIdx.y;
+  const double sh = shifts[k];
+  const long cv = (long)c * v, total = cv * cv;
+  double e = 0.0, nr = 0.0, n3 = 0.0, dmin = 1e300;
+  for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < total;
+       q += (long)gridDim.x * blockDim.x) {
+    const long ia = q / cv, jb = q % cv;
+    const int i = ia / v, a = ia % v, j = jb / v, b = jb % v;
+    const double num = KK[q];
+    const double D = eps[c + a] + eps[c + b] - eps[i] - eps[j] + sh;
+    const double inv = 1.0 / D;
+    const double x = num * inv;
+    e += x;
+    nr = fma(x, inv, nr);
+    n3 = fma(x * inv, inv, n3);
+    if (num != 0.0) dmin = fmin(dmin, fabs(D));
+  }
+  const int ncol = 3 * nshift + 1;
+  double* out = partial + ((long)blockIdx.y * gridDim.x + blockIdx.x) * ncol;
+  for (int t = threadIdx.x; t < 3 * nshift; t += blockDim.x) out[t] = 0.0;
+  __syncthreads();
+  e = block_sum(e, red);
+  if (threadIdx.x == 0) out[k] = e;
+  nr = block_sum(nr, red);
+  if (threadIdx.x == 0) out[nshift + k] = nr;
+  n3 = block_sum(n3, red);
+  if (threadIdx.x == 0) out[2 * nshift + k] = n3;
+  dmin = block_min(dmin, red);
+  if (threadIdx.x == 0) out[3 * nshift] = dmin;
+}
+
 cudaError_t launch_eps_cv(const double* f, const Dims& d, double* eps, cudaStream_t s) {
   if (d.c + d.v == 0) return cudaSuccess;
   ++launch_counter();
@@ -312,6 +365,47 @@ cudaError_t launch_classH(const double* f, const double* B, const double* Ftil, 
   const int ncol = 3 * nshift + 1;
   ++launch_counter();
   k_reduce_cols<<<ncol, 256, 0, s>>>(w.partial, nb, ncol, w.sums);
+  ++launch_counter();
+  k_classH_combine<<<1, 256, 0, s>>>(w.sums, w.W, n, scheme, ecls, ncls, mom, mindenom, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_classH_split(const double* f, const double* B, const double* Ftil,
+                                const double* E0, double shift, int scheme, const Dims& d,
+                                ClassHWork& w, int* status, double* ecls, double* ncls,
+                                double* mom, double* mindenom, OzWork& oz, double* pack,
+                                double* K, double* KK, cudaStream_t s) {
+  const int n = d.n, nmo = d.nmo();
+  const int nshift = classH_nshift(d, scheme);
+  cudaError_t e;
+  if (d.c == 0 || d.v == 0) {
+    e = cudaMemsetAsync(ecls, 0, sizeof(double) * n * n, s);
+    if (e != cudaSuccess) return e;
+    return cudaMemsetAsync(ncls, 0, sizeof(double) * n, s);
+  }
+  ++launch_counter();
+  k_eps_cv<<<(d.c + d.v + 127) / 128, 128, 0, s>>>(f, nmo, d.c, d.a, d.v, w.eps);
+  e = launch_sym_eig(Ftil, n, w.W, w.omega, 0, status, s);
+  if (e != cudaSuccess) return e;
+  ++launch_counter();
+  k_classH_shifts<<<1, kMaxShift, 0, s>>>(w.omega, E0, shift, n, scheme, w.shifts);
+  const long cv = (long)d.c * d.v;
+  if ((e = launch_pack_block(B, d, SP_C, SP_V, pack, s)) != cudaSuccess) return e;
+  if (w.ev_gemm0) cudaEventRecord(w.ev_gemm0, s);
+  const OzView vp{pack, 1, cv, (long)d.X, 0};     // rows (ia), K = Q
+  if ((e = oz_matmul(oz, vp, vp, true, (int)cv, (int)cv, d.X, 1.0, 0.0, K, cv, s)) != cudaSuccess)
+    return e;
+  if (w.ev_gemm1) cudaEventRecord(w.ev_gemm1, s);
+  const long total = cv * cv;
+  ++launch_counter();
+  k_classH_num<<<(int)std::min<long>((total + 255) / 256, 152L * 32), 256, 0, s>>>(K, d.c, d.v, KK);
+  const int nblk = (int)std::max<long>(1, std::min<long>(w.nblocks / nshift, 152L * 4));
+  ++launch_counter();
+  k_classH_sums<<<dim3(nblk, nshift), 256, 0, s>>>(KK, w.eps, w.shifts, nshift, d.c, d.v,
+                                                   w.partial);
+  const int ncol = 3 * nshift + 1;
+  ++launch_counter();
+  k_reduce_cols<<<ncol, 256, 0, s>>>(w.partial, (long)nblk * nshift, ncol, w.sums);
   ++launch_counter();
   k_classH_combine<<<1, 256, 0, s>>>(w.sums, w.W, n, scheme, ecls, ncls, mom, mindenom, status);
   return cudaGetLastError();

@@ -387,10 +387,21 @@ __global__ void k_symmetrize(double* __restrict__ x, int nmo, long batch) {
 // X = sum over (pre, post) of A(x, .) B(y, .) for [pre][Ns][post] tensors, finished
 // into `out` according to `mode` (see k_gram_finish).
 int gram_product(const double* A, const double* B, long pre, long Ns, long post, int mode,
-                 double* out, long ld, long off, double* part, long partmax, cudaStream_t s) {
+                 double* out, long ld, long off, double* part, long partmax, cudaStream_t s,
+                 OzWork* oz) {
   if (pre * Ns * post == 0) return CASPT2_OK;
   const long K = pre * post;
   if (K >= (1L << 31) || Ns * Ns > partmax) return CASPT2_EINVAL;
+  if (oz && oz->on) {
+    // element (x, (p, q)) of a [pre][Ns][post] tensor: x * post + p * Ns * post + q
+    const OzView va{A, post, 1, post, Ns * post}, vb{B, post, 1, post, Ns * post};
+    CASPT2_CUDA_TRY(oz_matmul(*oz, va, vb, A == B, (int)Ns, (int)Ns, (int)K, 1.0, 0.0, part, Ns,
+                              s));
+    ++launch_counter();
+    k_gram_finish<<<launch_blocks(Ns * Ns), 256, 0, s>>>(part, 1, Ns, mode, out, ld, off);
+    CASPT2_CUDA_TRY(cudaGetLastError());
+    return CASPT2_OK;
+  }
   const long ntile = (Ns + kGS - 1) / kGS;
   const int TS = (int)((Ns + ntile - 1) / ntile);        // tile edge fitted to Ns
   const long tiles = ntile * ntile;
@@ -424,7 +435,7 @@ cudaError_t launch_symmetrize(double* x, int nmo, long batch, cudaStream_t s) {
 
 int class_densities(ClassWork& w, DensWork& dw, const Dims& d, int scheme, double shift,
                     RdmPtrs rdm, const double* E0, const double* eps_cv, const double* R, int P,
-                    const double* NL, const EriBlocks& G, double* d1, double* d2,
+                    const double* NL, const EriBlocks& G, double* d1, double* d2, OzWork* oz,
                     cudaStream_t s) {
   (void)scheme;
   const int m = w.m, n = d.n, a = d.a, nmo = d.nmo();
@@ -474,7 +485,7 @@ int class_densities(ClassWork& w, DensWork& dw, const Dims& d, int scheme, doubl
       for (int k2 = k + 1; k2 < C.next; ++k2) post *= w.ed.d[k2];
       const int sp = C.slot_space[C.ext[k]];
       const int st = gram_product(Lm, U, pre, Ns, post, sp == SP_C ? 1 : 2, d2, nmo,
-                                  space_off(d, sp), dw.part, dw.partmax, s);
+                                  space_off(d, sp), dw.part, dw.partmax, s, oz);
       if (st != CASPT2_OK) return st;
       pre *= Ns;
     }
@@ -490,14 +501,14 @@ int class_densities(ClassWork& w, DensWork& dw, const Dims& d, int scheme, doubl
     if (st != CASPT2_OK) return st;
   }
   // ---- active block: D^pi = sum_(tuple, L) lambda x T^pi, contracted with dF_act/df
-  st = gram_product(dw.Lam, dw.T, ntot * n, m, 1, 0, dw.Dm, m, 0, dw.part, dw.partmax, s);
+  st = gram_product(dw.Lam, dw.T, ntot * n, m, 1, 0, dw.Dm, m, 0, dw.part, dw.partmax, s, oz);
   if (st != CASPT2_OK) return st;
   if (pair) {
     ++launch_counter();
     k_swap_tuples<<<launch_blocks(tall), 256, 0, s>>>(dw.T, C, w.ed, ntot, (long)n * m, dw.Tsw);
     CASPT2_CUDA_TRY(cudaGetLastError());
     st = gram_product(dw.Lam, dw.Tsw, ntot * n, m, 1, 0, dw.Dm + mm, m, 0, dw.part, dw.partmax,
-                      s);
+                      s, oz);
     if (st != CASPT2_OK) return st;
   } else {
     CASPT2_CUDA_TRY(cudaMemsetAsync(dw.Dm + mm, 0, sizeof(double) * mm, s));

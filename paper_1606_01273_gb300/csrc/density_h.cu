@@ -20,6 +20,7 @@
 #include "class_dev.cuh"
 #include "kernels.cuh"
 #include "linalg.cuh"
+#include "ozaki.cuh"
 
 namespace caspt2 {
 
@@ -225,7 +226,8 @@ __global__ void k_h_act_finish(const double* __restrict__ part, int nblk,
 
 int classH_densities(const double* B, const Dims& d, const ClassHWork& hw, int scheme,
                      double shift, const double* R, int P, const double* NL, const double* g1,
-                     const HDensWork& hd, double* d2, double* gdf, cudaStream_t s) {
+                     const HDensWork& hd, double* d2, double* gdf, OzWork* oz, bool k_ready,
+                     cudaStream_t s) {
   const int c = d.c, v = d.v, n = d.n, a = d.a, nmo = d.nmo();
   if (c == 0 || v == 0) return CASPT2_OK;
   const long cv = (long)c * v, total = cv * cv;
@@ -234,16 +236,29 @@ int classH_densities(const double* B, const Dims& d, const ClassHWork& hw, int s
   ++launch_counter();
   k_h_coef<<<1, kMaxStates * kMaxStates, 0, s>>>(hw.W, hw.shifts, R, P, n, scheme, shift, hd.coef);
   CASPT2_CUDA_TRY(cudaGetLastError());
+  const bool split = oz && oz->on;
   // K[(ia)][(jb)] = sum_Q B[Q][i][a] B[Q][j][b]
   CASPT2_CUDA_TRY(launch_pack_block(B, d, SP_C, SP_V, hd.pack, s));
-  CASPT2_CUDA_TRY(dgemm((int)cv, (int)cv, d.X, 1.0, hd.pack, (int)cv, true, hd.pack, (int)cv, false,
-                        0.0, hd.K, (int)cv, s));
+  if (!k_ready) {
+    if (split) {
+      const OzView vp{hd.pack, 1, cv, (long)d.X, 0};     // rows (ia), K = Q
+      CASPT2_CUDA_TRY(oz_matmul(*oz, vp, vp, true, (int)cv, (int)cv, d.X, 1.0, 0.0, hd.K, cv, s));
+    } else {
+      CASPT2_CUDA_TRY(dgemm((int)cv, (int)cv, d.X, 1.0, hd.pack, (int)cv, true, hd.pack, (int)cv,
+                            false, 0.0, hd.K, (int)cv, s));
+    }
+  }
   ++launch_counter();
   k_h_wt<<<launch_blocks(total), 256, 0, s>>>(hd.K, hw.eps, c, v, hd.coef, ns, hd.B1, hd.B2);
   CASPT2_CUDA_TRY(cudaGetLastError());
   // GDF[Q][i][a] += -2 sum_jb B[Q][jb] Wt[ia][jb]
-  CASPT2_CUDA_TRY(dgemm(d.X, (int)cv, (int)cv, -2.0, hd.pack, (int)cv, false, hd.B1, (int)cv, true,
-                        0.0, hd.tmp, (int)cv, s));
+  if (split) {
+    const OzView vq{hd.pack, cv, 1, cv, 0}, vw{hd.B1, cv, 1, cv, 0};   // rows Q / (ia), K = (jb)
+    CASPT2_CUDA_TRY(oz_matmul(*oz, vq, vw, false, d.X, (int)cv, (int)cv, -2.0, 0.0, hd.tmp, cv, s));
+  } else {
+    CASPT2_CUDA_TRY(dgemm(d.X, (int)cv, (int)cv, -2.0, hd.pack, (int)cv, false, hd.B1, (int)cv,
+                          true, 0.0, hd.tmp, (int)cv, s));
+  }
   CASPT2_CUDA_TRY(launch_unpack_add(hd.tmp, d, SP_C, SP_V, gdf, s));
   // active block (MS-MR): pairs nu, nu' of the same state through <nu|E_rs|nu'>
   if (scheme != CASPT2_SSSR && a > 0) {
@@ -264,9 +279,9 @@ int classH_densities(const double* B, const Dims& d, const ClassHWork& hw, int s
     ++launch_counter();
     k_h_lt<<<launch_blocks(total), 256, 0, s>>>(hd.K, hw.eps, c, v, hd.coef + 6 * q, hd.B1, hd.B2);
     CASPT2_CUDA_TRY(cudaGetLastError());
-    int st = gram_product(hd.B1, hd.B2, c, v, cv, 2, d2, nmo, c + a, hd.part, hd.partmax, s);
+    int st = gram_product(hd.B1, hd.B2, c, v, cv, 2, d2, nmo, c + a, hd.part, hd.partmax, s, oz);
     if (st != CASPT2_OK) return st;
-    st = gram_product(hd.B1, hd.B2, 1, c, (long)v * cv, 1, d2, nmo, 0, hd.part, hd.partmax, s);
+    st = gram_product(hd.B1, hd.B2, 1, c, (long)v * cv, 1, d2, nmo, 0, hd.part, hd.partmax, s, oz);
     if (st != CASPT2_OK) return st;
   }
   return CASPT2_OK;

@@ -65,9 +65,20 @@ struct HDensWork {
 };
 // Class-H share of d2 (closed, active, virtual blocks) and GDF of target state P
 // (Sec. II.D), accumulated; needs the W, shifts and eps left by launch_classH.
+struct OzWork;
+// Class H with K[(ia)][(jb)] (cv x cv, in K) formed by the split BF16 tensor-core GEMM
+// and the energy sums taken over the stored matrix (KK: cv x cv work, pack: X c v).
+cudaError_t launch_classH_split(const double* f, const double* B, const double* Ftil,
+                                const double* E0, double shift, int scheme, const Dims& d,
+                                ClassHWork& w, int* status, double* ecls, double* ncls,
+                                double* mom, double* mindenom, OzWork& oz, double* pack,
+                                double* K, double* KK, cudaStream_t s);
+// oz (optional, on): the DF and Gram products run as split BF16 GEMMs; k_ready: hd.K
+// already holds K[(ia)][(jb)] (formed by the split class-H energy path).
 int classH_densities(const double* B, const Dims& d, const ClassHWork& hw, int scheme,
                      double shift, const double* R, int P, const double* NL, const double* g1,
-                     const HDensWork& hd, double* d2, double* gdf, cudaStream_t s);
+                     const HDensWork& hd, double* d2, double* gdf, OzWork* oz, bool k_ready,
+                     cudaStream_t s);
 // eps[0..c) closed and eps[c..c+v) virtual orbital energies (diagonal of f)
 cudaError_t launch_eps_cv(const double* f, const Dims& d, double* eps, cudaStream_t s);
 // out[r][s] = f[c + r][c + s] (active block, compact)

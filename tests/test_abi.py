@@ -47,6 +47,20 @@ def test_host_only_entry_points(so):
     assert so.caspt2_get_densities(None, 0, None, None, None) == -1
 
 
+def test_options_precision_defaults_and_validation(so):
+    """The precision form is opt-in (plain FP64 by default, 7 slices) and bad values are
+    rejected before any device work."""
+    import paper_1606_01273_gb300 as cp
+    o = cp.default_options()
+    assert o.precision == cp.FP64 and o.slices == 7
+    dims = cp.Dims(2, 2, 2, 4, 1)
+    h = C.c_void_p()
+    for bad in (dict(precision=7), dict(precision=cp.BF16X, slices=0),
+                dict(precision=cp.BF16X, slices=8)):
+        ob = cp.default_options(**bad)
+        assert cp.lib().caspt2_create(C.byref(h), C.byref(dims), C.byref(ob)) == cp.EINVAL
+
+
 def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     import paper_1606_01273_gb300 as cp
     monkeypatch.setattr(cp, "LIBPATH", str(tmp_path / "missing.so"))

@@ -1,0 +1,79 @@
+"""The precision form (CASPT2_BF16X): the DF integral contractions, the class-H pair
+integrals and the density Gram products run as exact-split BF16 GEMMs on the tcgen05
+tensor cores.  With 7 slices every product is within FP64 rounding of the plain form, so
+the same oracle tolerances apply; with 5 slices the energies stay within 1e-8 Eh and the
+densities within 1e-6 relative.  At the full workload the precision form is compared with
+the plain FP64 form on the same inputs."""
+import os
+
+import numpy as np
+import pytest
+
+from synth import make_problem, WORKLOADS
+from oracle import o2_rdm as o2
+from oracle import o2_classes as oc
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cp():
+    from paper_1606_01273_gb300 import build as b
+    if not os.path.exists(b.LIB):
+        b.build()
+    import paper_1606_01273_gb300 as cp
+    return cp
+
+
+def _sym(x):
+    return 0.5 * (x + np.swapaxes(x, -1, -2))
+
+
+def _oracle(p, opt):
+    st = o2.setup(p, xms=bool(opt["xms"]), kmax=4)
+    sch = "sssr" if opt["scheme"] == 1 else "msmr"
+    mom = oc.all_moments(p, st, shift=opt["shift"], scheme=sch)
+    parts = {c: (-np.einsum("llk->lk", M1), np.diagonal(M2).copy()) for c, (M1, M2, M3) in mom.items()}
+    H, w, R = o2.heff(st, parts, opt["shift"])
+    d1 = np.zeros((p.nmo, p.nmo))
+    d2 = np.zeros_like(d1)
+    G = np.zeros_like(p.B)
+    for cls in "ABCDEFG":
+        a1, b1, c1, _ = oc.class_densities(p, st, cls, opt["shift"], sch, R, 0)
+        d1 += a1
+        G += b1
+        d2 += c1
+    a2, b2, _ = o2.class_h_densities(p, st, R, 0, opt["shift"], sch)
+    return parts, w, _sym(d1), _sym(d2 + a2), _sym(G + b2)
+
+
+@pytest.mark.parametrize("slices,etol,drel", [(7, 1e-9, 1e-9), (5, 1e-8, 1e-6)])
+@pytest.mark.parametrize("opt", [dict(xms=1, scheme=0, shift=0.2), dict(xms=1, scheme=1, shift=0.1)],
+                         ids=["xms_msmr", "xms_sssr"])
+def test_split_form_vs_oracle(cp, slices, etol, drel, opt):
+    p = make_problem(nclosed=5, nact=3, nvirt=70, naux=37, nstate=3, seed=21, nelact=2)
+    parts, w, d1, d2, G = _oracle(p, opt)
+    r = cp.solve_problem(p, densities=True, precision=cp.BF16X, slices=slices, **opt)
+    for cls, (e, nr) in parts.items():
+        scale = max(1.0, np.abs(e).max())
+        assert np.abs(r.e_class[cls] - e).max() <= etol * scale, cls
+    assert np.abs(r.Ems - w).max() <= etol
+    for got, ref, name in ((r.d1, d1, "d1"), (r.d2, d2, "d2"), (r.gdf, G, "GDF")):
+        err = np.linalg.norm(got - ref) / max(1e-300, np.linalg.norm(ref))
+        assert err <= drel, (name, err)
+
+
+def test_split_form_vs_plain_at_bench_size(cp):
+    """c20 a8 v200 naux700 n3: the 7-slice form reproduces the plain FP64 form."""
+    p = make_problem(**WORKLOADS["c20a8v200x700n3"])
+    opt = dict(xms=1, scheme=0, shift=0.2)
+    ref = cp.solve_problem(p, densities=True, **opt)
+    got = cp.solve_problem(p, densities=True, precision=cp.BF16X, slices=7, **opt)
+    assert np.abs(got.Ems - ref.Ems).max() <= 1e-8
+    for cls in "ABCDEFGH":
+        scale = max(1.0, np.abs(ref.e_class[cls]).max())
+        assert np.abs(got.e_class[cls] - ref.e_class[cls]).max() <= 1e-9 * scale, cls
+    for name in ("d1", "d2", "gdf"):
+        a, b = getattr(got, name), getattr(ref, name)
+        err = np.linalg.norm(a - b) / max(1e-300, np.linalg.norm(b))
+        assert err <= 1e-8, (name, err)
