@@ -39,6 +39,15 @@ FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 rate (no measured FP64 peak is pr
 CLASSH_TRAFFIC_BYTES = None
 
 
+def measured_peak(key, fallback):
+    """A peak from MEASURED_PEAKS.json (driver-written), else the stated fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)[key])
+    except (OSError, KeyError, ValueError):
+        return fallback
+
+
 def classh_flops(c, v, X):
     """Algorithmic flops of the class-H DF contraction: K_ij^ab = sum_P B_Pai B_Pbj for
     i <= j and all (a, b) (K_ji is K_ij transposed), 2 flops per multiply-add."""
@@ -140,6 +149,63 @@ def time_oracle(p, budget_s=20.0, max_runs=3):
     return ts, last
 
 
+SERVE_DESC = ("Poisson arrivals (mean 20/s) of XMS-CASPT2 requests (MS-MR, shift 0.2, all "
+              "classes, target-state densities for every other request) drawn from 12 "
+              "synthetic problems with nclosed 4-16, nact 2-6, nvirt 20-120, 1-3 states, "
+              "naux ~ 3 nmo (the C5 size range reduced to what the generator builds here)")
+
+
+def serve_problems(count=12, seed=5000):
+    """The serving pool: distinct seeded problems of mixed size (inputs only)."""
+    from synth import make_problem
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(count):
+        nact = int(rng.integers(2, 7))
+        c, v, n = int(rng.integers(4, 17)), int(rng.integers(20, 121)), int(rng.integers(1, 4))
+        nel = nact if nact % 2 == 0 else nact - 1
+        out.append(make_problem(nclosed=c, nact=nact, nvirt=v, naux=3 * (c + nact + v),
+                                nstate=n, seed=seed + k, nelact=nel))
+    return out
+
+
+def run_serve(nreq=32, rate=20.0, slots=4, seed=7):
+    """Submit nreq requests at Poisson arrival times, wait for all; latencies measured by
+    the server (submit -> results ready)."""
+    import threading
+    import paper_1606_01273_gb300 as cp
+    pool = serve_problems()
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate, nreq)
+    picks = rng.integers(0, len(pool), nreq)
+    srv = cp.Server(slots=slots)
+    tickets, lock = [], threading.Lock()
+    t0 = time.perf_counter()
+    tnext = t0
+    for k in range(nreq):
+        tnext += gaps[k]
+        dt = tnext - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        tk = srv.submit(pool[picks[k]], densities=(k % 2 == 0), xms=1, scheme=0, shift=0.2)
+        with lock:
+            tickets.append(tk)
+    outs, errors = [], []
+    for k, t in enumerate(tickets):
+        try:
+            outs.append(srv.wait(t))
+        except cp.CASPT2Error as exc:
+            p = pool[picks[k]]
+            errors.append(f"{exc} at c{p.nclosed} a{p.nact} v{p.nvirt} n{p.nstate}")
+    span = time.perf_counter() - t0
+    srv.close()
+    lat = np.array([o["latency_ms"] for o in outs]) if outs else np.array([np.nan])
+    return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "solves_per_s": len(outs) / span, "requests": nreq, "slots": slots,
+            "errors": len(errors), "first_error": errors[0] if errors else None,
+            "workload": SERVE_DESC}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -195,47 +261,57 @@ def run_ours(args):
     dev_in = [torch.from_numpy(x).to(dev) for x in host]   # f, B, rdm1-4
     popt = dict(OPTS, precision=cp.BF16X if args.precision == "bf16x" else cp.FP64,
                 slices=args.slices)
-    ctx = cp.Context(p.nclosed, p.nact, p.nvirt, p.naux, p.nstate, **popt)
-    ctx.set_inputs(*dev_in)
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            ctx.solve(stream.cuda_stream)
-            ctx.compute_densities(stream=stream.cuda_stream)
-    torch.cuda.synchronize(dev)
-
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    kern_ms, launches, tri, dens_ms = [], 0, [], []
-    if ws > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize(dev)
-    with ClockSampler(dev.index) as clk:
-        for k in range(args.steps):
-            with torch.cuda.stream(stream):
-                flush.fill_(float(k))                # L2 flush outside the timed events
-                ev[k][0].record(stream)
+    def time_device(opts):
+        """W warm-up + K timed steps (solve + densities) with inputs resident in HBM."""
+        ctx = cp.Context(p.nclosed, p.nact, p.nvirt, p.naux, p.nstate, **opts)
+        ctx.set_inputs(*dev_in)
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
                 ctx.solve(stream.cuda_stream)
                 ctx.compute_densities(stream=stream.cuda_stream)
-                ev[k][1].record(stream)
-            r = ctx.result()
-            dens_ms.append(r.timings_ms[8])
-            kern_ms.append(r.timings_ms[4])
-            tri.append((r.timings_ms[5], r.timings_ms[6], r.timings_ms[7]))
-            launches += r.launches
         torch.cuda.synchronize(dev)
-    if ws > 1:
-        torch.distributed.barrier()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_s = sum(step_ms) / 1e3
-    if ws > 1:
-        t = torch.tensor([total_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_s = float(t.item())
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        rec = {"kern_ms": [], "tri": [], "dens_ms": [], "launches": 0}
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+        with ClockSampler(dev.index) as clk:
+            for k in range(args.steps):
+                with torch.cuda.stream(stream):
+                    flush.fill_(float(k))                # L2 flush outside the timed events
+                    ev[k][0].record(stream)
+                    ctx.solve(stream.cuda_stream)
+                    ctx.compute_densities(stream=stream.cuda_stream)
+                    ev[k][1].record(stream)
+                r = ctx.result()
+                rec["dens_ms"].append(r.timings_ms[8])
+                rec["kern_ms"].append(r.timings_ms[4])
+                rec["tri"].append((r.timings_ms[5], r.timings_ms[6], r.timings_ms[7]))
+                rec["launches"] += r.launches
+            torch.cuda.synchronize(dev)
+        if ws > 1:
+            torch.distributed.barrier()
+        total = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+        if ws > 1:
+            t = torch.tensor([total], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            total = float(t.item())
+        rec.update(total_s=total, clk=clk.summary(), last=ctx.result())
+        ctx.close()
+        return rec
+
+    main = time_device(popt)
+    total_s, last = main["total_s"], main["last"]
+    kern_ms, tri, dens_ms, launches, clk = (main["kern_ms"], main["tri"], main["dens_ms"],
+                                            main["launches"], main["clk"])
     value = ws * args.steps / total_s
-    last = ctx.result()
+    other = None
+    if args.precision == "bf16x" and not args.no_compare:
+        other = time_device(dict(OPTS, precision=cp.FP64))
 
     # end to end through the C ABI with host buffers (pinned), H2D + D2H inside the timing
     pinned = [torch.from_numpy(x).pin_memory() for x in host]
@@ -264,14 +340,31 @@ def run_ours(args):
     ctx_h.close()
 
     if rank != 0:
-        ctx.close()
         if ws > 1:
             torch.distributed.destroy_process_group()
         return 0
 
     kavg = statistics.mean(kern_ms)
-    flops = classh_flops(p.nclosed, p.nvirt, p.naux)
-    achieved = flops / (kavg * 1e-3) / 1e12
+    if args.precision == "bf16x":
+        # the split form forms the full K = Bcv^T Bcv from S slices per operand: S(S+1)/2
+        # BF16 products of 2 (c v)^2 X flops each, against the measured BF16 tensor peak
+        cv = p.nclosed * p.nvirt
+        npair = args.slices * (args.slices + 1) // 2
+        flops = npair * 2.0 * cv * cv * p.naux
+        achieved = flops / (kavg * 1e-3) / 1e12
+        peak = measured_peak("bf16_tflops", 1900.0)
+        roof_h = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                  "frac": achieved / peak, "traffic": None, "kernel": "k_oz_gemm",
+                  "kernel_ms": kavg, "flops_per_launch": flops,
+                  "fp64_equivalent_tflops": 2.0 * cv * cv * p.naux / (kavg * 1e-3) / 1e12,
+                  "peak_kind": "measured bf16 burst (MEASURED_PEAKS.json)"}
+    else:
+        flops = classh_flops(p.nclosed, p.nvirt, p.naux)
+        achieved = flops / (kavg * 1e-3) / 1e12
+        roof_h = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                  "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                  "traffic": CLASSH_TRAFFIC_BYTES, "kernel": "k_classH", "kernel_ms": kavg,
+                  "flops_per_launch": flops, "peak_kind": "nominal FP64"}
     tri_ms = sum(t[0] for t in tri)
     tri_fl = sum(t[1] for t in tri)
     tri_n = sum(t[2] for t in tri)
@@ -280,12 +373,16 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f64 (bf16 slices on tensor cores)",
         "data": "synthetic",
         "config": {"workload": WORKLOAD_DESC, "classes": cp.supported_classes(),
-                   "form": "plain FP64", "parallelism": f"{ws} independent solve(s)",
+                   "form": ("split-BF16 tensor-core products, %d slices (FP64-accurate), "
+                            "FP64 eigensolvers and reductions" % args.slices
+                            if args.precision == "bf16x" else "plain FP64"),
+                   "parallelism": f"{ws} independent solve(s)",
                    "l2": "256 MB write between steps; B (291 MB) larger than L2"},
-        "tflops_classH_kernel": achieved,
+        "tflops_classH_kernel": achieved,   # see roofline_classH
         # dominant kernel by device time (see profiles/): the Householder tridiagonalisation
         # of the class overlap / Fock matrices; FP64, 4/3 m^3 algorithmic flops per launch
         "roofline": {"bound": "alu", "achieved": tri_achieved, "peak": FP64_PEAK_TFLOPS,
@@ -294,18 +391,23 @@ def run_ours(args):
                      "launches_per_step": tri_n / max(len(tri), 1),
                      "flops_per_launch": tri_fl / max(tri_n, 1),
                      "peak_kind": "nominal FP64 (no measured FP64 peak in MEASURED_PEAKS)"},
-        "roofline_classH": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                            "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                            "traffic": CLASSH_TRAFFIC_BYTES, "kernel": "k_classH",
-                            "kernel_ms": kavg, "flops_per_launch": flops},
+        "roofline_classH": roof_h,
         "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
-        "clocks": clk.summary(),
+        "clocks": clk,
+        "fp64_form": None if other is None else {
+            "value": ws * args.steps / other["total_s"], "unit": "solves/s",
+            "ms_per_step": 1e3 * other["total_s"] / args.steps,
+            "speedup_of_value": (ws * args.steps / total_s) / (ws * args.steps / other["total_s"]),
+            "max_abs_dE_vs_value_Eh": float(np.abs(other["last"].Ems - last.Ems).max()),
+            "clocks": other["clk"]},
         "stage_ms_last": dict(zip(["setup", "classH", "classesAG", "heff_lambda", "classH_kernel",
                                    "tridiag_kernel_total"], last.timings_ms[:6]),
                               densities=statistics.mean(dens_ms)),
     }
+    if ws == 1 and not args.no_serve:
+        line["serve"] = run_serve()
     if ws == 1 and not args.no_cpu_baseline:
         ts, ref = time_oracle(p)
         w = ref[1]
@@ -318,7 +420,6 @@ def run_ours(args):
                                            "bound for the oracle's full step")}
         line["parity"] = {"max_abs_dE_Eh": float(np.abs(last.Ems - w).max()), "tol_Eh": 1e-8}
     print(json.dumps(line))
-    ctx.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
@@ -331,7 +432,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--precision", choices=["fp64", "bf16x"], default="fp64")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--precision", choices=["fp64", "bf16x"], default="bf16x")
+    ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--slices", type=int, default=7)
     args = ap.parse_args()
     if args.warmup < 3:

@@ -202,6 +202,53 @@ int caspt2_classH_noalloc(const caspt2_dims* dims, const caspt2_options* opt,
                           const double* fock, const double* dfB, const double* rdm1,
                           double* e, double* norm, void* cuda_stream);
 
+/* ---------------------------------------------------------------- serving form
+ * A server that admits (X)MS-CASPT2 requests of different sizes while others run:
+ * max_slots host workers, each with its own non-blocking CUDA stream on the device that
+ * is current at creation, take queued requests in submission order as soon as a slot is
+ * free and the request's estimated device memory fits the remaining budget, run
+ * caspt2_create / set_inputs / solve (and caspt2_densities if requested) on their stream,
+ * copy the results to host memory and free the request's device memory.  Work of
+ * different requests overlaps on the device (separate streams); each request's
+ * arithmetic is the same as a solve alone.  The paper has no counterpart (it distributes
+ * one solve over MPI ranks). */
+typedef struct caspt2_server caspt2_server;
+
+typedef struct {
+    caspt2_dims    dims;
+    caspt2_options opt;
+    /* host pointers, layouts as in caspt2_set_inputs; copied by caspt2_server_submit */
+    const double *fock, *dfB, *rdm1, *rdm2, *rdm3, *rdm4;
+    int densities;          /* 1: also caspt2_densities for opt.target_state (all classes) */
+} caspt2_request;
+
+typedef struct {
+    int status;             /* status of the request's solve (OK, WINTRUDER, or an error) */
+    double latency_ms;      /* submit -> results ready, measured by the server */
+    double queue_ms;        /* submit -> admitted to a slot */
+    /* caller-owned host outputs, any may be NULL: Ems [n], R and Heff [n][n],
+       d1 and d2 [nmo][nmo], gdf [naux][nmo][nmo] */
+    double *Ems, *R, *Heff, *d1, *d2, *gdf;
+} caspt2_result;
+
+/* hbm_budget_bytes: device memory the server may hold for requests at once (0: 90% of
+ * the free memory at creation); max_slots: concurrent requests (1..64).
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+int caspt2_server_create(caspt2_server** srv, size_t hbm_budget_bytes, int max_slots);
+
+/* Queue a request (its inputs are copied; the caller may free them on return) and get
+ * its ticket.  EINVAL for bad sizes/options/pointers or a request whose estimate exceeds
+ * the whole budget; ESTATE after destroy has begun. */
+int caspt2_server_submit(caspt2_server* srv, const caspt2_request* req, long* ticket);
+
+/* Wait up to timeout_ms (< 0: no limit) for a ticket, copy its results into *out and
+ * release it.  Returns the request's status, ETIMEOUT if it is not done yet (the ticket
+ * stays valid), EINVAL for an unknown ticket. */
+int caspt2_server_wait(caspt2_server* srv, long ticket, int timeout_ms, caspt2_result* out);
+
+/* Finish the queued and running requests, then free the server. */
+void caspt2_server_destroy(caspt2_server* srv);
+
 #ifdef __cplusplus
 }
 #endif

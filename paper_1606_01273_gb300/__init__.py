@@ -35,6 +35,19 @@ class Options(C.Structure):
                 ("class_mask", C.c_uint), ("precision", C.c_int), ("slices", C.c_int)]
 
 
+class Request(C.Structure):
+    _fields_ = [("dims", Dims), ("opt", Options),
+                ("fock", C.c_void_p), ("dfB", C.c_void_p), ("rdm1", C.c_void_p),
+                ("rdm2", C.c_void_p), ("rdm3", C.c_void_p), ("rdm4", C.c_void_p),
+                ("densities", C.c_int)]
+
+
+class ServeResult(C.Structure):
+    _fields_ = [("status", C.c_int), ("latency_ms", C.c_double), ("queue_ms", C.c_double),
+                ("Ems", C.c_void_p), ("R", C.c_void_p), ("Heff", C.c_void_p),
+                ("d1", C.c_void_p), ("d2", C.c_void_p), ("gdf", C.c_void_p)]
+
+
 _lib = None
 
 
@@ -66,6 +79,11 @@ def lib():
         L.caspt2_destroy.restype = None
         L.caspt2_densities.argtypes = [P, C.c_uint, P]
         L.caspt2_get_densities.argtypes = [P, C.c_int, P, P, P]
+        L.caspt2_server_create.argtypes = [C.POINTER(P), C.c_size_t, C.c_int]
+        L.caspt2_server_submit.argtypes = [P, C.POINTER(Request), C.POINTER(C.c_long)]
+        L.caspt2_server_wait.argtypes = [P, C.c_long, C.c_int, C.POINTER(ServeResult)]
+        L.caspt2_server_destroy.argtypes = [P]
+        L.caspt2_server_destroy.restype = None
         L.caspt2_classH_noalloc.argtypes = [C.POINTER(Dims), C.POINTER(Options), P, P, P, P, P, P]
         L.caspt2_strerror.argtypes = [C.c_int]
         L.caspt2_strerror.restype = C.c_char_p
@@ -260,3 +278,47 @@ def solve_problem(prob, densities=None, **opts) -> Result:
         return r
     finally:
         ctx.close()
+
+
+class Server:
+    """caspt2_server_*: concurrent requests admitted by device-memory budget."""
+
+    def __init__(self, budget_bytes: int = 0, slots: int = 4):
+        h = C.c_void_p()
+        _check(lib().caspt2_server_create(C.byref(h), budget_bytes, slots), "caspt2_server_create")
+        self._h = h
+
+    def submit(self, prob, densities: bool = False, **opts) -> int:
+        """Queue a synth.Problem (inputs copied by the library); returns the ticket."""
+        f, B, r1, r2, r3, r4 = problem_inputs(prob)
+        req = Request()
+        req.dims = Dims(prob.nclosed, prob.nact, prob.nvirt, prob.naux, prob.nstate)
+        req.opt = default_options(**opts)
+        ptr = lambda x: None if x is None else C.c_void_p(x.ctypes.data)
+        req.fock, req.dfB, req.rdm1, req.rdm2, req.rdm3, req.rdm4 = (ptr(x) for x in (f, B, r1, r2, r3, r4))
+        req.densities = 1 if densities else 0
+        t = C.c_long()
+        _check(lib().caspt2_server_submit(self._h, C.byref(req), C.byref(t)), "caspt2_server_submit")
+        self._shapes = getattr(self, "_shapes", {})
+        self._shapes[t.value] = (prob.nstate, prob.nmo, prob.naux, densities)
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: int = -1) -> dict:
+        n, nmo, X, dens = self._shapes.pop(ticket)
+        out = {"Ems": np.zeros(n), "R": np.zeros((n, n)), "Heff": np.zeros((n, n))}
+        if dens:
+            out.update(d1=np.zeros((nmo, nmo)), d2=np.zeros((nmo, nmo)), gdf=np.zeros((X, nmo, nmo)))
+        res = ServeResult()
+        for k, v in out.items():
+            setattr(res, k, C.c_void_p(v.ctypes.data))
+        st = lib().caspt2_server_wait(self._h, ticket, timeout_ms, C.byref(res))
+        _check(st, "caspt2_server_wait", warn_ok=True)
+        out.update(status=st, latency_ms=res.latency_ms, queue_ms=res.queue_ms)
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().caspt2_server_destroy(self._h)
+            self._h = None
+
+    __del__ = close

@@ -659,7 +659,7 @@ int caspt2_densities(caspt2_ctx* c, unsigned class_mask, void* stream) {
     for (auto& kv : c->gblk) {
       const int sp4[4] = {kv.first / 27, (kv.first / 9) % 3, (kv.first / 3) % 3, kv.first % 3};
       CASPT2_CUDA_TRY(gdf_from_block(c->B, d, sp4, kv.second, c->pack0, c->pack1, c->gtmp,
-                                     c->dgdf, s));
+                                     c->dgdf, s, &c->oz));
     }
   }
   if ((class_mask >> CASPT2_CLASS_H & 1u) && d.c > 0 && d.v > 0) {

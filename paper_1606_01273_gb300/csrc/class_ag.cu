@@ -132,6 +132,92 @@ __global__ void k_src_eval(const SrcPlan* __restrict__ plans, int nplan, DevClas
   }
 }
 
+// Same sources with one thread per (fam, ext, act) holding all n^2 (M, L) results (n <=
+// NS): each plan term's integral value and RDM offset are formed once and applied to the
+// n^2 state pairs (Gamma[M][L][off] at stride a^(2 rank)).
+template <int NS>
+__global__ void k_src_eval_ml(const SrcPlan* __restrict__ plans, int nplan, DevClass C, Dims d,
+                              RdmPtrs g, const double* __restrict__ h, EriBlocks eri,
+                              double* __restrict__ V, long total2) {
+  const int n = d.n, a = d.a, nmo = d.nmo();
+  const int dimsp[3] = {d.c, d.a, d.v};
+  const int offsp[3] = {0, d.c, d.c + d.a};
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total2;
+       e += (long)gridDim.x * blockDim.x) {
+    long r = e;
+    int vals[24];
+    for (int k = C.nact - 1; k >= 0; --k) {
+      vals[kRefBra + C.act[k]] = r % a;
+      r /= a;
+    }
+    for (int k = C.next - 1; k >= 0; --k) {
+      const int dm = dimsp[C.slot_space[C.ext[k]]];
+      vals[kRefBra + C.ext[k]] = r % dm;
+      r /= dm;
+    }
+    const int fam = (int)r;
+    double acc[NS * NS];
+#pragma unroll
+    for (int q = 0; q < NS * NS; ++q) acc[q] = 0.0;
+    for (int t = 0; t < nplan; ++t) {
+      const SrcPlan& P = plans[t];
+      if (P.fb != fam) continue;
+      bool ok = true;
+      for (int q = 0; q < P.neq; ++q)
+        if (vals[P.eq[q][0]] != vals[P.eq[q][1]]) ok = false;
+      if (!ok) continue;
+      long niter = 1;
+      for (int j = 0; j < P.nloop; ++j) niter *= dimsp[P.loop_space[j]];
+      const double* blk = nullptr;
+      long bd[4] = {1, 1, 1, 1};
+      if (P.kind == 1) {
+        const int key = ((P.ispace[0] * 3 + P.ispace[1]) * 3 + P.ispace[2]) * 3 + P.ispace[3];
+        blk = eri.p[key];
+        for (int j = 0; j < 4; ++j) bd[j] = dimsp[P.ispace[j]];
+      }
+      const long stride = ipow(a, 2 * P.rank);
+      for (long it = 0; it < niter; ++it) {
+        long q = it;
+        for (int j = 0; j < P.nloop; ++j) {
+          const int dm = dimsp[P.loop_space[j]];
+          vals[kRefLoop + j] = q % dm;
+          q /= dm;
+        }
+        double x;
+        if (P.kind == 0) {
+          x = h[(long)(offsp[P.ispace[0]] + vals[P.iidx[0]]) * nmo + offsp[P.ispace[1]] +
+                vals[P.iidx[1]]];
+        } else {
+          x = blk[((vals[P.iidx[0]] * bd[1] + vals[P.iidx[1]]) * bd[2] + vals[P.iidx[2]]) * bd[3] +
+                  vals[P.iidx[3]]];
+        }
+        if (x == 0.0) continue;
+        x *= P.coeff;
+        if (P.rank == 0) {
+#pragma unroll
+          for (int M = 0; M < NS; ++M)
+            if (M < n) acc[M * NS + M] += x;
+        } else {
+          long off = 0;
+          for (int j = 0; j < 2 * P.rank; ++j) off = off * a + vals[P.idx[j]];
+          const double* gp = g.p[P.rank] + off;
+#pragma unroll
+          for (int M = 0; M < NS; ++M)
+#pragma unroll
+            for (int L = 0; L < NS; ++L)
+              if (M < n && L < n) acc[M * NS + L] += x * gp[(long)(M * n + L) * stride];
+        }
+      }
+    }
+    double* out = V + e * n * n;
+#pragma unroll
+    for (int M = 0; M < NS; ++M)
+#pragma unroll
+      for (int L = 0; L < NS; ++L)
+        if (M < n && L < n) out[M * n + L] = acc[M * NS + L];
+  }
+}
+
 // Pack B[P][off0 + x][off1 + y] -> out[P][x][y]
 __global__ void k_pack_block(const double* __restrict__ B, int X, int nmo, int off0, int n0,
                              int off1, int n1, double* __restrict__ out) {
@@ -401,7 +487,8 @@ cudaError_t launch_unpack_add(const double* tmp, const Dims& d, int sp0, int sp1
 }
 
 cudaError_t gdf_from_block(const double* B, const Dims& d, const int sp[4], const double* G,
-                           double* pack0, double* pack1, double* tmp, double* gdf, cudaStream_t s) {
+                           double* pack0, double* pack1, double* tmp, double* gdf, cudaStream_t s,
+                           OzWork* oz) {
   const int n0 = space_dim(d, sp[0]), n1 = space_dim(d, sp[1]);
   const int n2 = space_dim(d, sp[2]), n3 = space_dim(d, sp[3]);
   if ((long)n0 * n1 * n2 * n3 == 0) return cudaSuccess;
@@ -415,14 +502,25 @@ cudaError_t gdf_from_block(const double* B, const Dims& d, const int sp[4], cons
                                                 space_off(d, sp[3]), n3, pack1);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  const bool split = oz && oz->on;
   // d/dB[Q][pq] = sum_rt G[pq][rt] B[Q][rt]
-  e = dgemm(d.X, n01, n23, 1.0, pack1, n23, false, G, n23, true, 0.0, tmp, n01, s);
+  if (split) {
+    const OzView vb{pack1, n23, 1, n23, 0}, vg{G, n23, 1, n23, 0};   // rows Q / pq, K = rt
+    e = oz_matmul(*oz, vb, vg, false, d.X, n01, n23, 1.0, 0.0, tmp, n01, s);
+  } else {
+    e = dgemm(d.X, n01, n23, 1.0, pack1, n23, false, G, n23, true, 0.0, tmp, n01, s);
+  }
   if (e != cudaSuccess) return e;
   ++launch_counter();
   k_unpack_add<<<launch_blocks(t0), 256, 0, s>>>(tmp, d.X, d.nmo(), space_off(d, sp[0]), n0,
                                                 space_off(d, sp[1]), n1, gdf);
   // d/dB[Q][rt] = sum_pq G[pq][rt] B[Q][pq]
-  e = dgemm(d.X, n23, n01, 1.0, pack0, n01, false, G, n23, false, 0.0, tmp, n23, s);
+  if (split) {
+    const OzView va{pack0, n01, 1, n01, 0}, vg{G, 1, n23, n01, 0};   // rows Q / rt, K = pq
+    e = oz_matmul(*oz, va, vg, false, d.X, n23, n01, 1.0, 0.0, tmp, n23, s);
+  } else {
+    e = dgemm(d.X, n23, n01, 1.0, pack0, n01, false, G, n23, false, 0.0, tmp, n23, s);
+  }
   if (e != cudaSuccess) return e;
   ++launch_counter();
   k_unpack_add<<<launch_blocks(t1), 256, 0, s>>>(tmp, d.X, d.nmo(), space_off(d, sp[2]), n2,
@@ -530,7 +628,14 @@ int class_solve(ClassWork& w, SectorWork& sw, const Dims& d, int scheme, double 
   ++launch_counter();
   k_act_eval<<<launch_blocks(mm), 256, 0, s>>>(w.dF, w.nF, w.dc, d.a, n, rdm, f_act, w.Fact, m);
   ++launch_counter();
-  k_src_eval<<<launch_blocks(w.vsize), 256, 0, s>>>(w.dV, w.nV, w.dc, d, rdm, h, eri, w.V, w.vsize);
+  if (n <= 4) {
+    const long total2 = w.vsize / ((long)n * n);
+    k_src_eval_ml<4><<<launch_blocks(total2), 256, 0, s>>>(w.dV, w.nV, w.dc, d, rdm, h, eri, w.V,
+                                                          total2);
+  } else {
+    k_src_eval<<<launch_blocks(w.vsize), 256, 0, s>>>(w.dV, w.nV, w.dc, d, rdm, h, eri, w.V,
+                                                      w.vsize);
+  }
   CASPT2_CUDA_TRY(cudaGetLastError());
 
   const int nsec = w.dc.pair0 < 0 ? 1 : 2;

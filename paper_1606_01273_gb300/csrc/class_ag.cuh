@@ -110,7 +110,8 @@ int class_densities(ClassWork& w, DensWork& dw, const Dims& d, int scheme, doubl
 // GDF[Q][p][q] += sum_rt G[pq][rt] B[Q][rt] and GDF[Q][r][t] += sum_pq G[pq][rt] B[Q][pq]
 // for one adjoint block with spaces sp; pack0/pack1/tmp hold X * (block pair) doubles.
 cudaError_t gdf_from_block(const double* B, const Dims& d, const int sp[4], const double* G,
-                           double* pack0, double* pack1, double* tmp, double* gdf, cudaStream_t s);
+                           double* pack0, double* pack1, double* tmp, double* gdf, cudaStream_t s,
+                           OzWork* oz = nullptr);
 
 // Split-K FP64 Gram product over [pre][Ns][post] tensors:
 //   X[x][y] = sum_(p, q) A[(p Ns + x) post + q] B[(p Ns + y) post + q],

@@ -367,6 +367,110 @@ __global__ void k_src_adj(const SrcPlan* __restrict__ plans, int nplan, DevClass
   }
 }
 
+// Source adjoint with one thread per (fam, ext, act) and the n^2 multipliers W[M][L'] (n <=
+// NS) in registers: each plan term adds coeff * sum_(M,L') W Gamma[M][L'][off] to its
+// target with one atomic per run of equal targets.
+template <int NS>
+__global__ void k_src_adj_ml(const SrcPlan* __restrict__ plans, int nplan, DevClass C, Dims d,
+                             RdmPtrs g, const double* __restrict__ W, long m, long total2,
+                             double* __restrict__ d1, EriBlocks G) {
+  const int n = d.n, a = d.a, nmo = d.nmo();
+  const int dimsp[3] = {d.c, d.a, d.v};
+  const int offsp[3] = {0, d.c, d.c + d.a};
+  const long A = ipow(a, C.nact);
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total2;
+       e += (long)gridDim.x * blockDim.x) {
+    long r = e;
+    const long actlin = r % A;
+    r /= A;
+    int vals[24];
+    long q = actlin;
+    for (int k = C.nact - 1; k >= 0; --k) {
+      vals[kRefBra + C.act[k]] = q % a;
+      q /= a;
+    }
+    int co[3];
+    for (int k = C.next - 1; k >= 0; --k) {
+      const int dm = dimsp[C.slot_space[C.ext[k]]];
+      co[k] = r % dm;
+      vals[kRefBra + C.ext[k]] = co[k];
+      r /= dm;
+    }
+    const int fam = (int)r;
+    long t = 0;
+    for (int k = 0; k < C.next; ++k) t = t * dimsp[C.slot_space[C.ext[k]]] + co[k];
+    double wv[NS * NS];
+    bool any = false;
+#pragma unroll
+    for (int M = 0; M < NS; ++M)
+#pragma unroll
+      for (int L = 0; L < NS; ++L) {
+        const double x = (M < n && L < n) ? W[(t * n + L) * m + (fam * A + actlin) * n + M] : 0.0;
+        wv[M * NS + L] = x;
+        any = any || x != 0.0;
+      }
+    if (!any) continue;
+    double* last = nullptr;
+    double run = 0.0;
+    for (int tp = 0; tp < nplan; ++tp) {
+      const SrcPlan& P = plans[tp];
+      if (P.fb != fam) continue;
+      bool ok = true;
+      for (int qq = 0; qq < P.neq; ++qq)
+        if (vals[P.eq[qq][0]] != vals[P.eq[qq][1]]) ok = false;
+      if (!ok) continue;
+      long niter = 1;
+      for (int j = 0; j < P.nloop; ++j) niter *= dimsp[P.loop_space[j]];
+      double* blk = nullptr;
+      long bd[4] = {1, 1, 1, 1};
+      if (P.kind == 1) {
+        const int key = ((P.ispace[0] * 3 + P.ispace[1]) * 3 + P.ispace[2]) * 3 + P.ispace[3];
+        blk = const_cast<double*>(G.p[key]);
+        for (int j = 0; j < 4; ++j) bd[j] = dimsp[P.ispace[j]];
+      }
+      const long stride = ipow(a, 2 * P.rank);
+      for (long it = 0; it < niter; ++it) {
+        long qi = it;
+        for (int j = 0; j < P.nloop; ++j) {
+          const int dm = dimsp[P.loop_space[j]];
+          vals[kRefLoop + j] = qi % dm;
+          qi /= dm;
+        }
+        double gs = 0.0;
+        if (P.rank == 0) {
+#pragma unroll
+          for (int M = 0; M < NS; ++M) gs += wv[M * NS + M];
+        } else {
+          long off = 0;
+          for (int j = 0; j < 2 * P.rank; ++j) off = off * a + vals[P.idx[j]];
+          const double* gp = g.p[P.rank] + off;
+#pragma unroll
+          for (int M = 0; M < NS; ++M)
+#pragma unroll
+            for (int L = 0; L < NS; ++L)
+              if (M < n && L < n) gs += wv[M * NS + L] * gp[(long)(M * n + L) * stride];
+        }
+        if (gs == 0.0) continue;
+        double* tgt;
+        if (P.kind == 0) {
+          tgt = d1 + (long)(offsp[P.ispace[0]] + vals[P.iidx[0]]) * nmo + offsp[P.ispace[1]] +
+                vals[P.iidx[1]];
+        } else {
+          tgt = blk + ((vals[P.iidx[0]] * bd[1] + vals[P.iidx[1]]) * bd[2] + vals[P.iidx[2]]) *
+                          bd[3] + vals[P.iidx[3]];
+        }
+        if (tgt != last) {
+          flush_add(last, run);
+          last = tgt;
+          run = 0.0;
+        }
+        run += P.coeff * gs;
+      }
+    }
+    flush_add(last, run);
+  }
+}
+
 __global__ void k_symmetrize(double* __restrict__ x, int nmo, long batch) {
   const long nn = (long)nmo * nmo;
   const long total = batch * nn;
@@ -533,8 +637,14 @@ int class_densities(ClassWork& w, DensWork& dw, const Dims& d, int scheme, doubl
   ++launch_counter();
   k_wsrc<<<launch_blocks(tall), 256, 0, s>>>(dw.T, dw.Lam, R, P, n, m, tall, dw.U1);
   ++launch_counter();
-  k_src_adj<<<launch_blocks(w.vsize), 256, 0, s>>>(w.dV, w.nV, C, d, rdm, dw.U1, m, w.vsize, d1,
-                                                   G);
+  if (n <= 4) {
+    const long total2 = w.vsize / ((long)n * n);
+    k_src_adj_ml<4><<<launch_blocks(total2), 256, 0, s>>>(w.dV, w.nV, C, d, rdm, dw.U1, m, total2,
+                                                         d1, G);
+  } else {
+    k_src_adj<<<launch_blocks(w.vsize), 256, 0, s>>>(w.dV, w.nV, C, d, rdm, dw.U1, m, w.vsize, d1,
+                                                     G);
+  }
   CASPT2_CUDA_TRY(cudaGetLastError());
   return CASPT2_OK;
 }

@@ -345,9 +345,10 @@ k_tridiag_smem(const double* __restrict__ A, int m, double* __restrict__ vbuf,
 }
 
 // Shared memory of k_tridiag_smem for m columns on G blocks (0 if it does not fit).
+constexpr size_t kTridiagSmemMax = 200ull * 1024;
 size_t tridiag_smem_bytes(int m, int G) {
   const size_t b = 8ull * ((size_t)((m + G - 1) / G) * m + 3ull * m);
-  return b <= 200ull * 1024 ? b : 0;
+  return b <= kTridiagSmemMax ? b : 0;
 }
 
 __global__ void k_tail(const double* __restrict__ A, int m, double* d, double* e) {
@@ -581,7 +582,7 @@ k_vtz(const double* __restrict__ vbuf, int m, int k, const double* __restrict__ 
 }
 
 // Back-transformation V = H_0 ... H_{m-3} Z with each block owning cb consecutive columns
-// (cb = ceil(m / #SMs), one block per SM): for every reflector (in reverse order) the block
+// (cb = 8 with 32 row groups of 256 threads): for every reflector (in reverse order) the block
 // forms r_c = v . Z[k+1.., c] for its columns over rg = blockDim / cb row groups and
 // applies Z[k+1+i][c] -= tau v_i r_c.  Columns are independent, so no grid-wide
 // synchronisation is needed.
@@ -662,9 +663,11 @@ int sym_eig_tridiag(double* A, int m, double* w, double* V, double* work, cudaSt
     unsigned* sync = reinterpret_cast<unsigned*>(r);   // r is free until the back-transform
     double* pbuf = u0;                                 // u0.. are free until inverse iteration
     double* rowbuf = u0 + 2 * (long)m;
+    // the attribute is global to the kernel: set the fixed maximum (never a per-launch
+    // size) so that concurrent solves of different sizes cannot lower it under each other
     CASPT2_CUDA_TRY(cudaFuncSetAttribute(k_tridiag_smem,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem_b));
+                                         (int)kTridiagSmemMax));
     CASPT2_CUDA_TRY(cudaMemsetAsync(sync, 0, 4 * sizeof(unsigned), s));
     const double* Ac = A;
     void* args[] = {&Ac, (void*)&m, &vbuf, &tau, &d, &e, &pbuf, &rowbuf, &sync};
@@ -759,7 +762,7 @@ int sym_eig_tridiag(double* A, int m, double* w, double* V, double* work, cudaSt
   // 5. back-transformation V = H_0 ... H_{m-3} Z (column-owned, one launch)
   if (m >= 3) {
     ++launch_counter();
-    const int cb = std::max(1, std::min(32, (m + nsm - 1) / nsm));
+    const int cb = 8;       // 8 columns x 32 row groups per block
     k_backtransform<<<(m + cb - 1) / cb, 256, 0, s>>>(vbuf, tau, m, cb, V);
   }
   CASPT2_CUDA_TRY(cudaGetLastError());

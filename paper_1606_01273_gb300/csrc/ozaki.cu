@@ -1,7 +1,8 @@
 // FP64-accurate GEMM from exact BF16 slices on the tcgen05 tensor cores (see ozaki.cuh).
 //
 // One CTA computes a 128 x 64 tile of C.  Its K loop runs over stages of 32: all 256
-// threads copy the S slices of the A and B tiles into one of two shared-memory buffers
+// threads copy (cp.async, 16 bytes each, all in flight together) the S slices of the A
+// and B tiles into one of two shared-memory buffers
 // (canonical K-major layout without swizzle: core matrices of 8 rows x 16 bytes, K-adjacent
 // core matrices 128 bytes apart, row groups 512 bytes apart), one thread issues the
 // tcgen05.mma instructions of every slice pair (s, t) with s + t < S into the TMEM
@@ -142,16 +143,18 @@ k_oz_gemm(const __nv_bfloat16* __restrict__ As, const double* __restrict__ sa,
       const int rr = (qq / (kOzKStage / 8)) % (isA ? kOzM : kOzN);
       const int s = qq / ((kOzKStage / 8) * (isA ? kOzM : kOzN));
       const int grow = (isA ? m0 : n0) + rr;
-      uint4 val = make_uint4(0u, 0u, 0u, 0u);
-      if (grow < (isA ? M : N)) {
-        const __nv_bfloat16* src =
-            (isA ? As + s * sliceA : Bs + s * sliceB) + (long)grow * Kp + k0 + 8 * c;
-        val = __ldg(reinterpret_cast<const uint4*>(src));
-      }
+      const bool ok = grow < (isA ? M : N);
+      // rows past the edge read nothing (source size 0) and are zero-filled
+      const __nv_bfloat16* src =
+          ok ? (isA ? As + s * sliceA : Bs + s * sliceB) + (long)grow * Kp + k0 + 8 * c : As;
       uint8_t* dst = buf + (isA ? s * kOzASlice : S * kOzASlice + s * kOzBSlice) +
                      (rr >> 3) * kOzSbo + c * 128 + (rr & 7) * 16;
-      *reinterpret_cast<uint4*>(dst) = val;
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)),
+                   "l"(src), "r"(ok ? 16 : 0)
+                   : "memory");
     }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (tid == 0) {
@@ -240,22 +243,44 @@ __global__ void k_oz_reduce(const double* __restrict__ part, int nsplit, int M, 
   }
 }
 
-// Row maxima of |x| as the bit patterns of non-negative doubles (order-independent
-// atomicMax, so the result does not depend on the schedule).  grid (kblocks, R).
-__global__ void k_oz_rowmax(OzView v, int R, int K, unsigned long long* __restrict__ mx) {
-  for (int r = blockIdx.y; r < R; r += gridDim.y) {
-    double m = 0.0;
-    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < K;
-         k += (long)gridDim.x * blockDim.x)
-      m = fmax(m, fabs(v.X[r * v.rs + (k / v.kin) * v.kout + (k % v.kin) * v.cs]));
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0 && m > 0.0)
-      atomicMax(mx + r, (unsigned long long)__double_as_longlong(m));
+// Element (r, k) of a view; k = (k / kin, k % kin) in 32-bit arithmetic (k, kin < 2^31).
+__device__ __forceinline__ double oz_at(const OzView& v, long r, unsigned k, bool split_k) {
+  if (!split_k) return v.X[r * v.rs + (long)k * v.cs];
+  const unsigned kin = (unsigned)v.kin, p = k / kin, q = k - p * kin;
+  return v.X[r * v.rs + (long)p * v.kout + (long)q * v.cs];
+}
+
+// 32 x 32 tiles (rows x K) staged in shared memory: global reads run along the unit stride
+// of the view (rows when rs == 1, else K), then row maxima or slices are formed per tile.
+constexpr int kOzTile = 32;
+
+__device__ __forceinline__ void oz_load_tile(const OzView& v, int R, int K, int r0, int k0,
+                                             bool split_k, double (*t)[kOzTile + 1]) {
+  const bool rows_fast = v.rs == 1 && v.cs != 1;
+  for (int q = threadIdx.x; q < kOzTile * kOzTile; q += blockDim.x) {
+    const int a = q % kOzTile, b = q / kOzTile;     // a runs along the fast index
+    const int rr = rows_fast ? a : b, kk = rows_fast ? b : a;
+    const int r = r0 + rr, k = k0 + kk;
+    t[rr][kk] = (r < R && k < K) ? oz_at(v, r, (unsigned)k, split_k) : 0.0;
   }
 }
 
-// sigma_r = 2^(floor(log2 max|x_r|) + 1) (1 for a zero row); slices of x / sigma.
+// Row maxima of |x| as the bit patterns of non-negative doubles (order-independent
+// atomicMax, so the result does not depend on the schedule).  grid (K tiles, row tiles).
+__global__ void k_oz_rowmax(OzView v, int R, int K, bool split_k,
+                            unsigned long long* __restrict__ mx) {
+  __shared__ double t[kOzTile][kOzTile + 1];
+  const int r0 = blockIdx.y * kOzTile, k0 = blockIdx.x * kOzTile;
+  oz_load_tile(v, R, K, r0, k0, split_k, t);
+  __syncthreads();
+  if (threadIdx.x < kOzTile && r0 + (int)threadIdx.x < R) {
+    double m = 0.0;
+    for (int kk = 0; kk < kOzTile; ++kk) m = fmax(m, fabs(t[threadIdx.x][kk]));
+    if (m > 0.0) atomicMax(mx + r0 + threadIdx.x, (unsigned long long)__double_as_longlong(m));
+  }
+}
+
+// sigma_r = 2^(floor(log2 max|x_r|) + 1) (1 for a zero row).
 __global__ void k_oz_scale(const unsigned long long* __restrict__ mx, int R,
                            double* __restrict__ scale) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -264,19 +289,28 @@ __global__ void k_oz_scale(const unsigned long long* __restrict__ mx, int R,
   scale[r] = m > 0.0 ? ldexp(1.0, ilogb(m) + 1) : 1.0;
 }
 
-__global__ void k_oz_split(OzView v, int R, int K, int Kp, int S, const double* __restrict__ scale,
-                           __nv_bfloat16* __restrict__ out) {
-  const long total = (long)R * Kp;
-  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
-       e += (long)gridDim.x * blockDim.x) {
-    const int r = e / Kp;
-    const long k = e % Kp;
-    double x = k < K ? v.X[r * v.rs + (k / v.kin) * v.kout + (k % v.kin) * v.cs] / scale[r] : 0.0;
+// S slices of x / sigma_r into out[s][r][Kp] (zeros for K <= k < Kp); grid (Kp tiles,
+// row tiles), writes along K.
+__global__ void k_oz_split(OzView v, int R, int K, int Kp, int S, bool split_k,
+                           const double* __restrict__ scale, __nv_bfloat16* __restrict__ out) {
+  __shared__ double t[kOzTile][kOzTile + 1];
+  const int r0 = blockIdx.y * kOzTile, k0 = blockIdx.x * kOzTile;
+  oz_load_tile(v, R, K, r0, k0, split_k, t);
+  __syncthreads();
+  const long plane = (long)R * Kp;
+  for (int q = threadIdx.x; q < kOzTile * kOzTile; q += blockDim.x) {
+    const int kk = q % kOzTile, rr = q / kOzTile;
+    const int r = r0 + rr, k = k0 + kk;
+    if (r >= R || k >= Kp) continue;
+    // x / sigma in (-1, 1) as a 2^56 fixed-point integer; slice s is its signed 7-bit
+    // digit of weight 2^(49 - 7 s), rounded to nearest, so |a_0| <= 128, |a_s| <= 64
+    long long X = __double2ll_rn(t[rr][kk] * (0x1p56 / scale[r]));
+    const long e = (long)r * Kp + k;
     for (int s = 0; s < S; ++s) {
-      const double y = x * 128.0;
-      const double a = rint(y);
-      out[(long)s * total + e] = __double2bfloat16(a);
-      x = y - a;
+      const int sh = 49 - 7 * s;
+      const long long a = (X + (1LL << (sh - 1))) >> sh;
+      X -= a << sh;
+      out[(long)s * plane + e] = __float2bfloat16_rn((float)a);
     }
   }
 }
@@ -286,19 +320,20 @@ __global__ void k_oz_split(OzView v, int R, int K, int Kp, int S, const double* 
 cudaError_t oz_split(const OzView& v, int R, int K, int Kp, int S, __nv_bfloat16* out,
                      double* scale, cudaStream_t s) {
   if (R <= 0) return cudaSuccess;
+  if (R > 65535 * kOzTile || (long)Kp >= (1L << 31)) return cudaErrorInvalidValue;
+  const bool split_k = v.kin < K;
   // the row maxima are staged in the scale array itself (same size, 8 bytes each)
   unsigned long long* mx = reinterpret_cast<unsigned long long*>(scale);
   cudaError_t e = cudaMemsetAsync(mx, 0, sizeof(unsigned long long) * R, s);
   if (e != cudaSuccess) return e;
-  const int kb = (int)std::max<long>(1, std::min<long>(((long)K + 255) / 256, std::max(1L, 1216L / R)));
+  const unsigned rt = (R + kOzTile - 1) / kOzTile;
   ++launch_counter();
-  k_oz_rowmax<<<dim3(kb, std::min(R, 65535)), 256, 0, s>>>(v, R, K, mx);
+  k_oz_rowmax<<<dim3((K + kOzTile - 1) / kOzTile, rt), 256, 0, s>>>(v, R, K, split_k, mx);
   ++launch_counter();
   k_oz_scale<<<(R + 255) / 256, 256, 0, s>>>(mx, R, scale);
-  const long total = (long)R * Kp;
   ++launch_counter();
-  k_oz_split<<<(int)std::max<long>(1, std::min<long>((total + 255) / 256, 152L * 16)), 256, 0, s>>>(
-      v, R, K, Kp, S, scale, out);
+  k_oz_split<<<dim3((Kp + kOzTile - 1) / kOzTile, rt), 256, 0, s>>>(v, R, K, Kp, S, split_k,
+                                                                    scale, out);
   return cudaGetLastError();
 }
 
@@ -307,9 +342,12 @@ cudaError_t oz_gemm(const __nv_bfloat16* As, const double* sa, const __nv_bfloat
                     double* C, long ldc, int* err, cudaStream_t s, int nsplit, double* part) {
   if (M <= 0 || N <= 0) return cudaSuccess;
   if (S < 1 || S > kOzMaxSlices || Kp % kOzKStage != 0) return cudaErrorInvalidValue;
-  // at least 116 KB so that one CTA (holding all 512 TMEM columns) runs per SM
+  // at least 116 KB so that one CTA (holding all 512 TMEM columns) runs per SM; the
+  // attribute is global to the kernel, so it is set to the fixed maximum (7 slices)
   const int smem = std::max(2 * S * (kOzASlice + kOzBSlice), 116 * 1024);
-  cudaError_t e = cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  const int smem_max = std::max(2 * kOzMaxSlices * (kOzASlice + kOzBSlice), 116 * 1024);
+  cudaError_t e =
+      cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
   if (e != cudaSuccess) return e;
   const int nchunk = (Kp + kOzKChunk - 1) / kOzKChunk;
   nsplit = std::max(1, std::min(nsplit, nchunk));

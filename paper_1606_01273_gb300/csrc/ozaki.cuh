@@ -1,8 +1,9 @@
 // FP64-accurate GEMM on the tcgen05 tensor cores by exact BF16 splitting (internal).
 //
-// Each row x of an operand is scaled by a power of two sigma_x >= 2 max|x| and written as
+// Each row x of an operand is scaled by a power of two sigma_x > max|x| and written as
 // S integer slices, x / sigma_x = sum_s a_s 2^(-7(s+1)) + r with |a_0| <= 128,
-// |a_s| <= 64 (s >= 1), |r| <= 2^(-7S-1): every a_s is exact in BF16.  A product of two
+// |a_s| <= 64 (s >= 1), |r| <= 2^(-7S-1) (the signed 7-bit digits of x / sigma_x as a
+// 2^56 fixed-point integer, rounded to nearest): every a_s is exact in BF16.  A product of two
 // slices is an integer below 2^14, so the tensor core's FP32 accumulation of any level
 // l = s + t (at most l + 1 slice pairs) over a K chunk of 256 stays an exact integer below
 // 2^24.  Per chunk the S level sums are read from TMEM and combined in FP64:

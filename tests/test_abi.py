@@ -47,6 +47,16 @@ def test_host_only_entry_points(so):
     assert so.caspt2_get_densities(None, 0, None, None, None) == -1
 
 
+def test_server_entry_points_reject_null(so):
+    """Serving entry points validate their arguments before touching the device."""
+    so.caspt2_server_create.argtypes = [C.c_void_p, C.c_size_t, C.c_int]
+    assert so.caspt2_server_create(None, 0, 2) == -1
+    so.caspt2_server_submit.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+    assert so.caspt2_server_submit(None, None, None) == -1
+    so.caspt2_server_wait.argtypes = [C.c_void_p, C.c_long, C.c_int, C.c_void_p]
+    assert so.caspt2_server_wait(None, 1, 0, None) == -1
+
+
 def test_options_precision_defaults_and_validation(so):
     """The precision form is opt-in (plain FP64 by default, 7 slices) and bad values are
     rejected before any device work."""
