@@ -346,6 +346,7 @@ k_tridiag_smem(const double* __restrict__ A, int m, double* __restrict__ vbuf,
 
 // Shared memory of k_tridiag_smem for m columns on G blocks (0 if it does not fit).
 constexpr size_t kTridiagSmemMax = 200ull * 1024;
+constexpr size_t kBisectSmemMax = 200ull * 1024;    // d and e^2 of the tridiagonal matrix
 size_t tridiag_smem_bytes(int m, int G) {
   const size_t b = 8ull * ((size_t)((m + G - 1) / G) * m + 3ull * m);
   return b <= kTridiagSmemMax ? b : 0;
@@ -382,23 +383,31 @@ __global__ void k_e2(const double* __restrict__ e, int m, double* __restrict__ e
 }
 
 // Number of eigenvalues of T below x from the sign changes of the leading principal
-// minors p_i = (d_i - x) p_{i-1} - e_{i-1}^2 p_{i-2} (p_{-1} = 1): two multiply-adds per
-// step and no division; the pair (p_i, p_{i-1}) is rescaled by powers of two to stay in
-// range, and an exact zero takes the sign opposite to its predecessor.
+// minors p_i = (d_i - x) p_{i-1} - e_{i-1}^2 p_{i-2} (p_{-1} = 1): three FP64 operations
+// per step and no division.  Signs, exact zeros (which take the sign opposite to their
+// predecessor) and the range check are integer operations on the bit patterns; the pair
+// (p_i, p_{i-1}) is rescaled by 2^(-+500) when |p_i| leaves [2^-600, 2^600], checked every
+// 4 steps (|p| grows by at most (2||T|| + ||T||^2) per step, far inside the FP64 range).
+__device__ __forceinline__ long long dbits(double v) { return __double_as_longlong(v); }
+
 __device__ int sturm_nodiv(const double* __restrict__ d, const double* __restrict__ e2, int m,
                            double x) {
   double pm = 1.0, pc = d[0] - x;
-  if (pc == 0.0) pc = -1e-300;
-  int cnt = pc < 0.0 ? 1 : 0;
+  if ((dbits(pc) << 1) == 0) pc = -1e-300;
+  int cnt = (int)((unsigned long long)dbits(pc) >> 63);
   for (int i = 1; i < m; ++i) {
-    double pn = (d[i] - x) * pc - e2[i - 1] * pm;
-    if (pn == 0.0) pn = pc > 0.0 ? -1e-300 : 1e-300;
-    cnt += ((pn < 0.0) != (pc < 0.0)) ? 1 : 0;
+    double pn = fma(d[i] - x, pc, -e2[i - 1] * pm);
+    const long long bn = dbits(pn), bc = dbits(pc);
+    if ((bn << 1) == 0) pn = bc < 0 ? 1e-300 : -1e-300;
+    cnt += (int)((unsigned long long)(dbits(pn) ^ bc) >> 63);
     pm = pc;
     pc = pn;
-    const double a = fabs(pc);
-    if (a > 1e150) { pc *= 0x1p-500; pm *= 0x1p-500; }
-    else if (a < 1e-150 && fabs(pm) < 1e-150) { pc *= 0x1p500; pm *= 0x1p500; }
+    if ((i & 3) == 0) {
+      const int ex = (int)((dbits(pc) >> 52) & 0x7FF);
+      const int exm = (int)((dbits(pm) >> 52) & 0x7FF);
+      if (ex > 1023 + 600) { pc *= 0x1p-500; pm *= 0x1p-500; }
+      else if (ex < 1023 - 600 && exm < 1023 - 600) { pc *= 0x1p500; pm *= 0x1p500; }
+    }
   }
   return cnt;
 }
@@ -406,9 +415,17 @@ __device__ int sturm_nodiv(const double* __restrict__ d, const double* __restric
 // j-th smallest eigenvalue by 4-way multisection inside the Gershgorin interval: four
 // lanes per eigenvalue evaluate the Sturm count at the three interior quarter points
 // (lane 3 idles), so each step removes two bits; stop at an absolute width of tol.
-__global__ void k_bisect(const double* __restrict__ d, const double* __restrict__ e,
-                         const double* __restrict__ e2, int m, double glo, double ghi, double tol,
+__global__ void k_bisect(const double* __restrict__ dg, const double* __restrict__ e,
+                         const double* __restrict__ e2g, int m, double glo, double ghi, double tol,
                          double* __restrict__ w) {
+  extern __shared__ double sde[];      // d[m], e2[m] staged per block
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    sde[i] = dg[i];
+    sde[m + i] = e2g[i];
+  }
+  __syncthreads();
+  const double* d = sde;
+  const double* e2 = sde + m;
   const int gid = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = gid >> 2, q = gid & 3;
   const unsigned grp = 0xFu << (threadIdx.x & 28);
@@ -479,6 +496,12 @@ __global__ void k_inviter(const double* __restrict__ d, const double* __restrict
     }
   }
   if (u0[IX(m - 1)] == 0.0) u0[IX(m - 1)] = tiny;
+  // pivots -> reciprocals (|pivot| raised to tiny), so the solves below multiply
+  for (int i = 0; i < m; ++i) {
+    double piv = u0[IX(i)];
+    if (fabs(piv) < tiny) piv = copysign(tiny, piv == 0.0 ? 1.0 : piv);
+    u0[IX(i)] = 1.0 / piv;
+  }
   // start vector
   for (int i = 0; i < m; ++i) Z[IX(i)] = hash_unit(i, j);
   for (int iter = 0; iter < 3; ++iter) {
@@ -497,9 +520,7 @@ __global__ void k_inviter(const double* __restrict__ d, const double* __restrict
       double x = Z[IX(i)];
       if (i + 1 < m) x -= u1[IX(i)] * Z[IX(i + 1)];
       if (i + 2 < m) x -= u2[IX(i)] * Z[IX(i + 2)];
-      double piv = u0[IX(i)];
-      if (fabs(piv) < tiny) piv = copysign(tiny, piv == 0.0 ? 1.0 : piv);
-      x /= piv;
+      x *= u0[IX(i)];
       Z[IX(i)] = x;
       big = fmax(big, fabs(x));
       if (big > 1e100) {  // rescale the partial solution
@@ -746,8 +767,11 @@ int sym_eig_tridiag(double* A, int m, double* w, double* V, double* work, cudaSt
   ++launch_counter();
   k_e2<<<(m + 255) / 256, 256, 0, s>>>(e, m, e2);
   ++launch_counter();
-  k_bisect<<<(4 * m + 31) / 32, 32, 0, s>>>(d, e, e2, m, glo, ghi,
-                                            4.0 * 2.2e-16 * std::max(1.0, tnorm), w);
+  if (2 * sizeof(double) * (size_t)m > kBisectSmemMax) return CASPT2_EINVAL;
+  CASPT2_CUDA_TRY(cudaFuncSetAttribute(k_bisect, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kBisectSmemMax));
+  k_bisect<<<(4 * m + 127) / 128, 128, 2 * sizeof(double) * m, s>>>(
+      d, e, e2, m, glo, ghi, 4.0 * 2.2e-16 * std::max(1.0, tnorm), w);
   // 3. eigenvectors of T
   ++launch_counter();
   k_inviter<<<(m + 127) / 128, 128, 0, s>>>(d, e, w, m, tnorm, u0, u1, u2, lm, pv, Z);
