@@ -167,6 +167,19 @@ int caspt2_densities(caspt2_ctx* ctx, unsigned class_mask, void* cuda_stream);
  * Errors: EINVAL, ESTATE (no densities computed since the last solve). */
 int caspt2_get_densities(caspt2_ctx* ctx, int mem, double* d1, double* d2, double* gdf);
 
+/* Gradient of the target state's MS energy E_P (opt.target_state) with respect to the
+ * library's inputs, the Fock matrix f and the DF factors B, with the reference RDMs held
+ * fixed (Sec. II.D: the densities chained through h = f - g(B, d_sa), the reference
+ * Hamiltonian and the denominators):
+ *   grad_f[p][q]     = dE_P/df_pq  = gamma_P + d1 + d2, d2 on the parts of f the solve
+ *                      reads (closed diagonal, active block, virtual diagonal);
+ *   grad_B[Q][p][q]  = dE_P/dB_Qpq at fixed f;
+ * both symmetrised, in the layouts of the inputs, to host or device buffers (mem).  MS
+ * only (opt.xms = 0): the XMS rotation response is not formed.  Recomputes the densities
+ * of all solved classes.  Errors: EINVAL (xms, target_state < 0), ESTATE (no solve),
+ * ENOMEM, ECUDA. */
+int caspt2_gradient(caspt2_ctx* ctx, int mem, double* grad_f, double* grad_B, void* cuda_stream);
+
 /* Number of CUDA kernels the library launched during the last solve (-1 if ctx is NULL). */
 long caspt2_get_kernel_launches(caspt2_ctx* ctx);
 

@@ -79,6 +79,7 @@ def lib():
         L.caspt2_destroy.restype = None
         L.caspt2_densities.argtypes = [P, C.c_uint, P]
         L.caspt2_get_densities.argtypes = [P, C.c_int, P, P, P]
+        L.caspt2_gradient.argtypes = [P, C.c_int, P, P, P]
         L.caspt2_server_create.argtypes = [C.POINTER(P), C.c_size_t, C.c_int]
         L.caspt2_server_submit.argtypes = [P, C.POINTER(Request), C.POINTER(C.c_long)]
         L.caspt2_server_wait.argtypes = [P, C.c_long, C.c_int, C.POINTER(ServeResult)]
@@ -234,6 +235,17 @@ class Context:
                "caspt2_get_densities")
         return d1, d2, gdf
 
+    def gradient(self, stream=None):
+        """caspt2_gradient: host copies (dE/df [nmo][nmo], dE/dB [naux][nmo][nmo]) of the
+        target state's MS energy (MS only, reference RDMs fixed)."""
+        nmo = self.dims.nclosed + self.dims.nact + self.dims.nvirt
+        gf = np.zeros((nmo, nmo))
+        gB = np.zeros((self.dims.naux, nmo, nmo))
+        s = C.c_void_p(stream) if stream is not None else None
+        _check(lib().caspt2_gradient(self._h, MEM_HOST, C.c_void_p(gf.ctypes.data),
+                                     C.c_void_p(gB.ctypes.data), s), "caspt2_gradient")
+        return gf, gB
+
     def densities(self, class_mask=None, stream=None):
         """compute_densities + get_densities: host copies (d1, d2, gdf), each symmetrised."""
         self.compute_densities(class_mask, stream)
@@ -322,3 +334,43 @@ class Server:
             self._h = None
 
     __del__ = close
+
+
+def ms_energy(f, B, rdms, nclosed, target_state=0, **opts):
+    """E_MS of `target_state` as a differentiable function of the Fock matrix f and the DF
+    factors B (CUDA float64 tensors; the RDMs (rdm1..rdm4, device tensors in the layouts of
+    caspt2_set_inputs, higher ranks may be None) are held fixed).  The forward pass is a
+    caspt2_solve; the backward pass is caspt2_gradient (densities chained through the
+    solve's definitions), so torch.autograd gives dE/df and dE/dB.  MS only (xms = 0)."""
+    import torch
+
+    nmo = f.shape[0]
+    X = B.shape[0]
+    n = rdms[0].shape[0]
+    a = int(round(np.sqrt(rdms[0][0, 0].numel()))) if rdms[0].numel() else 0
+    dims = (nclosed, a, nmo - nclosed - a, X, n)
+    kw = dict(opts, xms=0, target_state=target_state)
+
+    class _E(torch.autograd.Function):
+        @staticmethod
+        def forward(fctx, f_, B_):
+            ctx = Context(*dims, **kw)
+            ctx.set_inputs(f_.contiguous(), B_.contiguous(), *[r.contiguous() if r is not None
+                                                                 else None for r in rdms])
+            st = ctx.solve()
+            r = ctx.result(st)
+            fctx.lib_ctx = ctx
+            return torch.tensor(r.Ems[target_state], dtype=f_.dtype, device=f_.device)
+
+        @staticmethod
+        def backward(fctx, g):
+            ctx = fctx.lib_ctx
+            gf = torch.empty((nmo, nmo), dtype=torch.float64, device=g.device)
+            gB = torch.empty((X, nmo, nmo), dtype=torch.float64, device=g.device)
+            torch.cuda.synchronize(g.device)
+            _check(lib().caspt2_gradient(ctx._h, MEM_DEVICE, C.c_void_p(gf.data_ptr()),
+                                         C.c_void_p(gB.data_ptr()), None), "caspt2_gradient")
+            ctx.close()
+            return g * gf, g * gB
+
+    return _E.apply(f, B)

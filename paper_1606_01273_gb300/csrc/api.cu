@@ -66,6 +66,10 @@ struct caspt2_ctx {
   // precision form: split BF16 tensor-core GEMMs, class-H pair integrals kept for the densities
   OzWork oz{};
   double *hK = nullptr, *hKK = nullptr, *hpack = nullptr;
+  // energy gradient (allocated on the first caspt2_gradient call)
+  bool grad_alloc = false;
+  GradWork gw{};
+  double *gradf = nullptr, *gradB = nullptr;
   cudaEvent_t dev0 = nullptr, dev1 = nullptr;
   // results
   double *heff = nullptr, *ems = nullptr, *R = nullptr;
@@ -699,3 +703,47 @@ int caspt2_get_densities(caspt2_ctx* c, int mem, double* d1, double* d2, double*
 }
 
 }  // extern "C"
+
+extern "C" int caspt2_gradient(caspt2_ctx* c, int mem, double* grad_f, double* grad_B,
+                               void* stream) {
+  if (!c) return CASPT2_EINVAL;
+  if (mem != CASPT2_MEM_HOST && mem != CASPT2_MEM_DEVICE) return CASPT2_EINVAL;
+  if (!c->solved) return CASPT2_ESTATE;
+  const caspt2_options& o = c->opt;
+  if (o.xms != 0 || o.target_state < 0) return CASPT2_EINVAL;
+  CASPT2_CUDA_TRY(cudaSetDevice(c->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int st = caspt2_densities(c, o.class_mask, stream);
+  if (st != CASPT2_OK) return st;
+  const Dims& d = c->d;
+  const size_t nmo = d.nmo(), a = d.a, X = d.X;
+  if (!c->grad_alloc) {
+    int e = CASPT2_OK;
+#define ALLOC(ptr, cnt) \
+  if (e == CASPT2_OK) e = c->alloc(&(ptr), (cnt))
+    ALLOC(c->gw.g1, a * a);
+    ALLOC(c->gw.g2, a * a * a * a);
+    ALLOC(c->gw.D, nmo * nmo);
+    ALLOC(c->gw.dsa, nmo * nmo);
+    ALLOC(c->gw.gD, X);
+    ALLOC(c->gw.tq, X);
+    ALLOC(c->gw.T, X * nmo * nmo);
+    ALLOC(c->gw.M, X * nmo * nmo);
+    ALLOC(c->gradf, nmo * nmo);
+    ALLOC(c->gradB, X * nmo * nmo);
+#undef ALLOC
+    if (e != CASPT2_OK) return e;
+    c->grad_alloc = true;
+  }
+  if (a == 0) {
+    CASPT2_CUDA_TRY(cudaMemsetAsync(c->gw.g1, 0, sizeof(double), s));
+  }
+  st = assemble_gradient(d, c->B, c->R, o.target_state, c->rdm1r, c->rdm2r, c->dact, c->bsum,
+                         c->gam, c->dd1, c->dd2, c->dgdf, c->gw, c->gradf, c->gradB, s);
+  if (st != CASPT2_OK) return st;
+  CASPT2_CUDA_TRY(cudaStreamSynchronize(s));
+  const cudaMemcpyKind k = mem == CASPT2_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  if (grad_f) CASPT2_CUDA_TRY(cudaMemcpy(grad_f, c->gradf, sizeof(double) * nmo * nmo, k));
+  if (grad_B) CASPT2_CUDA_TRY(cudaMemcpy(grad_B, c->gradB, sizeof(double) * X * nmo * nmo, k));
+  return CASPT2_OK;
+}

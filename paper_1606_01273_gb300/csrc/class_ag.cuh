@@ -128,6 +128,20 @@ cudaError_t launch_pack_block(const double* B, const Dims& d, int sp0, int sp1, 
 cudaError_t launch_unpack_add(const double* tmp, const Dims& d, int sp0, int sp1, double* gdf,
                               cudaStream_t s);
 
+// Work space of the energy gradient (gradient.cu): target-state active RDMs g1 [a^2], g2
+// [a^4]; D, dsa [nmo^2]; per-Q scalars gD, tq [X]; T, M [X][nmo][nmo].
+struct GradWork {
+  double *g1 = nullptr, *g2 = nullptr, *D = nullptr, *dsa = nullptr, *gD = nullptr,
+         *tq = nullptr, *T = nullptr, *M = nullptr;
+};
+// grad_f [nmo][nmo] and grad_B [X][nmo][nmo] of E_P (MS) from the densities d1, d2, Gamma
+// (gdf) and the reference pieces (see gradient.cu).
+int assemble_gradient(const Dims& d, const double* B, const double* R, int P,
+                      const double* rdm1, const double* rdm2, const double* dact,
+                      const double* bsum, const double* gam, const double* d1, const double* d2,
+                      const double* gdf, const GradWork& gw, double* grad_f, double* grad_B,
+                      cudaStream_t s);
+
 // x <- (x + x^T) / 2 for `batch` square nmo x nmo matrices.
 cudaError_t launch_symmetrize(double* x, int nmo, long batch, cudaStream_t s);
 

@@ -565,8 +565,17 @@ int class_densities(ClassWork& w, DensWork& dw, const Dims& d, int scheme, doubl
         lam);
     CASPT2_CUDA_TRY(cudaGetLastError());
     // rows = Y (msec x nk) times sector columns, for amp and lam together
-    CASPT2_CUDA_TRY(dgemm(K.msec, (int)ncol, K.nk, 1.0, K.Y, K.nk, false, dw.sec, (int)ncol, false,
-                          0.0, dw.tmp, (int)ncol, s, 2, 0, dw.secmax, dw.secmax));
+    if (oz && oz->on) {
+      const OzView vy{K.Y, K.nk, 1, K.nk, 0};                   // rows i, K = mu
+      for (int q = 0; q < 2; ++q) {
+        const OzView vs{dw.sec + q * dw.secmax, 1, ncol, K.nk, 0};   // rows col, K = mu
+        CASPT2_CUDA_TRY(oz_matmul(*oz, vy, vs, false, K.msec, (int)ncol, K.nk, 1.0, 0.0,
+                                  dw.tmp + q * dw.secmax, ncol, s));
+      }
+    } else {
+      CASPT2_CUDA_TRY(dgemm(K.msec, (int)ncol, K.nk, 1.0, K.Y, K.nk, false, dw.sec, (int)ncol,
+                            false, 0.0, dw.tmp, (int)ncol, s, 2, 0, dw.secmax, dw.secmax));
+    }
     ++launch_counter();
     k_tuple_scatter<<<launch_blocks((long)K.msec * ncol), 256, 0, s>>>(
         dw.tmp, dw.tmp + dw.secmax, C, w.ed, n, m, K.sec, K.Lsel, K.ntup, K.msec, dw.T, dw.Lam);
@@ -575,11 +584,18 @@ int class_densities(ClassWork& w, DensWork& dw, const Dims& d, int scheme, doubl
   const bool pair = C.pair0 >= 0;
   const long mm = (long)m * m;
   // ---- overlap applied to T: U1 = S^id T, U2 = S^sw T (rows of T are (tuple, L))
-  CASPT2_CUDA_TRY(dgemm((int)(ntot * n), m, m, 1.0, dw.T, m, false, w.Sact, m, true, 0.0, dw.U1, m,
-                        s));
-  if (pair)
-    CASPT2_CUDA_TRY(dgemm((int)(ntot * n), m, m, 1.0, dw.T, m, false, w.Sact + mm, m, true, 0.0,
-                          dw.U2, m, s));
+  if (oz && oz->on) {
+    const OzView vt{dw.T, m, 1, m, 0}, vs1{w.Sact, m, 1, m, 0}, vs2{w.Sact + mm, m, 1, m, 0};
+    CASPT2_CUDA_TRY(oz_matmul(*oz, vt, vs1, false, (int)(ntot * n), m, m, 1.0, 0.0, dw.U1, m, s));
+    if (pair)
+      CASPT2_CUDA_TRY(oz_matmul(*oz, vt, vs2, false, (int)(ntot * n), m, m, 1.0, 0.0, dw.U2, m, s));
+  } else {
+    CASPT2_CUDA_TRY(dgemm((int)(ntot * n), m, m, 1.0, dw.T, m, false, w.Sact, m, true, 0.0, dw.U1,
+                          m, s));
+    if (pair)
+      CASPT2_CUDA_TRY(dgemm((int)(ntot * n), m, m, 1.0, dw.T, m, false, w.Sact + mm, m, true, 0.0,
+                            dw.U2, m, s));
+  }
   // ---- closed and virtual blocks: one external slot moves
   auto slot_blocks = [&](const double* Lm, const double* U) -> int {
     long pre = 1;

@@ -1,15 +1,16 @@
 // FP64-accurate GEMM from exact BF16 slices on the tcgen05 tensor cores (see ozaki.cuh).
 //
-// One CTA computes a 128 x 64 tile of C.  Its K loop runs over stages of 32: all 256
+// One CTA computes a 128 x 64 tile of C.  Its K loop runs over stages of 16: all 256
 // threads copy (cp.async, 16 bytes each, all in flight together) the S slices of the A
-// and B tiles into one of two shared-memory buffers
+// and B tiles into a ring of four shared-memory buffers, two stages ahead of the MMAs
 // (canonical K-major layout without swizzle: core matrices of 8 rows x 16 bytes, K-adjacent
-// core matrices 128 bytes apart, row groups 512 bytes apart), one thread issues the
+// core matrices 128 bytes apart, row groups 256 bytes apart), one thread issues the
 // tcgen05.mma instructions of every slice pair (s, t) with s + t < S into the TMEM
 // accumulator of level s + t (128 lanes x 64 FP32 columns per level) and commits them to
-// that buffer's mbarrier, so the copy of the next stage overlaps the MMAs.  After each
+// that buffer's mbarrier; a buffer is refilled once its stage's MMAs have completed.  After each
 // K chunk of 256 the eight warps read the S levels from TMEM (warp w: lanes 32 (w % 4).., 32
-// columns at 32 (w / 4)) and add 2^(-7(l+2)) L_l to FP64 registers.  Every mbarrier wait
+// columns at 32 (w / 4)); the level sums (exact integers) are added, shifted, into two
+// int64 accumulators per output, converted to FP64 once at the end.  Every mbarrier wait
 // is bounded; on timeout the CTA records the error, stops issuing work, waits (bounded)
 // for its committed MMAs and frees its TMEM.
 #include <algorithm>
@@ -24,9 +25,11 @@ namespace {
 constexpr int kOzM = 128, kOzN = 64;
 constexpr int kOzThreads = 256;
 constexpr long kOzSpin = 1L << 22;
-constexpr int kOzASlice = kOzM * kOzKStage * 2;     // bytes of one A slice tile per stage
-constexpr int kOzBSlice = kOzN * kOzKStage * 2;
-constexpr int kOzSbo = (kOzKStage / 8) * 128;       // row-group stride (bytes)
+constexpr int kOzKs = 16;                           // K per shared-memory stage (one MMA)
+constexpr int kOzBufs = 4;                          // stage ring; copies run 2 stages ahead
+constexpr int kOzASlice = kOzM * kOzKs * 2;         // bytes of one A slice tile per stage
+constexpr int kOzBSlice = kOzN * kOzKs * 2;
+constexpr int kOzSbo = (kOzKs / 8) * 128;           // row-group stride (bytes)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -92,7 +95,7 @@ k_oz_gemm(const __nv_bfloat16* __restrict__ As, const double* __restrict__ sa,
           int Kp, int S, int chunks_per_split, double alpha, double beta, double* __restrict__ C,
           long ldc, double* __restrict__ part, int* err) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  __shared__ uint64_t bars[2];
+  __shared__ uint64_t bars[kOzBufs];
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -108,8 +111,8 @@ k_oz_gemm(const __nv_bfloat16* __restrict__ As, const double* __restrict__ sa,
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[0])));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[1])));
+    for (int q = 0; q < kOzBufs; ++q)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[q])));
     asm volatile("fence.mbarrier_init.release.cluster;");
     abort_flag = 0;
   }
@@ -118,30 +121,29 @@ k_oz_gemm(const __nv_bfloat16* __restrict__ As, const double* __restrict__ sa,
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tbase = tmem_base;
 
-  double acc[32];
+  // exact integer accumulation of the level sums: hi = sum_(l<3) L_l 2^(7(2-l)),
+  // lo = sum_(l>=3) L_l 2^(7(S-1-l)); value = hi 2^-28 + lo 2^(-7(S+1))
+  long long hi[32], lo[32];
 #pragma unroll
-  for (int j = 0; j < 32; ++j) acc[j] = 0.0;
+  for (int j = 0; j < 32; ++j) hi[j] = lo[j] = 0;
 
-  const int spc = kOzKChunk / kOzKStage;          // stages per exact chunk
+  const int spc = kOzKChunk / kOzKs;              // stages per exact chunk
   // stages of this split (blockIdx.z): exact chunks [z cps, (z + 1) cps)
   const int gbeg = blockIdx.z * chunks_per_split * spc;
-  const int nst = max(0, min(Kp / kOzKStage, gbeg + chunks_per_split * spc) - gbeg);
-  int committed = 0;                              // stages whose MMAs were committed
-  for (int g = 0; g < nst; ++g) {
-    const int b = g & 1;
-    if (g >= 2 && !bar_wait(&bars[b], ((g - 2) >> 1) & 1)) abort_flag = 1;
-    __syncthreads();
-    if (abort_flag) break;
-    uint8_t* buf = smem + (long)b * stage_bytes;
-    // copy the stage: S slices of A (128 rows) and B (64 rows), 16-byte pieces of 8 K values
-    const int nA = S * kOzM * (kOzKStage / 8), nB = S * kOzN * (kOzKStage / 8);
-    const int k0 = (gbeg + g) * kOzKStage;
+  const int nst = max(0, min(Kp / kOzKs, gbeg + chunks_per_split * spc) - gbeg);
+
+  // copy of stage g into ring buffer g % kOzBufs: S slices of A (128 rows) and B (64 rows),
+  // 16-byte pieces of 8 K values, all in flight together; one commit group per stage
+  auto issue_copy = [&](int g) {
+    uint8_t* buf = smem + (long)(g % kOzBufs) * stage_bytes;
+    const int nA = S * kOzM * (kOzKs / 8), nB = S * kOzN * (kOzKs / 8);
+    const int k0 = (gbeg + g) * kOzKs;
     for (int q = tid; q < nA + nB; q += kOzThreads) {
       const bool isA = q < nA;
       const int qq = isA ? q : q - nA;
-      const int c = qq % (kOzKStage / 8);
-      const int rr = (qq / (kOzKStage / 8)) % (isA ? kOzM : kOzN);
-      const int s = qq / ((kOzKStage / 8) * (isA ? kOzM : kOzN));
+      const int c = qq % (kOzKs / 8);
+      const int rr = (qq / (kOzKs / 8)) % (isA ? kOzM : kOzN);
+      const int s = qq / ((kOzKs / 8) * (isA ? kOzM : kOzN));
       const int grow = (isA ? m0 : n0) + rr;
       const bool ok = grow < (isA ? M : N);
       // rows past the edge read nothing (source size 0) and are zero-filled
@@ -154,52 +156,79 @@ k_oz_gemm(const __nv_bfloat16* __restrict__ As, const double* __restrict__ sa,
                    : "memory");
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
+  };
+  // MMAs of stage g complete the (g / kOzBufs)-th phase of bars[g % kOzBufs]
+  auto stage_parity = [](int g) { return (uint32_t)((g / kOzBufs) & 1); };
+
+  for (int g = 0; g < 2 && g < nst; ++g) issue_copy(g);
+  int committed = 0;                              // stages whose MMAs were committed
+  for (int g = 0; g < nst; ++g) {
+    // copy of stage g done (the copy of g + 1 may still be in flight)
+    if (g + 1 < nst) asm volatile("cp.async.wait_group 1;" ::: "memory");
+    else asm volatile("cp.async.wait_group 0;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
+    if (abort_flag) break;
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;");
       const bool first = (g % spc) == 0;
-      const uint32_t ab = smem_u32(buf), bb = ab + S * kOzASlice;
+      const uint32_t ab = smem_u32(smem + (long)(g % kOzBufs) * stage_bytes);
+      const uint32_t bb = ab + S * kOzASlice;
       for (int s = 0; s < S; ++s)
-        for (int t = 0; t < S - s; ++t)
-#pragma unroll
-          for (int j = 0; j < kOzKStage / 16; ++j) {
-            const uint64_t ad = sdesc(ab + s * kOzASlice + j * 256, 128, kOzSbo);
-            const uint64_t bd = sdesc(bb + t * kOzBSlice + j * 256, 128, kOzSbo);
-            const uint32_t accf = (first && s == 0 && j == 0) ? 0u : 1u;
-            mma_bf16(tbase + (uint32_t)((s + t) * kOzN), ad, bd, accf);
-          }
-      mma_commit(&bars[b]);
+        for (int t = 0; t < S - s; ++t) {
+          const uint64_t ad = sdesc(ab + s * kOzASlice, 128, kOzSbo);
+          const uint64_t bd = sdesc(bb + t * kOzBSlice, 128, kOzSbo);
+          const uint32_t accf = (first && s == 0) ? 0u : 1u;
+          mma_bf16(tbase + (uint32_t)((s + t) * kOzN), ad, bd, accf);
+        }
+      mma_commit(&bars[g % kOzBufs]);
     }
     committed = g + 1;
+    // prefetch stage g + 2 into the buffer of stage g - 2 once its MMAs are done
+    if (g + 2 < nst) {
+      if (g >= 2 && !bar_wait(&bars[(g + 2) % kOzBufs], stage_parity(g - 2))) abort_flag = 1;
+      issue_copy(g + 2);
+    }
     if ((g % spc) == spc - 1 || g == nst - 1) {
-      // end of an exact chunk: fold the S level sums into the FP64 accumulators
-      if (!bar_wait(&bars[b], (g >> 1) & 1)) abort_flag = 1;
+      // end of an exact chunk: add the S level sums into the integer accumulators
+      if (!bar_wait(&bars[g % kOzBufs], stage_parity(g))) abort_flag = 1;
       __syncthreads();
       if (abort_flag) break;
       asm volatile("tcgen05.fence::after_thread_sync;");
       const uint32_t lb = (uint32_t)(32 * (warp & 3)) << 16;
       const uint32_t cb = (uint32_t)(32 * (warp >> 2));
-      double w = 0x1p-14;
       for (int l = 0; l < S; ++l) {
         uint32_t r[32];
         tmem_ld32(tbase + lb + (uint32_t)(l * kOzN) + cb, r);
+        // each level sum is an integer below 2^24: exact in FP32 and in int32
+        if (l < 3) {
+          const int sh = 7 * (2 - l);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) acc[j] = fma(w, (double)__uint_as_float(r[j]), acc[j]);
-        w *= 0x1p-7;
+          for (int j = 0; j < 32; ++j)
+            hi[j] += (long long)__float2int_rn(__uint_as_float(r[j])) << sh;
+        } else {
+          const int sh = 7 * (S - 1 - l);
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            lo[j] += (long long)__float2int_rn(__uint_as_float(r[j])) << sh;
+        }
       }
       asm volatile("tcgen05.fence::before_thread_sync;");
       __syncthreads();
     }
   }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
   // drain: the MMAs of the last committed stages must finish before TMEM is freed
   if (abort_flag) {
     if (tid == 0) atomicExch(err, 1);
-    for (int g = committed - 2; g < committed; ++g)
-      if (g >= 0) bar_wait(&bars[g & 1], (g >> 1) & 1);
+    for (int g = committed - kOzBufs; g < committed; ++g)
+      if (g >= 0) bar_wait(&bars[g % kOzBufs], (uint32_t)((g / kOzBufs) & 1));
   } else {
     const int row = m0 + 32 * (warp & 3) + lane;
+    double acc[32];
+    const double wlo = ldexp(1.0, -7 * (S + 1));
+#pragma unroll
+    for (int j = 0; j < 32; ++j) acc[j] = (double)hi[j] * 0x1p-28 + (double)lo[j] * wlo;
     if (row < M) {
       const double sr = alpha * sa[row];
       if (part) {   // split K: this split's share, summed in a fixed order afterwards
@@ -266,17 +295,25 @@ __device__ __forceinline__ void oz_load_tile(const OzView& v, int R, int K, int 
 }
 
 // Row maxima of |x| as the bit patterns of non-negative doubles (order-independent
-// atomicMax, so the result does not depend on the schedule).  grid (K tiles, row tiles).
+// atomicMax on integers, so the result does not depend on the schedule and no FP64
+// instruction is spent).  grid (K tiles, row tiles).
 __global__ void k_oz_rowmax(OzView v, int R, int K, bool split_k,
                             unsigned long long* __restrict__ mx) {
   __shared__ double t[kOzTile][kOzTile + 1];
-  const int r0 = blockIdx.y * kOzTile, k0 = blockIdx.x * kOzTile;
-  oz_load_tile(v, R, K, r0, k0, split_k, t);
-  __syncthreads();
-  if (threadIdx.x < kOzTile && r0 + (int)threadIdx.x < R) {
-    double m = 0.0;
-    for (int kk = 0; kk < kOzTile; ++kk) m = fmax(m, fabs(t[threadIdx.x][kk]));
-    if (m > 0.0) atomicMax(mx + r0 + threadIdx.x, (unsigned long long)__double_as_longlong(m));
+  const int k0 = blockIdx.x * kOzTile;
+  for (int r0 = blockIdx.y * kOzTile; r0 < R; r0 += gridDim.y * kOzTile) {
+    oz_load_tile(v, R, K, r0, k0, split_k, t);
+    __syncthreads();
+    if (threadIdx.x < kOzTile && r0 + (int)threadIdx.x < R) {
+      unsigned long long m = 0;
+      for (int kk = 0; kk < kOzTile; ++kk) {
+        const unsigned long long b =
+            (unsigned long long)__double_as_longlong(t[threadIdx.x][kk]) & 0x7FFFFFFFFFFFFFFFull;
+        m = b > m ? b : m;
+      }
+      if (m) atomicMax(mx + r0 + threadIdx.x, m);
+    }
+    __syncthreads();
   }
 }
 
@@ -294,24 +331,41 @@ __global__ void k_oz_scale(const unsigned long long* __restrict__ mx, int R,
 __global__ void k_oz_split(OzView v, int R, int K, int Kp, int S, bool split_k,
                            const double* __restrict__ scale, __nv_bfloat16* __restrict__ out) {
   __shared__ double t[kOzTile][kOzTile + 1];
-  const int r0 = blockIdx.y * kOzTile, k0 = blockIdx.x * kOzTile;
-  oz_load_tile(v, R, K, r0, k0, split_k, t);
-  __syncthreads();
+  __shared__ int er[kOzTile];
+  const int k0 = blockIdx.x * kOzTile;
   const long plane = (long)R * Kp;
-  for (int q = threadIdx.x; q < kOzTile * kOzTile; q += blockDim.x) {
-    const int kk = q % kOzTile, rr = q / kOzTile;
-    const int r = r0 + rr, k = k0 + kk;
-    if (r >= R || k >= Kp) continue;
-    // x / sigma in (-1, 1) as a 2^56 fixed-point integer; slice s is its signed 7-bit
-    // digit of weight 2^(49 - 7 s), rounded to nearest, so |a_0| <= 128, |a_s| <= 64
-    long long X = __double2ll_rn(t[rr][kk] * (0x1p56 / scale[r]));
-    const long e = (long)r * Kp + k;
-    for (int s = 0; s < S; ++s) {
-      const int sh = 49 - 7 * s;
-      const long long a = (X + (1LL << (sh - 1))) >> sh;
-      X -= a << sh;
-      out[(long)s * plane + e] = __float2bfloat16_rn((float)a);
+  for (int r0 = blockIdx.y * kOzTile; r0 < R; r0 += gridDim.y * kOzTile) {
+    oz_load_tile(v, R, K, r0, k0, split_k, t);
+    if (threadIdx.x < kOzTile)
+      er[threadIdx.x] = r0 + (int)threadIdx.x < R ? ilogb(scale[r0 + threadIdx.x]) : 0;
+    __syncthreads();
+    for (int q = threadIdx.x; q < kOzTile * kOzTile; q += blockDim.x) {
+      const int kk = q % kOzTile, rr = q / kOzTile;
+      const int r = r0 + rr, k = k0 + kk;
+      if (r >= R || k >= Kp) continue;
+      // x / sigma_r (|.| < 1) as a 2^56 fixed-point integer, taken from the bits of x: the
+      // 53-bit significand shifted by (exponent - 52 + 56 - log2 sigma_r), rounded to nearest
+      const long long bits = __double_as_longlong(t[rr][kk]);
+      const int ex = (int)((bits >> 52) & 0x7FF);
+      long long X = 0;
+      if (ex != 0) {
+        const long long mant = (bits & 0xFFFFFFFFFFFFFLL) | (1LL << 52);
+        const int sh = ex - 1023 + 4 - er[rr];
+        if (sh >= 0) X = mant << sh;
+        else if (sh > -60) X = (mant + (1LL << (-sh - 1))) >> (-sh);
+        if (bits < 0) X = -X;
+      }
+      // slice s: the signed 7-bit digit of weight 2^(49 - 7 s), rounded to nearest, so
+      // |a_0| <= 128 and |a_s| <= 64
+      const long e = (long)r * Kp + k;
+      for (int s = 0; s < S; ++s) {
+        const int sh = 49 - 7 * s;
+        const long long a = (X + (1LL << (sh - 1))) >> sh;
+        X -= a << sh;
+        out[(long)s * plane + e] = __float2bfloat16_rn((float)a);
+      }
     }
+    __syncthreads();
   }
 }
 
@@ -320,13 +374,13 @@ __global__ void k_oz_split(OzView v, int R, int K, int Kp, int S, bool split_k,
 cudaError_t oz_split(const OzView& v, int R, int K, int Kp, int S, __nv_bfloat16* out,
                      double* scale, cudaStream_t s) {
   if (R <= 0) return cudaSuccess;
-  if (R > 65535 * kOzTile || (long)Kp >= (1L << 31)) return cudaErrorInvalidValue;
+  if ((long)Kp >= (1L << 31)) return cudaErrorInvalidValue;
   const bool split_k = v.kin < K;
   // the row maxima are staged in the scale array itself (same size, 8 bytes each)
   unsigned long long* mx = reinterpret_cast<unsigned long long*>(scale);
   cudaError_t e = cudaMemsetAsync(mx, 0, sizeof(unsigned long long) * R, s);
   if (e != cudaSuccess) return e;
-  const unsigned rt = (R + kOzTile - 1) / kOzTile;
+  const unsigned rt = std::min<unsigned>((R + kOzTile - 1) / kOzTile, 65535u);
   ++launch_counter();
   k_oz_rowmax<<<dim3((K + kOzTile - 1) / kOzTile, rt), 256, 0, s>>>(v, R, K, split_k, mx);
   ++launch_counter();
@@ -344,8 +398,8 @@ cudaError_t oz_gemm(const __nv_bfloat16* As, const double* sa, const __nv_bfloat
   if (S < 1 || S > kOzMaxSlices || Kp % kOzKStage != 0) return cudaErrorInvalidValue;
   // at least 116 KB so that one CTA (holding all 512 TMEM columns) runs per SM; the
   // attribute is global to the kernel, so it is set to the fixed maximum (7 slices)
-  const int smem = std::max(2 * S * (kOzASlice + kOzBSlice), 116 * 1024);
-  const int smem_max = std::max(2 * kOzMaxSlices * (kOzASlice + kOzBSlice), 116 * 1024);
+  const int smem = std::max(kOzBufs * S * (kOzASlice + kOzBSlice), 116 * 1024);
+  const int smem_max = std::max(kOzBufs * kOzMaxSlices * (kOzASlice + kOzBSlice), 116 * 1024);
   cudaError_t e =
       cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
   if (e != cudaSuccess) return e;

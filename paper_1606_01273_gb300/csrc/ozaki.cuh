@@ -6,8 +6,10 @@
 // 2^56 fixed-point integer, rounded to nearest): every a_s is exact in BF16.  A product of two
 // slices is an integer below 2^14, so the tensor core's FP32 accumulation of any level
 // l = s + t (at most l + 1 slice pairs) over a K chunk of 256 stays an exact integer below
-// 2^24.  Per chunk the S level sums are read from TMEM and combined in FP64:
-//   C_ij = sigma_i tau_j sum_l 2^(-7(l+2)) L_l(ij).
+// 2^24.  Per chunk the S level sums are read from TMEM and added, as exact integers shifted
+// to a common scale, into two int64 accumulators (levels 0-2 and 3..S-1), so that
+//   C_ij = sigma_i tau_j sum_l 2^(-7(l+2)) L_l(ij)
+// is rounded to FP64 only once, at the end.
 // Dropped terms (pairs with s + t >= S and the residuals) bound the error by about
 // 2^(-7S+1) K max|a| max|b| per element (S = 5: ~3e-11 relative to that scale).
 #pragma once
