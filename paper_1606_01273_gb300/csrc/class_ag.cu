@@ -671,7 +671,7 @@ int class_solve(ClassWork& w, SectorWork& sw, const Dims& d, int scheme, double 
       CASPT2_CUDA_TRY(cudaGetLastError());
       CASPT2_CUDA_TRY(dgemm(msec, nk, msec, 1.0, sw.Fsec, msec, false, sw.X, nk, false, 0.0,
                             sw.FX, nk, s));
-      CASPT2_CUDA_TRY(dgemm(nk, nk, msec, 1.0, sw.X, nk, true, sw.FX, nk, false, 0.0, sw.Ft, nk, s));
+      CASPT2_CUDA_TRY(dgemm_sym(nk, msec, 1.0, sw.X, nk, true, sw.FX, nk, false, 0.0, sw.Ft, nk, s));
       st = sym_eig(sw.Ft, nk, K.omega, sw.Qf, sw.jac, s, tm);
       if (st != CASPT2_OK) return st;
       CASPT2_CUDA_TRY(dgemm(msec, nk, nk, 1.0, sw.X, nk, false, sw.Qf, nk, false, 0.0, K.Y, nk, s));

@@ -109,25 +109,30 @@ __device__ bool grid_sync_bounded(unsigned* count, volatile unsigned* gen, int* 
   __syncthreads();
   __shared__ int ok;
   if (threadIdx.x == 0) {
-    const unsigned g = *gen;
-    __threadfence();
-    if (atomicAdd(count, 1u) == gridDim.x - 1) {
+    unsigned g;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(g) : "l"(gen) : "memory");
+    unsigned prev;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;"
+                 : "=r"(prev) : "l"(count) : "memory");
+    if (prev == gridDim.x - 1) {
       *count = 0;
-      __threadfence();
-      atomicAdd((unsigned*)gen, 1u);
+      asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(gen), "r"(g + 1u) : "memory");
       ok = 1;
     } else {
       long it = 0;
-      while (*gen == g && *(volatile int*)err == 0) {
+      unsigned cur;
+      for (;;) {
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(gen) : "memory");
+        if (cur != g) break;
+        if (*(volatile int*)err != 0) break;
         if (++it > kSpinLimit) {
           atomicExch(err, 1);
           break;
         }
-        __nanosleep(64);
+        if (it > 64) __nanosleep(32);
       }
       ok = (*(volatile int*)err == 0);
     }
-    __threadfence();
   }
   __syncthreads();
   return ok != 0;
@@ -262,7 +267,7 @@ k_tridiag_smem(const double* __restrict__ A, int m, double* __restrict__ vbuf,
   const int nloc = (m - b + G - 1) / G;            // rows b, b+G, ...
   double* rows = smem;
   double* v = rows + (long)((m + G - 1) / G) * m;
-  double* w = v + m;
+  double* w = v + m;                               // p of this step (all rows)
   double* r = w + m;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
   for (long q = threadIdx.x; q < (long)nloc * m; q += blockDim.x) {
@@ -280,18 +285,27 @@ k_tridiag_smem(const double* __restrict__ A, int m, double* __restrict__ vbuf,
   }
   for (int k = 0; k + 2 < m; ++k) {
     const int k1 = k + 1;
-    // p for the owned trailing rows
+    // p = tau A v for the owned trailing rows (one warp per row, four partial sums)
     const int lfirst = (k1 - b + G - 1) / G;       // first owned row index >= k+1
     for (int li = lfirst + warp; li < nloc; li += nwarp) {
       const double* row = rows + (long)li * m;
-      double s = 0.0;
-      for (int j = k1 + lane; j < m; j += 32) s += row[j] * v[j];
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      int j = k1 + lane;
+      for (; j + 96 < m; j += 128) {
+        s0 += row[j] * v[j];
+        s1 += row[j + 32] * v[j + 32];
+        s2 += row[j + 64] * v[j + 64];
+        s3 += row[j + 96] * v[j + 96];
+      }
+      for (; j < m; j += 32) s0 += row[j] * v[j];
+      double s = (s0 + s1) + (s2 + s3);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
       if (lane == 0) pbuf[(long)(k & 1) * m + b + li * G] = t * s;
     }
     if (!grid_sync_bounded(sync, sync + 1, err)) return;
-    // w = p - (tau/2)(p.v) v
+    // g = (tau/2) p.v; with w = p - g v the update A -= v w^T + w v^T reads
+    // A_ij -= v_i p_j + (p_i - 2 g v_i) v_j  (two FMAs per element)
     double s = 0.0;
     for (int j = k1 + threadIdx.x; j < m; j += blockDim.x) {
       const double pj = __ldcg(pbuf + (long)(k & 1) * m + j);
@@ -299,23 +313,24 @@ k_tridiag_smem(const double* __restrict__ A, int m, double* __restrict__ vbuf,
       s += pj * v[j];
     }
     s = block_sum(s, red);
-    if (threadIdx.x == 0) sh[3] = 0.5 * t * s;
+    if (threadIdx.x == 0) sh[3] = t * s;             // 2 g
     __syncthreads();
-    const double g = sh[3];
-    for (int j = k1 + threadIdx.x; j < m; j += blockDim.x) w[j] -= g * v[j];
-    __syncthreads();
+    const double g2 = sh[3];
     // update of the owned rows
-    const long nq = (long)(nloc - lfirst) * (m - k1);
-    for (long q = threadIdx.x; q < nq; q += blockDim.x) {
-      const int li = lfirst + (int)(q / (m - k1));
-      const int j = k1 + (int)(q % (m - k1));
+    for (int li = lfirst; li < nloc; ++li) {
       const int i = b + li * G;
-      rows[(long)li * m + j] -= v[i] * w[j] + w[i] * v[j];
+      const double vi = v[i], bi = fma(-g2, vi, w[i]);
+      double* row = rows + (long)li * m;
+      for (int j = k1 + threadIdx.x; j < m; j += blockDim.x)
+        row[j] = fma(-bi, v[j], fma(-vi, w[j], row[j]));
     }
     // row k+1 after this step (every block, from the copy published before the barrier)
     const double* old = (k == 0) ? A + (long)k1 * m : rowbuf + (long)(k1 & 1) * m;
-    for (int j = k1 + threadIdx.x; j < m; j += blockDim.x)
-      r[j] = __ldcg(old + j) - (v[k1] * w[j] + w[k1] * v[j]);
+    {
+      const double vi = v[k1], bi = fma(-g2, vi, w[k1]);
+      for (int j = k1 + threadIdx.x; j < m; j += blockDim.x)
+        r[j] = fma(-bi, v[j], fma(-vi, w[j], __ldcg(old + j)));
+    }
     __syncthreads();
     // the owner of row k+2 publishes it for the next step
     const int k2 = k + 2;
@@ -347,6 +362,7 @@ k_tridiag_smem(const double* __restrict__ A, int m, double* __restrict__ vbuf,
 // Shared memory of k_tridiag_smem for m columns on G blocks (0 if it does not fit).
 constexpr size_t kTridiagSmemMax = 200ull * 1024;
 constexpr size_t kBisectSmemMax = 200ull * 1024;    // d and e^2 of the tridiagonal matrix
+constexpr size_t kBackSmemMax = 200ull * 1024;      // resident columns of the back-transform
 size_t tridiag_smem_bytes(int m, int G) {
   const size_t b = 8ull * ((size_t)((m + G - 1) / G) * m + 3ull * m);
   return b <= kTridiagSmemMax ? b : 0;
@@ -426,20 +442,24 @@ __global__ void k_bisect(const double* __restrict__ dg, const double* __restrict
   __syncthreads();
   const double* d = sde;
   const double* e2 = sde + m;
+  // eight lanes per eigenvalue: lanes 0..6 count at the seven interior eighth points of
+  // the bracket (three bits per pass); one Sturm chain per lane, many warps, so that every
+  // SM sub-partition's FP64 unit has work
   const int gid = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = gid >> 2, q = gid & 3;
-  const unsigned grp = 0xFu << (threadIdx.x & 28);
-  if ((gid & ~3) >= ((m + 0) << 2)) return;          // whole group beyond m
+  const int j = gid >> 3, q = gid & 7;
+  const unsigned sh = threadIdx.x & 24;
+  const unsigned grp = 0xFFu << sh;
+  if ((gid & ~7) >= (m << 3)) return;          // whole group beyond m
   const bool live = j < m;
   double lo = glo, hi = ghi;
-  for (int it = 0; it < 80; ++it) {
+  for (int it = 0; it < 60; ++it) {
     if (hi - lo <= tol) break;
-    const double h = 0.25 * (hi - lo);
+    const double h = 0.125 * (hi - lo);
     const double x = lo + h * (q + 1);
-    const bool above = live && q < 3 && x > lo && x < hi && sturm_nodiv(d, e2, m, x) > j;
-    const unsigned b = (__ballot_sync(grp, above) >> (threadIdx.x & 28)) & 0x7u;
-    const int first = b ? (__ffs(b) - 1) : 3;           // first quarter point above j
-    const double nhi = first < 3 ? lo + h * (first + 1) : hi;
+    const bool above = live && q < 7 && x > lo && x < hi && sturm_nodiv(d, e2, m, x) > j;
+    const unsigned b = (__ballot_sync(grp, above) >> sh) & 0x7Fu;
+    const int first = b ? (__ffs(b) - 1) : 7;           // first eighth point above j
+    const double nhi = first < 7 ? lo + h * (first + 1) : hi;
     const double nlo = first > 0 ? lo + h * first : lo;
     if (!(nhi < hi || nlo > lo)) break;
     lo = nlo;
@@ -456,90 +476,150 @@ __device__ __forceinline__ double hash_unit(unsigned a, unsigned b) {
 
 // Inverse iteration for eigenvalue j (thread j).  Scratch arrays are laid out
 // [i][j] so that threads access consecutive addresses.  Z[i][j] = component i of vector j.
-__global__ void k_inviter(const double* __restrict__ d, const double* __restrict__ e,
+__global__ void k_inviter(const double* __restrict__ dg, const double* __restrict__ eg,
                           const double* __restrict__ w, int m, double tnorm,
                           double* __restrict__ u0, double* __restrict__ u1,
                           double* __restrict__ u2, double* __restrict__ lm,
                           double* __restrict__ pv, double* __restrict__ Z) {
+  extern __shared__ double sde[];      // d[m], e[m] staged per block
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    sde[i] = dg[i];
+    sde[m + i] = eg[i];
+  }
+  __syncthreads();
+  const double* d = sde;
+  const double* e = sde + m;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= m) return;
   const double lam = w[j];
   const double tiny = 2.2e-16 * (tnorm > 0 ? tnorm : 1.0);
 #define IX(i) ((long)(i) * m + j)
-  // factor T - lam I = P L U, U with two superdiagonals
-  for (int i = 0; i < m; ++i) {
-    u0[IX(i)] = d[i] - lam;
-    u1[IX(i)] = (i < m - 1) ? e[i] : 0.0;
-    u2[IX(i)] = 0.0;
-  }
+  // Factor T - lam I = P L U (U with two superdiagonals), the current row carried in
+  // registers; rows are final once passed, so their pivots are stored as reciprocals
+  // (|pivot| raised to tiny) and the solves below multiply.
+  auto raise = [&](double piv, double rp) {   // reciprocal of the pivot raised to tiny
+    return fabs(piv) < tiny ? 1.0 / copysign(tiny, piv == 0.0 ? 1.0 : piv) : rp;
+  };
+  double a = d[0] - lam, b = m > 1 ? e[0] : 0.0;
   for (int i = 0; i < m - 1; ++i) {
     const double c = e[i];          // subdiagonal element of row i+1
-    const double a = u0[IX(i)];
+    const double an = d[i + 1] - lam, bn = (i + 1 < m - 1) ? e[i + 1] : 0.0;
     if (fabs(a) >= fabs(c)) {
       const double piv = (a == 0.0) ? tiny : a;
-      u0[IX(i)] = piv;
-      const double l = c / piv;
+      const double rp = 1.0 / piv;
+      const double l = c * rp;
+      u0[IX(i)] = raise(piv, rp);
+      u1[IX(i)] = b;
+      u2[IX(i)] = 0.0;
       lm[IX(i)] = l;
       pv[IX(i)] = 0.0;
-      u0[IX(i + 1)] -= l * u1[IX(i)];
+      a = an - l * b;
+      b = bn;
     } else {
-      const double l = a / c;
+      const double rp = 1.0 / c;
+      const double l = a * rp;
+      u0[IX(i)] = raise(c, rp);
+      u1[IX(i)] = an;
+      u2[IX(i)] = bn;
       lm[IX(i)] = l;
       pv[IX(i)] = 1.0;
-      const double b_i = u1[IX(i)];
-      const double a_n = u0[IX(i + 1)], b_n = u1[IX(i + 1)];
-      u0[IX(i)] = c;
-      u1[IX(i)] = a_n;
-      u2[IX(i)] = b_n;
-      u0[IX(i + 1)] = b_i - l * a_n;
-      u1[IX(i + 1)] = -l * b_n;
+      a = b - l * an;
+      b = -l * bn;
     }
   }
-  if (u0[IX(m - 1)] == 0.0) u0[IX(m - 1)] = tiny;
-  // pivots -> reciprocals (|pivot| raised to tiny), so the solves below multiply
-  for (int i = 0; i < m; ++i) {
-    double piv = u0[IX(i)];
-    if (fabs(piv) < tiny) piv = copysign(tiny, piv == 0.0 ? 1.0 : piv);
-    u0[IX(i)] = 1.0 / piv;
+  {
+    const double piv = a == 0.0 ? tiny : a;
+    u0[IX(m - 1)] = raise(piv, 1.0 / piv);
   }
-  // start vector
-  for (int i = 0; i < m; ++i) Z[IX(i)] = hash_unit(i, j);
+  u1[IX(m - 1)] = 0.0;
+  u2[IX(m - 1)] = 0.0;
+  // three inverse iterations from a fixed start vector; the normalisation of each
+  // iterate is folded into the next forward pass.  Both passes go in chunks of eight
+  // rows whose operands are loaded before the dependent chain runs through them.
+  constexpr int CH = 8;
+  double scale = 1.0;
   for (int iter = 0; iter < 3; ++iter) {
     // apply L^-1 with the row interchanges
-    for (int i = 0; i < m - 1; ++i) {
-      double yi = Z[IX(i)], yn = Z[IX(i + 1)];
-      if (pv[IX(i)] != 0.0) {
-        const double t = yi; yi = yn; yn = t;
+    double cur = iter == 0 ? hash_unit(0, j) : Z[IX(0)] * scale;
+    for (int i0 = 0; i0 < m - 1; i0 += CH) {
+      const int cnt = min(CH, m - 1 - i0);
+      double yv[CH], lv[CH], pq[CH];
+#pragma unroll
+      for (int u = 0; u < CH; ++u) {
+        if (u < cnt) {
+          const int i = i0 + u;
+          yv[u] = iter == 0 ? hash_unit(i + 1, j) : Z[IX(i + 1)] * scale;
+          lv[u] = lm[IX(i)];
+          pq[u] = pv[IX(i)];
+        }
       }
-      Z[IX(i)] = yi;
-      Z[IX(i + 1)] = yn - lm[IX(i)] * yi;
-    }
-    // U^-1 with overflow guard
-    double big = 0.0;
-    for (int i = m - 1; i >= 0; --i) {
-      double x = Z[IX(i)];
-      if (i + 1 < m) x -= u1[IX(i)] * Z[IX(i + 1)];
-      if (i + 2 < m) x -= u2[IX(i)] * Z[IX(i + 2)];
-      x *= u0[IX(i)];
-      Z[IX(i)] = x;
-      big = fmax(big, fabs(x));
-      if (big > 1e100) {  // rescale the partial solution
-        for (int k2 = i; k2 < m; ++k2) Z[IX(k2)] *= 1e-100;
-        big *= 1e-100;
+#pragma unroll
+      for (int u = 0; u < CH; ++u) {
+        if (u < cnt) {
+          double yn = yv[u];
+          if (pq[u] != 0.0) {
+            const double t = cur; cur = yn; yn = t;
+          }
+          Z[IX(i0 + u)] = cur;
+          cur = yn - lv[u] * cur;
+        }
       }
     }
-    double nrm = 0.0;
-    for (int i = 0; i < m; ++i) nrm += Z[IX(i)] * Z[IX(i)];
-    nrm = 1.0 / sqrt(nrm);
-    for (int i = 0; i < m; ++i) Z[IX(i)] *= nrm;
+    // U^-1 with overflow guard (x1 = x_{i+1}, x2 = x_{i+2})
+    double big = 0.0, nrm = 0.0, x1 = 0.0, x2 = 0.0;
+    for (int i0 = m - 1; i0 >= 0; i0 -= CH) {
+      const int cnt = min(CH, i0 + 1);
+      double zv[CH], a0[CH], a1[CH], a2[CH];
+#pragma unroll
+      for (int u = 0; u < CH; ++u) {
+        if (u < cnt) {
+          const int i = i0 - u;
+          zv[u] = i == m - 1 ? cur : Z[IX(i)];
+          a0[u] = u0[IX(i)];
+          a1[u] = u1[IX(i)];
+          a2[u] = u2[IX(i)];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < CH; ++u) {
+        if (u < cnt) {
+          const int i = i0 - u;
+          double x = zv[u];
+          x -= a1[u] * x1;
+          x -= a2[u] * x2;
+          x *= a0[u];
+          Z[IX(i)] = x;
+          nrm += x * x;
+          x2 = x1;
+          x1 = x;
+          big = fmax(big, fabs(x));
+          if (big > 1e100) {  // rescale the partial solution
+            for (int k2 = i; k2 < m; ++k2) Z[IX(k2)] *= 1e-100;
+            big *= 1e-100;
+            nrm *= 1e-200;
+            x1 *= 1e-100;
+            x2 *= 1e-100;
+          }
+        }
+      }
+    }
+    scale = 1.0 / sqrt(nrm);
   }
+  for (int i = 0; i < m; ++i) Z[IX(i)] *= scale;
 #undef IX
 }
 
 // Modified Gram-Schmidt inside each cluster of (numerically) equal eigenvalues.
 // One block per eigenvalue index; only cluster starts do work.
-__global__ void k_cluster_mgs(const double* __restrict__ w, int m, double tol,
-                              double* __restrict__ Z) {
+// Orthonormalise each cluster of close eigenvalues (w sorted): the block of the cluster's
+// first index takes the cluster's columns, in shared memory when they fit (else in place
+// in Z), and applies classical Gram-Schmidt twice per vector (each pass projects the
+// vector on all earlier cluster vectors at once), then normalises it.
+__global__ void __launch_bounds__(256)
+k_cluster_cgs2(const double* __restrict__ w, int m, double tol, int smem_bytes,
+               double* __restrict__ Z) {
+  extern __shared__ double cs[];
+  __shared__ double part[8][33];
   __shared__ double red[32];
   __shared__ double sc;
   const int j0 = blockIdx.x;
@@ -547,26 +627,72 @@ __global__ void k_cluster_mgs(const double* __restrict__ w, int m, double tol,
   if (j0 + 1 >= m || w[j0 + 1] - w[j0] > tol) return;         // singleton
   int j1 = j0 + 1;
   while (j1 + 1 < m && w[j1 + 1] - w[j1] <= tol) ++j1;
-  for (int j = j0; j <= j1; ++j) {
-    for (int k = j0; k < j; ++k) {
-      double s = 0.0;
-      for (int i = threadIdx.x; i < m; i += blockDim.x) s += Z[(long)i * m + k] * Z[(long)i * m + j];
-      s = block_sum(s, red);
-      if (threadIdx.x == 0) sc = s;
-      __syncthreads();
-      const double proj = sc;
-      for (int i = threadIdx.x; i < m; i += blockDim.x) Z[(long)i * m + j] -= proj * Z[(long)i * m + k];
-      __syncthreads();
-    }
-    double s = 0.0;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) s += Z[(long)i * m + j] * Z[(long)i * m + j];
-    s = block_sum(s, red);
-    if (threadIdx.x == 0) sc = (s > 0.0) ? 1.0 / sqrt(s) : 0.0;
-    __syncthreads();
-    const double nr = sc;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) Z[(long)i * m + j] *= nr;
+  const int c = j1 - j0 + 1;
+  const bool in_smem = ((long)m * c + c) * 8 <= smem_bytes;
+  double* Zb = in_smem ? cs : Z + j0;          // column q of the cluster: Zb[i * ld + q]
+  const long ld = in_smem ? c : m;
+  double* pk = in_smem ? cs + (long)m * c : cs;
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  if (in_smem) {
+    for (long t = threadIdx.x; t < (long)m * c; t += blockDim.x)
+      cs[t] = Z[(t / c) * m + j0 + t % c];
     __syncthreads();
   }
+  for (int q = 0; q < c; ++q) {
+    for (int pass = 0; pass < 2 && q > 0; ++pass) {
+      // pk[r] = sum_i Zb[i][r] Zb[i][q] for r < q: lanes over 32 columns, warps over rows
+      // (four independent partial sums each), fixed-order sums over the warps
+      for (int r0 = 0; r0 < q; r0 += 32) {
+        const int r = r0 + lane;
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        if (r < q) {
+          int i = wp;
+          for (; i + 24 < m; i += 32) {
+            a0 += Zb[i * ld + r] * Zb[i * ld + q];
+            a1 += Zb[(i + 8) * ld + r] * Zb[(i + 8) * ld + q];
+            a2 += Zb[(i + 16) * ld + r] * Zb[(i + 16) * ld + q];
+            a3 += Zb[(i + 24) * ld + r] * Zb[(i + 24) * ld + q];
+          }
+          for (; i < m; i += 8) a0 += Zb[i * ld + r] * Zb[i * ld + q];
+        }
+        part[wp][lane] = (a0 + a1) + (a2 + a3);
+        __syncthreads();
+        if (wp == 0 && r < q) {
+          double t = 0.0;
+#pragma unroll
+          for (int g = 0; g < 8; ++g) t += part[g][lane];
+          pk[r] = t;
+        }
+        __syncthreads();
+      }
+      // Zb[i][q] -= sum_r pk[r] Zb[i][r]: one thread per row
+      for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        const double* zr = Zb + i * ld;
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        int r = 0;
+        for (; r + 3 < q; r += 4) {
+          a0 += pk[r] * zr[r];
+          a1 += pk[r + 1] * zr[r + 1];
+          a2 += pk[r + 2] * zr[r + 2];
+          a3 += pk[r + 3] * zr[r + 3];
+        }
+        for (; r < q; ++r) a0 += pk[r] * zr[r];
+        Zb[i * ld + q] -= (a0 + a1) + (a2 + a3);
+      }
+      __syncthreads();
+    }
+    double s2 = 0.0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) s2 += Zb[i * ld + q] * Zb[i * ld + q];
+    s2 = block_sum(s2, red);
+    if (threadIdx.x == 0) sc = (s2 > 0.0) ? 1.0 / sqrt(s2) : 0.0;
+    __syncthreads();
+    const double nr = sc;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) Zb[i * ld + q] *= nr;
+    __syncthreads();
+  }
+  if (in_smem)
+    for (long t = threadIdx.x; t < (long)m * c; t += blockDim.x)
+      Z[(t / c) * m + j0 + t % c] = cs[t];
 }
 
 // G = 1.5 I - 0.5 G (in place)
@@ -635,6 +761,68 @@ k_backtransform(const double* __restrict__ vbuf, const double* __restrict__ tau,
       for (int i = ry; i < n1; i += rg) Z[(long)(k + 1 + i) * m + c] -= v[i] * r;
     }
     __syncthreads();
+  }
+}
+
+// Same back-transformation with the block's cb columns of Z resident in shared memory
+// (column-major, zs[c][i]) for the whole reflector loop and one warp per column: the warp
+// forms v . z_c with a shuffle reduction and updates its column, so the block synchronises
+// once per reflector, when the next reflector (double-buffered in shared memory by
+// 8-byte cp.async copies) has landed.  Z is read and written once.
+__global__ void __launch_bounds__(512)
+k_backtransform_smem(const double* __restrict__ vbuf, const double* __restrict__ tau, int m,
+                     int cb, double* __restrict__ Z) {
+  extern __shared__ double zs[];                 // zs[cb][m], then vs[2][m]
+  double* vs = zs + (long)cb * m;
+  const int c0 = blockIdx.x * cb;
+  const int ncol = min(cb, m - c0);
+  const int lane = threadIdx.x & 31, wc = threadIdx.x >> 5;
+  const int nth = blockDim.x;
+  for (long q = threadIdx.x; q < (long)m * cb; q += nth) {
+    const int i = q / cb, c = q % cb;            // row-major walk of Z (coalesced per row)
+    zs[(long)c * m + i] = c < ncol ? Z[(long)i * m + c0 + c] : 0.0;
+  }
+  auto prefetch = [&](int k) {                   // v_k -> vs[k & 1]
+    const int n1 = m - k - 1;
+    const double* v = vbuf + (long)k * m + k + 1;
+    double* dst = vs + (long)(k & 1) * m;
+    for (int i = threadIdx.x; i < n1; i += nth) {
+      const unsigned sa = (unsigned)__cvta_generic_to_shared(dst + i);
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(v + i) : "memory");
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  if (m >= 3) prefetch(m - 3);
+  const bool act = wc < ncol;
+  double* zc = zs + (long)wc * m;
+  for (int k = m - 3; k >= 0; --k) {
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    __syncthreads();                             // v_k visible; step k+1 done with vs[(k+1)&1]
+    if (k > 0) prefetch(k - 1);
+    if (!act) continue;
+    const int n1 = m - k - 1;
+    const double* v = vs + (long)(k & 1) * m;
+    double* z = zc + k + 1;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int i = lane;
+    for (; i + 96 < n1; i += 128) {
+      s0 += v[i] * z[i];
+      s1 += v[i + 32] * z[i + 32];
+      s2 += v[i + 64] * z[i + 64];
+      s3 += v[i + 96] * z[i + 96];
+    }
+    for (; i < n1; i += 32) s0 += v[i] * z[i];
+    double sum = (s0 + s1) + (s2 + s3);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    const double r = sum * tau[k];
+    for (int i2 = lane; i2 < n1; i2 += 32) z[i2] -= v[i2] * r;
+  }
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  __syncthreads();
+  for (long q = threadIdx.x; q < (long)m * cb; q += nth) {
+    const int i = q / cb, c = q % cb;
+    if (c < ncol) Z[(long)i * m + c0 + c] = zs[(long)c * m + i];
   }
 }
 
@@ -770,24 +958,45 @@ int sym_eig_tridiag(double* A, int m, double* w, double* V, double* work, cudaSt
   if (2 * sizeof(double) * (size_t)m > kBisectSmemMax) return CASPT2_EINVAL;
   CASPT2_CUDA_TRY(cudaFuncSetAttribute(k_bisect, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)kBisectSmemMax));
-  k_bisect<<<(4 * m + 127) / 128, 128, 2 * sizeof(double) * m, s>>>(
+  k_bisect<<<(8 * m + 31) / 32, 32, 2 * sizeof(double) * m, s>>>(
       d, e, e2, m, glo, ghi, 4.0 * 2.2e-16 * std::max(1.0, tnorm), w);
   // 3. eigenvectors of T
   ++launch_counter();
-  k_inviter<<<(m + 127) / 128, 128, 0, s>>>(d, e, w, m, tnorm, u0, u1, u2, lm, pv, Z);
+  // one warp per block so that the m independent LU chains spread over the SMs
+  CASPT2_CUDA_TRY(cudaFuncSetAttribute(k_inviter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kBisectSmemMax));
+  k_inviter<<<(m + 31) / 32, 32, 2 * sizeof(double) * m, s>>>(d, e, w, m, tnorm, u0, u1, u2, lm,
+                                                               pv, Z);
   ++launch_counter();
-  k_cluster_mgs<<<m, 256, 0, s>>>(w, m, 1e-12 * std::max(1.0, tnorm), Z);
+  CASPT2_CUDA_TRY(cudaFuncSetAttribute(k_cluster_cgs2, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kBisectSmemMax));
+  {
+    const int cbytes = (int)std::min<size_t>(kBisectSmemMax, 8ull * ((size_t)m * m + m));
+    k_cluster_cgs2<<<m, 256, cbytes, s>>>(w, m, 1e-12 * std::max(1.0, tnorm), cbytes, Z);
+  }
   CASPT2_CUDA_TRY(cudaGetLastError());
   // 4. Newton-Schulz: Z <- Z (1.5 I - 0.5 Z^T Z)
-  CASPT2_CUDA_TRY(dgemm(m, m, m, 1.0, Z, m, true, Z, m, false, 0.0, G, m, s));
+  CASPT2_CUDA_TRY(dgemm_sym(m, m, 1.0, Z, m, true, Z, m, false, 0.0, G, m, s));
   ++launch_counter();
   k_ns_coef<<<nblocks(mm), kT, 0, s>>>(G, m);
   CASPT2_CUDA_TRY(dgemm(m, m, m, 1.0, Z, m, false, G, m, false, 0.0, V, m, s));
   // 5. back-transformation V = H_0 ... H_{m-3} Z (column-owned, one launch)
   if (m >= 3) {
     ++launch_counter();
-    const int cb = 8;       // 8 columns x 32 row groups per block
-    k_backtransform<<<(m + cb - 1) / cb, 256, 0, s>>>(vbuf, tau, m, cb, V);
+    // columns resident in shared memory: ceil(m / SMs) per block (one block per SM, the
+    // FP64 work spread evenly, one warp per column), fewer per block when they do not fit
+    const long fit = (long)(kBackSmemMax / (8ull * m)) - 2;      // minus the v buffers
+    const int cbs = (int)std::min<long>(std::min<long>(16, (m + nsm - 1) / nsm), fit);
+    if (cbs >= 1) {
+      CASPT2_CUDA_TRY(cudaFuncSetAttribute(k_backtransform_smem,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)kBackSmemMax));
+      k_backtransform_smem<<<(m + cbs - 1) / cbs, 32 * cbs, sizeof(double) * (size_t)m * (cbs + 2),
+                             s>>>(vbuf, tau, m, cbs, V);
+    } else {
+      const int cb = 8;     // 8 columns x 32 row groups per block
+      k_backtransform<<<(m + cb - 1) / cb, 256, 0, s>>>(vbuf, tau, m, cb, V);
+    }
   }
   CASPT2_CUDA_TRY(cudaGetLastError());
   return CASPT2_OK;

@@ -11,12 +11,20 @@ constexpr int kGT = 64, kGK = 16;
 __global__ void __launch_bounds__(256)
 k_dgemm(int M, int N, int K, double alpha, const double* __restrict__ A, int lda, int ta,
         const double* __restrict__ B, int ldb, int tb, double beta, double* __restrict__ C, int ldc,
-        long sA, long sB, long sC) {
+        long sA, long sB, long sC, int sym) {
   __shared__ double sa[kGK][kGT + 1], sb[kGK][kGT + 1];
   A += blockIdx.z * sA;
   B += blockIdx.z * sB;
   C += blockIdx.z * sC;
-  const int i0 = blockIdx.y * kGT, j0 = blockIdx.x * kGT;
+  int by = blockIdx.y, bx = blockIdx.x;
+  if (sym) {          // symmetric result: upper-triangle tiles only, blockIdx.x linear
+    const int T = (N + kGT - 1) / kGT;
+    int rem = blockIdx.x;
+    by = 0;
+    while (rem >= T - by) { rem -= T - by; ++by; }
+    bx = by + rem;
+  }
+  const int i0 = by * kGT, j0 = bx * kGT;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   double acc[4][4] = {};
   for (int k0 = 0; k0 < K; k0 += kGK) {
@@ -57,6 +65,10 @@ k_dgemm(int M, int N, int K, double alpha, const double* __restrict__ A, int lda
       if (gi < M && gj < N) {
         double* c = C + (long)gi * ldc + gj;
         *c = alpha * acc[p][q] + (beta == 0.0 ? 0.0 : beta * *c);
+        if (sym && bx != by) {
+          double* ct = C + (long)gj * ldc + gi;
+          *ct = alpha * acc[p][q] + (beta == 0.0 ? 0.0 : beta * *ct);
+        }
       }
     }
 }
@@ -135,8 +147,22 @@ cudaError_t dgemm(int M, int N, int K, double alpha, const double* A, int lda, b
   } else {
     dim3 grid((N + kGT - 1) / kGT, (M + kGT - 1) / kGT, batch);
     k_dgemm<<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, ta ? 1 : 0, B, ldb, tb ? 1 : 0, beta, C,
-                                 ldc, sA, sB, sC);
+                                 ldc, sA, sB, sC, 0);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t dgemm_sym(int N, int K, double alpha, const double* A, int lda, bool ta,
+                      const double* B, int ldb, bool tb, double beta, double* C, int ldc,
+                      cudaStream_t s) {
+  const int T = (N + kGT - 1) / kGT;
+  const double pad64 = (double)T * kGT * T * kGT / ((double)N * N);
+  if (N <= 0 || pad64 > 1.3 || T > 2048)
+    return dgemm(N, N, K, alpha, A, lda, ta, B, ldb, tb, beta, C, ldc, s);
+  ++launch_counter();
+  dim3 grid((unsigned)((long)T * (T + 1) / 2), 1, 1);
+  k_dgemm<<<grid, 256, 0, s>>>(N, N, K, alpha, A, lda, ta ? 1 : 0, B, ldb, tb ? 1 : 0, beta, C,
+                               ldc, 0, 0, 0, 1);
   return cudaGetLastError();
 }
 

@@ -19,6 +19,11 @@ struct KernelTimer {
 cudaError_t dgemm(int M, int N, int K, double alpha, const double* A, int lda, bool ta,
                   const double* B, int ldb, bool tb, double beta, double* C, int ldc,
                   cudaStream_t s, int batch = 1, long sA = 0, long sB = 0, long sC = 0);
+// Same product when the N x N result is known to be symmetric (A^T A, X^T F X): only the
+// upper-triangle tiles are computed, each written to both triangles.
+cudaError_t dgemm_sym(int N, int K, double alpha, const double* A, int lda, bool ta,
+                      const double* B, int ldb, bool tb, double beta, double* C, int ldc,
+                      cudaStream_t s);
 
 // Eigenpairs of a symmetric m x m matrix by parallel cyclic Jacobi.  A is destroyed
 // (left holding the diagonalised matrix); w[m] eigenvalues (ascending), V[m][m] with
