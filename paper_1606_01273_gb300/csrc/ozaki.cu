@@ -1,20 +1,29 @@
 // FP64-accurate GEMM from exact BF16 slices on the tcgen05 tensor cores (see ozaki.cuh).
 //
-// One CTA computes a 128 x 64 tile of C.  Its K loop runs over stages of 16: all 256
-// threads copy (cp.async, 16 bytes each, all in flight together) the S slices of the A
-// and B tiles into a ring of four shared-memory buffers, two stages ahead of the MMAs
-// (canonical K-major layout without swizzle: core matrices of 8 rows x 16 bytes, K-adjacent
-// core matrices 128 bytes apart, row groups 256 bytes apart), one thread issues the
-// tcgen05.mma instructions of every slice pair (s, t) with s + t < S into the TMEM
-// accumulator of level s + t (128 lanes x 64 FP32 columns per level) and commits them to
-// that buffer's mbarrier; a buffer is refilled once its stage's MMAs have completed.  After each
-// K chunk of 256 the eight warps read the S levels from TMEM (warp w: lanes 32 (w % 4).., 32
-// columns at 32 (w / 4)); the level sums (exact integers) are added, shifted, into two
-// int64 accumulators per output, converted to FP64 once at the end.  Every mbarrier wait
-// is bounded; on timeout the CTA records the error, stops issuing work, waits (bounded)
-// for its committed MMAs and frees its TMEM.
+// One CTA computes a 128 x 64 tile of C with warp-specialised roles and a ring of five
+// shared-memory stages of K = 16:
+//   warp 0 (one thread)  TMA producer: per stage four bulk-tensor copies (two K groups of 8
+//                        for A and for B, each box holding all S slices: {8 K, rows, S}),
+//                        completing the stage's `full` mbarrier by transaction bytes;
+//   warp 1 (one thread)  MMA issuer: per stage, for every A slice s, the tcgen05.mma of
+//                        slice s with the B slices t < S - s (stacked along N, up to four
+//                        per instruction) into the TMEM accumulators of levels s + t (128
+//                        lanes x 64 FP32 columns per level), committed to the stage's `empty`
+//                        mbarrier, and at the end of every exact K chunk of 256 to `tfull`;
+//   warps 2-9            epilogue: after each chunk they read the S levels from TMEM (warp w:
+//                        lanes 32 (w % 4).., 32 columns at 32 ((w - 2) / 4)), add the exact
+//                        integer level sums, shifted, into two int64 accumulators per output
+//                        and release TMEM through `tempty`; FP64 conversion once at the end.
+// The shared-memory layout is the canonical K-major one without swizzle: core matrices of
+// 8 rows x 16 bytes, M/N-adjacent core matrices 128 bytes apart (the TMA box rows), K-adjacent
+// ones one box apart.  Every mbarrier wait is bounded; on timeout the CTA records the error,
+// stops issuing work, waits (bounded) for its copies and MMAs in flight and frees its TMEM.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <cstdint>
+#include <mutex>
 
 #include "ozaki.cuh"
 
@@ -23,13 +32,13 @@ namespace caspt2 {
 namespace {
 
 constexpr int kOzM = 128, kOzN = 64;
-constexpr int kOzThreads = 256;
+constexpr int kOzThreads = 320;                     // warps: TMA, MMA, eight epilogue
 constexpr long kOzSpin = 1L << 22;
 constexpr int kOzKs = 16;                           // K per shared-memory stage (one MMA)
-constexpr int kOzBufs = 4;                          // stage ring; copies run 2 stages ahead
-constexpr int kOzASlice = kOzM * kOzKs * 2;         // bytes of one A slice tile per stage
-constexpr int kOzBSlice = kOzN * kOzKs * 2;
-constexpr int kOzSbo = (kOzKs / 8) * 128;           // row-group stride (bytes)
+constexpr int kOzStages = 5;                        // stage ring
+constexpr int kOzABox = kOzM * 8 * 2;               // bytes of one slice of an A box (8 K)
+constexpr int kOzBBox = kOzN * 8 * 2;
+__host__ __device__ inline int oz_stage_bytes(int S) { return 2 * S * (kOzABox + kOzBBox); }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -45,14 +54,17 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
 
 // Instruction descriptor, kind::f16: D F32 (bits 4-5 = 1), A and B BF16 (bits 7-9 and
 // 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) |
-                            ((uint32_t)(kOzN >> 3) << 17) | ((uint32_t)(kOzM >> 4) << 24);
+__host__ __device__ constexpr uint32_t oz_idesc(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(kOzM >> 4) << 24);
+}
 
-__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t acc) {
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc,
+                                         uint32_t acc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dtmem),
-      "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc));
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -89,37 +101,67 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+__device__ __forceinline__ void bar_arrive_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void tma_load3(uint32_t dst, const CUtensorMap* map, int c0, int c1,
+                                          int c2, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+      : "memory");
+}
+
 __global__ void __launch_bounds__(kOzThreads, 1)
-k_oz_gemm(const __nv_bfloat16* __restrict__ As, const double* __restrict__ sa,
-          const __nv_bfloat16* __restrict__ Bs, const double* __restrict__ sb, int M, int N,
-          int Kp, int S, int chunks_per_split, double alpha, double beta, double* __restrict__ C,
+k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+          const double* __restrict__ sa, const double* __restrict__ sb, int M, int N, int Kp,
+          int S, int chunks_per_split, double alpha, double beta, double* __restrict__ C,
           long ldc, double* __restrict__ part, int* err) {
-  extern __shared__ __align__(1024) uint8_t smem[];
-  __shared__ uint64_t bars[kOzBufs];
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ uint64_t full[kOzStages], empty[kOzStages], tfull, tempty;
   __shared__ uint32_t tmem_base;
-  __shared__ int abort_flag;
+  __shared__ int abort_flag, n_issued, n_committed;
+  volatile int* abort_v = &abort_flag;
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.y * kOzM, n0 = blockIdx.x * kOzN;
-  const long sliceA = (long)M * Kp, sliceB = (long)N * Kp;
-  const int stage_bytes = S * (kOzASlice + kOzBSlice);
+  const int stage_bytes = oz_stage_bytes(S);
   const uint32_t tcols = 512;
 
-  if (warp == 0) {
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&tmem_base)),
                  "r"(tcols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    for (int q = 0; q < kOzBufs; ++q)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[q])));
+    for (int q = 0; q < kOzStages; ++q) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[q])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[q])));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&tfull)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;" ::"r"(smem_u32(&tempty)));
     asm volatile("fence.mbarrier_init.release.cluster;");
     abort_flag = 0;
+    n_issued = n_committed = 0;
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tbase = tmem_base;
+
+  const int spc = kOzKChunk / kOzKs;              // stages per exact chunk
+  // stages of this split (blockIdx.z): exact chunks [z cps, (z + 1) cps)
+  const int gbeg = blockIdx.z * chunks_per_split * spc;
+  const int nst = max(0, min(Kp / kOzKs, gbeg + chunks_per_split * spc) - gbeg);
+  const int nchunk = (nst + spc - 1) / spc;
 
   // exact integer accumulation of the level sums: hi = sum_(l<3) L_l 2^(7(2-l)),
   // lo = sum_(l>=3) L_l 2^(7(S-1-l)); value = hi 2^-28 + lo 2^(-7(S+1))
@@ -127,79 +169,75 @@ k_oz_gemm(const __nv_bfloat16* __restrict__ As, const double* __restrict__ sa,
 #pragma unroll
   for (int j = 0; j < 32; ++j) hi[j] = lo[j] = 0;
 
-  const int spc = kOzKChunk / kOzKs;              // stages per exact chunk
-  // stages of this split (blockIdx.z): exact chunks [z cps, (z + 1) cps)
-  const int gbeg = blockIdx.z * chunks_per_split * spc;
-  const int nst = max(0, min(Kp / kOzKs, gbeg + chunks_per_split * spc) - gbeg);
-
-  // copy of stage g into ring buffer g % kOzBufs: S slices of A (128 rows) and B (64 rows),
-  // 16-byte pieces of 8 K values, all in flight together; one commit group per stage
-  auto issue_copy = [&](int g) {
-    uint8_t* buf = smem + (long)(g % kOzBufs) * stage_bytes;
-    const int nA = S * kOzM * (kOzKs / 8), nB = S * kOzN * (kOzKs / 8);
-    const int k0 = (gbeg + g) * kOzKs;
-    for (int q = tid; q < nA + nB; q += kOzThreads) {
-      const bool isA = q < nA;
-      const int qq = isA ? q : q - nA;
-      const int c = qq % (kOzKs / 8);
-      const int rr = (qq / (kOzKs / 8)) % (isA ? kOzM : kOzN);
-      const int s = qq / ((kOzKs / 8) * (isA ? kOzM : kOzN));
-      const int grow = (isA ? m0 : n0) + rr;
-      const bool ok = grow < (isA ? M : N);
-      // rows past the edge read nothing (source size 0) and are zero-filled
-      const __nv_bfloat16* src =
-          ok ? (isA ? As + s * sliceA : Bs + s * sliceB) + (long)grow * Kp + k0 + 8 * c : As;
-      uint8_t* dst = buf + (isA ? s * kOzASlice : S * kOzASlice + s * kOzBSlice) +
-                     (rr >> 3) * kOzSbo + c * 128 + (rr & 7) * 16;
-      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)),
-                   "l"(src), "r"(ok ? 16 : 0)
-                   : "memory");
-    }
-    asm volatile("cp.async.commit_group;" ::: "memory");
-  };
-  // MMAs of stage g complete the (g / kOzBufs)-th phase of bars[g % kOzBufs]
-  auto stage_parity = [](int g) { return (uint32_t)((g / kOzBufs) & 1); };
-
-  for (int g = 0; g < 2 && g < nst; ++g) issue_copy(g);
-  int committed = 0;                              // stages whose MMAs were committed
-  for (int g = 0; g < nst; ++g) {
-    // copy of stage g done (the copy of g + 1 may still be in flight)
-    if (g + 1 < nst) asm volatile("cp.async.wait_group 1;" ::: "memory");
-    else asm volatile("cp.async.wait_group 0;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (abort_flag) break;
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      const bool first = (g % spc) == 0;
-      const uint32_t ab = smem_u32(smem + (long)(g % kOzBufs) * stage_bytes);
-      const uint32_t bb = ab + S * kOzASlice;
-      for (int s = 0; s < S; ++s)
-        for (int t = 0; t < S - s; ++t) {
-          const uint64_t ad = sdesc(ab + s * kOzASlice, 128, kOzSbo);
-          const uint64_t bd = sdesc(bb + t * kOzBSlice, 128, kOzSbo);
-          const uint32_t accf = (first && s == 0) ? 0u : 1u;
-          mma_bf16(tbase + (uint32_t)((s + t) * kOzN), ad, bd, accf);
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int g = 0; g < nst; ++g) {
+        const int b = g % kOzStages;
+        if (g >= kOzStages && !bar_wait(&empty[b], (uint32_t)(((g / kOzStages) - 1) & 1))) {
+          *abort_v = 1;
+          break;
         }
-      mma_commit(&bars[g % kOzBufs]);
+        if (*abort_v) break;
+        bar_arrive_tx(&full[b], (uint32_t)stage_bytes);
+        const uint32_t da = smem_u32(smem + (long)b * stage_bytes);
+        const uint32_t db = da + 2 * S * kOzABox;
+        const int k0 = (gbeg + g) * kOzKs;
+        tma_load3(da, &tmA, k0, m0, 0, &full[b]);
+        tma_load3(da + S * kOzABox, &tmA, k0 + 8, m0, 0, &full[b]);
+        tma_load3(db, &tmB, k0, n0, 0, &full[b]);
+        tma_load3(db + S * kOzBBox, &tmB, k0 + 8, n0, 0, &full[b]);
+        n_issued = g + 1;
+      }
     }
-    committed = g + 1;
-    // prefetch stage g + 2 into the buffer of stage g - 2 once its MMAs are done
-    if (g + 2 < nst) {
-      if (g >= 2 && !bar_wait(&bars[(g + 2) % kOzBufs], stage_parity(g - 2))) abort_flag = 1;
-      issue_copy(g + 2);
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint64_t adesc0 = sdesc(smem_u32(smem), S * kOzABox, 128);
+      const uint64_t bdesc0 = sdesc(smem_u32(smem) + 2 * S * kOzABox, S * kOzBBox, 128);
+      for (int g = 0; g < nst; ++g) {
+        const int b = g % kOzStages;
+        const int c = g / spc;
+        const bool first = (g % spc) == 0;
+        if (first && c > 0 && !bar_wait(&tempty, (uint32_t)((c - 1) & 1))) {
+          *abort_v = 1;
+          break;
+        }
+        if (!bar_wait(&full[b], (uint32_t)((g / kOzStages) & 1))) {
+          *abort_v = 1;
+          break;
+        }
+        if (*abort_v) break;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint64_t soff = (uint64_t)((b * stage_bytes) >> 4);
+        // the B slices of a stage are stacked along N (slice t at rows 64 t..), so one MMA
+        // multiplies A slice s by B slices t0 .. t0 + cnt - 1 into the TMEM column blocks
+        // s + t0 .. (levels), up to four slices (N = 256) per instruction
+        for (int s = 0; s < S; ++s) {
+          const uint64_t ad = adesc0 + soff + (uint64_t)((s * kOzABox) >> 4);
+          for (int t0 = 0; t0 < S - s; t0 += 4) {
+            const int cnt = min(4, S - s - t0);
+            const uint64_t bd = bdesc0 + soff + (uint64_t)((t0 * kOzBBox) >> 4);
+            mma_bf16(tbase + (uint32_t)((s + t0) * kOzN), ad, bd, oz_idesc(kOzN * cnt),
+                     (first && s == 0) ? 0u : 1u);
+          }
+        }
+        mma_commit(&empty[b]);
+        if ((g % spc) == spc - 1 || g == nst - 1) mma_commit(&tfull);
+        n_committed = g + 1;
+      }
     }
-    if ((g % spc) == spc - 1 || g == nst - 1) {
-      // end of an exact chunk: add the S level sums into the integer accumulators
-      if (!bar_wait(&bars[g % kOzBufs], stage_parity(g))) abort_flag = 1;
-      __syncthreads();
-      if (abort_flag) break;
+  } else {
+    // epilogue: one chunk of S levels at a time
+    const int q = warp & 3, h = (warp - 2) >> 2;
+    const uint32_t lb = (uint32_t)(32 * q) << 16;
+    for (int c = 0; c < nchunk; ++c) {
+      if (!bar_wait(&tfull, (uint32_t)(c & 1))) {
+        *abort_v = 1;
+        break;
+      }
       asm volatile("tcgen05.fence::after_thread_sync;");
-      const uint32_t lb = (uint32_t)(32 * (warp & 3)) << 16;
-      const uint32_t cb = (uint32_t)(32 * (warp >> 2));
       for (int l = 0; l < S; ++l) {
         uint32_t r[32];
-        tmem_ld32(tbase + lb + (uint32_t)(l * kOzN) + cb, r);
+        tmem_ld32(tbase + lb + (uint32_t)(l * kOzN + 32 * h), r);
         // each level sum is an integer below 2^24: exact in FP32 and in int32
         if (l < 3) {
           const int sh = 7 * (2 - l);
@@ -214,17 +252,23 @@ k_oz_gemm(const __nv_bfloat16* __restrict__ As, const double* __restrict__ sa,
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;");
-      __syncthreads();
+      __syncwarp();
+      if (lane == 0) bar_arrive(&tempty);
     }
   }
-  asm volatile("cp.async.wait_group 0;" ::: "memory");
-  // drain: the MMAs of the last committed stages must finish before TMEM is freed
-  if (abort_flag) {
+  __syncthreads();
+  if (*abort_v) {
+    // drain: copies in flight must land and committed MMAs finish before the CTA leaves
     if (tid == 0) atomicExch(err, 1);
-    for (int g = committed - kOzBufs; g < committed; ++g)
-      if (g >= 0) bar_wait(&bars[g % kOzBufs], (uint32_t)((g / kOzBufs) & 1));
-  } else {
-    const int row = m0 + 32 * (warp & 3) + lane;
+    if (tid == 0)
+      for (int g = max(0, n_issued - kOzStages); g < n_issued; ++g)
+        bar_wait(&full[g % kOzStages], (uint32_t)((g / kOzStages) & 1));
+    if (tid == 32)
+      for (int g = max(0, n_committed - kOzStages); g < n_committed; ++g)
+        bar_wait(&empty[g % kOzStages], (uint32_t)((g / kOzStages) & 1));
+  } else if (warp >= 2) {
+    const int q = warp & 3, h = (warp - 2) >> 2;
+    const int row = m0 + 32 * q + lane;
     double acc[32];
     const double wlo = ldexp(1.0, -7 * (S + 1));
 #pragma unroll
@@ -235,14 +279,14 @@ k_oz_gemm(const __nv_bfloat16* __restrict__ As, const double* __restrict__ sa,
         double* prow = part + ((long)blockIdx.z * M + row) * N;
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
-          const int col = n0 + 32 * (warp >> 2) + j;
+          const int col = n0 + 32 * h + j;
           if (col < N) prow[col] = sr * sb[col] * acc[j];
         }
       } else {
         double* crow = C + (long)row * ldc;
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
-          const int col = n0 + 32 * (warp >> 2) + j;
+          const int col = n0 + 32 * h + j;
           if (col < N) {
             const double v = sr * sb[col] * acc[j];
             crow[col] = beta == 0.0 ? v : v + beta * crow[col];
@@ -253,7 +297,7 @@ k_oz_gemm(const __nv_bfloat16* __restrict__ As, const double* __restrict__ sa,
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  if (warp == 0) {
+  if (warp == 1) {
     asm volatile("tcgen05.fence::after_thread_sync;");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(tcols));
   }
@@ -391,15 +435,50 @@ cudaError_t oz_split(const OzView& v, int R, int K, int Kp, int S, __nv_bfloat16
   return cudaGetLastError();
 }
 
+namespace {
+// cuTensorMapEncodeTiled through the runtime's driver entry point (resolved once)
+PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// 3-D map of slices out[s][r][Kp] (BF16): dims (Kp, R, S), box (8 K, rows, S).
+bool slice_map(CUtensorMap* map, const __nv_bfloat16* X, int R, int Kp, int S, int rows) {
+  auto enc = tmap_encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)R, (cuuint64_t)S};
+  const cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)R * Kp * 2};
+  const cuuint32_t box[3] = {8u, (cuuint32_t)rows, (cuuint32_t)S};
+  const cuuint32_t es[3] = {1u, 1u, 1u};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16*>(X), dims,
+             strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+}  // namespace
+
 cudaError_t oz_gemm(const __nv_bfloat16* As, const double* sa, const __nv_bfloat16* Bs,
                     const double* sb, int M, int N, int Kp, int S, double alpha, double beta,
                     double* C, long ldc, int* err, cudaStream_t s, int nsplit, double* part) {
   if (M <= 0 || N <= 0) return cudaSuccess;
   if (S < 1 || S > kOzMaxSlices || Kp % kOzKStage != 0) return cudaErrorInvalidValue;
-  // at least 116 KB so that one CTA (holding all 512 TMEM columns) runs per SM; the
-  // attribute is global to the kernel, so it is set to the fixed maximum (7 slices)
-  const int smem = std::max(kOzBufs * S * (kOzASlice + kOzBSlice), 116 * 1024);
-  const int smem_max = std::max(kOzBufs * kOzMaxSlices * (kOzASlice + kOzBSlice), 116 * 1024);
+  if ((reinterpret_cast<uintptr_t>(As) | reinterpret_cast<uintptr_t>(Bs)) & 15)
+    return cudaErrorInvalidValue;
+  CUtensorMap ma, mb;
+  if (!slice_map(&ma, As, M, Kp, S, kOzM) || !slice_map(&mb, Bs, N, Kp, S, kOzN))
+    return cudaErrorInvalidValue;
+  // the ring of five stages (1 KB alignment slack); the attribute is global to the kernel,
+  // so it is set to the fixed maximum (7 slices)
+  const int smem = kOzStages * oz_stage_bytes(S) + 1024;
+  const int smem_max = kOzStages * oz_stage_bytes(kOzMaxSlices) + 1024;
   cudaError_t e =
       cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
   if (e != cudaSuccess) return e;
@@ -410,7 +489,7 @@ cudaError_t oz_gemm(const __nv_bfloat16* As, const double* sa, const __nv_bfloat
   if (nsplit > 1 && !part) return cudaErrorInvalidValue;
   dim3 grid((N + kOzN - 1) / kOzN, (M + kOzM - 1) / kOzM, nsplit);
   ++launch_counter();
-  k_oz_gemm<<<grid, kOzThreads, smem, s>>>(As, sa, Bs, sb, M, N, Kp, S, cps, alpha, beta, C, ldc,
+  k_oz_gemm<<<grid, kOzThreads, smem, s>>>(ma, mb, sa, sb, M, N, Kp, S, cps, alpha, beta, C, ldc,
                                            nsplit > 1 ? part : nullptr, err);
   if (nsplit > 1) {
     const long total = (long)M * N;
