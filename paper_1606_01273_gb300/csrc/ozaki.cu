@@ -1,7 +1,8 @@
 // FP64-accurate GEMM from exact BF16 slices on the tcgen05 tensor cores (see ozaki.cuh).
 //
-// One CTA computes a 128 x 64 tile of C with warp-specialised roles and a ring of five
-// shared-memory stages of K = 16:
+// Persistent CTAs (one per SM) walk the 128 x 64 tiles of C (and K splits) with
+// warp-specialised roles and a ring of five shared-memory stages of K = 16 that runs on
+// across tiles:
 //   warp 0 (one thread)  TMA producer: per stage four bulk-tensor copies (two K groups of 8
 //                        for A and for B, each box holding all S slices: {8 K, rows, S}),
 //                        completing the stage's `full` mbarrier by transaction bytes;
@@ -121,8 +122,8 @@ __device__ __forceinline__ void tma_load3(uint32_t dst, const CUtensorMap* map, 
 __global__ void __launch_bounds__(kOzThreads, 1)
 k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
           const double* __restrict__ sa, const double* __restrict__ sb, int M, int N, int Kp,
-          int S, int chunks_per_split, double alpha, double beta, double* __restrict__ C,
-          long ldc, double* __restrict__ part, int* err) {
+          int S, int chunks_per_split, int nsplit, double alpha, double beta,
+          double* __restrict__ C, long ldc, double* __restrict__ part, int* err) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint64_t full[kOzStages], empty[kOzStages], tfull, tempty;
   __shared__ uint32_t tmem_base;
@@ -131,7 +132,6 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int m0 = blockIdx.y * kOzM, n0 = blockIdx.x * kOzN;
   const int stage_bytes = oz_stage_bytes(S);
   const uint32_t tcols = 512;
 
@@ -157,103 +157,157 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tbase = tmem_base;
 
+  // tiles (n tile, m tile, K split) in a persistent loop; every role walks the same
+  // sequence, and the stage ring and barrier phases run on across tiles
+  const int ntn = (N + kOzN - 1) / kOzN, ntm = (M + kOzM - 1) / kOzM;
+  const long ntiles = (long)ntn * ntm * nsplit;
   const int spc = kOzKChunk / kOzKs;              // stages per exact chunk
-  // stages of this split (blockIdx.z): exact chunks [z cps, (z + 1) cps)
-  const int gbeg = blockIdx.z * chunks_per_split * spc;
-  const int nst = max(0, min(Kp / kOzKs, gbeg + chunks_per_split * spc) - gbeg);
-  const int nchunk = (nst + spc - 1) / spc;
-
-  // exact integer accumulation of the level sums: hi = sum_(l<3) L_l 2^(7(2-l)),
-  // lo = sum_(l>=3) L_l 2^(7(S-1-l)); value = hi 2^-28 + lo 2^(-7(S+1))
-  long long hi[32], lo[32];
-#pragma unroll
-  for (int j = 0; j < 32; ++j) hi[j] = lo[j] = 0;
+  auto tile_of = [&](long ti, int& m0, int& n0, int& z, int& gbeg, int& nst) {
+    n0 = (int)(ti % ntn) * kOzN;
+    m0 = (int)((ti / ntn) % ntm) * kOzM;
+    z = (int)(ti / ((long)ntn * ntm));
+    gbeg = z * chunks_per_split * spc;            // stages of K split z
+    nst = max(0, min(Kp / kOzKs, gbeg + chunks_per_split * spc) - gbeg);
+  };
 
   if (warp == 0) {
     if (lane == 0) {
-      for (int g = 0; g < nst; ++g) {
-        const int b = g % kOzStages;
-        if (g >= kOzStages && !bar_wait(&empty[b], (uint32_t)(((g / kOzStages) - 1) & 1))) {
-          *abort_v = 1;
-          break;
+      int G = 0;                                  // stages issued by this CTA
+      for (long ti = blockIdx.x; ti < ntiles && !*abort_v; ti += gridDim.x) {
+        int m0, n0, z, gbeg, nst;
+        tile_of(ti, m0, n0, z, gbeg, nst);
+        for (int g = 0; g < nst; ++g, ++G) {
+          const int b = G % kOzStages;
+          if (G >= kOzStages && !bar_wait(&empty[b], (uint32_t)(((G / kOzStages) - 1) & 1))) {
+            *abort_v = 1;
+            break;
+          }
+          if (*abort_v) break;
+          bar_arrive_tx(&full[b], (uint32_t)stage_bytes);
+          const uint32_t da = smem_u32(smem + (long)b * stage_bytes);
+          const uint32_t db = da + 2 * S * kOzABox;
+          const int k0 = (gbeg + g) * kOzKs;
+          tma_load3(da, &tmA, k0, m0, 0, &full[b]);
+          tma_load3(da + S * kOzABox, &tmA, k0 + 8, m0, 0, &full[b]);
+          tma_load3(db, &tmB, k0, n0, 0, &full[b]);
+          tma_load3(db + S * kOzBBox, &tmB, k0 + 8, n0, 0, &full[b]);
+          n_issued = G + 1;
         }
-        if (*abort_v) break;
-        bar_arrive_tx(&full[b], (uint32_t)stage_bytes);
-        const uint32_t da = smem_u32(smem + (long)b * stage_bytes);
-        const uint32_t db = da + 2 * S * kOzABox;
-        const int k0 = (gbeg + g) * kOzKs;
-        tma_load3(da, &tmA, k0, m0, 0, &full[b]);
-        tma_load3(da + S * kOzABox, &tmA, k0 + 8, m0, 0, &full[b]);
-        tma_load3(db, &tmB, k0, n0, 0, &full[b]);
-        tma_load3(db + S * kOzBBox, &tmB, k0 + 8, n0, 0, &full[b]);
-        n_issued = g + 1;
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
       const uint64_t adesc0 = sdesc(smem_u32(smem), S * kOzABox, 128);
       const uint64_t bdesc0 = sdesc(smem_u32(smem) + 2 * S * kOzABox, S * kOzBBox, 128);
-      for (int g = 0; g < nst; ++g) {
-        const int b = g % kOzStages;
-        const int c = g / spc;
-        const bool first = (g % spc) == 0;
-        if (first && c > 0 && !bar_wait(&tempty, (uint32_t)((c - 1) & 1))) {
-          *abort_v = 1;
-          break;
-        }
-        if (!bar_wait(&full[b], (uint32_t)((g / kOzStages) & 1))) {
-          *abort_v = 1;
-          break;
-        }
-        if (*abort_v) break;
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        const uint64_t soff = (uint64_t)((b * stage_bytes) >> 4);
-        // the B slices of a stage are stacked along N (slice t at rows 64 t..), so one MMA
-        // multiplies A slice s by B slices t0 .. t0 + cnt - 1 into the TMEM column blocks
-        // s + t0 .. (levels), up to four slices (N = 256) per instruction
-        for (int s = 0; s < S; ++s) {
-          const uint64_t ad = adesc0 + soff + (uint64_t)((s * kOzABox) >> 4);
-          for (int t0 = 0; t0 < S - s; t0 += 4) {
-            const int cnt = min(4, S - s - t0);
-            const uint64_t bd = bdesc0 + soff + (uint64_t)((t0 * kOzBBox) >> 4);
-            mma_bf16(tbase + (uint32_t)((s + t0) * kOzN), ad, bd, oz_idesc(kOzN * cnt),
-                     (first && s == 0) ? 0u : 1u);
+      int G = 0, Cc = 0;                          // stages and chunks of this CTA
+      for (long ti = blockIdx.x; ti < ntiles && !*abort_v; ti += gridDim.x) {
+        int m0, n0, z, gbeg, nst;
+        tile_of(ti, m0, n0, z, gbeg, nst);
+        for (int g = 0; g < nst; ++g, ++G) {
+          const int b = G % kOzStages;
+          const bool first = (g % spc) == 0;
+          if (first && Cc > 0 && !bar_wait(&tempty, (uint32_t)((Cc - 1) & 1))) {
+            *abort_v = 1;
+            break;
           }
+          if (!bar_wait(&full[b], (uint32_t)((G / kOzStages) & 1))) {
+            *abort_v = 1;
+            break;
+          }
+          if (*abort_v) break;
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const uint64_t soff = (uint64_t)((b * stage_bytes) >> 4);
+          // the B slices of a stage are stacked along N (slice t at rows 64 t..), so one MMA
+          // multiplies A slice s by B slices t0 .. t0 + cnt - 1 into the TMEM column blocks
+          // s + t0 .. (levels), up to four slices (N = 256) per instruction
+          for (int s = 0; s < S; ++s) {
+            const uint64_t ad = adesc0 + soff + (uint64_t)((s * kOzABox) >> 4);
+            for (int t0 = 0; t0 < S - s; t0 += 4) {
+              const int cnt = min(4, S - s - t0);
+              const uint64_t bd = bdesc0 + soff + (uint64_t)((t0 * kOzBBox) >> 4);
+              mma_bf16(tbase + (uint32_t)((s + t0) * kOzN), ad, bd, oz_idesc(kOzN * cnt),
+                       (first && s == 0) ? 0u : 1u);
+            }
+          }
+          mma_commit(&empty[b]);
+          if ((g % spc) == spc - 1 || g == nst - 1) {
+            mma_commit(&tfull);
+            ++Cc;
+          }
+          n_committed = G + 1;
         }
-        mma_commit(&empty[b]);
-        if ((g % spc) == spc - 1 || g == nst - 1) mma_commit(&tfull);
-        n_committed = g + 1;
       }
     }
   } else {
-    // epilogue: one chunk of S levels at a time
+    // epilogue: per tile, one chunk of S levels at a time; TMEM is released as soon as the
+    // levels are in registers, so the next chunk's (or tile's) MMAs overlap the stores
     const int q = warp & 3, h = (warp - 2) >> 2;
     const uint32_t lb = (uint32_t)(32 * q) << 16;
-    for (int c = 0; c < nchunk; ++c) {
-      if (!bar_wait(&tfull, (uint32_t)(c & 1))) {
-        *abort_v = 1;
-        break;
+    int Cc = 0;
+    for (long ti = blockIdx.x; ti < ntiles && !*abort_v; ti += gridDim.x) {
+      int m0, n0, z, gbeg, nst;
+      tile_of(ti, m0, n0, z, gbeg, nst);
+      const int nchunk = (nst + spc - 1) / spc;
+      // exact integer accumulation of the level sums: hi = sum_(l<3) L_l 2^(7(2-l)),
+      // lo = sum_(l>=3) L_l 2^(7(S-1-l)); value = hi 2^-28 + lo 2^(-7(S+1))
+      long long hi[32], lo[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) hi[j] = lo[j] = 0;
+      bool ok = true;
+      for (int c = 0; c < nchunk; ++c, ++Cc) {
+        if (!bar_wait(&tfull, (uint32_t)(Cc & 1))) {
+          *abort_v = 1;
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        for (int l = 0; l < S; ++l) {
+          uint32_t r[32];
+          tmem_ld32(tbase + lb + (uint32_t)(l * kOzN + 32 * h), r);
+          // each level sum is an integer below 2^24: exact in FP32 and in int32
+          if (l < 3) {
+            const int sh = 7 * (2 - l);
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              hi[j] += (long long)__float2int_rn(__uint_as_float(r[j])) << sh;
+          } else {
+            const int sh = 7 * (S - 1 - l);
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              lo[j] += (long long)__float2int_rn(__uint_as_float(r[j])) << sh;
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncwarp();
+        if (lane == 0) bar_arrive(&tempty);
       }
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      for (int l = 0; l < S; ++l) {
-        uint32_t r[32];
-        tmem_ld32(tbase + lb + (uint32_t)(l * kOzN + 32 * h), r);
-        // each level sum is an integer below 2^24: exact in FP32 and in int32
-        if (l < 3) {
-          const int sh = 7 * (2 - l);
+      if (!ok) break;
+      const int row = m0 + 32 * q + lane;
+      double acc[32];
+      const double wlo = ldexp(1.0, -7 * (S + 1));
 #pragma unroll
-          for (int j = 0; j < 32; ++j)
-            hi[j] += (long long)__float2int_rn(__uint_as_float(r[j])) << sh;
+      for (int j = 0; j < 32; ++j) acc[j] = (double)hi[j] * 0x1p-28 + (double)lo[j] * wlo;
+      if (row < M) {
+        const double sr = alpha * sa[row];
+        if (part) {   // split K: this split's share, summed in a fixed order afterwards
+          double* prow = part + ((long)z * M + row) * N;
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int col = n0 + 32 * h + j;
+            if (col < N) prow[col] = sr * sb[col] * acc[j];
+          }
         } else {
-          const int sh = 7 * (S - 1 - l);
+          double* crow = C + (long)row * ldc;
 #pragma unroll
-          for (int j = 0; j < 32; ++j)
-            lo[j] += (long long)__float2int_rn(__uint_as_float(r[j])) << sh;
+          for (int j = 0; j < 32; ++j) {
+            const int col = n0 + 32 * h + j;
+            if (col < N) {
+              const double v = sr * sb[col] * acc[j];
+              crow[col] = beta == 0.0 ? v : v + beta * crow[col];
+            }
+          }
         }
       }
-      asm volatile("tcgen05.fence::before_thread_sync;");
-      __syncwarp();
-      if (lane == 0) bar_arrive(&tempty);
     }
   }
   __syncthreads();
@@ -266,34 +320,6 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     if (tid == 32)
       for (int g = max(0, n_committed - kOzStages); g < n_committed; ++g)
         bar_wait(&empty[g % kOzStages], (uint32_t)((g / kOzStages) & 1));
-  } else if (warp >= 2) {
-    const int q = warp & 3, h = (warp - 2) >> 2;
-    const int row = m0 + 32 * q + lane;
-    double acc[32];
-    const double wlo = ldexp(1.0, -7 * (S + 1));
-#pragma unroll
-    for (int j = 0; j < 32; ++j) acc[j] = (double)hi[j] * 0x1p-28 + (double)lo[j] * wlo;
-    if (row < M) {
-      const double sr = alpha * sa[row];
-      if (part) {   // split K: this split's share, summed in a fixed order afterwards
-        double* prow = part + ((long)blockIdx.z * M + row) * N;
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int col = n0 + 32 * h + j;
-          if (col < N) prow[col] = sr * sb[col] * acc[j];
-        }
-      } else {
-        double* crow = C + (long)row * ldc;
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int col = n0 + 32 * h + j;
-          if (col < N) {
-            const double v = sr * sb[col] * acc[j];
-            crow[col] = beta == 0.0 ? v : v + beta * crow[col];
-          }
-        }
-      }
-    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
@@ -487,10 +513,15 @@ cudaError_t oz_gemm(const __nv_bfloat16* As, const double* sa, const __nv_bfloat
   const int cps = (nchunk + nsplit - 1) / nsplit;
   nsplit = (nchunk + cps - 1) / cps;
   if (nsplit > 1 && !part) return cudaErrorInvalidValue;
-  dim3 grid((N + kOzN - 1) / kOzN, (M + kOzM - 1) / kOzM, nsplit);
+  // persistent CTAs (one per SM: the ring and all 512 TMEM columns) over the tiles
+  const long ntiles = (long)((N + kOzN - 1) / kOzN) * ((M + kOzM - 1) / kOzM) * nsplit;
+  int dev = 0, nsm = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = (int)std::min<long>(ntiles, nsm);
   ++launch_counter();
-  k_oz_gemm<<<grid, kOzThreads, smem, s>>>(ma, mb, sa, sb, M, N, Kp, S, cps, alpha, beta, C, ldc,
-                                           nsplit > 1 ? part : nullptr, err);
+  k_oz_gemm<<<grid, kOzThreads, smem, s>>>(ma, mb, sa, sb, M, N, Kp, S, cps, nsplit, alpha, beta,
+                                           C, ldc, nsplit > 1 ? part : nullptr, err);
   if (nsplit > 1) {
     const long total = (long)M * N;
     ++launch_counter();
