@@ -37,15 +37,22 @@ FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 rate (no measured FP64 peak is pr
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_classH launch at this workload
 # (ncu capture summarised in profiles/); None until captured for the current kernel.
 CLASSH_TRAFFIC_BYTES = None
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) from ncu captures of the current
+# kernels on this workload (bench.py --profile-case classA / classH):
+#   k_tridiag_smem, m = 1536: 18.94 MB + 14.08 MB against 28.31 MB algorithmic
+#   k_oz_gemm, class-H K = Bcv^T Bcv (4000 x 4000 x 700, 7 slices): 45.89 MB + 85.85 MB
+TRIDIAG_DRAM_PER_ALG_BYTE = (18.944512e6 + 14.080000e6) / (8.0 * 1536 ** 2 + 4.0 * 1536 * 1535)
+CLASSH_SPLIT_TRAFFIC_BYTES = 45.892096e6 + 85.852416e6
 
 
 def measured_peak(key, fallback):
-    """A peak from MEASURED_PEAKS.json (driver-written), else the stated fallback."""
+    """(peak, kind): a peak from MEASURED_PEAKS.json (driver-written), else the stated
+    fallback (one earlier GB300 measurement)."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
-            return float(json.load(fh)[key])
-    except (OSError, KeyError, ValueError):
-        return fallback
+            return float(json.load(fh)[key]), "measured (MEASURED_PEAKS.json %s)" % key
+    except (OSError, KeyError, ValueError, TypeError):
+        return fallback, "fallback (MEASURED_PEAKS.json absent on this machine)"
 
 
 def classh_flops(c, v, X):
@@ -290,7 +297,8 @@ def run_ours(args):
                 r = ctx.result()
                 rec["dens_ms"].append(r.timings_ms[8])
                 rec["kern_ms"].append(r.timings_ms[4])
-                rec["tri"].append((r.timings_ms[5], r.timings_ms[6], r.timings_ms[7]))
+                rec["tri"].append((r.timings_ms[5], r.timings_ms[6], r.timings_ms[7],
+                                   r.timings_ms[9]))
                 rec["launches"] += r.launches
             torch.cuda.synchronize(dev)
         if ws > 1:
@@ -352,12 +360,14 @@ def run_ours(args):
         npair = args.slices * (args.slices + 1) // 2
         flops = npair * 2.0 * cv * cv * p.naux
         achieved = flops / (kavg * 1e-3) / 1e12
-        peak = measured_peak("bf16_tflops", 1900.0)
+        peak, peak_kind = measured_peak("bf16_tflops", 1900.0)
         roof_h = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                  "frac": achieved / peak, "traffic": None, "kernel": "k_oz_gemm",
+                  "frac": achieved / peak,
+                  "traffic": CLASSH_SPLIT_TRAFFIC_BYTES if args.slices == 7 else None,
+                  "kernel": "k_oz_gemm",
                   "kernel_ms": kavg, "flops_per_launch": flops,
                   "fp64_equivalent_tflops": 2.0 * cv * cv * p.naux / (kavg * 1e-3) / 1e12,
-                  "peak_kind": "measured bf16 burst (MEASURED_PEAKS.json)"}
+                  "peak_kind": "bf16 burst, " + peak_kind}
     else:
         flops = classh_flops(p.nclosed, p.nvirt, p.naux)
         achieved = flops / (kavg * 1e-3) / 1e12
@@ -368,6 +378,7 @@ def run_ours(args):
     tri_ms = sum(t[0] for t in tri)
     tri_fl = sum(t[1] for t in tri)
     tri_n = sum(t[2] for t in tri)
+    tri_alg_bytes = sum(t[3] for t in tri) / max(tri_n, 1)
     tri_avg_ms = tri_ms / max(tri_n, 1)
     tri_achieved = tri_fl / max(tri_ms * 1e-3, 1e-12) / 1e12
     line = {
@@ -387,7 +398,11 @@ def run_ours(args):
         # of the class overlap / Fock matrices; FP64, 4/3 m^3 algorithmic flops per launch
         "roofline": {"bound": "alu", "achieved": tri_achieved, "peak": FP64_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": tri_achieved / FP64_PEAK_TFLOPS,
-                     "traffic": None, "kernel": "k_tridiag", "kernel_ms": tri_avg_ms,
+                     "traffic": TRIDIAG_DRAM_PER_ALG_BYTE * tri_alg_bytes,
+                     "traffic_note": "ncu DRAM bytes of the m = 1536 launch scaled by the "
+                                     "launches' algorithmic bytes (matrix read, reflectors "
+                                     "written)",
+                     "kernel": "k_tridiag", "kernel_ms": tri_avg_ms,
                      "launches_per_step": tri_n / max(len(tri), 1),
                      "flops_per_launch": tri_fl / max(tri_n, 1),
                      "peak_kind": "nominal FP64 (no measured FP64 peak in MEASURED_PEAKS)"},
@@ -425,6 +440,22 @@ def run_ours(args):
     return 0
 
 
+# class masks (bit k = class "ABCDEFGH"[k]) for kernel captures: class A alone makes the
+# first tridiagonalisation the 1536 x 1536 class-A overlap matrix; class H alone makes the
+# first split GEMM the class-H pair-integral product K = Bcv^T Bcv (4000 x 4000 x 700)
+PROFILE_CASES = {"classA": 1 << 0, "classH": 1 << 7}
+
+
+def run_profile_case(args):
+    import paper_1606_01273_gb300 as cp
+    p = make_inputs()
+    prec = cp.BF16X if args.precision == "bf16x" else cp.FP64
+    r = cp.solve_problem(p, class_mask=PROFILE_CASES[args.profile_case], precision=prec,
+                         slices=args.slices, **OPTS)
+    print("profile case", args.profile_case, "E_MS", list(np.round(r.Ems, 10)))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -436,7 +467,12 @@ def main():
     ap.add_argument("--precision", choices=["fp64", "bf16x"], default="bf16x")
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--slices", type=int, default=7)
+    ap.add_argument("--profile-case", choices=sorted(PROFILE_CASES),
+                    help="one solve of the benchmark workload restricted to one class (a "
+                         "small command for kernel captures); prints no JSON line")
     args = ap.parse_args()
+    if args.profile_case:
+        return run_profile_case(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -20,8 +20,8 @@ using namespace caspt2;
 namespace {
 
 constexpr int kNumStages = 4;  // setup, class H, classes A-G, H^eff
-constexpr int kNumTimes = kNumStages + 5;  // + class-H kernel, tridiagonalisation ms/flops/launches,
-                                           //   densities
+constexpr int kNumTimes = kNumStages + 6;  // + class-H kernel, tridiagonalisation ms/flops/launches,
+                                           //   densities, tridiagonalisation bytes
 
 }  // namespace
 
@@ -372,7 +372,7 @@ int caspt2_solve(caspt2_ctx* c, void* stream) {
   const long a2 = (long)d.a * d.a;
   const double big = 1e300;
   const long launches0 = launch_counter();
-  c->tri.ms = c->tri.flops = 0.0;
+  c->tri.ms = c->tri.flops = c->tri.bytes = 0.0;
   c->tri.launches = 0;
   CASPT2_CUDA_TRY(cudaMemsetAsync(c->status, 0, sizeof(int), s));
   CASPT2_CUDA_TRY(cudaMemcpyAsync(c->mindenom, &big, sizeof(double), cudaMemcpyHostToDevice, s));
@@ -489,6 +489,7 @@ int caspt2_solve(caspt2_ctx* c, void* stream) {
   c->times[kNumStages + 1] = c->tri.ms;
   c->times[kNumStages + 2] = c->tri.flops;
   c->times[kNumStages + 3] = (double)c->tri.launches;
+  c->times[kNumStages + 5] = c->tri.bytes;
   c->times[kNumStages + 4] = 0.0;
   c->launches = launch_counter() - launches0;
   c->solved = true;

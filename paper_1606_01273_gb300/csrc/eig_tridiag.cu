@@ -893,6 +893,8 @@ int sym_eig_tridiag(double* A, int m, double* w, double* V, double* work, cudaSt
       CASPT2_CUDA_TRY(cudaEventElapsedTime(&ms, tm->e0, tm->e1));
       tm->ms += ms;
       tm->flops += 4.0 / 3.0 * (double)m * m * m;   // Householder tridiagonalisation
+      // the matrix read once and the reflectors (lower triangle) written once
+      tm->bytes += 8.0 * m * m + 4.0 * m * (m - 1.0);
       ++tm->launches;
     }
   } else if (m > 64) {
@@ -915,6 +917,8 @@ int sym_eig_tridiag(double* A, int m, double* w, double* V, double* work, cudaSt
       CASPT2_CUDA_TRY(cudaEventElapsedTime(&ms, tm->e0, tm->e1));
       tm->ms += ms;
       tm->flops += 4.0 / 3.0 * (double)m * m * m;   // Householder tridiagonalisation
+      // the matrix read once and the reflectors (lower triangle) written once
+      tm->bytes += 8.0 * m * m + 4.0 * m * (m - 1.0);
       ++tm->launches;
     }
   } else {

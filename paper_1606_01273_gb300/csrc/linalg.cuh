@@ -11,6 +11,7 @@ struct KernelTimer {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   double ms = 0.0;       // summed device time
   double flops = 0.0;    // summed algorithmic flops
+  double bytes = 0.0;    // summed algorithmic DRAM bytes
   long launches = 0;
 };
 
