@@ -7,8 +7,9 @@
 //   3. every eigenvector of T by inverse iteration on the pivoted tridiagonal LU
 //      (one thread per eigenvalue), Gram-Schmidt inside clusters of equal eigenvalues;
 //   4. one Newton-Schulz step Z <- Z (3 - Z^T Z) / 2 to restore orthogonality to
-//      rounding level;
+//      rounding level (skipped when Z^T Z is already within 1e-13 of the identity);
 //   5. back-transformation V = Q Z by applying the reflectors in reverse order.
+#include <cstring>
 #include <vector>
 
 #include "linalg.cuh"
@@ -696,11 +697,25 @@ k_cluster_cgs2(const double* __restrict__ w, int m, double tol, int smem_bytes,
 }
 
 // G = 1.5 I - 0.5 G (in place)
-__global__ void k_ns_coef(double* __restrict__ G, int m) {
+// and dev = max |G - I| (order-independent integer maximum of the bit patterns)
+__global__ void k_ns_coef(double* __restrict__ G, int m, unsigned long long* __restrict__ dev) {
   const long total = (long)m * m;
+  unsigned long long mx = 0;
   for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total;
-       t += (long)gridDim.x * blockDim.x)
-    G[t] = ((t / m == t % m) ? 1.5 : 0.0) - 0.5 * G[t];
+       t += (long)gridDim.x * blockDim.x) {
+    const bool diag = t / m == t % m;
+    const double g = G[t];
+    const unsigned long long b =
+        (unsigned long long)__double_as_longlong(g - (diag ? 1.0 : 0.0)) & 0x7FFFFFFFFFFFFFFFull;
+    mx = b > mx ? b : mx;
+    G[t] = (diag ? 1.5 : 0.0) - 0.5 * g;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long y = __shfl_xor_sync(0xffffffffu, mx, o);
+    mx = y > mx ? y : mx;
+  }
+  if ((threadIdx.x & 31) == 0 && mx) atomicMax(dev, mx);
 }
 
 // r[c] = sum_i v[i] Z[k+1+i][c]: 32 columns x 8 row groups per block (coalesced rows),
@@ -979,11 +994,24 @@ int sym_eig_tridiag(double* A, int m, double* w, double* V, double* work, cudaSt
     k_cluster_cgs2<<<m, 256, cbytes, s>>>(w, m, 1e-12 * std::max(1.0, tnorm), cbytes, Z);
   }
   CASPT2_CUDA_TRY(cudaGetLastError());
-  // 4. Newton-Schulz: Z <- Z (1.5 I - 0.5 Z^T Z)
+  // 4. Newton-Schulz: Z <- Z (1.5 I - 0.5 Z^T Z), skipped when Z is already orthonormal to
+  //    1e-13 (the step would change it by less than that)
+  unsigned long long* ns_dev = reinterpret_cast<unsigned long long*>(r + m);
+  CASPT2_CUDA_TRY(cudaMemsetAsync(ns_dev, 0, sizeof(unsigned long long), s));
   CASPT2_CUDA_TRY(dgemm_sym(m, m, 1.0, Z, m, true, Z, m, false, 0.0, G, m, s));
   ++launch_counter();
-  k_ns_coef<<<nblocks(mm), kT, 0, s>>>(G, m);
-  CASPT2_CUDA_TRY(dgemm(m, m, m, 1.0, Z, m, false, G, m, false, 0.0, V, m, s));
+  k_ns_coef<<<nblocks(mm), kT, 0, s>>>(G, m, ns_dev);
+  CASPT2_CUDA_TRY(cudaGetLastError());
+  unsigned long long hdev = 0;
+  CASPT2_CUDA_TRY(cudaMemcpyAsync(&hdev, ns_dev, sizeof(hdev), cudaMemcpyDeviceToHost, s));
+  CASPT2_CUDA_TRY(cudaStreamSynchronize(s));
+  double dev_ortho;
+  std::memcpy(&dev_ortho, &hdev, sizeof(double));
+  if (!(dev_ortho == dev_ortho)) return CASPT2_ENAN;
+  if (dev_ortho <= 1e-13)
+    CASPT2_CUDA_TRY(cudaMemcpyAsync(V, Z, sizeof(double) * mm, cudaMemcpyDeviceToDevice, s));
+  else
+    CASPT2_CUDA_TRY(dgemm(m, m, m, 1.0, Z, m, false, G, m, false, 0.0, V, m, s));
   // 5. back-transformation V = H_0 ... H_{m-3} Z (column-owned, one launch)
   if (m >= 3) {
     ++launch_counter();
