@@ -62,10 +62,8 @@ def classh_flops(c, v, X):
 
 
 def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    from paper_1606_01273_gb300.shard import dist_env as env
+    return env()
 
 
 class ClockSampler:
@@ -248,6 +246,7 @@ def run_reference(args):
 def run_ours(args):
     import torch
     import paper_1606_01273_gb300 as cp
+    from paper_1606_01273_gb300.shard import job_rate, max_over_ranks, sum_over_ranks
 
     ws, rank, local = dist_env()
     if ws > 1:
@@ -304,10 +303,7 @@ def run_ours(args):
         if ws > 1:
             torch.distributed.barrier()
         total = sum(a.elapsed_time(b) for a, b in ev) / 1e3
-        if ws > 1:
-            t = torch.tensor([total], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            total = float(t.item())
+        total = max_over_ranks(total, dev)
         rec.update(total_s=total, clk=clk.summary(), last=ctx.result())
         ctx.close()
         return rec
@@ -316,7 +312,7 @@ def run_ours(args):
     total_s, last = main["total_s"], main["last"]
     kern_ms, tri, dens_ms, launches, clk = (main["kern_ms"], main["tri"], main["dens_ms"],
                                             main["launches"], main["clk"])
-    value = ws * args.steps / total_s
+    value = job_rate(sum_over_ranks(args.steps, dev), total_s)
     other = None
     if args.precision == "bf16x" and not args.no_compare:
         other = time_device(dict(OPTS, precision=cp.FP64))
@@ -339,12 +335,8 @@ def run_ours(args):
         ctx_h.result()
         ctx_h.get_densities(with_gdf=False)
     torch.cuda.synchronize(dev)
-    e2e_s = time.perf_counter() - t0
-    if ws > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = ws * args.steps / e2e_s
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dev)
+    e2e_value = job_rate(sum_over_ranks(args.steps, dev), e2e_s)
     ctx_h.close()
 
     if rank != 0:
