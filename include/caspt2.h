@@ -127,6 +127,28 @@ int caspt2_get_class_energy(caspt2_ctx* ctx, int cls, double* e, double* norm);
  * Either pointer may be NULL.  Errors: EINVAL (class not enabled, or target_state < 0). */
 int caspt2_get_class_lambda(caspt2_ctx* ctx, int cls, double* NL, double* lv);
 
+/* Number of first-order amplitudes of a class per (L, N): nfam * (external tuples) *
+ * a^(active indices) for the classes A-G (0 if the class is not enabled), c^2 v^2 for
+ * class H.  Negative (EINVAL) for a null context or a bad class index. */
+long caspt2_amplitude_size(const caspt2_ctx* ctx, int cls);
+
+/* First-order amplitudes T_LN (Eq. ampeq, Sec. II.B: the solution of the class's amplitude
+ * equation for reference state L, component N of the MS-MR basis;
+ * SS-SR: zero for N != L) and the Lagrange multipliers lambda_LN of the target state
+ * P = opt.target_state (Eq. lambdaeq, Sec. II.C), of a class A-G, in the range-projected gauge (the
+ * amplitudes are expanded in the class's orthonormalised basis Y = X Q, X = V s^(-1/2) over
+ * the overlap eigenvalues kept by the threshold).  out[amplitude_size] is laid out
+ * [family][external indices in slot order][active indices], row-major, in the caller's
+ * memory (mem = CASPT2_MEM_HOST or CASPT2_MEM_DEVICE).  The vector is rebuilt from the
+ * sector eigenbases the solve keeps (the solve never stores amplitudes); the call runs on
+ * cuda_stream and returns after the result is in out.  Errors: EINVAL (bad index, class H
+ * (its amplitudes are never formed), class not enabled, or lambda with target_state < 0),
+ * ESTATE (no solve yet), ETIMEOUT (a bounded wait of a split GEMM gave up). */
+int caspt2_get_amplitudes(caspt2_ctx* ctx, int cls, int L, int N, int mem, double* out,
+                          void* cuda_stream);
+int caspt2_get_lambda(caspt2_ctx* ctx, int cls, int L, int N, int mem, double* out,
+                      void* cuda_stream);
+
 /* Core energy E_core = <core|H|core> (closed orbitals doubly occupied) of the last solve. */
 int caspt2_get_core_energy(caspt2_ctx* ctx, double* ecore);
 

@@ -80,6 +80,10 @@ def lib():
         L.caspt2_densities.argtypes = [P, C.c_uint, P]
         L.caspt2_get_densities.argtypes = [P, C.c_int, P, P, P]
         L.caspt2_gradient.argtypes = [P, C.c_int, P, P, P]
+        L.caspt2_amplitude_size.argtypes = [P, C.c_int]
+        L.caspt2_amplitude_size.restype = C.c_long
+        L.caspt2_get_amplitudes.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int, P, P]
+        L.caspt2_get_lambda.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int, P, P]
         L.caspt2_server_create.argtypes = [C.POINTER(P), C.c_size_t, C.c_int]
         L.caspt2_server_submit.argtypes = [P, C.POINTER(Request), C.POINTER(C.c_long)]
         L.caspt2_server_wait.argtypes = [P, C.c_long, C.c_int, C.POINTER(ServeResult)]
@@ -250,6 +254,29 @@ class Context:
         """compute_densities + get_densities: host copies (d1, d2, gdf), each symmetrised."""
         self.compute_densities(class_mask, stream)
         return self.get_densities()
+
+    def amplitude_size(self, cls: int) -> int:
+        """caspt2_amplitude_size: elements of T_LN (or lambda_LN) of class index cls."""
+        n = int(lib().caspt2_amplitude_size(self._h, cls))
+        if n < 0:
+            raise CASPT2Error(n, "caspt2_amplitude_size")
+        return n
+
+    def _class_vector(self, fn, name, cls, L, N, stream):
+        out = np.zeros(self.amplitude_size(cls))
+        s = C.c_void_p(stream) if stream is not None else None
+        _check(fn(self._h, cls, L, N, MEM_HOST, C.c_void_p(out.ctypes.data), s), name)
+        return out
+
+    def amplitudes(self, cls: int, L: int, N: int, stream=None) -> np.ndarray:
+        """T_LN of class cls (0-6 = A-G), flat [family][external...][active...]."""
+        return self._class_vector(lib().caspt2_get_amplitudes, "caspt2_get_amplitudes", cls, L,
+                                  N, stream)
+
+    def lambdas(self, cls: int, L: int, N: int, stream=None) -> np.ndarray:
+        """lambda_LN of the target state, class cls (0-6 = A-G), same layout as amplitudes."""
+        return self._class_vector(lib().caspt2_get_lambda, "caspt2_get_lambda", cls, L, N,
+                                  stream)
 
 
 def classH_noalloc(dims: Dims, opts: Options, fock, dfB, rdm1, e, norm, stream=None) -> int:

@@ -11,6 +11,7 @@
 #include <map>
 
 #include "class_ag.cuh"
+#include "class_dev.cuh"
 #include "kernels.cuh"
 #include "linalg.cuh"
 #include "ozaki.cuh"
@@ -688,6 +689,66 @@ int caspt2_densities(caspt2_ctx* c, unsigned class_mask, void* stream) {
   c->launches += launch_counter() - launches0;
   c->dens_done = true;
   return CASPT2_OK;
+}
+
+long caspt2_amplitude_size(const caspt2_ctx* c, int cls) {
+  if (!c || cls < 0 || cls > CASPT2_CLASS_H) return CASPT2_EINVAL;
+  if (cls == CASPT2_CLASS_H) return (long)c->d.c * c->d.c * c->d.v * c->d.v;
+  if (!c->cw_on[cls]) return 0;
+  const ClassWork& w = c->cw[cls];
+  return (long)w.dc.nfam * all_tuples(w) * w.A;
+}
+
+}  // extern "C"
+
+namespace {
+// T_LN (lam = false) or lambda_LN of the target state (lam = true) of a class A-G, rebuilt
+// from the sector eigenbases kept by the solve and gathered into out[fam][ext...][act...].
+int get_class_vector(caspt2_ctx* c, int cls, int L, int N, int mem, double* out, bool lam,
+                     void* stream) {
+  if (!c || !out || cls < 0 || cls >= CASPT2_CLASS_H) return CASPT2_EINVAL;
+  if (mem != CASPT2_MEM_HOST && mem != CASPT2_MEM_DEVICE) return CASPT2_EINVAL;
+  if (!c->solved) return CASPT2_ESTATE;
+  const caspt2_options& o = c->opt;
+  const Dims& d = c->d;
+  if (!c->cw_on[cls] || L < 0 || L >= d.n || N < 0 || N >= d.n || d.a > 16) return CASPT2_EINVAL;
+  if (lam && o.target_state < 0) return CASPT2_EINVAL;
+  CASPT2_CUDA_TRY(cudaSetDevice(c->device));
+  if (!c->dens_alloc) {
+    const int st = alloc_densities(c);
+    if (st != CASPT2_OK) return st;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ClassWork& w = c->cw[cls];
+  const long size = (long)w.dc.nfam * all_tuples(w) * w.A;
+  if (size == 0) return CASPT2_OK;
+  const int P = o.target_state >= 0 ? o.target_state : 0;
+  int st = class_tuple_amplitudes(w, c->dw, d, o.shift, c->E0, c->eps, c->R, P, &c->oz, s);
+  if (st != CASPT2_OK) return st;
+  // device output directly; host output through the (free) S T buffer, which holds
+  // ntuples * n * m >= size doubles
+  double* dst = mem == CASPT2_MEM_DEVICE ? out : c->dw.U1;
+  CASPT2_CUDA_TRY(gather_amplitudes(w, d, lam ? c->dw.Lam : c->dw.T, L, N, dst, s));
+  if (mem == CASPT2_MEM_HOST)
+    CASPT2_CUDA_TRY(cudaMemcpyAsync(out, dst, sizeof(double) * size, cudaMemcpyDeviceToHost, s));
+  int ozerr = 0;
+  if (c->oz.err)
+    CASPT2_CUDA_TRY(cudaMemcpyAsync(&ozerr, c->oz.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CASPT2_CUDA_TRY(cudaStreamSynchronize(s));
+  return ozerr != 0 ? CASPT2_ETIMEOUT : CASPT2_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int caspt2_get_amplitudes(caspt2_ctx* c, int cls, int L, int N, int mem, double* out,
+                          void* cuda_stream) {
+  return get_class_vector(c, cls, L, N, mem, out, false, cuda_stream);
+}
+
+int caspt2_get_lambda(caspt2_ctx* c, int cls, int L, int N, int mem, double* out,
+                      void* cuda_stream) {
+  return get_class_vector(c, cls, L, N, mem, out, true, cuda_stream);
 }
 
 int caspt2_get_densities(caspt2_ctx* c, int mem, double* d1, double* d2, double* gdf) {

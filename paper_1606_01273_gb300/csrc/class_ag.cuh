@@ -102,6 +102,14 @@ cudaError_t launch_lambda(const double* mom, const double* R, int n, int P, doub
 // virtual blocks of dL/df) and the adjoint integral blocks G (same keys and layout
 // as the (pq|rt) blocks of the solve).  Uses the sector bases kept by class_solve;
 // NL = this class's <lambda_L|S|T_L>.
+// First-order amplitudes T_L and lambda_L (target state P) of every sector of a class,
+// back-transformed to all index tuples: dw.T and dw.Lam [tuple][L][(fam, act..., N)].
+int class_tuple_amplitudes(ClassWork& w, DensWork& dw, const Dims& d, double shift,
+                           const double* E0, const double* eps_cv, const double* R, int P,
+                           OzWork* oz, cudaStream_t s);
+// out[fam][ext...][act...] = src[tuple][L][(fam, act..., N)] for one (L, N).
+cudaError_t gather_amplitudes(const ClassWork& w, const Dims& d, const double* src, int L, int N,
+                              double* out, cudaStream_t s);
 int class_densities(ClassWork& w, DensWork& dw, const Dims& d, int scheme, double shift,
                     RdmPtrs rdm, const double* E0, const double* eps_cv, const double* R, int P,
                     const double* NL, const EriBlocks& G, double* d1, double* d2, OzWork* oz,

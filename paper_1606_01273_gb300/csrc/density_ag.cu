@@ -537,17 +537,15 @@ cudaError_t launch_symmetrize(double* x, int nmo, long batch, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-int class_densities(ClassWork& w, DensWork& dw, const Dims& d, int scheme, double shift,
-                    RdmPtrs rdm, const double* E0, const double* eps_cv, const double* R, int P,
-                    const double* NL, const EriBlocks& G, double* d1, double* d2, OzWork* oz,
-                    cudaStream_t s) {
-  (void)scheme;
-  const int m = w.m, n = d.n, a = d.a, nmo = d.nmo();
+int class_tuple_amplitudes(ClassWork& w, DensWork& dw, const Dims& d, double shift,
+                           const double* E0, const double* eps_cv, const double* R, int P,
+                           OzWork* oz, cudaStream_t s) {
+  const int m = w.m, n = d.n;
   if (w.vsize == 0 || m == 0) return CASPT2_OK;
   const DevClass& C = w.dc;
   const long ntot = all_tuples(w);
   const long tall = ntot * n * m;
-  if (tall > dw.tall || a * a > 256) return CASPT2_EINVAL;
+  if (tall > dw.tall) return CASPT2_EINVAL;
   CASPT2_CUDA_TRY(cudaMemsetAsync(dw.T, 0, sizeof(double) * tall, s));
   CASPT2_CUDA_TRY(cudaMemsetAsync(dw.Lam, 0, sizeof(double) * tall, s));
 
@@ -580,6 +578,24 @@ int class_densities(ClassWork& w, DensWork& dw, const Dims& d, int scheme, doubl
     k_tuple_scatter<<<launch_blocks((long)K.msec * ncol), 256, 0, s>>>(
         dw.tmp, dw.tmp + dw.secmax, C, w.ed, n, m, K.sec, K.Lsel, K.ntup, K.msec, dw.T, dw.Lam);
     CASPT2_CUDA_TRY(cudaGetLastError());
+  }
+  return CASPT2_OK;
+}
+
+int class_densities(ClassWork& w, DensWork& dw, const Dims& d, int scheme, double shift,
+                    RdmPtrs rdm, const double* E0, const double* eps_cv, const double* R, int P,
+                    const double* NL, const EriBlocks& G, double* d1, double* d2, OzWork* oz,
+                    cudaStream_t s) {
+  (void)scheme;
+  const int m = w.m, n = d.n, a = d.a, nmo = d.nmo();
+  if (w.vsize == 0 || m == 0) return CASPT2_OK;
+  const DevClass& C = w.dc;
+  const long ntot = all_tuples(w);
+  const long tall = ntot * n * m;
+  if (a * a > 256) return CASPT2_EINVAL;
+  {
+    const int st = class_tuple_amplitudes(w, dw, d, shift, E0, eps_cv, R, P, oz, s);
+    if (st != CASPT2_OK) return st;
   }
   const bool pair = C.pair0 >= 0;
   const long mm = (long)m * m;
@@ -663,6 +679,32 @@ int class_densities(ClassWork& w, DensWork& dw, const Dims& d, int scheme, doubl
   }
   CASPT2_CUDA_TRY(cudaGetLastError());
   return CASPT2_OK;
+}
+
+namespace {
+// out[fam][ext...][act...] = src[tuple][L][(fam, act..., N)] for one (L, N)
+__global__ void k_gather_amp(const double* __restrict__ src, int nfam, long ntot, long A, int n,
+                             int L, int N, double* __restrict__ out) {
+  const long total = (long)nfam * ntot * A;
+  const long m = (long)nfam * A * n;
+  for (long o = blockIdx.x * (long)blockDim.x + threadIdx.x; o < total;
+       o += (long)gridDim.x * blockDim.x) {
+    const long act = o % A;
+    const long t = (o / A) % ntot;
+    const long fam = o / (A * ntot);
+    out[o] = src[(t * n + L) * m + (fam * A + act) * n + N];
+  }
+}
+}  // namespace
+
+cudaError_t gather_amplitudes(const ClassWork& w, const Dims& d, const double* src, int L, int N,
+                              double* out, cudaStream_t s) {
+  const long total = (long)w.dc.nfam * all_tuples(w) * w.A;
+  if (total == 0) return cudaSuccess;
+  ++launch_counter();
+  k_gather_amp<<<launch_blocks(total), 256, 0, s>>>(src, w.dc.nfam, all_tuples(w), w.A, d.n, L, N,
+                                                    out);
+  return cudaGetLastError();
 }
 
 }  // namespace caspt2
