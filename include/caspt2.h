@@ -162,6 +162,23 @@ int caspt2_get_core_energy(caspt2_ctx* ctx, double* ecore);
  *   times[k] is written for k < *count on input; *count = number of entries on output. */
 int caspt2_get_timings(caspt2_ctx* ctx, double* times, int* count);
 
+/* State of a context after its last calls: the last caspt2_solve's status (OK, WINTRUDER
+ * or the error it returned; ESTATE before the first solve), whether a solve and a density
+ * pass have completed, the smallest |denominator| e_ext + omega - E0_L + E_s of the last
+ * solve (Eh; below 1e-3 the solve returned WINTRUDER; 0 before a solve), the library
+ * kernels launched by the last solve, and the timings of caspt2_get_timings.
+ * Errors: EINVAL (NULL pointer). */
+#define CASPT2_REPORT_TIMES 10
+typedef struct {
+  int last_status;
+  int solved;
+  int densities_done;
+  double min_denominator;
+  long kernel_launches;
+  double times_ms[CASPT2_REPORT_TIMES];
+} caspt2_report;
+int caspt2_get_status(caspt2_ctx* ctx, caspt2_report* out);
+
 /* Correlated densities of the target state P = opt.target_state (Sec. II.D: the
  * derivatives of the Lagrangian L = sum_LL' R_LP R_L'P Heff_LL' + sum <lambda|..> at the
  * converged amplitudes and lambda), computed on the device for the classes in

@@ -80,6 +80,7 @@ def lib():
         L.caspt2_densities.argtypes = [P, C.c_uint, P]
         L.caspt2_get_densities.argtypes = [P, C.c_int, P, P, P]
         L.caspt2_gradient.argtypes = [P, C.c_int, P, P, P]
+        L.caspt2_get_status.argtypes = [P, C.POINTER(Report)]
         L.caspt2_amplitude_size.argtypes = [P, C.c_int]
         L.caspt2_amplitude_size.restype = C.c_long
         L.caspt2_get_amplitudes.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int, P, P]
@@ -94,6 +95,13 @@ def lib():
         L.caspt2_strerror.restype = C.c_char_p
         _lib = L
     return _lib
+
+
+class Report(C.Structure):
+    """caspt2_report (caspt2_get_status)."""
+    _fields_ = [("last_status", C.c_int), ("solved", C.c_int), ("densities_done", C.c_int),
+                ("min_denominator", C.c_double), ("kernel_launches", C.c_long),
+                ("times_ms", C.c_double * 10)]
 
 
 class CASPT2Error(RuntimeError):
@@ -254,6 +262,15 @@ class Context:
         """compute_densities + get_densities: host copies (d1, d2, gdf), each symmetrised."""
         self.compute_densities(class_mask, stream)
         return self.get_densities()
+
+    def status(self) -> dict:
+        """caspt2_get_status: last solve status, flags, smallest |denominator|, launches,
+        timings."""
+        r = Report()
+        _check(lib().caspt2_get_status(self._h, C.byref(r)), "caspt2_get_status")
+        return {"last_status": r.last_status, "solved": bool(r.solved),
+                "densities_done": bool(r.densities_done), "min_denominator": r.min_denominator,
+                "kernel_launches": r.kernel_launches, "times_ms": list(r.times_ms)}
 
     def amplitude_size(self, cls: int) -> int:
         """caspt2_amplitude_size: elements of T_LN (or lambda_LN) of class index cls."""

@@ -33,6 +33,7 @@ struct caspt2_ctx {
   bool have_inputs = false;
   bool have_rdm3 = false, have_rdm4 = false;
   bool solved = false;
+  int last_status = CASPT2_ESTATE;   // of the last caspt2_solve (ESTATE before the first)
   std::vector<void*> allocs;
 
   // inputs (device copies)
@@ -362,7 +363,39 @@ int caspt2_set_inputs(caspt2_ctx* c, int mem, const double* fock, const double* 
   return CASPT2_OK;
 }
 
+}  // extern "C"
+
+namespace {
+int solve_impl(caspt2_ctx* c, void* stream);
+}  // namespace
+
+extern "C" {
+
 int caspt2_solve(caspt2_ctx* c, void* stream) {
+  if (!c) return CASPT2_EINVAL;
+  const int st = solve_impl(c, stream);
+  c->last_status = st;
+  return st;
+}
+
+int caspt2_get_status(caspt2_ctx* c, caspt2_report* out) {
+  if (!c || !out) return CASPT2_EINVAL;
+  std::memset(out, 0, sizeof(*out));
+  out->last_status = c->last_status;
+  out->solved = c->solved ? 1 : 0;
+  out->densities_done = c->dens_done ? 1 : 0;
+  out->min_denominator = c->solved ? c->hMinDenom : 0.0;
+  out->kernel_launches = c->launches;
+  const int k = kNumTimes < CASPT2_REPORT_TIMES ? kNumTimes : CASPT2_REPORT_TIMES;
+  for (int i = 0; i < k; ++i) out->times_ms[i] = c->times[i];
+  return CASPT2_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+int solve_impl(caspt2_ctx* c, void* stream) {
   if (!c) return CASPT2_EINVAL;
   if (!c->have_inputs) return CASPT2_ESTATE;
   CASPT2_CUDA_TRY(cudaSetDevice(c->device));
@@ -501,6 +534,10 @@ int caspt2_solve(caspt2_ctx* c, void* stream) {
   if (c->hMinDenom < 1e-3) return CASPT2_WINTRUDER;
   return CASPT2_OK;
 }
+
+}  // namespace
+
+extern "C" {
 
 int caspt2_get_energies(caspt2_ctx* c, double* U, double* E0, double* Href, double* Heff,
                         double* Ems, double* R) {

@@ -45,6 +45,16 @@ def test_host_only_entry_points(so):
     assert so.caspt2_densities(None, 0xFF, None) == -1
     so.caspt2_get_densities.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
     assert so.caspt2_get_densities(None, 0, None, None, None) == -1
+    so.caspt2_get_status.argtypes = [C.c_void_p, C.c_void_p]
+    assert so.caspt2_get_status(None, None) == -1
+    so.caspt2_solve.argtypes = [C.c_void_p, C.c_void_p]
+    assert so.caspt2_solve(None, None) == -1
+    so.caspt2_amplitude_size.argtypes = [C.c_void_p, C.c_int]
+    so.caspt2_amplitude_size.restype = C.c_long
+    assert so.caspt2_amplitude_size(None, 0) == -1
+    for fn in (so.caspt2_get_amplitudes, so.caspt2_get_lambda):
+        fn.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p]
+        assert fn(None, 0, 0, 0, 0, None, None) == -1
 
 
 def test_server_entry_points_reject_null(so):

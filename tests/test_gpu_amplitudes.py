@@ -85,3 +85,23 @@ def test_amplitudes_and_lambda_vs_oracle(cp, name, opt):
             ctx.amplitudes(7, 0, 0)                      # class H amplitudes are never formed
     finally:
         ctx.close()
+
+
+def test_status_report(cp):
+    """caspt2_get_status after create, solve and densities."""
+    p = make_problem(**CASES["c4a4v20x84n2"])
+    ctx = cp.Context(p.nclosed, p.nact, p.nvirt, p.naux, p.nstate, xms=1, scheme=0, shift=0.2,
+                     target_state=0)
+    try:
+        r0 = ctx.status()
+        assert r0["last_status"] == cp.ESTATE and not r0["solved"]
+        ctx.set_inputs(*cp.problem_inputs(p))
+        st = ctx.solve()
+        r1 = ctx.status()
+        assert r1["last_status"] == st and r1["solved"] and not r1["densities_done"]
+        assert r1["min_denominator"] > 0.0 and r1["kernel_launches"] > 0
+        assert (st == 1) == (r1["min_denominator"] < 1e-3)
+        ctx.densities()
+        assert ctx.status()["densities_done"]
+    finally:
+        ctx.close()
