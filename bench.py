@@ -46,7 +46,7 @@ CLASSH_SPLIT_TRAFFIC_BYTES = 45.892096e6 + 85.852416e6
 
 
 def measured_peak(key, fallback):
-    """(peak, kind): a peak from MEASURED_PEAKS.json (driver-written), else the stated
+    """(peak, kind): a peak from MEASURED_PEAKS.json (measured on this machine), else the stated
     fallback (one earlier GB300 measurement)."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
