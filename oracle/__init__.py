@@ -9,4 +9,10 @@ inputs of the `synth` package.
                   explicit excitation operators, explicit overlap / zeroth-order
                   Hamiltonian matrices, explicit expectation values.
   mp2_closed_form textbook closed-shell MP2 (nact = 0 special case), used as a pin.
+  o2_rdm, o2_classes, wick
+                  RDM / orbital-tensor form for sizes the brute force cannot reach
+                  (class H pair form; classes A-G from a spin-free normal-ordering
+                  engine), pinned against o1_determinant.
+  o2_offdiag      off-diagonal blocks of the density d-bar(2) (class-to-class couplings
+                  through E_xy), pinned against o1_determinant.
 """

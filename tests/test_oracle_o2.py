@@ -213,3 +213,21 @@ def test_density_identities(xms, scheme, shift):
             assert abs(tr[k] - OCC_CHANGE[cls][k] * NL.sum()) < 1e-12, (cls, k)
         src = r @ parts[cls][0] @ r + np.trace(lv)
         assert abs(np.sum(d1 * h) + 0.5 * np.sum(G * p.B) - src) < 1e-12 * max(1.0, abs(src)), cls
+
+
+@pytest.mark.parametrize("xms,scheme,shift", [(True, "msmr", 0.2), (False, "msmr", 0.0),
+                                              (True, "sssr", 0.1)])
+def test_offdiag_dbar2_matches_o1(cprob, xms, scheme, shift):
+    """The closed-active, active-virtual and closed-virtual blocks of dbar2 (Sec. II.D), which
+    couple different classes through E_xy, equal O1's <Psi_lambda_L|E_xy|Psi1_L> summed
+    over L, block by block."""
+    from oracle.o2_offdiag import offdiag_dbar2
+    st, R = _o2_state(cprob, xms, scheme, shift)
+    r = o1.solve_problem(cprob, xms=xms, scheme=scheme, shift=shift)
+    got = offdiag_dbar2(cprob, st, shift, scheme, R, 0)
+    c, a = cprob.nclosed, cprob.nact
+    off = np.ones((cprob.nmo, cprob.nmo))
+    off[:c, :c] = off[c:c + a, c:c + a] = off[c + a:, c + a:] = 0.0
+    scale = max(1.0, float(np.abs(r.dbar2 * off).max()))
+    assert np.abs((got - r.dbar2) * off).max() <= 1e-11 * scale
+    assert np.abs(got * (1.0 - off)).max() == 0.0
