@@ -38,6 +38,8 @@ extern "C" {
 #define CASPT2_ESTATE      (-7)   /* call out of order (e.g. solve before inputs) */
 #define CASPT2_ESCRATCH    (-8)   /* too large for the fixed scratch of caspt2_classH_noalloc */
 #define CASPT2_WINTRUDER     1    /* smallest |denominator| below 1e-3 Eh          */
+#define CASPT2_WDEGEN        2    /* XMS: two zeroth-order energies closer than    */
+                                  /* options.degen_thresh (U not unique there)     */
 
 /* memory kinds for caspt2_set_inputs */
 #define CASPT2_MEM_HOST      0
@@ -77,10 +79,15 @@ typedef struct {
     int    slices;       /* BF16 slices per operand for CASPT2_BF16X, 1..7 (default 7: every   */
                          /* product within FP64 rounding of the plain form; 5: ~2e-12 of the   */
                          /* row x column scale)                                                */
+    double degen_thresh; /* XMS: |E0_M - E0_N| (Eh) below which the pair counts as degenerate */
+                         /* (default 1e-8).  The rotation U is then fixed only up to a        */
+                         /* rotation inside the degenerate subspace, which leaves every energy */
+                         /* unchanged (Sec. II.D: the XMS response of such a pair is taken as  */
+                         /* zero); the solve returns WDEGEN as a warning.                      */
 } caspt2_options;
 
 /* Fill *opt with defaults: XMS, MS-MR, shift 0, 1e-9, enuc 0, target 0, all classes,
- * plain FP64, 7 slices. */
+ * plain FP64, 7 slices, degen_thresh 1e-8. */
 void caspt2_default_options(caspt2_options* opt);
 
 /* Create a context for the given sizes.  Allocates its device buffers
@@ -90,11 +97,18 @@ int caspt2_create(caspt2_ctx** ctx, const caspt2_dims* dims, const caspt2_option
 /* Copy the inputs into the context (Sec. II.A, II.B: reference states through their
  * RDMs, the state-averaged Fock matrix f and the DF factors defining (xy|zw)).
  *   mem   CASPT2_MEM_HOST or CASPT2_MEM_DEVICE (pointers on the context's device)
- *   fock  [nmo][nmo] symmetric SA Fock matrix f = h + g(d_sa)
+ *   fock  [nmo][nmo] symmetric SA Fock matrix f = h + g(d_sa), block diagonal: the
+ *         closed-active, active-virtual and closed-virtual blocks are zero and the closed
+ *         and virtual blocks are diagonal (canonical orbitals).  The classes then decouple
+ *         and each is solved exactly in one step (Eq. ampeq); a Fock matrix with inter-class
+ *         coupling needs the iterative solve of Sec. II.B, which this library does not do,
+ *         so such an f is refused rather than solved with its coupling dropped.
  *   dfB   [naux][nmo][nmo] DF factors, (xy|zw) = sum_P B[P][x][y] B[P][z][w], symmetric in x,y
  *   rdm1  [n][n][a][a], rdm2 [n][n][a^4]   (required)
  *   rdm3, rdm4 may be NULL while only classes that do not need them are enabled.
- * Errors: EINVAL (NULL required pointer), ECUDA. */
+ * Errors: EINVAL (NULL required pointer; f not symmetric, or an entry of a coupling block
+ * or an off-diagonal closed/virtual entry above 1e-10 x max(1, max|f|) in magnitude — the
+ * context then holds no inputs), ECUDA. */
 int caspt2_set_inputs(caspt2_ctx* ctx, int mem, const double* fock, const double* dfB,
                       const double* rdm1, const double* rdm2, const double* rdm3,
                       const double* rdm4);
@@ -103,7 +117,9 @@ int caspt2_set_inputs(caspt2_ctx* ctx, int mem, const double* fock, const double
  * SA density and core Fock (Sec. II.B), XMS rotation and H^ref (Sec. II.A),
  * first-order amplitudes of the enabled classes (Eq. ampeq), the effective
  * Hamiltonian and its eigenpairs (Sec. II.B).  Synchronises the stream before
- * returning.  Returns WINTRUDER if a denominator fell below 1e-3 Eh.
+ * returning.  Returns WINTRUDER if a denominator fell below 1e-3 Eh, else WDEGEN if XMS
+ * met two zeroth-order energies closer than opt.degen_thresh (both are reported in
+ * caspt2_get_status's warnings).
  * Errors: ESTATE (no inputs), ENOTCONV, ENAN, ECUDA. */
 int caspt2_solve(caspt2_ctx* ctx, void* cuda_stream);
 
@@ -169,6 +185,8 @@ int caspt2_get_timings(caspt2_ctx* ctx, double* times, int* count);
  * kernels launched by the last solve, and the timings of caspt2_get_timings.
  * Errors: EINVAL (NULL pointer). */
 #define CASPT2_REPORT_TIMES 10
+#define CASPT2_WARN_INTRUDER 1u   /* warnings bit: WINTRUDER condition met */
+#define CASPT2_WARN_DEGEN    2u   /* warnings bit: WDEGEN condition met    */
 typedef struct {
   int last_status;
   int solved;
@@ -176,6 +194,9 @@ typedef struct {
   double min_denominator;
   long kernel_launches;
   double times_ms[CASPT2_REPORT_TIMES];
+  unsigned warnings;      /* CASPT2_WARN_* bits of the last solve                        */
+  double min_e0_gap;      /* smallest |E0_M - E0_N| over M != N of the last solve (Eh;     */
+                          /* 0 for one state)                                             */
 } caspt2_report;
 int caspt2_get_status(caspt2_ctx* ctx, caspt2_report* out);
 
@@ -201,11 +222,14 @@ int caspt2_get_status(caspt2_ctx* ctx, caspt2_report* out);
  * < 0, nact > 16), ESTATE (no solve), ENOMEM, ECUDA. */
 int caspt2_densities(caspt2_ctx* ctx, unsigned class_mask, void* cuda_stream);
 
-/* Copy the densities of the last caspt2_densities call: d1 and d2 [nmo][nmo], gdf
+/* Copy the densities of the last caspt2_densities call: d1 and d2 [nmo][nmo], NL [n], gdf
  * [naux][nmo][nmo] (the layout of the dfB input), to host (mem = CASPT2_MEM_HOST) or
  * device (CASPT2_MEM_DEVICE) buffers owned by the caller.  Any pointer may be NULL.
+ *   NL[L] = sum_MN <M~|lambda_LM^dag T_LN|N~> over all eight classes (Sec. II.D, the
+ *           normalisation term that multiplies <L~|E_xy|L~> in d(2)).
  * Errors: EINVAL, ESTATE (no densities computed since the last solve). */
-int caspt2_get_densities(caspt2_ctx* ctx, int mem, double* d1, double* d2, double* gdf);
+int caspt2_get_densities(caspt2_ctx* ctx, int mem, double* d1, double* d2, double* NL,
+                         double* gdf);
 
 /* Gradient of the target state's MS energy E_P (opt.target_state) with respect to the
  * library's inputs, the Fock matrix f and the DF factors B, with the reference RDMs held
@@ -215,7 +239,11 @@ int caspt2_get_densities(caspt2_ctx* ctx, int mem, double* d1, double* d2, doubl
  *                      reads (closed diagonal, active block, virtual diagonal);
  *   grad_B[Q][p][q]  = dE_P/dB_Qpq at fixed f;
  * both symmetrised, in the layouts of the inputs, to host or device buffers (mem).  MS
- * only (opt.xms = 0): the XMS rotation response is not formed.  Recomputes the densities
+ * only (opt.xms = 0): the XMS rotation response is not formed.  Because the solve takes a
+ * block-diagonal f (see caspt2_set_inputs), grad_f is the derivative along the blocks
+ * it reads; its closed-active, active-virtual and closed-virtual entries and the
+ * off-diagonal closed/virtual entries are left zero (their derivative needs the
+ * inter-class coupling of Sec. II.D's d-bar(2), not built).  Recomputes the densities
  * of all solved classes.  Errors: EINVAL (xms, target_state < 0), ESTATE (no solve),
  * ENOMEM, ECUDA. */
 int caspt2_gradient(caspt2_ctx* ctx, int mem, double* grad_f, double* grad_B, void* cuda_stream);
@@ -250,7 +278,9 @@ const char* caspt2_strerror(int status);
  * array: calls that overlap on the GPU (other threads or streams) race and must be
  * serialised by the caller.  Returns ESCRATCH when the problem needs more scratch than
  * the array holds (about 4 MiB: n <= 16 and nclosed + nvirt up to ~2e5 fit), EINVAL for
- * bad sizes or NULL pointers, ENOTCONV / ENAN / ECUDA, or WINTRUDER as caspt2_solve. */
+ * bad sizes, NULL pointers or an f that is not block diagonal (as caspt2_set_inputs; f is
+ * read back to host memory for that check), ENOTCONV / ENAN / ECUDA, or WINTRUDER as
+ * caspt2_solve. */
 int caspt2_classH_noalloc(const caspt2_dims* dims, const caspt2_options* opt,
                           const double* fock, const double* dfB, const double* rdm1,
                           double* e, double* norm, void* cuda_stream);

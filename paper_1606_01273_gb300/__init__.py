@@ -17,7 +17,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIBPATH = os.path.join(HERE, "libcaspt2.so")
 
 OK, EINVAL, ENOMEM, ENOTCONV, ENAN, ETIMEOUT, ECUDA, ESTATE, ESCRATCH = 0, -1, -2, -3, -4, -5, -6, -7, -8
-WINTRUDER = 1
+WINTRUDER, WDEGEN = 1, 2
+WARN_INTRUDER, WARN_DEGEN = 1, 2
 MEM_HOST, MEM_DEVICE = 0, 1
 MSMR, SSSR = 0, 1
 FP64, BF16X = 0, 1
@@ -32,7 +33,8 @@ class Dims(C.Structure):
 class Options(C.Structure):
     _fields_ = [("xms", C.c_int), ("scheme", C.c_int), ("shift", C.c_double),
                 ("ovl_thresh", C.c_double), ("enuc", C.c_double), ("target_state", C.c_int),
-                ("class_mask", C.c_uint), ("precision", C.c_int), ("slices", C.c_int)]
+                ("class_mask", C.c_uint), ("precision", C.c_int), ("slices", C.c_int),
+                ("degen_thresh", C.c_double)]
 
 
 class Request(C.Structure):
@@ -78,7 +80,7 @@ def lib():
         L.caspt2_destroy.argtypes = [P]
         L.caspt2_destroy.restype = None
         L.caspt2_densities.argtypes = [P, C.c_uint, P]
-        L.caspt2_get_densities.argtypes = [P, C.c_int, P, P, P]
+        L.caspt2_get_densities.argtypes = [P, C.c_int, P, P, P, P]
         L.caspt2_gradient.argtypes = [P, C.c_int, P, P, P]
         L.caspt2_get_status.argtypes = [P, C.POINTER(Report)]
         L.caspt2_amplitude_size.argtypes = [P, C.c_int]
@@ -101,7 +103,8 @@ class Report(C.Structure):
     """caspt2_report (caspt2_get_status)."""
     _fields_ = [("last_status", C.c_int), ("solved", C.c_int), ("densities_done", C.c_int),
                 ("min_denominator", C.c_double), ("kernel_launches", C.c_long),
-                ("times_ms", C.c_double * 10)]
+                ("times_ms", C.c_double * 10), ("warnings", C.c_uint),
+                ("min_e0_gap", C.c_double)]
 
 
 class CASPT2Error(RuntimeError):
@@ -236,16 +239,19 @@ class Context:
         s = C.c_void_p(stream) if stream is not None else None
         _check(lib().caspt2_densities(self._h, mask, s), "caspt2_densities")
 
-    def get_densities(self, with_gdf: bool = True):
-        """Host copies (d1, d2, gdf) of the last densities (gdf None if not requested)."""
+    def get_densities(self, with_gdf: bool = True, with_nl: bool = False):
+        """Host copies (d1, d2, gdf) of the last densities (gdf None if not requested);
+        with_nl: (d1, d2, gdf, NL), NL[L] summed over the classes."""
         nmo = self.dims.nclosed + self.dims.nact + self.dims.nvirt
         d1, d2 = np.zeros((nmo, nmo)), np.zeros((nmo, nmo))
+        nl = np.zeros(self.n)
         gdf = np.zeros((self.dims.naux, nmo, nmo)) if with_gdf else None
         gp = C.c_void_p(gdf.ctypes.data) if with_gdf else None
         _check(lib().caspt2_get_densities(self._h, MEM_HOST, C.c_void_p(d1.ctypes.data),
-                                          C.c_void_p(d2.ctypes.data), gp),
+                                          C.c_void_p(d2.ctypes.data),
+                                          C.c_void_p(nl.ctypes.data), gp),
                "caspt2_get_densities")
-        return d1, d2, gdf
+        return (d1, d2, gdf, nl) if with_nl else (d1, d2, gdf)
 
     def gradient(self, stream=None):
         """caspt2_gradient: host copies (dE/df [nmo][nmo], dE/dB [naux][nmo][nmo]) of the
@@ -270,7 +276,8 @@ class Context:
         _check(lib().caspt2_get_status(self._h, C.byref(r)), "caspt2_get_status")
         return {"last_status": r.last_status, "solved": bool(r.solved),
                 "densities_done": bool(r.densities_done), "min_denominator": r.min_denominator,
-                "kernel_launches": r.kernel_launches, "times_ms": list(r.times_ms)}
+                "kernel_launches": r.kernel_launches, "times_ms": list(r.times_ms),
+                "warnings": int(r.warnings), "min_e0_gap": r.min_e0_gap}
 
     def amplitude_size(self, cls: int) -> int:
         """caspt2_amplitude_size: elements of T_LN (or lambda_LN) of class index cls."""

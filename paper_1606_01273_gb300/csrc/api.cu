@@ -34,6 +34,8 @@ struct caspt2_ctx {
   bool have_rdm3 = false, have_rdm4 = false;
   bool solved = false;
   int last_status = CASPT2_ESTATE;   // of the last caspt2_solve (ESTATE before the first)
+  unsigned warnings = 0;             // CASPT2_WARN_* of the last solve
+  double min_e0_gap = 0.0;           // smallest |E0_M - E0_N| of the last solve
   std::vector<void*> allocs;
 
   // inputs (device copies)
@@ -97,6 +99,31 @@ struct caspt2_ctx {
   }
 };
 
+namespace caspt2 {
+
+int check_block_diagonal_fock(const double* f, const Dims& d) {
+  const int nmo = d.nmo();
+  double fmax = 0.0;
+  for (long k = 0; k < (long)nmo * nmo; ++k) {
+    if (!(f[k] == f[k]) || std::fabs(f[k]) > 1e300) return CASPT2_ENAN;
+    fmax = std::max(fmax, std::fabs(f[k]));
+  }
+  const double tol = 1e-10 * std::max(1.0, fmax);
+  auto space = [&](int p) { return p < d.c ? 0 : (p < d.c + d.a ? 1 : 2); };
+  for (int p = 0; p < nmo; ++p)
+    for (int q = 0; q < nmo; ++q) {
+      const double x = f[(long)p * nmo + q];
+      if (std::fabs(x - f[(long)q * nmo + p]) > tol) return CASPT2_EINVAL;
+      if (p == q) continue;
+      const int sp = space(p), sq = space(q);
+      // coupling blocks, and off-diagonal entries of the closed and virtual blocks
+      if ((sp != sq || sp != 1) && std::fabs(x) > tol) return CASPT2_EINVAL;
+    }
+  return CASPT2_OK;
+}
+
+}  // namespace caspt2
+
 extern "C" {
 
 void caspt2_default_options(caspt2_options* o) {
@@ -110,6 +137,7 @@ void caspt2_default_options(caspt2_options* o) {
   o->class_mask = caspt2_supported_classes();
   o->precision = CASPT2_FP64;
   o->slices = 7;
+  o->degen_thresh = 1e-8;
 }
 
 unsigned caspt2_supported_classes(void) { return (1u << CASPT2_NCLASS) - 1u; }
@@ -127,6 +155,8 @@ const char* caspt2_strerror(int st) {
     case CASPT2_ESCRATCH:
       return "problem exceeds the fixed 4 MiB device scratch of caspt2_classH_noalloc";
     case CASPT2_WINTRUDER: return "warning: a denominator is below 1e-3 Eh (intruder state)";
+    case CASPT2_WDEGEN:
+      return "warning: two XMS zeroth-order energies are degenerate (rotation not unique there)";
     default: return "unknown status";
   }
 }
@@ -166,6 +196,7 @@ int caspt2_create(caspt2_ctx** out, const caspt2_dims* dims, const caspt2_option
   if (o.target_state >= q.nstate) return CASPT2_EINVAL;
   if (o.precision != CASPT2_FP64 && o.precision != CASPT2_BF16X) return CASPT2_EINVAL;
   if (o.precision == CASPT2_BF16X && (o.slices < 1 || o.slices > 7)) return CASPT2_EINVAL;
+  if (!(o.degen_thresh >= 0.0)) return CASPT2_EINVAL;
 
   caspt2_ctx* c = new (std::nothrow) caspt2_ctx();
   if (!c) return CASPT2_ENOMEM;
@@ -347,6 +378,18 @@ int caspt2_set_inputs(caspt2_ctx* c, int mem, const double* fock, const double* 
   const size_t nmo = d.nmo(), n = d.n, a2 = (size_t)d.a * d.a;
   const cudaMemcpyKind k = mem == CASPT2_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
   CASPT2_CUDA_TRY(cudaSetDevice(c->device));
+  c->have_inputs = false;
+  c->solved = false;
+  c->dens_done = false;
+  {
+    // the solve reads only the blocks of a block-diagonal f: refuse any other f
+    std::vector<double> hf(nmo * nmo);
+    CASPT2_CUDA_TRY(cudaMemcpy(hf.data(), fock, sizeof(double) * nmo * nmo,
+                               mem == CASPT2_MEM_HOST ? cudaMemcpyHostToHost
+                                                      : cudaMemcpyDeviceToHost));
+    const int st = check_block_diagonal_fock(hf.data(), d);
+    if (st != CASPT2_OK) return st;
+  }
   CASPT2_CUDA_TRY(cudaMemcpy(c->f, fock, sizeof(double) * nmo * nmo, k));
   CASPT2_CUDA_TRY(cudaMemcpy(c->B, dfB, sizeof(double) * d.X * nmo * nmo, k));
   CASPT2_CUDA_TRY(cudaMemcpy(c->rdm1, rdm1, sizeof(double) * n * n * a2, k));
@@ -373,6 +416,8 @@ extern "C" {
 
 int caspt2_solve(caspt2_ctx* c, void* stream) {
   if (!c) return CASPT2_EINVAL;
+  c->warnings = 0;
+  c->min_e0_gap = 0.0;
   const int st = solve_impl(c, stream);
   c->last_status = st;
   return st;
@@ -388,6 +433,8 @@ int caspt2_get_status(caspt2_ctx* c, caspt2_report* out) {
   out->kernel_launches = c->launches;
   const int k = kNumTimes < CASPT2_REPORT_TIMES ? kNumTimes : CASPT2_REPORT_TIMES;
   for (int i = 0; i < k; ++i) out->times_ms[i] = c->times[i];
+  out->warnings = c->solved ? c->warnings : 0u;
+  out->min_e0_gap = c->solved ? c->min_e0_gap : 0.0;
   return CASPT2_OK;
 }
 
@@ -531,7 +578,21 @@ int solve_impl(caspt2_ctx* c, void* stream) {
   if (hst != 0) return hst;
   for (double x : c->hEms)
     if (!(x == x) || x > 1e300 || x < -1e300) return CASPT2_ENAN;
-  if (c->hMinDenom < 1e-3) return CASPT2_WINTRUDER;
+  // warnings: intruder denominators; XMS zeroth-order energies that are degenerate
+  // (the rotation inside such a pair is arbitrary; energies do not depend on it)
+  double gap = 0.0;
+  bool first = true;
+  for (int M = 0; M < n; ++M)
+    for (int N = M + 1; N < n; ++N) {
+      const double g = std::fabs(c->hE0[M] - c->hE0[N]);
+      gap = first ? g : std::min(gap, g);
+      first = false;
+    }
+  c->min_e0_gap = gap;
+  if (c->hMinDenom < 1e-3) c->warnings |= CASPT2_WARN_INTRUDER;
+  if (o.xms && n > 1 && gap < o.degen_thresh) c->warnings |= CASPT2_WARN_DEGEN;
+  if (c->warnings & CASPT2_WARN_INTRUDER) return CASPT2_WINTRUDER;
+  if (c->warnings & CASPT2_WARN_DEGEN) return CASPT2_WDEGEN;
   return CASPT2_OK;
 }
 
@@ -788,7 +849,8 @@ int caspt2_get_lambda(caspt2_ctx* c, int cls, int L, int N, int mem, double* out
   return get_class_vector(c, cls, L, N, mem, out, true, cuda_stream);
 }
 
-int caspt2_get_densities(caspt2_ctx* c, int mem, double* d1, double* d2, double* gdf) {
+int caspt2_get_densities(caspt2_ctx* c, int mem, double* d1, double* d2, double* NL,
+                         double* gdf) {
   if (!c) return CASPT2_EINVAL;
   if (mem != CASPT2_MEM_HOST && mem != CASPT2_MEM_DEVICE) return CASPT2_EINVAL;
   if (!c->dens_done) return CASPT2_ESTATE;
@@ -797,6 +859,17 @@ int caspt2_get_densities(caspt2_ctx* c, int mem, double* d1, double* d2, double*
   const size_t nmo = c->d.nmo();
   if (d1) CASPT2_CUDA_TRY(cudaMemcpy(d1, c->dd1, sizeof(double) * nmo * nmo, k));
   if (d2) CASPT2_CUDA_TRY(cudaMemcpy(d2, c->dd2, sizeof(double) * nmo * nmo, k));
+  if (NL) {
+    // N_L summed over the classes in a fixed order (per-class shares of the last solve)
+    const int n = c->d.n;
+    std::vector<double> tot(n, 0.0);
+    for (int cls = 0; cls < CASPT2_NCLASS; ++cls)
+      if (c->opt.class_mask >> cls & 1u)
+        for (int L = 0; L < n; ++L) tot[L] += c->hLamNL[(size_t)cls * n + L];
+    CASPT2_CUDA_TRY(cudaMemcpy(NL, tot.data(), sizeof(double) * n,
+                               mem == CASPT2_MEM_HOST ? cudaMemcpyHostToHost
+                                                      : cudaMemcpyHostToDevice));
+  }
   if (gdf) CASPT2_CUDA_TRY(cudaMemcpy(gdf, c->dgdf, sizeof(double) * c->d.X * nmo * nmo, k));
   return CASPT2_OK;
 }

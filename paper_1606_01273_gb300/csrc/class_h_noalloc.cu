@@ -24,6 +24,7 @@
 // shared memory, so the scratch needed is bounded by the grid size rather than by
 // the problem size.
 #include <mutex>
+#include <vector>
 
 #include "kernels.cuh"
 
@@ -74,6 +75,20 @@ Layout layout(const Dims& d, int nshift, int grid) {
   return L;
 }
 
+// Pair index p -> (x, y), x <= y < R, enumerated row-major by x (64-bit, closed form
+// with an exact integer correction).
+__device__ __forceinline__ void tri_pair(long p, int R, int& x, int& y) {
+  const double b = 2.0 * R + 1.0;
+  long xx = (long)floor(0.5 * (b - sqrt(fmax(b * b - 8.0 * (double)p, 0.0))));
+  if (xx < 0) xx = 0;
+  if (xx > R - 1) xx = R - 1;
+  auto start = [&](long q) { return q * R - q * (q - 1) / 2; };
+  while (xx > 0 && start(xx) > p) --xx;
+  while (xx + 1 < R && start(xx + 1) <= p) ++xx;
+  x = (int)xx;
+  y = (int)(p - start(xx) + xx);
+}
+
 __global__ void k_na_prepare(const double* __restrict__ f, int nmo, int c, int a, int v,
                              double* eps, double* mindenom, int* status) {
   int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -109,14 +124,15 @@ k_na_classH(const double* __restrict__ B, const double* __restrict__ eps,
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const long strideP = (long)nmo * nmo;
 
+  const long ntp = (long)ntile * (ntile + 1) / 2;   // tile pairs ta <= tb
   for (long task = blockIdx.x; task < ntask; task += gridDim.x) {
-    long bid = task;
-    const int tb = bid % ntile; bid /= ntile;
-    const int ta = bid % ntile; bid /= ntile;
-    int pair = (int)bid, i = 0;
-    while (pair >= c - i) { pair -= c - i; ++i; }
-    const int j = i + pair;
+    int ta, tb, i, j;
+    tri_pair(task % ntp, ntile, ta, tb);
+    tri_pair(task / ntp, c, i, j);
     const bool same = (i == j);
+    // (a, b) and (b, a) give equal terms (K(a,b) of the pair ij is K'(b,a)), so a
+    // tile pair ta < tb stands for both orders
+    const double wt = (ta == tb) ? 1.0 : 2.0;
     const int a0 = ta * kNaT, b0 = tb * kNaT;
     const double* bi = B + (long)i * nmo + vo;
     const double* bj = B + (long)j * nmo + vo;
@@ -180,7 +196,7 @@ k_na_classH(const double* __restrict__ B, const double* __restrict__ eps,
         const double k2 = same ? k1 : t2[ii][jj];
         double nm = k1 * (2.0 * k1 - k2);
         if (!same) nm += k2 * (2.0 * k2 - k1);
-        num[ii * 4 + jj] = ok ? nm : 0.0;
+        num[ii * 4 + jj] = ok ? wt * nm : 0.0;
         d0[ii * 4 + jj] = ok ? (sEa[la] + sEb[lb] - ei - ej) : 1.0;
       }
     double dmin = 1e300;
@@ -276,6 +292,16 @@ extern "C" int caspt2_classH_noalloc(const caspt2_dims* dims, const caspt2_optio
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   const int n = d.n, nmo = d.nmo();
   int* status = reinterpret_cast<int*>(s0 + L.status);
+  {
+    // the class-H pieces use only the diagonal of f's closed and virtual blocks and its
+    // active block: refuse an f with inter-class coupling (host copy, no device memory)
+    std::vector<double> hf((size_t)nmo * nmo);
+    CASPT2_CUDA_TRY(cudaMemcpyAsync(hf.data(), fock, sizeof(double) * hf.size(),
+                                    cudaMemcpyDeviceToHost, s));
+    CASPT2_CUDA_TRY(cudaStreamSynchronize(s));
+    st = check_block_diagonal_fock(hf.data(), d);
+    if (st != CASPT2_OK) return st;
+  }
 
   k_na_prepare<<<(d.c + d.v + 127) / 128 + 1, 128, 0, s>>>(fock, nmo, d.c, d.a, d.v, s0 + L.eps,
                                                          s0 + L.mindenom, status);
@@ -291,14 +317,16 @@ extern "C" int caspt2_classH_noalloc(const caspt2_dims* dims, const caspt2_optio
   if (d.c == 0 || d.v == 0) {
     CASPT2_CUDA_TRY(cudaMemsetAsync(e, 0, sizeof(double) * n * n, s));
     CASPT2_CUDA_TRY(cudaMemsetAsync(norm, 0, sizeof(double) * n, s));
+    int hst0 = 0;   // the XMS eigensolve may have set ENOTCONV or ENAN
+    CASPT2_CUDA_TRY(cudaMemcpyAsync(&hst0, status, sizeof(int), cudaMemcpyDeviceToHost, s));
     CASPT2_CUDA_TRY(cudaStreamSynchronize(s));
-    return CASPT2_OK;
+    return hst0;
   }
   CASPT2_CUDA_TRY(launch_sym_eig(s0 + L.Ftil, n, s0 + L.W, s0 + L.omega, 0, status, s));
   k_na_shifts<<<1, kNaMaxShift, 0, s>>>(s0 + L.omega, s0 + L.E0, opt->shift, n, opt->scheme,
                                        s0 + L.shifts);
   const int ntile = (d.v + kNaT - 1) / kNaT;
-  const long ntask = (long)d.c * (d.c + 1) / 2 * ntile * ntile;
+  const long ntask = (long)d.c * (d.c + 1) / 2 * ((long)ntile * (ntile + 1) / 2);
   const int grid = (int)(ntask < kNaGrid ? ntask : kNaGrid);
   k_na_classH<<<grid, kNaThreads, 0, s>>>(dfB, s0 + L.eps, s0 + L.shifts, nshift, d.c, d.v, d.X,
                                          nmo, d.c + d.a, ntile, ntask, s0 + L.partial);

@@ -9,6 +9,12 @@ struct Dims {
   __host__ __device__ int nmo() const { return c + a + v; }
 };
 
+// Host check of the Fock matrix the solve accepts (api.cu): symmetric, with zero
+// closed-active, active-virtual and closed-virtual blocks and diagonal closed and
+// virtual blocks, each to 1e-10 x max(1, max|f|).  f is a host copy [nmo][nmo].
+// Returns CASPT2_OK, CASPT2_EINVAL (coupling found) or CASPT2_ENAN.
+int check_block_diagonal_fock(const double* f, const Dims& d);
+
 // ---- setup (setup.cu) --------------------------------------------------------
 // d_act = (1/n) sum_N rdm1[N][N]                         (Sec. II.B, d^(0)sa)
 cudaError_t launch_dsa(const double* rdm1, const Dims& d, double* dact, cudaStream_t s);

@@ -108,7 +108,8 @@ void run_request(Request& r, cudaStream_t st) {
         r.d1.assign(nmo * nmo, 0.0);
         r.d2.assign(nmo * nmo, 0.0);
         r.gdf.assign((size_t)q.dims.naux * nmo * nmo, 0.0);
-        g = caspt2_get_densities(ctx, CASPT2_MEM_HOST, r.d1.data(), r.d2.data(), r.gdf.data());
+        g = caspt2_get_densities(ctx, CASPT2_MEM_HOST, r.d1.data(), r.d2.data(), nullptr,
+                                 r.gdf.data());
       }
     }
     if (g != CASPT2_OK) s = g;

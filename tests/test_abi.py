@@ -43,8 +43,9 @@ def test_host_only_entry_points(so):
     assert so.caspt2_get_kernel_launches(None) == -1
     so.caspt2_densities.argtypes = [C.c_void_p, C.c_uint, C.c_void_p]
     assert so.caspt2_densities(None, 0xFF, None) == -1
-    so.caspt2_get_densities.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
-    assert so.caspt2_get_densities(None, 0, None, None, None) == -1
+    so.caspt2_get_densities.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                        C.c_void_p]
+    assert so.caspt2_get_densities(None, 0, None, None, None, None) == -1
     so.caspt2_get_status.argtypes = [C.c_void_p, C.c_void_p]
     assert so.caspt2_get_status(None, None) == -1
     so.caspt2_solve.argtypes = [C.c_void_p, C.c_void_p]
@@ -75,8 +76,9 @@ def test_options_precision_defaults_and_validation(so):
     assert o.precision == cp.FP64 and o.slices == 7
     dims = cp.Dims(2, 2, 2, 4, 1)
     h = C.c_void_p()
+    assert o.degen_thresh == 1e-8
     for bad in (dict(precision=7), dict(precision=cp.BF16X, slices=0),
-                dict(precision=cp.BF16X, slices=8)):
+                dict(precision=cp.BF16X, slices=8), dict(degen_thresh=-1.0)):
         ob = cp.default_options(**bad)
         assert cp.lib().caspt2_create(C.byref(h), C.byref(dims), C.byref(ob)) == cp.EINVAL
 

@@ -1,6 +1,7 @@
 """Differentiation form: dE_MS/df and dE_MS/dB of the target state (MS, reference RDMs
 fixed) from caspt2_gradient and through torch.autograd, checked against central finite
-differences of the library's own energies in random symmetric directions and, for the
+differences of the library's own energies in random symmetric directions (for f, inside
+the blocks a block-diagonal f carries: the library refuses any other f) and, for the
 parts of f that every form of the method shares (closed and virtual diagonals, active
 block), against the determinant-space oracle's densities."""
 import os
@@ -39,6 +40,13 @@ def _fd(cp, p, opt, df=None, dB=None):
     return (4.0 * central(STEP / 2) - central(STEP)) / 3.0
 
 
+def _read_mask(p):
+    c, a = p.nclosed, p.nact
+    m = np.eye(p.nmo)
+    m[c:c + a, c:c + a] = 1.0
+    return m
+
+
 def _energy(cp, p, f, B, opt):
     ctx = cp.Context(p.nclosed, p.nact, p.nvirt, p.naux, p.nstate, **opt)
     try:
@@ -65,8 +73,12 @@ def test_gradient_matches_finite_differences(cp, case, opt):
         ctx.close()
     rng = np.random.default_rng(case * 10 + opt.get("target_state", 0) + 7 * opt["scheme"])
     for _ in range(2):
+        # directions inside the blocks of f the solve accepts (closed and virtual
+        # diagonals, active block): any other direction makes f non-block-diagonal,
+        # which caspt2_set_inputs refuses
         df = rng.standard_normal(p.f.shape)
         df = df + df.T
+        df *= _read_mask(p)
         df /= np.linalg.norm(df)
         fd = _fd(cp, p, opt, df=df)
         an = np.sum(gf * df)

@@ -203,3 +203,47 @@ def test_rdm_sum_rules():
     for k in (2, 3, 4):
         lhs = np.trace(g[k], axis1=-2, axis2=-1)
         assert np.allclose(lhs, (N - k + 1) * g[k - 1], atol=1e-12)
+
+
+@pytest.mark.parametrize("scheme", ["msmr", "sssr"])
+def test_adjoint_identity(small, scheme):
+    """P7: the lambda equation has the same (symmetric) operator as the amplitude
+    equation, so for the two sources -- b_L = V_L^T H|L~> of T_L and the lambda source
+    w_L = R_LP sum_N R_NP b_LN - 2 E_s R_LP^2 S T_L -- <w_L, T_L> = <b_L, lambda_L>."""
+    s0 = 0.2
+    r = o1.solve_problem(small, shift=s0, scheme=scheme, densities=False)
+    P = 0
+    for L in range(small.nstate):
+        w = (r.R[L, P] * sum(r.R[N, P] * r.b_src[L][N] for N in range(small.nstate))
+             - 2.0 * s0 * r.R[L, P] ** 2 * (r.S[L] @ r.t[L]))
+        lhs = w @ r.t[L]
+        rhs = r.b_src[L][L] @ r.lam[L]
+        assert abs(lhs - rhs) <= 1e-12 * max(abs(lhs), 1e-300), (L, lhs, rhs)
+
+
+def test_degenerate_xms_energies_do_not_depend_on_rotation():
+    """P10: when the XMS zeroth-order energies are degenerate the rotation U is fixed
+    only up to a rotation inside the degenerate pair, and without a shift the energies
+    do not depend on it: MS on states rotated by any such U gives the XMS energies.
+    Controls: with non-degenerate E0 the same rotations change the MS energies; with a
+    shift they change too, because the shift correction -E_s <T_L|T_L> of H^eff is
+    diagonal in the rotated basis (Sec. II.B), so a degenerate pair under a shift leaves
+    the energies resting on the rotation chosen (the library flags it with WDEGEN)."""
+    from tests.cases import degenerate_xms_problem
+    p0 = make_problem(2, 4, 2, 24, 2, seed=5)
+    p = degenerate_xms_problem(p0)
+    ref = o1.solve_problem(p, shift=0.0, densities=False)
+    assert abs(ref.E0[1] - ref.E0[0]) < 1e-12
+
+    def rot(th):
+        return np.array([[np.cos(th), -np.sin(th)], [np.sin(th), np.cos(th)]])
+
+    for th in (0.0, 0.4, 1.3):
+        r = o1.solve_problem(p, shift=0.0, xms=False, ci=p.ci @ rot(th), densities=False)
+        assert np.abs(r.Ems - ref.Ems).max() < 1e-10, th
+    a = o1.solve_problem(p0, shift=0.0, xms=False, densities=False)
+    b = o1.solve_problem(p0, shift=0.0, xms=False, ci=p0.ci @ rot(0.4), densities=False)
+    assert np.abs(a.Ems - b.Ems).max() > 1e-5
+    a = o1.solve_problem(p, shift=0.2, xms=False, densities=False)
+    b = o1.solve_problem(p, shift=0.2, xms=False, ci=p.ci @ rot(0.4), densities=False)
+    assert np.abs(a.Ems - b.Ems).max() > 1e-6

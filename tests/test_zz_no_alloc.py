@@ -69,3 +69,21 @@ def test_noalloc_rejects_oversized(cp):
     st = cp.lib().caspt2_classH_noalloc(C.byref(dims), C.byref(opts), p, p, p, p, p, None)
     assert st == cp.ESCRATCH
     assert b"scratch" in cp.lib().caspt2_strerror(st)
+
+
+def test_noalloc_rejects_coupled_fock(cp):
+    """The entry point reads only the blocks of a block-diagonal f, so (like
+    caspt2_set_inputs) it refuses an f with a closed-virtual coupling entry."""
+    import torch
+    from tests.cases import rotated_fock
+    p = make_problem(nclosed=5, nact=3, nvirt=70, naux=37, nstate=3, seed=21, nelact=2, kmax=2)
+    _, f_cpl = rotated_fock(p)
+    _, B, rdm1 = cp.problem_inputs(p, kmax=1)[:3]
+    dev = torch.device("cuda", 0)
+    f_d, B_d, r_d = (torch.from_numpy(x).to(dev) for x in (f_cpl, B, rdm1))
+    e_d = torch.zeros((p.nstate, p.nstate), dtype=torch.float64, device=dev)
+    n_d = torch.zeros(p.nstate, dtype=torch.float64, device=dev)
+    dims = cp.Dims(p.nclosed, p.nact, p.nvirt, p.naux, p.nstate)
+    with pytest.raises(cp.CASPT2Error) as e:
+        cp.classH_noalloc(dims, cp.default_options(), f_d, B_d, r_d, e_d, n_d)
+    assert e.value.status == cp.EINVAL
