@@ -261,7 +261,7 @@ int caspt2_create(caspt2_ctx** out, const caspt2_dims* dims, const caspt2_option
   ALLOC(c->lamLV, (size_t)CASPT2_NCLASS * n * n);
   // classes A-G: plans, class matrices, sources, sector work space, integral blocks
   {
-    long m2max = 0, wmax = 0, pmax = 0;
+    long m2max = 0, wmax = 0, pmax = 0, vmax = 0;
     long packmax = 0;
     std::map<int, long> eri_need;
     for (int k = 0; k < 7 && st == CASPT2_OK; ++k) {
@@ -294,7 +294,7 @@ int caspt2_create(caspt2_ctx** out, const caspt2_dims* dims, const caspt2_option
       if (st == CASPT2_OK && class_upload_plans(w, S, F, V) != cudaSuccess) st = CASPT2_ECUDA;
       ALLOC(w.Sact, 2 * (size_t)w.m * w.m);
       ALLOC(w.Fact, 2 * (size_t)w.m * w.m);
-      ALLOC(w.V, (size_t)w.vsize);
+      vmax = std::max(vmax, w.vsize);   // the sources live only during the class's solve
       // sector bases kept for the densities
       class_keep_layout(w, d, o.scheme);
       for (SectorKeep& K : w.keep) {
@@ -311,13 +311,24 @@ int caspt2_create(caspt2_ctx** out, const caspt2_dims* dims, const caspt2_option
     c->wmax = wmax;
     c->m2max = m2max;
     c->packmax = packmax;
+    if (vmax > 0) {
+      double* vb = nullptr;
+      ALLOC(vb, (size_t)vmax);
+      for (int k = 0; k < 7; ++k)
+        if (c->cw_on[k]) c->cw[k].V = vb;
+    }
     if (m2max > 0) {
       SectorWork& q = c->sw;
       const long mx = (long)std::sqrt((double)m2max) + 1;
       ALLOC(q.Ssec, m2max); ALLOC(q.Fsec, m2max); ALLOC(q.s, mx); ALLOC(q.Qs, m2max);
       ALLOC(q.X, m2max); ALLOC(q.FX, m2max); ALLOC(q.Ft, m2max);
       ALLOC(q.Qf, m2max); ALLOC(q.jac, sym_eig_work((int)mx));
-      ALLOC(q.W, wmax); ALLOC(q.part, pmax);
+      // the sector pass works in tuple chunks: W and the moment partials are capped
+      const long pcol = (long)n * n * (n + 2);
+      q.wcap = std::max<long>(std::min(wmax, kSectorWCap), mx * (long)n);
+      q.pcap = std::max<long>(std::min(pmax, kSectorPartCap), pcol);
+      q.nb2 = kColsumBlocks;
+      ALLOC(q.W, q.wcap); ALLOC(q.part, q.pcap); ALLOC(q.part2, q.nb2 * pcol);
       ALLOC(c->h, nmo * nmo);
       ALLOC(c->fact, a2);
       ALLOC(c->eps, nmo);

@@ -261,11 +261,13 @@ __global__ void k_range_basis(const double* __restrict__ Q, const double* __rest
   }
 }
 
-// W[row][(tuple, L')] for the sector: rows (fam, act, M) (M == Lsel under SS-SR)
+// W[row][(tuple - t0, L')] for the sector tuples t0 .. t0 + nt - 1: rows (fam, act, M)
+// (M == Lsel under SS-SR)
 __global__ void k_sector_src(const double* __restrict__ V, DevClass C, ExtDims ed, int a, int n,
-                             int sector, int Lsel, long ntup, int msec, double* __restrict__ W) {
+                             int sector, int Lsel, long t0, long nt, int msec,
+                             double* __restrict__ W) {
   const long A = ipow(a, C.nact);
-  const long ncol = ntup * n;
+  const long ncol = nt * n;
   const long total = (long)msec * ncol;
   const double isq2 = 0.70710678118654752440;
   for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
@@ -273,7 +275,7 @@ __global__ void k_sector_src(const double* __restrict__ V, DevClass C, ExtDims e
     const int row = e / ncol;
     const long cidx = e % ncol;
     const int Lp = cidx % n;
-    const long t = cidx / n;
+    const long t = t0 + cidx / n;
     int co[3], cs[3];
     sector_tuple(C, ed.d, sector, t, co, cs);
     const int M = Lsel < 0 ? row % n : Lsel;
@@ -299,21 +301,25 @@ __global__ void k_sector_src(const double* __restrict__ V, DevClass C, ExtDims e
 //   M1[L][N][L'] += Vt_N Vt_L' / D_L (all L'),  M2[L][N] += Vt_N Vt_L / D_L^2,
 //   M3[L] += Vt_L^2 / D_L^3 (N == L),   D_L = e_ext(t) + omega_mu - E0_L + E_s.
 // part[t][Li][N][n + 2] (Li = L, or 0 under SS-SR where L = Lsel).
+// Tuples t0 .. t0 + nt - 1 of the sector (ntup in all; Vt has ntup * n columns); part
+// rows are local to the chunk.
 __global__ void k_sector_energy(const double* __restrict__ Vt, const double* __restrict__ omega,
                                 const double* __restrict__ E0,
                                 const double* __restrict__ eps, DevClass C, ExtDims ed, int c,
-                                int n, int sector, int Lsel, long ntup, int msec, double shift,
-                                double* __restrict__ part, double* __restrict__ mindenom) {
+                                int n, int sector, int Lsel, long ntup, long t0, long nt, int msec,
+                                double shift, double* __restrict__ part,
+                                double* __restrict__ mindenom) {
   const long ncol = ntup * n;
   const int nL = Lsel < 0 ? n : 1;
-  const long total = ntup * nL * n;
+  const long total = nt * nL * n;
   const int w = n + 2;
   double dmin = 1e300;
   for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
        e += (long)gridDim.x * blockDim.x) {
     const int N = e % n;
     const int Li = (e / n) % nL;
-    const long t = e / ((long)n * nL);
+    const long tl = e / ((long)n * nL);
+    const long t = t0 + tl;
     const int L = Lsel < 0 ? Li : Lsel;
     int co[3], cs[3];
     sector_tuple(C, ed.d, sector, t, co, cs);
@@ -332,7 +338,7 @@ __global__ void k_sector_energy(const double* __restrict__ Vt, const double* __r
       if (N == L) m3 += row[L] * row[L] * inv * inv * inv;
       dmin = fmin(dmin, fabs(D));
     }
-    double* o = part + (((t * nL + Li) * n) + N) * w;
+    double* o = part + (((tl * nL + Li) * n) + N) * w;
     for (int q = 0; q < n; ++q) o[q] = m1[q];
     o[n] = m2;
     o[n + 1] = m3;
@@ -340,6 +346,21 @@ __global__ void k_sector_energy(const double* __restrict__ Vt, const double* __r
   __shared__ double red[32];
   dmin = block_min(dmin, red);
   if (threadIdx.x == 0) atomicMin_double(mindenom, dmin);
+}
+
+// First stage of the fixed-order column sums: block b sums rows [b R, (b + 1) R) of
+// part[rows][ncol] (R = ceil(rows / gridDim.x)), one thread per column, rows in order
+// (reads coalesced across the columns) -> out[b][ncol].
+__global__ void k_colsum_rows(const double* __restrict__ part, long rows, int ncol,
+                              double* __restrict__ out) {
+  const long R = (rows + gridDim.x - 1) / gridDim.x;
+  const long r0 = (long)blockIdx.x * R;
+  const long r1 = r0 + R < rows ? r0 + R : rows;
+  for (int col = threadIdx.x; col < ncol; col += blockDim.x) {
+    double acc = 0.0;
+    for (long r = r0; r < r1; ++r) acc += part[r * ncol + col];
+    out[(long)blockIdx.x * ncol + col] = acc;
+  }
 }
 
 // Fixed-order column sums of part[rows][nL][n][n+2] accumulated into the class moments
@@ -632,6 +653,10 @@ int class_solve(ClassWork& w, SectorWork& sw, const Dims& d, int scheme, double 
     const long total2 = w.vsize / ((long)n * n);
     k_src_eval_ml<4><<<launch_blocks(total2), 256, 0, s>>>(w.dV, w.nV, w.dc, d, rdm, h, eri, w.V,
                                                           total2);
+  } else if (n <= 6) {
+    const long total2 = w.vsize / ((long)n * n);
+    k_src_eval_ml<6><<<launch_blocks(total2), 256, 0, s>>>(w.dV, w.nV, w.dc, d, rdm, h, eri, w.V,
+                                                          total2);
   } else {
     k_src_eval<<<launch_blocks(w.vsize), 256, 0, s>>>(w.dV, w.nV, w.dc, d, rdm, h, eri, w.V,
                                                       w.vsize);
@@ -676,21 +701,34 @@ int class_solve(ClassWork& w, SectorWork& sw, const Dims& d, int scheme, double 
       if (st != CASPT2_OK) return st;
       CASPT2_CUDA_TRY(dgemm(msec, nk, nk, 1.0, sw.X, nk, false, sw.Qf, nk, false, 0.0, K.Y, nk, s));
       const long ncol = ntup * n;
-      ++launch_counter();
-      k_sector_src<<<launch_blocks((long)msec * ncol), 256, 0, s>>>(w.V, w.dc, w.ed, d.a, n, sec,
-                                                                    Lsel, ntup, msec, sw.W);
-      CASPT2_CUDA_TRY(cudaGetLastError());
-      CASPT2_CUDA_TRY(dgemm(nk, (int)ncol, msec, 1.0, K.Y, nk, true, sw.W, (int)ncol, false,
-                            0.0, K.Vt, (int)ncol, s));
       const int nL = Lsel < 0 ? n : 1;
-      const long ne = ntup * nL * n;
-      ++launch_counter();
-      k_sector_energy<<<launch_blocks(ne), 256, 0, s>>>(K.Vt, K.omega, E0, eps_cv, w.dc, w.ed,
-                                                        d.c, n, sec, Lsel, ntup, nk, shift,
-                                                        sw.part, mindenom);
-      ++launch_counter();
-      k_moment_colsum<<<nL * n * (n + 2), 256, 0, s>>>(sw.part, ntup, n, nL, Lsel, mom);
-      CASPT2_CUDA_TRY(cudaGetLastError());
+      const int pcol = nL * n * (n + 2);
+      // tuples in chunks so that the sector sources W (msec x chunk n) and the moment
+      // partials (chunk x pcol) stay within the work arrays the context holds
+      long chunk = std::min<long>(ntup, sw.wcap / ((long)msec * n));
+      chunk = std::min<long>(chunk, sw.pcap / pcol);
+      if (chunk < 1 || (long)nk * ncol > (1L << 62)) return CASPT2_EINVAL;
+      for (long t0 = 0; t0 < ntup; t0 += chunk) {
+        const long nt = std::min(chunk, ntup - t0);
+        ++launch_counter();
+        k_sector_src<<<launch_blocks((long)msec * nt * n), 256, 0, s>>>(
+            w.V, w.dc, w.ed, d.a, n, sec, Lsel, t0, nt, msec, sw.W);
+        CASPT2_CUDA_TRY(cudaGetLastError());
+        CASPT2_CUDA_TRY(dgemm(nk, (int)(nt * n), msec, 1.0, K.Y, nk, true, sw.W, (int)(nt * n),
+                              false, 0.0, K.Vt + t0 * n, (int)ncol, s));
+        const long ne = nt * nL * n;
+        ++launch_counter();
+        k_sector_energy<<<launch_blocks(ne), 256, 0, s>>>(K.Vt, K.omega, E0, eps_cv, w.dc, w.ed,
+                                                          d.c, n, sec, Lsel, ntup, t0, nt, nk,
+                                                          shift, sw.part, mindenom);
+        // fixed-order column sums: row blocks, then the block partials in order
+        const long nb = std::min<long>(sw.nb2, std::max<long>(1, nt / 64));
+        ++launch_counter();
+        k_colsum_rows<<<(unsigned)nb, 256, 0, s>>>(sw.part, nt, pcol, sw.part2);
+        ++launch_counter();
+        k_moment_colsum<<<pcol, 256, 0, s>>>(sw.part2, nb, n, nL, Lsel, mom);
+        CASPT2_CUDA_TRY(cudaGetLastError());
+      }
     }
   }
   return CASPT2_OK;

@@ -51,8 +51,16 @@ struct ClassWork {
 struct SectorWork {
   double *Ssec = nullptr, *Fsec = nullptr, *s = nullptr, *Qs = nullptr, *X = nullptr,
          *FX = nullptr, *Ft = nullptr, *Qf = nullptr, *jac = nullptr, *W = nullptr,
-         *part = nullptr;
+         *part = nullptr, *part2 = nullptr;
+  long wcap = 0, pcap = 0;   // doubles held by W and part (the sector pass runs in tuple
+                             // chunks that fit them)
+  long nb2 = 0;              // row blocks of the first column-sum stage (part2: nb2 x pcol)
 };
+// Upper bounds on the solve's sector work arrays W and part (doubles): larger sectors are
+// processed in tuple chunks.
+constexpr long kSectorWCap = 1L << 28;
+constexpr long kSectorPartCap = 1L << 27;
+constexpr long kColsumBlocks = 1216;
 
 // Work space of the class densities (sized by the caller, see density_ag.cu).
 struct DensWork {

@@ -73,10 +73,29 @@ def _active_meanfield(eri_act: np.ndarray, d: np.ndarray) -> np.ndarray:
     return np.einsum("rstu,tu->rs", eri_act, d) - 0.5 * np.einsum("ruts,tu->rs", eri_act, d)
 
 
+DENSE_CASCI_MAX = 20000     # determinants: dense CASCI and spin-pattern RDMs up to here
+
+
+def _default_device() -> str:
+    try:
+        import torch
+        return "cuda" if torch.cuda.is_available() else "cpu"
+    except ImportError:
+        return "cpu"
+
+
+def _release_device(dev: str) -> None:
+    if str(dev).startswith("cuda"):
+        import torch
+        torch.cuda.empty_cache()
+
+
 def make_problem(nclosed: int, nact: int, nvirt: int, naux: int, nstate: int,
                  seed: int, nelact: int | None = None, decay: float = 10.0,
-                 kmax: int = 4) -> Problem:
-    """Build one seeded problem.  nelact defaults to nact (half filling)."""
+                 kmax: int = 4, device: str | None = None) -> Problem:
+    """Build one seeded problem.  nelact defaults to nact (half filling).  Active spaces
+    above DENSE_CASCI_MAX determinants use the Davidson / Gram-matrix path of
+    synth.casci_fast on `device` (default: the GPU when present)."""
     if nelact is None:
         nelact = nact
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -104,8 +123,18 @@ def make_problem(nclosed: int, nact: int, nvirt: int, naux: int, nstate: int,
     fc_act = t_act - _active_meanfield(eri_act, d_guess)
 
     space = ActiveSpace(nact, nelact)
-    e_cas, ci = lowest_singlets(space, fc_act, eri_act, nstate)
-    rdm = {k: space.rdm(ci, k) for k in range(1, kmax + 1)}
+    if space.ndet <= DENSE_CASCI_MAX:
+        e_cas, ci = lowest_singlets(space, fc_act, eri_act, nstate)
+        rdm = {k: space.rdm(ci, k) for k in range(1, kmax + 1)}
+    else:
+        # large active spaces: Davidson CASCI and Gram-matrix RDMs (on a GPU when present)
+        from .casci_fast import BigSpace, davidson_singlets, rdms
+        dev = device if device is not None else _default_device()
+        big = BigSpace(nact, nelact, dev)
+        e_cas, ci = davidson_singlets(big, fc_act, eri_act, nstate)
+        rdm = {k: v.cpu().numpy() for k, v in rdms(big, ci, kmax).items()}
+        del big
+        _release_device(dev)
     g1 = rdm[1].reshape(nstate, nstate, nact, nact)
     d_sa = sum(g1[m, m] for m in range(nstate)) / nstate
     f[act, act] = fc_act + _active_meanfield(eri_act, d_sa)
@@ -119,4 +148,7 @@ def make_problem(nclosed: int, nact: int, nvirt: int, naux: int, nstate: int,
 WORKLOADS = {
     "c4a4v20x84n2": dict(nclosed=4, nact=4, nvirt=20, naux=84, nstate=2, seed=0, decay=10.0),
     "c20a8v200x700n3": dict(nclosed=20, nact=8, nvirt=200, naux=700, nstate=3, seed=1, decay=10.0),
+    # copper-corrole shape: 10 active orbitals, 10 electrons (63504 determinants)
+    "c70a10v600x2000n5": dict(nclosed=70, nact=10, nvirt=600, naux=2000, nstate=5, seed=4,
+                              decay=40.0),
 }
