@@ -84,6 +84,12 @@ typedef struct {
                          /* rotation inside the degenerate subspace, which leaves every energy */
                          /* unchanged (Sec. II.D: the XMS response of such a pair is taken as  */
                          /* zero); the solve returns WDEGEN as a warning.                      */
+    int    closed_begin; /* partial solve for splitting one solve over GPUs: the class-H     */
+    int    closed_end;   /* pairs (i <= j) and class-G tuples (a, b, i) with closed_begin <=  */
+                         /* i < closed_end; classes A-F only when closed_begin == 0.  The     */
+                         /* per-class moments of the partitions summed (caspt2_get_moments)   */
+                         /* and passed to caspt2_finalize_moments give the whole solve.       */
+                         /* Default 0, -1 (all closed orbitals).                              */
 } caspt2_options;
 
 /* Fill *opt with defaults: XMS, MS-MR, shift 0, 1e-9, enuc 0, target 0, all classes,
@@ -247,6 +253,23 @@ int caspt2_get_densities(caspt2_ctx* ctx, int mem, double* d1, double* d2, doubl
  * of all solved classes.  Errors: EINVAL (xms, target_state < 0), ESTATE (no solve),
  * ENOMEM, ECUDA. */
 int caspt2_gradient(caspt2_ctx* ctx, int mem, double* grad_f, double* grad_B, void* cuda_stream);
+
+/* Per-class moment sums of the last solve (Sec. II.B, Eq. ampeq solved in each class's
+ * orthonormal sector basis mu: M1[L][N][L'] = sum Vt_N Vt_L' / D_L, M2[L][N] =
+ * sum Vt_N Vt_L / D_L^2, M3[L] = sum Vt_L^2 / D_L^3), laid out [class][n^3 + n^2 + n], to
+ * a host buffer of CASPT2_NCLASS * (n^3 + n^2 + n) doubles.  They are sums over the
+ * external index tuples, so the moments of partial solves over disjoint closed-orbital
+ * ranges (options.closed_begin/closed_end) add up to those of the whole solve.
+ * Errors: EINVAL, ESTATE (no solve). */
+int caspt2_get_moments(caspt2_ctx* ctx, double* mom);
+
+/* Replace the last solve's moments by `mom` (host, the layout of caspt2_get_moments; e.g.
+ * summed over the partitions of one solve in a fixed order) and recompute from them the
+ * per-class pieces, H^eff, E^MS, R and the lambda pieces of the target state, on
+ * cuda_stream (synchronised).  The getters then return the combined results; the
+ * densities and amplitude getters stay unavailable after a partial solve.
+ * Errors: EINVAL, ESTATE (no solve), ENOTCONV, ENAN, ECUDA. */
+int caspt2_finalize_moments(caspt2_ctx* ctx, const double* mom, void* cuda_stream);
 
 /* Number of CUDA kernels the library launched during the last solve (-1 if ctx is NULL). */
 long caspt2_get_kernel_launches(caspt2_ctx* ctx);

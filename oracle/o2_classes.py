@@ -170,12 +170,17 @@ def active_matrices(cls, rdm, n, a, f_act=None):
     return out
 
 
-def sources(cls, rdm, n, a, blocks):
-    """V[fam, ext..., act..., M, L] = <M~|E_Omega^dag H|L~> (Eq. ampeq source)."""
+def sources(cls, rdm, n, a, blocks, ext_range=None):
+    """V[fam, ext..., act..., M, L] = <M~|E_Omega^dag H|L~> (Eq. ampeq source).
+    ext_range = (external label, lo, hi): only the values lo..hi-1 of that external index
+    (every operand axis carrying the label is restricted to them)."""
     fams, ext, pair, act = CLASS_DEF[cls]
     dims = blocks["dims"]
     sp = _space_of_slot(cls)
-    shape = (len(fams),) + tuple(dims[sp[e]] for e in ext) + (a,) * len(act) + (n, n)
+    ext_dims = [dims[sp[e]] for e in ext]
+    if ext_range is not None:
+        ext_dims[ext.index(ext_range[0])] = ext_range[2] - ext_range[1]
+    shape = (len(fams),) + tuple(ext_dims) + (a,) * len(act) + (n, n)
     V = np.zeros(shape)
     for fb in range(len(fams)):
         for kind, spc, w, t in source_terms(cls, fb):
@@ -204,9 +209,20 @@ def sources(cls, rdm, n, a, blocks):
                 subs.append(L(x) + L(y))
                 opnds.append(np.eye(dims[lab_space[x]]))
             outsub = ("".join(L(e + "_b") for e in ext) + "".join(L(s + "_b") for s in act) + "MN")
+            if ext_range is not None:
+                ch, lo, hi = L(ext_range[0] + "_b"), ext_range[1], ext_range[2]
+                opnds = [_restrict(op, sub, ch, lo, hi) for op, sub in zip(opnds, subs)]
             val = np.einsum(",".join(subs) + "->" + outsub, *opnds, optimize=True)
             V[fb] += w * t.coeff * val
     return V
+
+
+def _restrict(op, sub, ch, lo, hi):
+    """op with every axis labelled ch restricted to lo..hi-1."""
+    if ch not in sub:
+        return op
+    idx = tuple(slice(lo, hi) if x == ch else slice(None) for x in sub)
+    return op[idx]
 
 
 def integral_blocks(prob, h):
@@ -225,17 +241,21 @@ def all_classes(prob, st, shift=0.0, scheme="msmr", thresh=1e-9):
     return out
 
 
-def all_moments(prob, st, shift=0.0, scheme="msmr", thresh=1e-9):
-    """{class: (M1, M2, M3)} for all eight classes."""
+def all_moments(prob, st, shift=0.0, scheme="msmr", thresh=1e-9, chunks=None, i_chunk=None):
+    """{class: (M1, M2, M3)} for all eight classes.  chunks: {class: (label, size)} for
+    classes whose sources are taken in groups (class_moments); i_chunk: closed orbitals
+    per group of class H (o2_rdm.class_h_moments)."""
     from .o2_rdm import class_h_moments
-    out = {cls: class_moments(prob, st, cls, shift, scheme, thresh) for cls in "ABCDEFG"}
-    out["H"] = class_h_moments(prob, st, shift=shift, scheme=scheme)
+    chunks = chunks or {}
+    out = {cls: class_moments(prob, st, cls, shift, scheme, thresh, chunk=chunks.get(cls))
+           for cls in "ABCDEFG"}
+    out["H"] = class_h_moments(prob, st, shift=shift, scheme=scheme, i_chunk=i_chunk)
     return out
 
 
-def class_energy(prob, st, cls, shift=0.0, scheme="msmr", thresh=1e-9, h=None):
+def class_energy(prob, st, cls, shift=0.0, scheme="msmr", thresh=1e-9, h=None, chunk=None):
     """(e, norm) of a class; see class_moments for the definitions."""
-    M1, M2, M3 = class_moments(prob, st, cls, shift, scheme, thresh, h)
+    M1, M2, M3 = class_moments(prob, st, cls, shift, scheme, thresh, h, chunk)
     n = prob.nstate
     e = -np.array([[M1[L, L, Lp] for Lp in range(n)] for L in range(n)])
     nr = np.array([M2[L, L] for L in range(n)])
@@ -255,13 +275,18 @@ def lambda_pieces(M1, M2, M3, R, P, shift):
     return NL, lv
 
 
-def class_moments(prob, st, cls, shift=0.0, scheme="msmr", thresh=1e-9, h=None):
+def class_moments(prob, st, cls, shift=0.0, scheme="msmr", thresh=1e-9, h=None, chunk=None):
     """Moment sums over the external tuples and sector eigenvectors mu of a class:
       M1[L, N, L'] = sum Vt_N Vt_L' / D_L,  M2[L, N] = sum Vt_N Vt_L / D_L^2,
       M3[L] = sum Vt_L^2 / D_L^3,   D_L = e_ext + omega_mu - E0_L + E_s,
     with Vt = Y^T V the sources in the orthonormal eigenbasis of the sector.  Then
     <Psi1_L|H|L'~> = -M1[L, L, L'] and <Psi1_L|Psi1_L> = M2[L, L].  For block-diagonal f,
-    from the rotated RDMs of `st` (an o2_rdm.Setup with kmax >= 4)."""
+    from the rotated RDMs of `st` (an o2_rdm.Setup with kmax >= 4).
+
+    chunk = (external label, size), for classes too large to hold all sources at once:
+    the tuples are taken in groups of `size` values of that external index (one that is
+    not part of the swapped pair), sources of one group at a time.  Tuples are solved
+    independently in the sector basis, so the grouping only orders the sums."""
     from .o2_rdm import g_of
     c, a, v, n = prob.nclosed, prob.nact, prob.nvirt, prob.nstate
     fams, ext, pair, act = CLASS_DEF[cls]
@@ -279,72 +304,97 @@ def class_moments(prob, st, cls, shift=0.0, scheme="msmr", thresh=1e-9, h=None):
     f_act = prob.f[c:c + a, c:c + a]
     rdm = st.rdm
     mats = active_matrices(cls, rdm, n, a, f_act)
-    V = sources(cls, rdm, n, a, integral_blocks(prob, h))
+    blocks = integral_blocks(prob, h)
     eps = np.diag(prob.f)
     ec, ev = eps[:c], eps[c + a:]
     nf = len(fams)
     m = nf * a ** len(act) * n
     S = {k: x.reshape(m, m) for k, x in mats["S"].items()}
     F = {k: x.reshape(m, m) for k, x in mats["F"].items()}
-    # external tuples and their energies
-    ranges = [range(dims[sp[e]]) for e in ext]
     M1 = np.zeros((n, n, n))
     M2 = np.zeros((n, n))
     M3 = np.zeros(n)
-    Vr = V.reshape((nf,) + V.shape[1:1 + len(ext)] + (a ** len(act), n, n))
-
-    sp_list = [sp[e] for e in ext]
-    grids = np.meshgrid(*[np.arange(r.stop) for r in ranges], indexing="ij")
-    tup_all = np.stack([g.ravel() for g in grids], axis=1)            # [ntup, next]
-    eext_all = np.zeros(len(tup_all))
-    for k, s_ in enumerate(sp_list):
-        eext_all += ev[tup_all[:, k]] if s_ == "v" else -ec[tup_all[:, k]]
-    Vflat = Vr.reshape((nf,) + (int(np.prod([r.stop for r in ranges])),) + (a ** len(act), n, n))
-    ext_shape = [r.stop for r in ranges]
-
-    def flat(tups):
-        return np.ravel_multi_index(tuple(tups.T), ext_shape)
-
     sectors = [("+", 1.0), ("-", -1.0)] if pair is not None else [("id", 0.0)]
+
+    # orthonormalised sector bases (independent of the external tuples)
+    bases = {}
     for name, sgn in sectors:
         if pair is None:
             Ssec, Fsec = S["id"], F["id"]
-            sel = np.arange(len(tup_all))
-            vmat = Vflat[:, sel]                                          # [nf, T, A, M, L]
         else:
             Ssec, Fsec = S["id"] + sgn * S["sw"], F["id"] + sgn * F["sw"]
-            pi_, pj_ = ext.index(pair[0]), ext.index(pair[1])
-            ti, tj = tup_all[:, pi_], tup_all[:, pj_]
-            sel = np.nonzero((ti < tj) if name == "-" else (ti <= tj))[0]
-            swp = tup_all[sel].copy()
-            swp[:, [pi_, pj_]] = swp[:, [pj_, pi_]]
-            v1 = Vflat[:, sel]
-            v2 = Vflat[:, flat(swp)]
-            diag = (ti[sel] == tj[sel])[None, :, None, None, None]
-            vmat = np.where(diag, v1, (v1 + sgn * v2) / np.sqrt(2.0))
         Ssec = 0.5 * (Ssec + Ssec.T)
         Fsec = 0.5 * (Fsec + Fsec.T)
-        ee_sel = eext_all[sel]
-        # rows (fam, act, M), columns (tuple, L)
-        Vm = np.moveaxis(vmat, 1, 3).reshape(m, len(sel), n)
         for Lsel in (range(n) if scheme == "sssr" else [None]):
             keep_idx = np.arange(m) if Lsel is None else np.arange(Lsel, m, n)
             Ss = Ssec[np.ix_(keep_idx, keep_idx)]
             Fs = Fsec[np.ix_(keep_idx, keep_idx)]
             s_, q_ = np.linalg.eigh(Ss)
             keep = s_ >= thresh
-            if not keep.any() or len(sel) == 0:
+            if not keep.any():
                 continue
             X = q_[:, keep] / np.sqrt(s_[keep])
             om, Q = np.linalg.eigh(X.T @ Fs @ X)
-            Y = X @ Q
-            Vt = np.einsum("ku,ktl->utl", Y, Vm[keep_idx])              # [mu, tuple, L']
-            Ls = range(n) if Lsel is None else [Lsel]
-            for L in Ls:
-                D = ee_sel[None, :] + om[:, None] - st.E0[L] + shift      # [mu, tuple]
-                M1[L] += np.einsum("utn,utl->nl", Vt / D[:, :, None], Vt)
-                M2[L] += np.einsum("utn,ut->n", Vt, Vt[:, :, L] / D ** 2)
-                M3[L] += np.sum(Vt[:, :, L] ** 2 / D ** 3)
+            bases[(name, Lsel)] = (keep_idx, X @ Q, om)
+
+    # external tuples, in groups of one external index when chunked
+    full = [dims[sp[e]] for e in ext]
+    if chunk is None:
+        groups = [None]
+    else:
+        lab, size = chunk
+        assert lab in ext and (pair is None or lab not in pair)
+        dim = full[ext.index(lab)]
+        groups = [(lab, lo, min(dim, lo + size)) for lo in range(0, dim, size)]
+    for grp in groups:
+        V = sources(cls, rdm, n, a, blocks, ext_range=grp)
+        ext_shape = list(full)
+        offs = [0] * len(ext)
+        if grp is not None:
+            k_ = ext.index(grp[0])
+            ext_shape[k_] = grp[2] - grp[1]
+            offs[k_] = grp[1]
+        grids = np.meshgrid(*[np.arange(r) for r in ext_shape], indexing="ij")
+        tup_all = np.stack([g.ravel() for g in grids], axis=1)            # [ntup, next]
+        eext_all = np.zeros(len(tup_all))
+        for k, e_ in enumerate(ext):
+            idx = tup_all[:, k] + offs[k]
+            eext_all += ev[idx] if sp[e_] == "v" else -ec[idx]
+        Vflat = V.reshape((nf, int(np.prod(ext_shape)), a ** len(act), n, n))
+        del V
+
+        def flat(tups):
+            return np.ravel_multi_index(tuple(tups.T), ext_shape)
+
+        for name, sgn in sectors:
+            if pair is None:
+                sel = np.arange(len(tup_all))
+                vmat = Vflat[:, sel]                                          # [nf, T, A, M, L]
+            else:
+                pi_, pj_ = ext.index(pair[0]), ext.index(pair[1])
+                ti, tj = tup_all[:, pi_], tup_all[:, pj_]
+                sel = np.nonzero((ti < tj) if name == "-" else (ti <= tj))[0]
+                swp = tup_all[sel].copy()
+                swp[:, [pi_, pj_]] = swp[:, [pj_, pi_]]
+                v1 = Vflat[:, sel]
+                v2 = Vflat[:, flat(swp)]
+                diag = (ti[sel] == tj[sel])[None, :, None, None, None]
+                vmat = np.where(diag, v1, (v1 + sgn * v2) / np.sqrt(2.0))
+            ee_sel = eext_all[sel]
+            # rows (fam, act, M), columns (tuple, L)
+            Vm = np.moveaxis(vmat, 1, 3).reshape(m, len(sel), n)
+            del vmat
+            for Lsel in (range(n) if scheme == "sssr" else [None]):
+                if (name, Lsel) not in bases or len(sel) == 0:
+                    continue
+                keep_idx, Y, om = bases[(name, Lsel)]
+                Vt = np.einsum("ku,ktl->utl", Y, Vm[keep_idx])              # [mu, tuple, L']
+                Ls = range(n) if Lsel is None else [Lsel]
+                for L in Ls:
+                    D = ee_sel[None, :] + om[:, None] - st.E0[L] + shift      # [mu, tuple]
+                    M1[L] += np.einsum("utn,utl->nl", Vt / D[:, :, None], Vt)
+                    M2[L] += np.einsum("utn,ut->n", Vt, Vt[:, :, L] / D ** 2)
+                    M3[L] += np.sum(Vt[:, :, L] ** 2 / D ** 3)
     return M1, M2, M3
 
 

@@ -114,11 +114,16 @@ def class_h(prob, st: Setup, shift: float = 0.0, scheme: str = "msmr"):
     return e, nr
 
 
-def class_h_moments(prob, st: Setup, shift: float = 0.0, scheme: str = "msmr"):
+def class_h_moments(prob, st: Setup, shift: float = 0.0, scheme: str = "msmr",
+                    i_chunk: int | None = None, i_groups: int | None = None):
     """Moment sums (M1, M2, M3) of class E_ai,bj in the eigenbasis nu of U^T Fref U, where the
     sources are Vt_N(nu) = W_N nu k and sum_tuples k^2 = sum_ijab K(2K - K'):
       M1[L,N,L'] = sum_nu W_Nnu W_L'nu S1[nu,L],  M2[L,N] = sum_nu W_Nnu W_Lnu S2[nu,L],
-      M3[L] = sum_nu W_Lnu^2 S3[nu,L],  Sk[nu,L] = sum_ijab K(2K - K') / D^k."""
+      M3[L] = sum_nu W_Lnu^2 S3[nu,L],  Sk[nu,L] = sum_ijab K(2K - K') / D^k.
+    i_chunk: the sums over i are taken for groups of i_chunk closed orbitals at a time
+    (K(ai|bj) and its exchange partner K(aj|bi) = K(bi|aj) share the row index i, so a group
+    needs only its own rows of K).  i_groups: stop after that many groups (a partial sum,
+    for timing samples only)."""
     c, a, v, n = prob.nclosed, prob.nact, prob.nvirt, prob.nstate
     M1, M2, M3 = np.zeros((n, n, n)), np.zeros((n, n)), np.zeros(n)
     if c == 0 or v == 0:
@@ -128,22 +133,35 @@ def class_h_moments(prob, st: Setup, shift: float = 0.0, scheme: str = "msmr"):
     ec, ev = eps[:c], eps[vo:]
     X = prob.B.shape[0]
     Bcv = np.ascontiguousarray(prob.B[:, :c, vo:]).reshape(X, c * v)
-    K = (Bcv.T @ Bcv).reshape(c, v, c, v)
-    num = K * (2.0 * K - K.transpose(0, 3, 2, 1))
-    D = (ev[None, :, None, None] + ev[None, None, None, :]
-         - ec[:, None, None, None] - ec[None, None, :, None])
+    step = c if i_chunk is None else i_chunk
+    if scheme == "sssr":
+        shifts = [(L, None) for L in range(n)]
+    else:
+        omega, W = np.linalg.eigh(0.5 * (st.Ftil + st.Ftil.T))
+        shifts = [(L, nu) for L in range(n) for nu in range(n)]
+    sums = {key: np.zeros(3) for key in shifts}
+    for g, i0 in enumerate(range(0, c, step)):
+        if i_groups is not None and g >= i_groups:
+            break
+        i1 = min(c, i0 + step)
+        K = (Bcv[:, i0 * v:i1 * v].T @ Bcv).reshape(i1 - i0, v, c, v)    # (ai|bj), i in group
+        num = K * (2.0 * K - K.transpose(0, 3, 2, 1))               # K (2K - (aj|bi))
+        del K
+        D = (ev[None, :, None, None] + ev[None, None, None, :]
+             - ec[i0:i1, None, None, None] - ec[None, None, :, None])
+        for L, nu in shifts:
+            dd = D + shift + (0.0 if nu is None else omega[nu] - st.E0[L])
+            sums[(L, nu)] += [np.sum(num / dd), np.sum(num / dd ** 2), np.sum(num / dd ** 3)]
     if scheme == "sssr":
         for L in range(n):
-            dd = D + shift
-            M1[L, L, L] = np.sum(num / dd)
-            M2[L, L] = np.sum(num / dd ** 2)
-            M3[L] = np.sum(num / dd ** 3)
+            s1, s2, s3 = sums[(L, None)]
+            M1[L, L, L] = s1
+            M2[L, L] = s2
+            M3[L] = s3
         return M1, M2, M3
-    omega, W = np.linalg.eigh(0.5 * (st.Ftil + st.Ftil.T))
     for L in range(n):
         for nu in range(n):
-            dd = D + omega[nu] - st.E0[L] + shift
-            s1, s2, s3 = np.sum(num / dd), np.sum(num / dd ** 2), np.sum(num / dd ** 3)
+            s1, s2, s3 = sums[(L, nu)]
             M1[L] += np.outer(W[:, nu], W[:, nu]) * s1
             M2[L] += W[:, nu] * W[L, nu] * s2
             M3[L] += W[L, nu] ** 2 * s3

@@ -34,7 +34,8 @@ class Options(C.Structure):
     _fields_ = [("xms", C.c_int), ("scheme", C.c_int), ("shift", C.c_double),
                 ("ovl_thresh", C.c_double), ("enuc", C.c_double), ("target_state", C.c_int),
                 ("class_mask", C.c_uint), ("precision", C.c_int), ("slices", C.c_int),
-                ("degen_thresh", C.c_double)]
+                ("degen_thresh", C.c_double), ("closed_begin", C.c_int),
+                ("closed_end", C.c_int)]
 
 
 class Request(C.Structure):
@@ -93,6 +94,8 @@ def lib():
         L.caspt2_server_destroy.argtypes = [P]
         L.caspt2_server_destroy.restype = None
         L.caspt2_classH_noalloc.argtypes = [C.POINTER(Dims), C.POINTER(Options), P, P, P, P, P, P]
+        L.caspt2_get_moments.argtypes = [P, P]
+        L.caspt2_finalize_moments.argtypes = [P, P, P]
         L.caspt2_strerror.argtypes = [C.c_int]
         L.caspt2_strerror.restype = C.c_char_p
         _lib = L
@@ -278,6 +281,21 @@ class Context:
                 "densities_done": bool(r.densities_done), "min_denominator": r.min_denominator,
                 "kernel_launches": r.kernel_launches, "times_ms": list(r.times_ms),
                 "warnings": int(r.warnings), "min_e0_gap": r.min_e0_gap}
+
+    def moments(self) -> np.ndarray:
+        """caspt2_get_moments: per-class moment sums [8][n^3 + n^2 + n] of the last solve."""
+        n = self.n
+        out = np.zeros((8, n ** 3 + n ** 2 + n))
+        _check(lib().caspt2_get_moments(self._h, C.c_void_p(out.ctypes.data)),
+               "caspt2_get_moments")
+        return out
+
+    def finalize_moments(self, mom: np.ndarray, stream=None) -> int:
+        """caspt2_finalize_moments: H^eff, E_MS, R and lambda from (summed) moments."""
+        m = np.ascontiguousarray(mom, dtype=np.float64)
+        s = C.c_void_p(stream) if stream is not None else None
+        return _check(lib().caspt2_finalize_moments(self._h, C.c_void_p(m.ctypes.data), s),
+                      "caspt2_finalize_moments", warn_ok=True)
 
     def amplitude_size(self, cls: int) -> int:
         """caspt2_amplitude_size: elements of T_LN (or lambda_LN) of class index cls."""

@@ -35,6 +35,9 @@ struct caspt2_ctx {
   bool solved = false;
   int last_status = CASPT2_ESTATE;   // of the last caspt2_solve (ESTATE before the first)
   unsigned warnings = 0;             // CASPT2_WARN_* of the last solve
+  bool partial() const {             // a closed-orbital range narrower than all orbitals
+    return opt.closed_begin > 0 || (opt.closed_end >= 0 && opt.closed_end < d.c);
+  }
   double min_e0_gap = 0.0;           // smallest |E0_M - E0_N| of the last solve
   std::vector<void*> allocs;
 
@@ -59,6 +62,9 @@ struct caspt2_ctx {
   double *pack0 = nullptr, *pack1 = nullptr;
   std::map<int, double*> eri_blk;     // canonical space key -> (pq|rt) block
   EriBlocks eri_tab{};
+  std::vector<PresumSpec> presum;     // pre-summed blocks of the solve's source plans
+  std::vector<double*> presum_blk;
+  PresumBlocks presum_tab{};
   long wmax = 0, m2max = 0, packmax = 0;
   // densities (allocated on the first caspt2_densities call)
   bool dens_alloc = false, dens_done = false;
@@ -138,6 +144,8 @@ void caspt2_default_options(caspt2_options* o) {
   o->precision = CASPT2_FP64;
   o->slices = 7;
   o->degen_thresh = 1e-8;
+  o->closed_begin = 0;
+  o->closed_end = -1;
 }
 
 unsigned caspt2_supported_classes(void) { return (1u << CASPT2_NCLASS) - 1u; }
@@ -197,6 +205,9 @@ int caspt2_create(caspt2_ctx** out, const caspt2_dims* dims, const caspt2_option
   if (o.precision != CASPT2_FP64 && o.precision != CASPT2_BF16X) return CASPT2_EINVAL;
   if (o.precision == CASPT2_BF16X && (o.slices < 1 || o.slices > 7)) return CASPT2_EINVAL;
   if (!(o.degen_thresh >= 0.0)) return CASPT2_EINVAL;
+  if (o.closed_begin < 0 || o.closed_begin > q.nclosed ||
+      (o.closed_end >= 0 && (o.closed_end < o.closed_begin || o.closed_end > q.nclosed)))
+    return CASPT2_EINVAL;
 
   caspt2_ctx* c = new (std::nothrow) caspt2_ctx();
   if (!c) return CASPT2_ENOMEM;
@@ -288,9 +299,12 @@ int caspt2_create(caspt2_ctx** out, const caspt2_dims* dims, const caspt2_option
           packmax = std::max(packmax, (long)X * dims3[t.ispace[2]] * dims3[t.ispace[3]]);
         }
       }
+      presum_src_plans(V, w.hVs, c->presum);
+      if (c->presum.size() > (size_t)kMaxPresum) st = CASPT2_EINVAL;
       ALLOC(w.dS, S.size());
       ALLOC(w.dF, F.size());
       ALLOC(w.dV, V.size());
+      ALLOC(w.dVs, w.hVs.size());
       if (st == CASPT2_OK && class_upload_plans(w, S, F, V) != cudaSuccess) st = CASPT2_ECUDA;
       ALLOC(w.Sact, 2 * (size_t)w.m * w.m);
       ALLOC(w.Fact, 2 * (size_t)w.m * w.m);
@@ -328,7 +342,9 @@ int caspt2_create(caspt2_ctx** out, const caspt2_dims* dims, const caspt2_option
       q.wcap = std::max<long>(std::min(wmax, kSectorWCap), mx * (long)n);
       q.pcap = std::max<long>(std::min(pmax, kSectorPartCap), pcol);
       q.nb2 = kColsumBlocks;
-      ALLOC(q.W, q.wcap); ALLOC(q.part, q.pcap); ALLOC(q.part2, q.nb2 * pcol);
+      // part2 also holds the per-eigenvector denominator minima and the refinement list
+      q.p2size = std::max<long>(q.nb2 * pcol, mx + 1);
+      ALLOC(q.W, q.wcap); ALLOC(q.part, q.pcap); ALLOC(q.part2, q.p2size);
       ALLOC(c->h, nmo * nmo);
       ALLOC(c->fact, a2);
       ALLOC(c->eps, nmo);
@@ -341,6 +357,12 @@ int caspt2_create(caspt2_ctx** out, const caspt2_dims* dims, const caspt2_option
         ALLOC(p, (size_t)std::max<long>(kv.second, 1));
         c->eri_blk[kv.first] = p;
         c->eri_tab.p[kv.first] = p;
+      }
+      for (size_t k = 0; k < c->presum.size() && st == CASPT2_OK; ++k) {
+        double* p = nullptr;
+        ALLOC(p, (size_t)std::max<long>(presum_size(d, c->presum[k]), 1));
+        c->presum_blk.push_back(p);
+        c->presum_tab.p[k] = p;
       }
       if (c->kmax >= 3) {
         ALLOC(c->rdm3, n * n * a2 * a2 * a2);
@@ -497,12 +519,14 @@ int solve_impl(caspt2_ctx* c, void* stream) {
                                         c->status, c->ecls + (long)CASPT2_CLASS_H * n * n,
                                         c->ncls + (long)CASPT2_CLASS_H * n,
                                         c->mom + (long)CASPT2_CLASS_H * msz, c->mindenom, c->oz,
-                                        c->hpack, c->hK, c->hKK, s));
+                                        c->hpack, c->hK, c->hKK, s, o.closed_begin,
+                                        o.closed_end));
   } else if (o.class_mask >> CASPT2_CLASS_H & 1u) {
     CASPT2_CUDA_TRY(launch_classH(c->f, c->B, c->Ftil, c->E0, o.shift, o.scheme, d, c->hw,
                                   c->status, c->ecls + (long)CASPT2_CLASS_H * n * n,
                                   c->ncls + (long)CASPT2_CLASS_H * n,
-                                  c->mom + (long)CASPT2_CLASS_H * msz, c->mindenom, s));
+                                  c->mom + (long)CASPT2_CLASS_H * msz, c->mindenom, s,
+                                  o.closed_begin, o.closed_end));
   }
   CASPT2_CUDA_TRY(cudaEventRecord(c->ev[2], s));
   // ---- stage 2: classes A-G
@@ -521,12 +545,19 @@ int solve_impl(caspt2_ctx* c, void* stream) {
         int sp4[4] = {kv.first / 27, (kv.first / 9) % 3, (kv.first / 3) % 3, kv.first % 3};
         CASPT2_CUDA_TRY(eri_block(c->B, d, sp4, c->pack0, c->pack1, kv.second, s, &c->oz));
       }
+      for (size_t k = 0; k < c->presum.size(); ++k) {
+        const PresumSpec& sp = c->presum[k];
+        const int key = ((sp.space[0] * 3 + sp.space[1]) * 3 + sp.space[2]) * 3 + sp.space[3];
+        CASPT2_CUDA_TRY(presum_block(d, sp, c->eri_blk.at(key), c->presum_blk[k], s));
+      }
       RdmPtrs g{{nullptr, c->rdm1r, c->rdm2r, c->rdm3r, c->rdm4r}};
       for (int k = 0; k < 7; ++k) {
         if (!c->cw_on[k]) continue;
+        // partial solves: classes A-F belong to the partition that starts at closed 0
+        if (k != CASPT2_CLASS_G && o.closed_begin > 0) continue;
         int st = class_solve(c->cw[k], c->sw, d, o.scheme, o.shift, o.ovl_thresh, g, c->fact, c->h,
-                             c->eri_tab, c->E0, c->eps, c->mom + (long)k * msz, c->mindenom, s,
-                             &c->tri);
+                             c->eri_tab, c->presum_tab, c->E0, c->eps, c->mom + (long)k * msz,
+                             c->mindenom, s, &c->tri, &c->oz, o.closed_begin, o.closed_end);
         if (st != CASPT2_OK) return st;
         CASPT2_CUDA_TRY(launch_moments_to_e(c->mom + (long)k * msz, n, c->ecls + (long)k * n * n,
                                             c->ncls + (long)k * n, s));
@@ -662,6 +693,62 @@ int caspt2_get_timings(caspt2_ctx* c, double* times, int* count) {
 
 long caspt2_get_kernel_launches(caspt2_ctx* c) { return c ? c->launches : -1; }
 
+int caspt2_get_moments(caspt2_ctx* c, double* mom) {
+  if (!c || !mom) return CASPT2_EINVAL;
+  if (!c->solved) return CASPT2_ESTATE;
+  const long n = c->d.n, msz = n * n * n + n * n + n;
+  CASPT2_CUDA_TRY(cudaSetDevice(c->device));
+  CASPT2_CUDA_TRY(cudaMemcpy(mom, c->mom, sizeof(double) * CASPT2_NCLASS * msz,
+                             cudaMemcpyDeviceToHost));
+  return CASPT2_OK;
+}
+
+int caspt2_finalize_moments(caspt2_ctx* c, const double* mom, void* stream) {
+  if (!c || !mom) return CASPT2_EINVAL;
+  if (!c->solved) return CASPT2_ESTATE;
+  CASPT2_CUDA_TRY(cudaSetDevice(c->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const caspt2_options& o = c->opt;
+  const int n = c->d.n;
+  const long msz = (long)n * n * n + n * n + n;
+  CASPT2_CUDA_TRY(cudaMemsetAsync(c->status, 0, sizeof(int), s));
+  CASPT2_CUDA_TRY(cudaMemcpyAsync(c->mom, mom, sizeof(double) * CASPT2_NCLASS * msz,
+                                  cudaMemcpyHostToDevice, s));
+  CASPT2_CUDA_TRY(cudaMemsetAsync(c->ecls, 0, sizeof(double) * CASPT2_NCLASS * n * n, s));
+  CASPT2_CUDA_TRY(cudaMemsetAsync(c->ncls, 0, sizeof(double) * CASPT2_NCLASS * n, s));
+  for (int k = 0; k < CASPT2_NCLASS; ++k) {
+    if (!(o.class_mask >> k & 1u)) continue;
+    CASPT2_CUDA_TRY(launch_moments_to_e(c->mom + (long)k * msz, n, c->ecls + (long)k * n * n,
+                                        c->ncls + (long)k * n, s));
+  }
+  CASPT2_CUDA_TRY(launch_heff(c->href, c->ecls, c->ncls, o.class_mask, o.shift, n, c->heff, s));
+  CASPT2_CUDA_TRY(launch_sym_eig(c->heff, n, c->R, c->ems, 0, c->status, s));
+  CASPT2_CUDA_TRY(cudaMemsetAsync(c->lamNL, 0, sizeof(double) * CASPT2_NCLASS * n, s));
+  CASPT2_CUDA_TRY(cudaMemsetAsync(c->lamLV, 0, sizeof(double) * CASPT2_NCLASS * n * n, s));
+  if (o.target_state >= 0) {
+    for (int k = 0; k < CASPT2_NCLASS; ++k) {
+      if (!(o.class_mask >> k & 1u)) continue;
+      CASPT2_CUDA_TRY(launch_lambda(c->mom + (long)k * msz, c->R, n, o.target_state, o.shift,
+                                    c->lamNL + (long)k * n, c->lamLV + (long)k * n * n, s));
+    }
+  }
+  int hst = 0;
+  CASPT2_CUDA_TRY(cudaMemcpyAsync(c->hHeff.data(), c->heff, sizeof(double) * n * n, cudaMemcpyDeviceToHost, s));
+  CASPT2_CUDA_TRY(cudaMemcpyAsync(c->hEms.data(), c->ems, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+  CASPT2_CUDA_TRY(cudaMemcpyAsync(c->hR.data(), c->R, sizeof(double) * n * n, cudaMemcpyDeviceToHost, s));
+  CASPT2_CUDA_TRY(cudaMemcpyAsync(c->hEcls.data(), c->ecls, sizeof(double) * CASPT2_NCLASS * n * n, cudaMemcpyDeviceToHost, s));
+  CASPT2_CUDA_TRY(cudaMemcpyAsync(c->hNcls.data(), c->ncls, sizeof(double) * CASPT2_NCLASS * n, cudaMemcpyDeviceToHost, s));
+  CASPT2_CUDA_TRY(cudaMemcpyAsync(c->hLamNL.data(), c->lamNL, sizeof(double) * CASPT2_NCLASS * n, cudaMemcpyDeviceToHost, s));
+  CASPT2_CUDA_TRY(cudaMemcpyAsync(c->hLamLV.data(), c->lamLV, sizeof(double) * CASPT2_NCLASS * n * n, cudaMemcpyDeviceToHost, s));
+  CASPT2_CUDA_TRY(cudaMemcpyAsync(&hst, c->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CASPT2_CUDA_TRY(cudaStreamSynchronize(s));
+  c->dens_done = false;
+  if (hst != 0) return hst;
+  for (double x : c->hEms)
+    if (!(x == x) || x > 1e300 || x < -1e300) return CASPT2_ENAN;
+  return CASPT2_OK;
+}
+
 }  // extern "C"
 
 namespace {
@@ -743,7 +830,8 @@ int caspt2_densities(caspt2_ctx* c, unsigned class_mask, void* stream) {
   if (!c) return CASPT2_EINVAL;
   if (!c->solved) return CASPT2_ESTATE;
   const caspt2_options& o = c->opt;
-  if (o.target_state < 0 || (class_mask & ~o.class_mask) || c->d.a > 16) return CASPT2_EINVAL;
+  if (o.target_state < 0 || (class_mask & ~o.class_mask) || c->d.a > 16 || c->partial())
+    return CASPT2_EINVAL;
   CASPT2_CUDA_TRY(cudaSetDevice(c->device));
   if (!c->dens_alloc) {
     const int st = alloc_densities(c);
@@ -820,7 +908,8 @@ int get_class_vector(caspt2_ctx* c, int cls, int L, int N, int mem, double* out,
   if (!c->solved) return CASPT2_ESTATE;
   const caspt2_options& o = c->opt;
   const Dims& d = c->d;
-  if (!c->cw_on[cls] || L < 0 || L >= d.n || N < 0 || N >= d.n || d.a > 16) return CASPT2_EINVAL;
+  if (!c->cw_on[cls] || L < 0 || L >= d.n || N < 0 || N >= d.n || d.a > 16 || c->partial())
+    return CASPT2_EINVAL;
   if (lam && o.target_state < 0) return CASPT2_EINVAL;
   CASPT2_CUDA_TRY(cudaSetDevice(c->device));
   if (!c->dens_alloc) {

@@ -70,9 +70,9 @@ __global__ void k_act_eval(const ActPlan* __restrict__ plans, int nplan, DevClas
 // Sources V[fam][ext...][act...][M][L] = <M~|E_Omega^dag H|L~> (Eq. ampeq).
 __global__ void k_src_eval(const SrcPlan* __restrict__ plans, int nplan, DevClass C, Dims d,
                            RdmPtrs g, const double* __restrict__ h, EriBlocks eri,
-                           double* __restrict__ V, long total) {
+                           PresumBlocks pb, double* __restrict__ V, long total) {
   const int n = d.n, a = d.a, nmo = d.nmo();
-  const int dimsp[3] = {d.c, d.a, d.v};
+  const int dimsp[4] = {d.c, d.a, d.v, 1};
   const int offsp[3] = {0, d.c, d.c + d.a};
   for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
        e += (long)gridDim.x * blockDim.x) {
@@ -80,6 +80,7 @@ __global__ void k_src_eval(const SrcPlan* __restrict__ plans, int nplan, DevClas
     const int L = r % n; r /= n;
     const int M = r % n; r /= n;
     int vals[24];
+    vals[kRefZero] = 0;
     for (int k = C.nact - 1; k >= 0; --k) {
       vals[kRefBra + C.act[k]] = r % a;
       r /= a;
@@ -105,6 +106,9 @@ __global__ void k_src_eval(const SrcPlan* __restrict__ plans, int nplan, DevClas
       if (P.kind == 1) {
         const int key = ((P.ispace[0] * 3 + P.ispace[1]) * 3 + P.ispace[2]) * 3 + P.ispace[3];
         blk = eri.p[key];
+        for (int j = 0; j < 4; ++j) bd[j] = dimsp[P.ispace[j]];
+      } else if (P.kind == 2) {
+        blk = pb.p[P.cb];
         for (int j = 0; j < 4; ++j) bd[j] = dimsp[P.ispace[j]];
       }
       double s = 0.0;
@@ -138,14 +142,15 @@ __global__ void k_src_eval(const SrcPlan* __restrict__ plans, int nplan, DevClas
 template <int NS>
 __global__ void k_src_eval_ml(const SrcPlan* __restrict__ plans, int nplan, DevClass C, Dims d,
                               RdmPtrs g, const double* __restrict__ h, EriBlocks eri,
-                              double* __restrict__ V, long total2) {
+                              PresumBlocks pb, double* __restrict__ V, long total2) {
   const int n = d.n, a = d.a, nmo = d.nmo();
-  const int dimsp[3] = {d.c, d.a, d.v};
+  const int dimsp[4] = {d.c, d.a, d.v, 1};
   const int offsp[3] = {0, d.c, d.c + d.a};
   for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total2;
        e += (long)gridDim.x * blockDim.x) {
     long r = e;
     int vals[24];
+    vals[kRefZero] = 0;
     for (int k = C.nact - 1; k >= 0; --k) {
       vals[kRefBra + C.act[k]] = r % a;
       r /= a;
@@ -173,6 +178,9 @@ __global__ void k_src_eval_ml(const SrcPlan* __restrict__ plans, int nplan, DevC
       if (P.kind == 1) {
         const int key = ((P.ispace[0] * 3 + P.ispace[1]) * 3 + P.ispace[2]) * 3 + P.ispace[3];
         blk = eri.p[key];
+        for (int j = 0; j < 4; ++j) bd[j] = dimsp[P.ispace[j]];
+      } else if (P.kind == 2) {
+        blk = pb.p[P.cb];
         for (int j = 0; j < 4; ++j) bd[j] = dimsp[P.ispace[j]];
       }
       const long stride = ipow(a, 2 * P.rank);
@@ -218,6 +226,123 @@ __global__ void k_src_eval_ml(const SrcPlan* __restrict__ plans, int nplan, DevC
   }
 }
 
+// Sources with one thread per (fam, ext, act, M) holding the n results over L (n <= NS):
+// fewer registers than the all-(M, L) variant, for larger state counts.
+template <int NS>
+__global__ void k_src_eval_m(const SrcPlan* __restrict__ plans, int nplan, DevClass C, Dims d,
+                              RdmPtrs g, const double* __restrict__ h, EriBlocks eri,
+                              PresumBlocks pb, double* __restrict__ V, long total2) {
+  const int n = d.n, a = d.a, nmo = d.nmo();
+  const int dimsp[4] = {d.c, d.a, d.v, 1};
+  const int offsp[3] = {0, d.c, d.c + d.a};
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total2 * n;
+       e += (long)gridDim.x * blockDim.x) {
+    const int Mt = (int)(e % n);
+    long r = e / n;
+    int vals[24];
+    vals[kRefZero] = 0;
+    for (int k = C.nact - 1; k >= 0; --k) {
+      vals[kRefBra + C.act[k]] = r % a;
+      r /= a;
+    }
+    for (int k = C.next - 1; k >= 0; --k) {
+      const int dm = dimsp[C.slot_space[C.ext[k]]];
+      vals[kRefBra + C.ext[k]] = r % dm;
+      r /= dm;
+    }
+    const int fam = (int)r;
+    double acc[NS];
+#pragma unroll
+    for (int q = 0; q < NS; ++q) acc[q] = 0.0;
+    for (int t = 0; t < nplan; ++t) {
+      const SrcPlan& P = plans[t];
+      if (P.fb != fam) continue;
+      bool ok = true;
+      for (int q = 0; q < P.neq; ++q)
+        if (vals[P.eq[q][0]] != vals[P.eq[q][1]]) ok = false;
+      if (!ok) continue;
+      long niter = 1;
+      for (int j = 0; j < P.nloop; ++j) niter *= dimsp[P.loop_space[j]];
+      const double* blk = nullptr;
+      long bd[4] = {1, 1, 1, 1};
+      if (P.kind == 1) {
+        const int key = ((P.ispace[0] * 3 + P.ispace[1]) * 3 + P.ispace[2]) * 3 + P.ispace[3];
+        blk = eri.p[key];
+        for (int j = 0; j < 4; ++j) bd[j] = dimsp[P.ispace[j]];
+      } else if (P.kind == 2) {
+        blk = pb.p[P.cb];
+        for (int j = 0; j < 4; ++j) bd[j] = dimsp[P.ispace[j]];
+      }
+      const long stride = ipow(a, 2 * P.rank);
+      for (long it = 0; it < niter; ++it) {
+        long q = it;
+        for (int j = 0; j < P.nloop; ++j) {
+          const int dm = dimsp[P.loop_space[j]];
+          vals[kRefLoop + j] = q % dm;
+          q /= dm;
+        }
+        double x;
+        if (P.kind == 0) {
+          x = h[(long)(offsp[P.ispace[0]] + vals[P.iidx[0]]) * nmo + offsp[P.ispace[1]] +
+                vals[P.iidx[1]]];
+        } else {
+          x = blk[((vals[P.iidx[0]] * bd[1] + vals[P.iidx[1]]) * bd[2] + vals[P.iidx[2]]) * bd[3] +
+                  vals[P.iidx[3]]];
+        }
+        if (x == 0.0) continue;
+        x *= P.coeff;
+        if (P.rank == 0) {
+#pragma unroll
+          for (int L = 0; L < NS; ++L)
+            if (L == Mt) acc[L] += x;
+        } else {
+          long off = 0;
+          for (int j = 0; j < 2 * P.rank; ++j) off = off * a + vals[P.idx[j]];
+          const double* gp = g.p[P.rank] + off + (long)Mt * n * stride;
+#pragma unroll
+          for (int L = 0; L < NS; ++L)
+            if (L < n) acc[L] += x * gp[(long)L * stride];
+        }
+      }
+    }
+    double* out = V + (e / n) * n * n + (long)Mt * n;
+#pragma unroll
+    for (int L = 0; L < NS; ++L)
+      if (L < n) out[L] = acc[L];
+  }
+}
+
+// Pre-summed block: out[i0][i1][i2][i3] (summed positions of size 1) = sum over the
+// summed variables' values of src at those indices (fixed order).
+__global__ void k_presum(const double* __restrict__ src, PresumSpec sp, int d0, int d1, int d2,
+                         int d3, double* __restrict__ out) {
+  const int sd[4] = {d0, d1, d2, d3};
+  int od[4], vd[2] = {1, 1};
+  for (int p = 0; p < 4; ++p) {
+    od[p] = sp.var[p] < 0 ? sd[p] : 1;
+    if (sp.var[p] >= 0) vd[sp.var[p]] = sd[p];
+  }
+  const long total = (long)od[0] * od[1] * od[2] * od[3];
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    int r[4];
+    long q = e;
+    for (int p = 3; p >= 0; --p) {
+      r[p] = (int)(q % od[p]);
+      q /= od[p];
+    }
+    double acc = 0.0;
+    for (int s0 = 0; s0 < vd[0]; ++s0)
+      for (int s1 = 0; s1 < vd[1]; ++s1) {
+        int x[4];
+        for (int p = 0; p < 4; ++p)
+          x[p] = sp.var[p] < 0 ? r[p] : (sp.var[p] == 0 ? s0 : s1);
+        acc += src[(((long)x[0] * sd[1] + x[1]) * sd[2] + x[2]) * sd[3] + x[3]];
+      }
+    out[e] = acc;
+  }
+}
+
 // Pack B[P][off0 + x][off1 + y] -> out[P][x][y]
 __global__ void k_pack_block(const double* __restrict__ B, int X, int nmo, int off0, int n0,
                              int off1, int n1, double* __restrict__ out) {
@@ -230,6 +355,11 @@ __global__ void k_pack_block(const double* __restrict__ B, int X, int nmo, int o
     const long P = r / n0;
     out[e] = B[(P * nmo + off0 + x) * nmo + off1 + y];
   }
+}
+
+__global__ void k_fill(double* __restrict__ x, long n, double v) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    x[i] = v;
 }
 
 // Sector matrices: out = sym(S_id + sgn S_sw) restricted to rows/cols with state Lsel
@@ -301,6 +431,255 @@ __global__ void k_sector_src(const double* __restrict__ V, DevClass C, ExtDims e
 //   M1[L][N][L'] += Vt_N Vt_L' / D_L (all L'),  M2[L][N] += Vt_N Vt_L / D_L^2,
 //   M3[L] += Vt_L^2 / D_L^3 (N == L),   D_L = e_ext(t) + omega_mu - E0_L + E_s.
 // part[t][Li][N][n + 2] (Li = L, or 0 under SS-SR where L = Lsel).
+// Same moment sums with one thread per (tuple, L) holding all N (n <= NS): each
+// denominator and its reciprocal are formed once and the row of Vt is read once.
+template <int NS>
+__global__ void k_sector_energy_ml(const double* __restrict__ Vt, const double* __restrict__ omega,
+                                   const double* __restrict__ E0, const double* __restrict__ eps,
+                                   DevClass C, ExtDims ed, int c, int n, int sector, int Lsel,
+                                   long ntup, long t0, long nt, int msec, double shift,
+                                   double* __restrict__ part, double* __restrict__ mindenom) {
+  const long ncol = ntup * n;
+  const int nL = Lsel < 0 ? n : 1;
+  const long total = nt * nL;
+  const int w = n + 2;
+  double dmin = 1e300;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    const int Li = e % nL;
+    const long tl = e / nL;
+    const long t = t0 + tl;
+    const int L = Lsel < 0 ? Li : Lsel;
+    int co[3], cs[3];
+    sector_tuple(C, ed.d, sector, t, co, cs);
+    double ee = 0.0;
+    for (int k = 0; k < C.next; ++k)
+      ee += (C.slot_space[C.ext[k]] == SP_V) ? eps[c + co[k]] : -eps[co[k]];
+    const double base = ee - E0[L] + shift;
+    double m1[NS * NS], m2[NS], m3 = 0.0;
+#pragma unroll
+    for (int q = 0; q < NS * NS; ++q) m1[q] = 0.0;
+#pragma unroll
+    for (int q = 0; q < NS; ++q) m2[q] = 0.0;
+    for (int mu = 0; mu < msec; ++mu) {
+      const double D = base + omega[mu];
+      const double inv = recip(D);
+      const double* row = Vt + (long)mu * ncol + t * n;
+      double r[NS];
+#pragma unroll
+      for (int q = 0; q < NS; ++q) r[q] = q < n ? row[q] : 0.0;
+      double rL = 0.0;
+#pragma unroll
+      for (int q = 0; q < NS; ++q) if (q == L) rL = r[q];
+      const double wL = rL * inv * inv;
+#pragma unroll
+      for (int N = 0; N < NS; ++N) {
+        const double vn = r[N] * inv;
+#pragma unroll
+        for (int q = 0; q < NS; ++q) m1[N * NS + q] = fma(vn, r[q], m1[N * NS + q]);
+        m2[N] = fma(r[N], wL, m2[N]);
+      }
+      m3 = fma(rL * rL * inv, inv * inv, m3);
+      dmin = fmin(dmin, fabs(D));
+    }
+#pragma unroll
+    for (int N = 0; N < NS; ++N) {
+      if (N >= n) continue;
+      double* o = part + (((tl * nL + Li) * n) + N) * w;
+#pragma unroll
+      for (int q = 0; q < NS; ++q)
+        if (q < n) o[q] = m1[N * NS + q];
+      o[n] = m2[N];
+      o[n + 1] = (N == L) ? m3 : 0.0;
+    }
+  }
+  __shared__ double red[32];
+  dmin = block_min(dmin, red);
+  if (threadIdx.x == 0) atomicMin_double(mindenom, dmin);
+}
+
+// Smallest |e_ext(t) + omega_mu - E0_L + E_s| over the tuples of the sector and the states
+// L of the scheme, for every eigenvector mu: mdn[mu] (order-independent minimum).
+__global__ void k_mu_mindenom(const double* __restrict__ omega, const double* __restrict__ E0,
+                              const double* __restrict__ eps, DevClass C, ExtDims ed, int c,
+                              int n, int sector, int Lsel, long ntup, int nk, double shift,
+                              double* __restrict__ mdn) {
+  __shared__ double red[32];
+  const int mu = blockIdx.y;
+  const int nL = Lsel < 0 ? n : 1;
+  double dmin = 1e300;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < ntup;
+       t += (long)gridDim.x * blockDim.x) {
+    int co[3], cs[3];
+    sector_tuple(C, ed.d, sector, t, co, cs);
+    double ee = 0.0;
+    for (int k = 0; k < C.next; ++k)
+      ee += (C.slot_space[C.ext[k]] == SP_V) ? eps[c + co[k]] : -eps[co[k]];
+    for (int Li = 0; Li < nL; ++Li) {
+      const int L = Lsel < 0 ? Li : Lsel;
+      dmin = fmin(dmin, fabs(ee + omega[mu] - E0[L] + shift));
+    }
+  }
+  dmin = block_min(dmin, red);
+  if (threadIdx.x == 0) atomicMin_double(mdn + mu, dmin);
+}
+
+// Double-double arithmetic from error-free transformations (Knuth's two-sum; the
+// product error of a fused multiply-add): a value is hi + lo with |lo| <= ulp(hi) / 2.
+struct DD { double hi, lo; };
+__device__ __forceinline__ DD dd_from_sum(double a, double b) {
+  const double s = a + b, bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ DD dd_add(DD x, DD y) {
+  DD s = dd_from_sum(x.hi, y.hi);
+  const double e = s.lo + x.lo + y.lo;
+  const double hi = s.hi + e;
+  return {hi, e - (hi - s.hi)};
+}
+// x + a * b with the product kept exactly
+__device__ __forceinline__ DD dd_add_prod(DD x, double a, double b) {
+  const double p = a * b, pe = fma(a, b, -p);
+  DD s = dd_from_sum(x.hi, p);
+  const double e = s.lo + x.lo + pe;
+  const double hi = s.hi + e;
+  return {hi, e - (hi - s.hi)};
+}
+__device__ __forceinline__ DD dd_shfl_down(DD x, int o) {
+  return {__shfl_down_sync(0xffffffffu, x.hi, o), __shfl_down_sync(0xffffffffu, x.lo, o)};
+}
+
+// Rayleigh quotient omega_mu = y^T F y / y^T S y of the sector eigenvectors y = Y[:, mu]
+// listed in `list`, in double-double.  The eigenvalue of a vector that is accurate to eps
+// is accurate to O(eps^2) in the quotient, so this removes the eigensolver's rounding from
+// the eigenvalues that sit next to a small denominator.  Stage 1: grid (row blocks,
+// eigenvectors), one warp per row, each block's partial sums (dd) of y_i (F y)_i and
+// y_i (S y)_i in a fixed order -> part[(list index * nrb + row block) * 4]; stage 2 sums
+// the row blocks in order and divides.
+constexpr int kRqThreads = 256;
+__global__ void __launch_bounds__(kRqThreads)
+k_rq_partial(const double* __restrict__ S, const double* __restrict__ F, int msec,
+             const double* __restrict__ Y, int nk, const int* __restrict__ list,
+             double* __restrict__ part) {
+  __shared__ DD accF[kRqThreads / 32], accS[kRqThreads / 32];
+  const int mu = list[blockIdx.y];
+  const int nrb = gridDim.x;
+  const int rows = (msec + nrb - 1) / nrb;
+  const int r0 = blockIdx.x * rows, r1 = min(msec, r0 + rows);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  DD nf{0.0, 0.0}, ns{0.0, 0.0};
+  for (int i = r0 + warp; i < r1; i += nw) {
+    DD uf{0.0, 0.0}, us{0.0, 0.0};
+    const double* fr = F + (long)i * msec;
+    const double* sr = S + (long)i * msec;
+    for (int j = lane; j < msec; j += 32) {
+      const double yj = Y[(long)j * nk + mu];
+      uf = dd_add_prod(uf, fr[j], yj);
+      us = dd_add_prod(us, sr[j], yj);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      uf = dd_add(uf, dd_shfl_down(uf, o));
+      us = dd_add(us, dd_shfl_down(us, o));
+    }
+    if (lane == 0) {
+      const double yi = Y[(long)i * nk + mu];
+      nf = dd_add(dd_add_prod(nf, yi, uf.hi), DD{yi * uf.lo, 0.0});
+      ns = dd_add(dd_add_prod(ns, yi, us.hi), DD{yi * us.lo, 0.0});
+    }
+  }
+  if (lane == 0) { accF[warp] = nf; accS[warp] = ns; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    DD tf = accF[0], ts = accS[0];
+    for (int w = 1; w < nw; ++w) { tf = dd_add(tf, accF[w]); ts = dd_add(ts, accS[w]); }
+    double* o = part + ((long)blockIdx.y * nrb + blockIdx.x) * 4;
+    o[0] = tf.hi; o[1] = tf.lo; o[2] = ts.hi; o[3] = ts.lo;
+  }
+}
+
+__global__ void k_rq_finish(const double* __restrict__ part, int nrb, const int* __restrict__ list,
+                            int nlist, double* __restrict__ omega) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nlist) return;
+  DD tf{0.0, 0.0}, ts{0.0, 0.0};
+  for (int b = 0; b < nrb; ++b) {
+    const double* o = part + ((long)q * nrb + b) * 4;
+    tf = dd_add(tf, DD{o[0], o[1]});
+    ts = dd_add(ts, DD{o[2], o[3]});
+  }
+  // (tf.hi + tf.lo) / (ts.hi + ts.lo) to double precision: one Newton correction
+  const double r0 = tf.hi / ts.hi;
+  const double p = r0 * ts.hi, pe = fma(r0, ts.hi, -p);
+  const double r = ((tf.hi - p) - pe + tf.lo - r0 * ts.lo) / ts.hi;
+  omega[list[q]] = r0 + r;
+}
+
+// Residual of the refined eigenpairs, r = F y - omega S y, in double-double per row
+// (a warp per row), rounded to double: R[i * nl + q] for list entry q.  Grid (row blocks,
+// list entries).
+__global__ void __launch_bounds__(kRqThreads)
+k_rq_resid(const double* __restrict__ S, const double* __restrict__ F, int msec,
+           const double* __restrict__ Y, int nk, const int* __restrict__ list, int nl,
+           const double* __restrict__ omega, double* __restrict__ R) {
+  const int q = blockIdx.y;
+  const int mu = list[q];
+  const double w = omega[mu];
+  const int nrb = gridDim.x;
+  const int rows = (msec + nrb - 1) / nrb;
+  const int r0 = blockIdx.x * rows, r1 = min(msec, r0 + rows);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int i = r0 + warp; i < r1; i += nw) {
+    DD uf{0.0, 0.0}, us{0.0, 0.0};
+    const double* fr = F + (long)i * msec;
+    const double* sr = S + (long)i * msec;
+    for (int j = lane; j < msec; j += 32) {
+      const double yj = Y[(long)j * nk + mu];
+      uf = dd_add_prod(uf, fr[j], yj);
+      us = dd_add_prod(us, sr[j], yj);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      uf = dd_add(uf, dd_shfl_down(uf, o));
+      us = dd_add(us, dd_shfl_down(us, o));
+    }
+    if (lane == 0) {
+      // (F y)_i - w (S y)_i with the product w (S y)_i kept exactly
+      DD r = dd_add_prod(uf, -w, us.hi);
+      r = dd_add(r, DD{-w * us.lo, 0.0});
+      R[(long)i * nl + q] = r.hi + r.lo;
+    }
+  }
+}
+
+// First-order correction coefficients of the refined eigenvectors from the other sector
+// eigenvectors: c_j = (y_j . r) / (omega_k - omega_j), zero for j = k and for eigenvalues
+// within 1e-12 of omega_k (a rotation inside a degenerate pair leaves the energies
+// unchanged).  Cm[j * nl + q] holds y_j . r on input.
+__global__ void k_rq_coef(double* __restrict__ Cm, int nk, const int* __restrict__ list, int nl,
+                          const double* __restrict__ omega) {
+  const long total = (long)nk * nl;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    const int j = (int)(e / nl), q = (int)(e % nl);
+    const int k = list[q];
+    const double gap = omega[k] - omega[j];
+    const double tol = 1e-12 * fmax(1.0, fabs(omega[k]));
+    Cm[e] = (j == k || fabs(gap) <= tol) ? 0.0 : Cm[e] / gap;
+  }
+}
+
+// Y[i][list[q]] += Dl[i * nl + q]
+__global__ void k_rq_apply(double* __restrict__ Y, int msec, int nk, const int* __restrict__ list,
+                           int nl, const double* __restrict__ Dl) {
+  const long total = (long)msec * nl;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / nl), q = (int)(e % nl);
+    Y[(long)i * nk + list[q]] += Dl[e];
+  }
+}
+
 // Tuples t0 .. t0 + nt - 1 of the sector (ntup in all; Vt has ntup * n columns); part
 // rows are local to the chunk.
 __global__ void k_sector_energy(const double* __restrict__ Vt, const double* __restrict__ omega,
@@ -624,12 +1003,34 @@ void class_keep_layout(ClassWork& w, const Dims& d, int scheme) {
     }
 }
 
+long presum_size(const Dims& d, const PresumSpec& sp) {
+  long n = 1;
+  for (int p = 0; p < 4; ++p) n *= sp.var[p] < 0 ? space_dim(d, sp.space[p]) : 1;
+  return n;
+}
+
+cudaError_t presum_block(const Dims& d, const PresumSpec& sp, const double* src, double* out,
+                         cudaStream_t s) {
+  const long total = presum_size(d, sp);
+  if (total == 0) return cudaSuccess;
+  ++launch_counter();
+  k_presum<<<launch_blocks(total), 256, 0, s>>>(src, sp, space_dim(d, sp.space[0]),
+                                                space_dim(d, sp.space[1]),
+                                                space_dim(d, sp.space[2]),
+                                                space_dim(d, sp.space[3]), out);
+  return cudaGetLastError();
+}
+
 cudaError_t class_upload_plans(ClassWork& w, const std::vector<ActPlan>& S,
                                const std::vector<ActPlan>& F, const std::vector<SrcPlan>& V) {
   cudaError_t e;
   if ((e = cudaMemcpy(w.dS, S.data(), sizeof(ActPlan) * S.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
   if ((e = cudaMemcpy(w.dF, F.data(), sizeof(ActPlan) * F.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
   if ((e = cudaMemcpy(w.dV, V.data(), sizeof(SrcPlan) * V.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+  if (w.dVs && (e = cudaMemcpy(w.dVs, w.hVs.data(), sizeof(SrcPlan) * w.hVs.size(),
+                               cudaMemcpyHostToDevice)) != cudaSuccess)
+    return e;
+  w.nVs = (int)w.hVs.size();
   w.nS = (int)S.size();
   w.nF = (int)F.size();
   w.nV = (int)V.size();
@@ -638,8 +1039,9 @@ cudaError_t class_upload_plans(ClassWork& w, const std::vector<ActPlan>& S,
 
 int class_solve(ClassWork& w, SectorWork& sw, const Dims& d, int scheme, double shift,
                 double thresh, RdmPtrs rdm, const double* f_act, const double* h,
-                const EriBlocks& eri, const double* E0, const double* eps_cv, double* mom,
-                double* mindenom, cudaStream_t s, KernelTimer* tm) {
+                const EriBlocks& eri, const PresumBlocks& pb, const double* E0,
+                const double* eps_cv, double* mom, double* mindenom, cudaStream_t s,
+                KernelTimer* tm, OzWork* oz, int ci0, int ci1) {
   const int m = w.m, n = d.n;
   if (w.vsize == 0 || m == 0) return CASPT2_OK;
   const long mm = (long)m * m;
@@ -651,15 +1053,15 @@ int class_solve(ClassWork& w, SectorWork& sw, const Dims& d, int scheme, double 
   ++launch_counter();
   if (n <= 4) {
     const long total2 = w.vsize / ((long)n * n);
-    k_src_eval_ml<4><<<launch_blocks(total2), 256, 0, s>>>(w.dV, w.nV, w.dc, d, rdm, h, eri, w.V,
-                                                          total2);
-  } else if (n <= 6) {
+    k_src_eval_ml<4><<<launch_blocks(total2), 256, 0, s>>>(w.dVs, w.nVs, w.dc, d, rdm, h, eri, pb,
+                                                          w.V, total2);
+  } else if (n <= 8) {
     const long total2 = w.vsize / ((long)n * n);
-    k_src_eval_ml<6><<<launch_blocks(total2), 256, 0, s>>>(w.dV, w.nV, w.dc, d, rdm, h, eri, w.V,
-                                                          total2);
+    k_src_eval_m<8><<<launch_blocks(total2 * n), 256, 0, s>>>(w.dVs, w.nVs, w.dc, d, rdm, h, eri,
+                                                              pb, w.V, total2);
   } else {
-    k_src_eval<<<launch_blocks(w.vsize), 256, 0, s>>>(w.dV, w.nV, w.dc, d, rdm, h, eri, w.V,
-                                                      w.vsize);
+    k_src_eval<<<launch_blocks(w.vsize), 256, 0, s>>>(w.dVs, w.nVs, w.dc, d, rdm, h, eri, pb,
+                                                      w.V, w.vsize);
   }
   CASPT2_CUDA_TRY(cudaGetLastError());
 
@@ -694,12 +1096,85 @@ int class_solve(ClassWork& w, SectorWork& sw, const Dims& d, int scheme, double 
       ++launch_counter();
       k_range_basis<<<launch_blocks((long)msec * nk), 256, 0, s>>>(sw.Qs, sw.s, msec, nk, sw.X);
       CASPT2_CUDA_TRY(cudaGetLastError());
-      CASPT2_CUDA_TRY(dgemm(msec, nk, msec, 1.0, sw.Fsec, msec, false, sw.X, nk, false, 0.0,
-                            sw.FX, nk, s));
-      CASPT2_CUDA_TRY(dgemm_sym(nk, msec, 1.0, sw.X, nk, true, sw.FX, nk, false, 0.0, sw.Ft, nk, s));
+      const bool ozx = oz && oz->on && oz->S >= kOzMaxSlices && msec >= kOzTransformMin;
+      if (ozx) {
+        // precision form, FP64-accurate split products (7 slices) for the sector
+        // transforms F X, X^T (F X) and X Q of the large sectors
+        const OzView vf{sw.Fsec, msec, 1, msec, 0}, vxt{sw.X, 1, nk, msec, 0};
+        CASPT2_CUDA_TRY(oz_matmul(*oz, vf, vxt, false, msec, nk, msec, 1.0, 0.0, sw.FX, nk, s));
+        const OzView vfx{sw.FX, 1, nk, msec, 0};
+        CASPT2_CUDA_TRY(oz_matmul(*oz, vxt, vfx, false, nk, nk, msec, 1.0, 0.0, sw.Ft, nk, s));
+        CASPT2_CUDA_TRY(launch_symmetrize(sw.Ft, nk, 1, s));
+      } else {
+        CASPT2_CUDA_TRY(dgemm(msec, nk, msec, 1.0, sw.Fsec, msec, false, sw.X, nk, false, 0.0,
+                              sw.FX, nk, s));
+        CASPT2_CUDA_TRY(dgemm_sym(nk, msec, 1.0, sw.X, nk, true, sw.FX, nk, false, 0.0, sw.Ft, nk,
+                                  s));
+      }
       st = sym_eig(sw.Ft, nk, K.omega, sw.Qf, sw.jac, s, tm);
       if (st != CASPT2_OK) return st;
-      CASPT2_CUDA_TRY(dgemm(msec, nk, nk, 1.0, sw.X, nk, false, sw.Qf, nk, false, 0.0, K.Y, nk, s));
+      if (ozx) {
+        const OzView vx{sw.X, nk, 1, nk, 0}, vq{sw.Qf, 1, nk, nk, 0};
+        CASPT2_CUDA_TRY(oz_matmul(*oz, vx, vq, false, msec, nk, nk, 1.0, 0.0, K.Y, nk, s));
+      } else {
+        CASPT2_CUDA_TRY(dgemm(msec, nk, nk, 1.0, sw.X, nk, false, sw.Qf, nk, false, 0.0, K.Y, nk,
+                              s));
+      }
+      {
+        // eigenvalues next to small denominators: Rayleigh quotients in double-double
+        // against the sector's S (rebuilt into Qs, free once X is formed) and F
+        double* mdn = sw.part2;      // nk minima (free until the column sums below)
+        if (nk > sw.p2size) return CASPT2_EINVAL;
+        const double big = 1e300;
+        ++launch_counter();
+        k_fill<<<launch_blocks(nk), 256, 0, s>>>(mdn, nk, big);
+        ++launch_counter();
+        k_mu_mindenom<<<dim3((unsigned)std::min<long>((ntup + 255) / 256, 64), nk), 256, 0, s>>>(
+            K.omega, E0, eps_cv, w.dc, w.ed, d.c, n, sec, Lsel, ntup, nk, shift, mdn);
+        CASPT2_CUDA_TRY(cudaGetLastError());
+        std::vector<double> hm(nk);
+        CASPT2_CUDA_TRY(cudaMemcpyAsync(hm.data(), mdn, sizeof(double) * nk, cudaMemcpyDeviceToHost, s));
+        CASPT2_CUDA_TRY(cudaStreamSynchronize(s));
+        std::vector<int> list;
+        for (int k = 0; k < nk; ++k)
+          if (hm[k] < kRefineDenom) list.push_back(k);
+        if (!list.empty()) {
+          // list (ints) at the start of part2, the stage-1 partials in W (free here)
+          const int nl = (int)list.size();
+          const int nrb = (int)std::max<long>(1, std::min<long>(
+              {(long)(msec + 63) / 64, 1216L / nl + 1, sw.wcap / (4L * nl)}));
+          if ((long)nl > sw.p2size || 4L * nl * nrb > sw.wcap) return CASPT2_EINVAL;
+          int* dlist = reinterpret_cast<int*>(sw.part2);
+          CASPT2_CUDA_TRY(cudaMemcpyAsync(dlist, list.data(), sizeof(int) * nl,
+                                          cudaMemcpyHostToDevice, s));
+          ++launch_counter();
+          k_sector<<<launch_blocks(ms2), 256, 0, s>>>(w.Sact, m, n, sgn, Lsel, sw.Qs, msec);
+          ++launch_counter();
+          k_rq_partial<<<dim3(nrb, nl), kRqThreads, 0, s>>>(sw.Qs, sw.Fsec, msec, K.Y, nk, dlist,
+                                                           sw.W);
+          ++launch_counter();
+          k_rq_finish<<<(nl + 127) / 128, 128, 0, s>>>(sw.W, nrb, dlist, nl, K.omega);
+          CASPT2_CUDA_TRY(cudaGetLastError());
+          // eigenvectors: y_k += sum_j c_j y_j with the double-double residual of (F, S)
+          double* R = sw.W;                                  // [msec][nl]
+          double* Cm = R + (long)msec * nl;                  // [nk][nl]
+          double* Dl = Cm + (long)nk * nl;                   // [msec][nl]
+          if ((long)(2 * msec + nk) * nl > sw.wcap) return CASPT2_EINVAL;
+          ++launch_counter();
+          k_rq_resid<<<dim3(nrb, nl), kRqThreads, 0, s>>>(sw.Qs, sw.Fsec, msec, K.Y, nk, dlist, nl,
+                                                         K.omega, R);
+          CASPT2_CUDA_TRY(cudaGetLastError());
+          CASPT2_CUDA_TRY(dgemm(nk, nl, msec, 1.0, K.Y, nk, true, R, nl, false, 0.0, Cm, nl, s));
+          ++launch_counter();
+          k_rq_coef<<<launch_blocks((long)nk * nl), 256, 0, s>>>(Cm, nk, dlist, nl, K.omega);
+          CASPT2_CUDA_TRY(cudaGetLastError());
+          CASPT2_CUDA_TRY(dgemm(msec, nl, nk, 1.0, K.Y, nk, false, Cm, nl, false, 0.0, Dl, nl, s));
+          ++launch_counter();
+          k_rq_apply<<<launch_blocks((long)msec * nl), 256, 0, s>>>(K.Y, msec, nk, dlist, nl, Dl);
+          CASPT2_CUDA_TRY(cudaGetLastError());
+          CASPT2_CUDA_TRY(cudaStreamSynchronize(s));   // the host list is released below
+        }
+      }
       const long ncol = ntup * n;
       const int nL = Lsel < 0 ? n : 1;
       const int pcol = nL * n * (n + 2);
@@ -708,19 +1183,47 @@ int class_solve(ClassWork& w, SectorWork& sw, const Dims& d, int scheme, double 
       long chunk = std::min<long>(ntup, sw.wcap / ((long)msec * n));
       chunk = std::min<long>(chunk, sw.pcap / pcol);
       if (chunk < 1 || (long)nk * ncol > (1L << 62)) return CASPT2_EINVAL;
-      for (long t0 = 0; t0 < ntup; t0 += chunk) {
-        const long nt = std::min(chunk, ntup - t0);
+      // class G under a closed-orbital range: the sector tuples are ordered with the
+      // closed index slowest, so the range is a contiguous run of them
+      long tb = 0, te = ntup;
+      if (w.cls == CASPT2_CLASS_G && (ci0 > 0 || (ci1 >= 0 && ci1 < d.c))) {
+        const long per_i = ntup / d.c;
+        tb = (long)ci0 * per_i;
+        te = (long)(ci1 < 0 || ci1 > d.c ? d.c : ci1) * per_i;
+      }
+      for (long t0 = tb; t0 < te; t0 += chunk) {
+        const long nt = std::min(chunk, te - t0);
         ++launch_counter();
         k_sector_src<<<launch_blocks((long)msec * nt * n), 256, 0, s>>>(
             w.V, w.dc, w.ed, d.a, n, sec, Lsel, t0, nt, msec, sw.W);
         CASPT2_CUDA_TRY(cudaGetLastError());
-        CASPT2_CUDA_TRY(dgemm(nk, (int)(nt * n), msec, 1.0, K.Y, nk, true, sw.W, (int)(nt * n),
-                              false, 0.0, K.Vt + t0 * n, (int)ncol, s));
-        const long ne = nt * nL * n;
+        if (oz && oz->on && oz->S >= kOzMaxSlices) {
+          // precision form with every product FP64-accurate (7 slices): the sector
+          // transform as a split-BF16 tensor-core product (fewer slices keep it in FP64:
+          // the energies are first order in its rounding)
+          const OzView vy{K.Y, 1, nk, msec, 0};               // rows mu, K = sector row
+          const OzView vw{sw.W, 1, nt * n, msec, 0};           // rows (t, L'), K = sector row
+          CASPT2_CUDA_TRY(oz_matmul(*oz, vy, vw, false, nk, (int)(nt * n), msec, 1.0, 0.0,
+                                    K.Vt + t0 * n, ncol, s));
+        } else {
+          CASPT2_CUDA_TRY(dgemm(nk, (int)(nt * n), msec, 1.0, K.Y, nk, true, sw.W,
+                                (int)(nt * n), false, 0.0, K.Vt + t0 * n, (int)ncol, s));
+        }
         ++launch_counter();
-        k_sector_energy<<<launch_blocks(ne), 256, 0, s>>>(K.Vt, K.omega, E0, eps_cv, w.dc, w.ed,
-                                                          d.c, n, sec, Lsel, ntup, t0, nt, nk,
-                                                          shift, sw.part, mindenom);
+        if (n <= 4) {
+          k_sector_energy_ml<4><<<launch_blocks(nt * nL), 256, 0, s>>>(
+              K.Vt, K.omega, E0, eps_cv, w.dc, w.ed, d.c, n, sec, Lsel, ntup, t0, nt, nk, shift,
+              sw.part, mindenom);
+        } else if (n <= 6) {
+          k_sector_energy_ml<6><<<launch_blocks(nt * nL), 256, 0, s>>>(
+              K.Vt, K.omega, E0, eps_cv, w.dc, w.ed, d.c, n, sec, Lsel, ntup, t0, nt, nk, shift,
+              sw.part, mindenom);
+        } else {
+          const long ne = nt * nL * n;
+          k_sector_energy<<<launch_blocks(ne), 256, 0, s>>>(K.Vt, K.omega, E0, eps_cv, w.dc, w.ed,
+                                                            d.c, n, sec, Lsel, ntup, t0, nt, nk,
+                                                            shift, sw.part, mindenom);
+        }
         // fixed-order column sums: row blocks, then the block partials in order
         const long nb = std::min<long>(sw.nb2, std::max<long>(1, nt / 64));
         ++launch_counter();

@@ -19,6 +19,8 @@ struct DevClass {
 struct RdmPtrs { const double* p[5]; };      // p[k] = rotated k-RDM [n][n][a^{2k}]
 struct EriBlocks { const double* p[81]; };   // (pq|rt) blocks keyed by the spaces of p,q,r,t
 struct ExtDims { int d[3]; };
+constexpr int kMaxPresum = 64;
+struct PresumBlocks { const double* p[kMaxPresum]; };   // pre-summed (pq|rt) blocks by spec
 
 __device__ __forceinline__ void atomicMin_double(double* addr, double v) {
   if (!(v >= 0.0)) return;
@@ -44,6 +46,8 @@ struct ClassWork {
   ActPlan* dS = nullptr; int nS = 0;
   ActPlan* dF = nullptr; int nF = 0;
   SrcPlan* dV = nullptr; int nV = 0;
+  SrcPlan* dVs = nullptr; int nVs = 0;   // the solve's variant: loop-only integrals pre-summed
+  std::vector<SrcPlan> hVs;
   double *Sact = nullptr, *Fact = nullptr, *V = nullptr;
   std::vector<SectorKeep> keep;   // one per (sector, SS-SR state), see class_keep_layout
 };
@@ -55,12 +59,19 @@ struct SectorWork {
   long wcap = 0, pcap = 0;   // doubles held by W and part (the sector pass runs in tuple
                              // chunks that fit them)
   long nb2 = 0;              // row blocks of the first column-sum stage (part2: nb2 x pcol)
+  long p2size = 0;           // doubles held by part2
 };
 // Upper bounds on the solve's sector work arrays W and part (doubles): larger sectors are
 // processed in tuple chunks.
 constexpr long kSectorWCap = 1L << 28;
 constexpr long kSectorPartCap = 1L << 27;
 constexpr long kColsumBlocks = 1216;
+// Sector eigenvalues whose smallest |denominator| is below this (Eh) are refined by a
+// double-double Rayleigh quotient before the energies are formed.
+constexpr double kRefineDenom = 1e-2;
+// Sector size from which the precision form (7 slices) runs the sector transforms F X,
+// X^T F X and X Q as split-BF16 tensor-core products.
+constexpr int kOzTransformMin = 1024;
 
 // Work space of the class densities (sized by the caller, see density_ag.cu).
 struct DensWork {
@@ -97,8 +108,13 @@ cudaError_t class_upload_plans(ClassWork& w, const std::vector<ActPlan>& S,
 // mom = [M1: n^3][M2: n^2][M3: n] (see k_sector_energy).
 int class_solve(ClassWork& w, SectorWork& sw, const Dims& d, int scheme, double shift,
                 double thresh, RdmPtrs rdm, const double* f, const double* h, const EriBlocks& eri,
-                const double* E0, const double* eps_cv, double* mom, double* mindenom,
-                cudaStream_t s, KernelTimer* tm = nullptr);
+                const PresumBlocks& pb, const double* E0, const double* eps_cv, double* mom,
+                double* mindenom, cudaStream_t s, KernelTimer* tm = nullptr,
+                OzWork* oz = nullptr, int ci0 = 0, int ci1 = -1);
+// Doubles of a pre-summed block, and its evaluation from the (pq|rt) block of its spaces.
+long presum_size(const Dims& d, const PresumSpec& sp);
+cudaError_t presum_block(const Dims& d, const PresumSpec& sp, const double* src, double* out,
+                         cudaStream_t s);
 // e = -M1[L][L][.], norm = M2[L][L] of one class
 cudaError_t launch_moments_to_e(const double* mom, int n, double* e, double* nr, cudaStream_t s);
 // lambda pieces of the target state P of one class from its moments and R

@@ -68,7 +68,7 @@ __global__ void k_classH_shifts(const double* __restrict__ omega, const double* 
 __global__ void __launch_bounds__(kHThreads)
 k_classH(const double* __restrict__ Bp, const double* __restrict__ eps,
          const double* __restrict__ shifts, int nshift, int c, int v, int X, int ntile,
-         double* __restrict__ partial) {
+         int pair0, double* __restrict__ partial) {
   __shared__ double sbuf[4 * kHK * kHT];   // operand tiles; reused for the diagonal transpose
   __shared__ double sEa[kHT], sEb[kHT];
   __shared__ double sShift[kMaxShift];
@@ -81,7 +81,7 @@ k_classH(const double* __restrict__ Bp, const double* __restrict__ eps,
   const int ntp = ntile * (ntile + 1) / 2;
   long bid = blockIdx.x;
   int tp = bid % ntp;
-  int pair = (int)(bid / ntp), i = 0;
+  int pair = pair0 + (int)(bid / ntp), i = 0;
   while (pair >= c - i) { pair -= c - i; ++i; }
   const int j = i + pair;
   int ta = 0;
@@ -268,9 +268,10 @@ __global__ void k_classH_combine(const double* __restrict__ sums, const double* 
 }
 
 // Split form: KK[(ia)][(jb)] = K_ij^ab (2 K_ij^ab - K_ij^ba) from the full K matrix.
-__global__ void k_classH_num(const double* __restrict__ K, int c, int v, double* __restrict__ KK) {
-  const long cv = (long)c * v, total = cv * cv;
-  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+__global__ void k_classH_num(const double* __restrict__ K, int c, int v, int i0, int i1,
+                             double* __restrict__ KK) {
+  const long cv = (long)c * v, e0 = (long)i0 * v * cv, total = (long)i1 * v * cv;
+  for (long e = e0 + blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
        e += (long)gridDim.x * blockDim.x) {
     const long ia = e / cv, jb = e % cv;
     const int i = ia / v, a = ia % v, j = jb / v, b = jb % v;
@@ -285,25 +286,35 @@ __global__ void k_classH_num(const double* __restrict__ K, int c, int v, double*
 // fixed-order column reduction of the fused kernel applies unchanged.
 __global__ void k_classH_sums(const double* __restrict__ KK, const double* __restrict__ eps,
                               const double* __restrict__ shifts, int nshift, int c, int v,
-                              double* __restrict__ partial) {
+                              int i0, int i1, double* __restrict__ partial) {
   __shared__ double red[32];
   const int k = blockIdx.y;
   const double sh = shifts[k];
-  const long cv = (long)c * v, total = cv * cv;
-  double e = 0.0, nr = 0.0, n3 = 0.0, dmin = 1e300;
-  for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < total;
-       q += (long)gridDim.x * blockDim.x) {
-    const long ia = q / cv, jb = q % cv;
-    const int i = ia / v, a = ia % v, j = jb / v, b = jb % v;
-    const double num = KK[q];
-    const double D = eps[c + a] + eps[c + b] - eps[i] - eps[j] + sh;
-    const double inv = 1.0 / D;
-    const double x = num * inv;
-    e += x;
-    nr = fma(x, inv, nr);
-    n3 = fma(x * inv, inv, n3);
-    if (num != 0.0) dmin = fmin(dmin, fabs(D));
+  const long cv = (long)c * v;
+  double e = 0.0, nr = 0.0, n3 = 0.0;
+  float dminf = 3.0e38f;   // smallest |D| (single precision suffices for the warning)
+  // rows (i, a) over the blocks, (j, b) of a row over the threads: index arithmetic once
+  // per row and per j, not per element
+  for (long ia = (long)i0 * v + blockIdx.x; ia < (long)i1 * v; ia += gridDim.x) {
+    const int i = (int)(ia / v), a = (int)(ia % v);
+    const double base = eps[c + a] - eps[i] + sh;
+    const double* row = KK + ia * cv;
+    for (int j = 0; j < c; ++j) {
+      const double bj = base - eps[j];
+      const double* rj = row + (long)j * v;
+      for (int b = threadIdx.x; b < v; b += blockDim.x) {
+        const double num = rj[b];
+        const double D = bj + eps[c + b];
+        const double inv = recip(D);
+        const double x = num * inv;
+        e += x;
+        nr = fma(x, inv, nr);
+        n3 = fma(x * inv, inv, n3);
+        if ((__double_as_longlong(num) << 1) != 0) dminf = fminf(dminf, fabsf((float)D));
+      }
+    }
   }
+  double dmin = dminf < 3.0e38f ? (double)dminf : 1e300;
   const int ncol = 3 * nshift + 1;
   double* out = partial + ((long)blockIdx.y * gridDim.x + blockIdx.x) * ncol;
   for (int t = threadIdx.x; t < 3 * nshift; t += blockDim.x) out[t] = 0.0;
@@ -336,7 +347,7 @@ int classH_nshift(const Dims& d, int scheme) { return scheme == CASPT2_SSSR ? 1 
 cudaError_t launch_classH(const double* f, const double* B, const double* Ftil, const double* E0,
                           double shift, int scheme, const Dims& d, ClassHWork& w, int* status,
                           double* ecls, double* ncls, double* mom, double* mindenom,
-                          cudaStream_t s) {
+                          cudaStream_t s, int i0, int i1) {
   const int n = d.n, nmo = d.nmo();
   const int nshift = classH_nshift(d, scheme);
   cudaError_t e;
@@ -356,11 +367,22 @@ cudaError_t launch_classH(const double* f, const double* B, const double* Ftil, 
   ++launch_counter();
   k_classH_shifts<<<1, kMaxShift, 0, s>>>(w.omega, E0, shift, n, scheme, w.shifts);
   const int ntile = (d.v + kHT - 1) / kHT;
-  const long nb = classH_blocks(d);
+  if (i1 < 0 || i1 > d.c) i1 = d.c;
+  // pairs (i <= j) with i in [i0, i1): a contiguous run of the row-major pair order
+  auto start = [&](long i) { return i * d.c - i * (i - 1) / 2; };
+  const long pair0 = start(i0), npair = start(i1) - start(i0);
+  const long nb = npair * ((long)ntile * (ntile + 1) / 2);
+  if (nb == 0) {
+    e = cudaMemsetAsync(ecls, 0, sizeof(double) * n * n, s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(mom, 0, sizeof(double) * (n * n * n + n * n + n), s);
+    if (e != cudaSuccess) return e;
+    return cudaMemsetAsync(ncls, 0, sizeof(double) * n, s);
+  }
   if (w.ev_gemm0) cudaEventRecord(w.ev_gemm0, s);
   ++launch_counter();
   k_classH<<<(unsigned)nb, kHThreads, 0, s>>>(w.Bp, w.eps, w.shifts, nshift, d.c, d.v, d.X, ntile,
-                                             w.partial);
+                                             (int)pair0, w.partial);
   if (w.ev_gemm1) cudaEventRecord(w.ev_gemm1, s);
   const int ncol = 3 * nshift + 1;
   ++launch_counter();
@@ -374,7 +396,7 @@ cudaError_t launch_classH_split(const double* f, const double* B, const double* 
                                 const double* E0, double shift, int scheme, const Dims& d,
                                 ClassHWork& w, int* status, double* ecls, double* ncls,
                                 double* mom, double* mindenom, OzWork& oz, double* pack,
-                                double* K, double* KK, cudaStream_t s) {
+                                double* K, double* KK, cudaStream_t s, int i0, int i1) {
   const int n = d.n, nmo = d.nmo();
   const int nshift = classH_nshift(d, scheme);
   cudaError_t e;
@@ -390,18 +412,36 @@ cudaError_t launch_classH_split(const double* f, const double* B, const double* 
   ++launch_counter();
   k_classH_shifts<<<1, kMaxShift, 0, s>>>(w.omega, E0, shift, n, scheme, w.shifts);
   const long cv = (long)d.c * d.v;
+  if (i1 < 0 || i1 > d.c) i1 = d.c;
+  if (i1 <= i0) {
+    e = cudaMemsetAsync(ecls, 0, sizeof(double) * n * n, s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(mom, 0, sizeof(double) * (n * n * n + n * n + n), s);
+    if (e != cudaSuccess) return e;
+    return cudaMemsetAsync(ncls, 0, sizeof(double) * n, s);
+  }
   if ((e = launch_pack_block(B, d, SP_C, SP_V, pack, s)) != cudaSuccess) return e;
   if (w.ev_gemm0) cudaEventRecord(w.ev_gemm0, s);
+  // rows (ia) with i in [i0, i1) of K = Bcv^T Bcv (the whole K for the full range); the
+  // exchange partner K(aj|bi) = K(bi|aj) lies in the same rows
+  const long r0 = (long)i0 * d.v, nr = (long)(i1 - i0) * d.v;
   const OzView vp{pack, 1, cv, (long)d.X, 0};     // rows (ia), K = Q
-  if ((e = oz_matmul(oz, vp, vp, true, (int)cv, (int)cv, d.X, 1.0, 0.0, K, cv, s)) != cudaSuccess)
+  const OzView vr{pack + r0, 1, cv, (long)d.X, 0};
+  if (nr == cv) {
+    if ((e = oz_matmul(oz, vp, vp, true, (int)cv, (int)cv, d.X, 1.0, 0.0, K, cv, s)) != cudaSuccess)
+      return e;
+  } else if ((e = oz_matmul(oz, vr, vp, false, (int)nr, (int)cv, d.X, 1.0, 0.0, K + r0 * cv, cv,
+                            s)) != cudaSuccess) {
     return e;
+  }
   if (w.ev_gemm1) cudaEventRecord(w.ev_gemm1, s);
-  const long total = cv * cv;
+  const long total = nr * cv;
   ++launch_counter();
-  k_classH_num<<<(int)std::min<long>((total + 255) / 256, 152L * 32), 256, 0, s>>>(K, d.c, d.v, KK);
+  k_classH_num<<<(int)std::min<long>((total + 255) / 256, 152L * 32), 256, 0, s>>>(K, d.c, d.v, i0,
+                                                                                  i1, KK);
   const int nblk = (int)std::max<long>(1, std::min<long>(w.nblocks / nshift, 152L * 4));
   ++launch_counter();
-  k_classH_sums<<<dim3(nblk, nshift), 256, 0, s>>>(KK, w.eps, w.shifts, nshift, d.c, d.v,
+  k_classH_sums<<<dim3(nblk, nshift), 256, 0, s>>>(KK, w.eps, w.shifts, nshift, d.c, d.v, i0, i1,
                                                    w.partial);
   const int ncol = 3 * nshift + 1;
   ++launch_counter();

@@ -39,6 +39,19 @@ __device__ __forceinline__ double block_sum(double v, double* smem32) {
   return v;
 }
 
+// 1/d for the energy denominators: Newton's iteration x <- x + x (1 - d x) from the
+// hardware's approximate double reciprocal (rcp.approx.ftz.f64, about 20 correct bits);
+// two steps take the seed past double precision (error within an ulp or so).  d must be
+// a normal number.
+__device__ __forceinline__ double recip(double d) {
+  double x;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(x) : "d"(d));
+  double e = fma(-d, x, 1.0);
+  x = fma(x, e, x);
+  e = fma(-d, x, 1.0);
+  return fma(x, e, x);
+}
+
 __device__ __forceinline__ double block_min(double v, double* smem32) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nwarp = (blockDim.x + 31) >> 5;

@@ -12,6 +12,7 @@
 #include <cstring>
 #include <vector>
 
+#include "class_ag.cuh"
 #include "linalg.cuh"
 
 namespace caspt2 {
@@ -215,6 +216,162 @@ k_tridiag(double* __restrict__ A, int m, double* __restrict__ vbuf, double* __re
     if (blockIdx.x == 0 && k + 3 < m) {
       __syncthreads();
       house_row(A, m, k + 1, vbuf, tau, d, e, red, sh);
+    }
+    if (!grid_sync_bounded(sync, sync + 1, err)) return;
+  }
+}
+
+// Blocked Householder reduction, one cooperative launch per panel of b columns
+// k0 .. k0+b-1 (the LAPACK dlatrd scheme, written from its definition): the trailing
+// matrix is left as it stands during the panel and its true value is
+// A22 - V W^T - W V^T, with V the panel's reflectors (rows of vbuf) and W the vectors
+// w = p - (tau/2)(p.v) v, p = tau (A22 - V W^T - W V^T) v.  After the panel the host
+// applies A22 -= V W^T + W V^T as two FP64 GEMMs.  Per column k = k0 + j, three bounded
+// grid barriers; blocks own contiguous runs of the rows (and of the columns of row k+1):
+//   A: every block forms the reflector of row k from the row (already up to date) into
+//      shared memory -- the reductions run in a fixed order, so every copy is the same;
+//      block 0 stores it (vbuf, tau, d, e);
+//   B: p_raw = A22 v (a warp per row) and partial sums of W^T v and V^T v;   | barrier
+//   C: p = tau (p_raw - V (W^T v) - W (V^T v)) and partial sums of p.v;     | barrier
+//   D: alpha = (tau/2) p.v, W[:, j] = p - alpha v, and the owned columns of row k+1
+//      brought up to date with the panel's columns 0..j.                    | barrier
+// W is [m][nb] row-major; p, pr [m]; part [grid][2 nb + 1]; sync[0..1] barrier, [2] error.
+// Dynamic shared memory: v [m].
+constexpr int kLatrdPanel = 64;
+constexpr int kLatrdMin = 1024;     // sizes at which the blocked reduction is used (when
+                                    // the rows do not fit in shared memory)
+__global__ void __launch_bounds__(512)
+k_latrd(double* __restrict__ A, int m, int k0, int b, double* __restrict__ vbuf,
+        double* __restrict__ tau, double* __restrict__ d, double* __restrict__ e,
+        double* __restrict__ W, double* __restrict__ p, double* __restrict__ pr,
+        double* __restrict__ part, unsigned* sync) {
+  constexpr int nb = kLatrdPanel;
+  extern __shared__ double vs[];                      // v of the current column, by row
+  __shared__ double red[32];
+  __shared__ double sh[4];
+  __shared__ double xy[2 * nb];
+  int* err = reinterpret_cast<int*>(sync + 2);
+  const int G = gridDim.x, bid = blockIdx.x;
+  const int warp = (bid * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const int nw = (G * blockDim.x) >> 5;
+  for (int j = 0; j < b; ++j) {
+    const int k = k0 + j;
+    const int n1 = m - k - 1;
+    // ---- A: reflector of row k (every block; block 0 stores it)
+    {
+      const double* x = A + (long)k * m + k + 1;
+      double s2 = 0.0;
+      for (int i = 1 + threadIdx.x; i < n1; i += blockDim.x) {
+        const double xi = __ldcg(x + i);
+        s2 = fma(xi, xi, s2);
+      }
+      s2 = block_sum(s2, red);
+      if (threadIdx.x == 0) {
+        const double alpha = __ldcg(x);
+        double beta, t, scale;
+        if (s2 == 0.0) { beta = alpha; t = 0.0; scale = 0.0; }
+        else {
+          beta = -copysign(sqrt(alpha * alpha + s2), alpha);
+          t = (beta - alpha) / beta;
+          scale = 1.0 / (alpha - beta);
+        }
+        sh[0] = t;
+        sh[1] = scale;
+        if (bid == 0) {
+          tau[k] = t;
+          d[k] = __ldcg(A + (long)k * m + k);
+          e[k] = beta;
+        }
+      }
+      __syncthreads();
+      const double scale = sh[1];
+      for (int i = threadIdx.x; i < n1; i += blockDim.x) {
+        const double vi = (i == 0) ? 1.0 : __ldcg(x + i) * scale;
+        vs[k + 1 + i] = vi;
+        if (bid == 0) vbuf[(long)k * m + k + 1 + i] = vi;
+      }
+      __syncthreads();
+    }
+    const double t = sh[0];
+    const int R = (n1 + G - 1) / G;                   // rows (and row-k+1 columns) owned
+    const int r0 = k + 1 + bid * R, r1 = min(m, r0 + R);
+    // ---- B: p_raw = A22 v over rows >= k+1; partials of W^T v, V^T v (columns l < j)
+    for (int i = warp; i < n1; i += nw) {
+      const double* row = A + (long)(k + 1 + i) * m;
+      double s0 = 0.0, s1 = 0.0;
+      int q = k + 1 + lane;
+      for (; q + 32 < m; q += 64) {
+        s0 = fma(__ldcg(row + q), vs[q], s0);
+        s1 = fma(__ldcg(row + q + 32), vs[q + 32], s1);
+      }
+      if (q < m) s0 = fma(__ldcg(row + q), vs[q], s0);
+      double sum = s0 + s1;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
+      if (lane == 0) pr[k + 1 + i] = sum;
+    }
+    if (threadIdx.x < 2 * j) {
+      const int tq = threadIdx.x;
+      const int l = tq < j ? tq : tq - j;
+      double acc = 0.0;
+      for (int i = r0; i < r1; ++i) {
+        const double c = tq < j ? __ldcg(W + (long)i * nb + l) : __ldcg(vbuf + (long)(k0 + l) * m + i);
+        acc = fma(c, vs[i], acc);
+      }
+      part[(long)bid * (2 * nb + 1) + tq] = acc;
+    }
+    if (!grid_sync_bounded(sync, sync + 1, err)) return;
+    // ---- C: p = tau (p_raw - V x - W y), x = W^T v, y = V^T v; partials of p . v
+    for (int q = threadIdx.x; q < 2 * j; q += blockDim.x) {
+      double acc = 0.0;
+      for (int g = 0; g < G; ++g) acc += __ldcg(part + (long)g * (2 * nb + 1) + q);
+      xy[q] = acc;
+    }
+    __syncthreads();
+    {
+      double sp = 0.0;
+      for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+        double c = __ldcg(pr + i);
+        for (int l = 0; l < j; ++l)
+          c -= __ldcg(vbuf + (long)(k0 + l) * m + i) * xy[l] + __ldcg(W + (long)i * nb + l) * xy[j + l];
+        c *= t;
+        p[i] = c;
+        sp = fma(c, vs[i], sp);
+      }
+      sp = block_sum(sp, red);
+      if (threadIdx.x == 0) part[(long)bid * (2 * nb + 1) + 2 * nb] = sp;
+    }
+    if (!grid_sync_bounded(sync, sync + 1, err)) return;
+    // ---- D: alpha = (tau/2) p.v (fixed order over the blocks), W[:, j] = p - alpha v;
+    //         the owned columns of row k+1 brought up to date (not after the panel's last
+    //         column: the trailing GEMM update takes over there)
+    if (threadIdx.x == 0) {
+      double sum = 0.0;
+      for (int g = 0; g < G; ++g) sum += __ldcg(part + (long)g * (2 * nb + 1) + 2 * nb);
+      sh[2] = 0.5 * t * sum;
+    }
+    __syncthreads();
+    const double alpha = sh[2];
+    for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x)
+      W[(long)i * nb + j] = __ldcg(p + i) - alpha * vs[i];
+    if (bid == 0)
+      for (int i = threadIdx.x; i <= k; i += blockDim.x) W[(long)i * nb + j] = 0.0;
+    if (j + 1 < b) {
+      const int k1 = k + 1;
+      // row k1 of V and W over l <= j (W[k1][j] formed here; p[k1] is visible)
+      const double wk1j = __ldcg(p + k1) - alpha * vs[k1];
+      for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+        double a = __ldcg(A + (long)k1 * m + i);
+        for (int l = 0; l <= j; ++l) {
+          const double* vl = vbuf + (long)(k0 + l) * m;
+          const double vk = (l == j) ? vs[k1] : __ldcg(vl + k1);
+          const double vi = (l == j) ? vs[i] : __ldcg(vl + i);
+          const double wk = (l == j) ? wk1j : __ldcg(W + (long)k1 * nb + l);
+          const double wi = (l == j) ? (__ldcg(p + i) - alpha * vs[i]) : __ldcg(W + (long)i * nb + l);
+          a -= vk * wi + wk * vi;
+        }
+        A[(long)k1 * m + i] = a;
+      }
     }
     if (!grid_sync_bounded(sync, sync + 1, err)) return;
   }
@@ -856,7 +1013,64 @@ __global__ void k_zupd(const double* __restrict__ vbuf, int m, int k,
   }
 }
 
+// Compact WY form of a panel of reflectors (Schreiber and Van Loan): H_k0 ... H_k0+b-1 =
+// I - Vp T Vp^T with T upper triangular, T_ii = tau_i and
+// T_{j,i} = -tau_i sum_{l = j..i-1} T_{j,l} (v_l . v_i) (j < i).  One block of b threads;
+// Gp[l][i] = v_{k0+l} . v_{k0+i}.
+__global__ void k_wy_T(const double* __restrict__ Gp, const double* __restrict__ tau, int k0,
+                       int b, double* __restrict__ T) {
+  const int j = threadIdx.x;
+  for (int i = 0; i < b; ++i) {
+    double acc = 0.0;
+    if (j < i)
+      for (int l = j; l < i; ++l) acc = fma(T[j * b + l], Gp[l * b + i], acc);
+    __syncthreads();
+    if (j < i) T[j * b + i] = -tau[k0 + i] * acc;
+    else if (j == i) T[j * b + i] = tau[k0 + i];
+    else if (j < b) T[j * b + i] = 0.0;
+    __syncthreads();
+  }
+}
+
 size_t sym_eig_tridiag_work(int m) { return (size_t)m * m * 9 + (size_t)m * 8 + 64; }
+
+namespace {
+constexpr int kWyPanel = 128;       // reflectors per compact-WY panel
+constexpr int kWyMinSize = 1024;    // blocked back-transformation from this size up
+
+// V <- H_0 H_1 ... H_{m-3} V as panels P_j = I - Vp T Vp^T applied last panel first:
+// W = Vp^T V (rows below the panel start), W <- T W, V -= Vp W, three FP64 GEMMs per
+// panel.  vbuf rows hold the reflectors with zeros left of their first entry, so a panel's
+// rows of vbuf are Vp^T as it stands.  scratch >= 2 b m + 2 b^2 + part doubles.
+int backtransform_wy(const double* vbuf, const double* tau, int m, double* V, double* scratch,
+                     long scratch_size, cudaStream_t s) {
+  const int nref = m - 2;
+  const int nb = kWyPanel;
+  double* W = scratch;
+  double* W2 = W + (long)nb * m;
+  double* Gp = W2 + (long)nb * m;
+  double* T = Gp + (long)nb * nb;
+  double* part = T + (long)nb * nb;
+  const long partmax = scratch_size - (part - scratch);
+  if (partmax < (long)nb * nb) return CASPT2_EINVAL;
+  for (int k0 = ((nref - 1) / nb) * nb; k0 >= 0; k0 -= nb) {
+    const int b = std::min(nb, nref - k0);
+    const int r = m - k0 - 1;                            // rows k0+1 .. m-1
+    const double* Vt = vbuf + (long)k0 * m;              // b x m, zeros left of each v
+    int st = gram_product(Vt, Vt, 1, b, m, 0, Gp, b, 0, part, partmax, s, nullptr);
+    if (st != CASPT2_OK) return st;
+    ++launch_counter();
+    k_wy_T<<<1, b, 0, s>>>(Gp, tau, k0, b, T);
+    CASPT2_CUDA_TRY(cudaGetLastError());
+    CASPT2_CUDA_TRY(dgemm(b, m, r, 1.0, Vt + k0 + 1, m, false, V + (long)(k0 + 1) * m, m, false,
+                          0.0, W, m, s));
+    CASPT2_CUDA_TRY(dgemm(b, m, b, 1.0, T, b, false, W, m, false, 0.0, W2, m, s));
+    CASPT2_CUDA_TRY(dgemm(r, m, b, -1.0, Vt + k0 + 1, m, true, W2, m, false, 1.0,
+                          V + (long)(k0 + 1) * m, m, s));
+  }
+  return CASPT2_OK;
+}
+}  // namespace
 
 int sym_eig_tridiag(double* A, int m, double* w, double* V, double* work, cudaStream_t s,
                     KernelTimer* tm) {
@@ -876,6 +1090,8 @@ int sym_eig_tridiag(double* A, int m, double* w, double* V, double* work, cudaSt
   double* tau = e2 + m;
   double* p = tau + m;
   double* r = p + m;
+  // reflector rows are read whole by the blocked back-transformation: zero them first
+  if (m >= kWyMinSize) CASPT2_CUDA_TRY(cudaMemsetAsync(vbuf, 0, sizeof(double) * mm, s));
   // 1. tridiagonalise (one cooperative launch for large matrices: rows resident in
   //    shared memory when they fit, else streamed through L2)
   int dev = 0, nsm = 0;
@@ -909,6 +1125,53 @@ int sym_eig_tridiag(double* A, int m, double* w, double* V, double* work, cudaSt
       tm->ms += ms;
       tm->flops += 4.0 / 3.0 * (double)m * m * m;   // Householder tridiagonalisation
       // the matrix read once and the reflectors (lower triangle) written once
+      tm->bytes += 8.0 * m * m + 4.0 * m * (m - 1.0);
+      ++tm->launches;
+    }
+  } else if (m > 64 && m >= kLatrdMin) {
+    // blocked reduction: panels of kLatrdPanel columns (one cooperative launch each) and
+    // the trailing update as two FP64 GEMMs per panel
+    unsigned* sync = reinterpret_cast<unsigned*>(r);   // r is free until the back-transform
+    double* Wp = u0;                                   // [m][kLatrdPanel]
+    double* pp = u1;
+    double* pr = u1 + m;
+    double* part = u1 + 2 * (long)m;                   // [grid][2 panel + 1]
+    if (sizeof(double) * (size_t)m > kBisectSmemMax) return CASPT2_EINVAL;
+    CASPT2_CUDA_TRY(cudaFuncSetAttribute(k_latrd, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kBisectSmemMax));
+    int per = 0;
+    CASPT2_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_latrd, 512,
+                                                                  sizeof(double) * (size_t)m));
+    const int grid = std::max(1, std::min(nsm * std::max(per, 1), nsm));
+    CASPT2_CUDA_TRY(cudaMemsetAsync(sync, 0, 4 * sizeof(unsigned), s));
+    if (tm && tm->e0) CASPT2_CUDA_TRY(cudaEventRecord(tm->e0, s));
+    for (int k0 = 0; k0 < m - 2; k0 += kLatrdPanel) {
+      const int b = std::min(kLatrdPanel, m - 2 - k0);
+      void* args[] = {&A, (void*)&m, (void*)&k0, (void*)&b, &vbuf, &tau, &d, &e, &Wp, &pp, &pr,
+                      &part, &sync};
+      ++launch_counter();
+      CASPT2_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_latrd, grid, 512, args,
+                                                  sizeof(double) * (size_t)m, s));
+      const int rr = m - k0 - b;
+      if (rr > 0) {
+        double* A22 = A + (long)(k0 + b) * m + k0 + b;
+        const double* Vp = vbuf + (long)k0 * m + k0 + b;
+        const double* Wr = Wp + (long)(k0 + b) * kLatrdPanel;
+        CASPT2_CUDA_TRY(dgemm(rr, rr, b, -1.0, Vp, m, true, Wr, kLatrdPanel, true, 1.0, A22, m, s));
+        CASPT2_CUDA_TRY(dgemm(rr, rr, b, -1.0, Wr, kLatrdPanel, false, Vp, m, false, 1.0, A22, m,
+                              s));
+      }
+    }
+    if (tm && tm->e1) CASPT2_CUDA_TRY(cudaEventRecord(tm->e1, s));
+    int herr = 0;
+    CASPT2_CUDA_TRY(cudaMemcpyAsync(&herr, sync + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CASPT2_CUDA_TRY(cudaStreamSynchronize(s));
+    if (herr != 0) return CASPT2_ETIMEOUT;
+    if (tm && tm->e0) {
+      float ms = 0.f;
+      CASPT2_CUDA_TRY(cudaEventElapsedTime(&ms, tm->e0, tm->e1));
+      tm->ms += ms;
+      tm->flops += 4.0 / 3.0 * (double)m * m * m;   // Householder tridiagonalisation
       tm->bytes += 8.0 * m * m + 4.0 * m * (m - 1.0);
       ++tm->launches;
     }
@@ -1012,8 +1275,13 @@ int sym_eig_tridiag(double* A, int m, double* w, double* V, double* work, cudaSt
     CASPT2_CUDA_TRY(cudaMemcpyAsync(V, Z, sizeof(double) * mm, cudaMemcpyDeviceToDevice, s));
   else
     CASPT2_CUDA_TRY(dgemm(m, m, m, 1.0, Z, m, false, G, m, false, 0.0, V, m, s));
-  // 5. back-transformation V = H_0 ... H_{m-3} Z (column-owned, one launch)
-  if (m >= 3) {
+  // 5. back-transformation V = H_0 ... H_{m-3} Z: blocked (compact WY panels as FP64
+  //    GEMMs) for large matrices, else column-owned in one launch.  Z, G and the
+  //    inverse-iteration scratch are free here.
+  if (m >= kWyMinSize) {
+    const int st = backtransform_wy(vbuf, tau, m, V, Z, 7 * mm, s);
+    if (st != CASPT2_OK) return st;
+  } else if (m >= 3) {
     ++launch_counter();
     // columns resident in shared memory: ceil(m / SMs) per block (one block per SM, the
     // FP64 work spread evenly, one warp per column), fewer per block when they do not fit

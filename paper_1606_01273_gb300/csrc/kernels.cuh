@@ -78,7 +78,7 @@ cudaError_t launch_classH_split(const double* f, const double* B, const double* 
                                 const double* E0, double shift, int scheme, const Dims& d,
                                 ClassHWork& w, int* status, double* ecls, double* ncls,
                                 double* mom, double* mindenom, OzWork& oz, double* pack,
-                                double* K, double* KK, cudaStream_t s);
+                                double* K, double* KK, cudaStream_t s, int i0 = 0, int i1 = -1);
 // oz (optional, on): the DF and Gram products run as split BF16 GEMMs; k_ready: hd.K
 // already holds K[(ia)][(jb)] (formed by the split class-H energy path).
 int classH_densities(const double* B, const Dims& d, const ClassHWork& hw, int scheme,
@@ -93,6 +93,6 @@ int  classH_nshift(const Dims& d, int scheme);
 cudaError_t launch_classH(const double* f, const double* B, const double* Ftil, const double* E0,
                           double shift, int scheme, const Dims& d, ClassHWork& w, int* status,
                           double* ecls, double* ncls, double* mom, double* mindenom,
-                          cudaStream_t s);
+                          cudaStream_t s, int i0 = 0, int i1 = -1);
 
 }  // namespace caspt2

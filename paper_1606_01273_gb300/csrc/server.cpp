@@ -68,11 +68,35 @@ struct Request {
   std::vector<double> Ems, R, Heff, d1, d2, gdf;
 };
 
+// Contexts of finished requests kept for reuse by a later request of the same shape
+// (dimensions and options): their device buffers stay claimed in in_use until reused or
+// evicted (oldest first) to make room.
+struct PooledCtx {
+  std::vector<long long> key;
+  caspt2_ctx* ctx = nullptr;
+  size_t est = 0;
+};
+
+std::vector<long long> shape_key(const caspt2_request& q) {
+  const caspt2_dims& d = q.dims;
+  const caspt2_options& o = q.opt;
+  long long sh, ov, en, dg;
+  std::memcpy(&sh, &o.shift, 8);
+  std::memcpy(&ov, &o.ovl_thresh, 8);
+  std::memcpy(&en, &o.enuc, 8);
+  std::memcpy(&dg, &o.degen_thresh, 8);
+  return {d.nclosed, d.nact, d.nvirt, d.naux, d.nstate, o.xms, o.scheme, sh, ov, en,
+          o.target_state, (long long)o.class_mask, o.precision, o.slices, dg};
+}
+
 }  // namespace
 
 struct caspt2_server {
   int device = 0;
   size_t budget = 0, in_use = 0;
+  std::deque<PooledCtx> pool;             // idle contexts, oldest first
+  size_t pool_max = 0;
+  long reused = 0;
   bool stopping = false;
   long next_ticket = 1;
   std::vector<std::thread> workers;
@@ -84,10 +108,11 @@ struct caspt2_server {
 
 namespace {
 
-void run_request(Request& r, cudaStream_t st) {
+// Runs one request on `ctx` (a pooled context of the same shape, or nullptr: created
+// here); returns the context for the pool, or nullptr after an error.
+caspt2_ctx* run_request(Request& r, cudaStream_t st, caspt2_ctx* ctx) {
   const caspt2_request& q = r.q;
-  caspt2_ctx* ctx = nullptr;
-  int s = caspt2_create(&ctx, &q.dims, &q.opt);
+  int s = ctx ? CASPT2_OK : caspt2_create(&ctx, &q.dims, &q.opt);
   if (s == CASPT2_OK) {
     const double* p[6];
     for (int k = 0; k < 6; ++k) p[k] = r.in[k].empty() ? nullptr : r.in[k].data();
@@ -114,8 +139,12 @@ void run_request(Request& r, cudaStream_t st) {
     }
     if (g != CASPT2_OK) s = g;
   }
-  caspt2_destroy(ctx);
   r.status = s;
+  if (s < 0 && ctx) {
+    caspt2_destroy(ctx);
+    ctx = nullptr;
+  }
+  return ctx;
 }
 
 void worker(caspt2_server* srv) {
@@ -124,24 +153,56 @@ void worker(caspt2_server* srv) {
   const bool have_stream = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess;
   for (;;) {
     std::shared_ptr<Request> r;
+    caspt2_ctx* ctx = nullptr;
     {
       std::unique_lock<std::mutex> lk(srv->m);
-      srv->cv_work.wait(lk, [&] {
-        if (srv->queue.empty()) return srv->stopping;
-        return srv->in_use + srv->queue.front()->est <= srv->budget;
-      });
+      // admit the oldest request: reuse an idle context of its shape (its memory is
+      // already claimed), else claim its estimate, evicting idle contexts (oldest first)
+      // while it does not fit
+      auto admit = [&]() -> bool {
+        if (srv->queue.empty()) return false;
+        const std::shared_ptr<Request>& h = srv->queue.front();
+        const std::vector<long long> key = shape_key(h->q);
+        for (auto it = srv->pool.begin(); it != srv->pool.end(); ++it)
+          if (it->key == key) {
+            ctx = it->ctx;
+            srv->in_use += h->est;
+            srv->in_use -= it->est;
+            srv->pool.erase(it);
+            ++srv->reused;
+            return true;
+          }
+        while (srv->in_use + h->est > srv->budget && !srv->pool.empty()) {
+          caspt2_destroy(srv->pool.front().ctx);
+          srv->in_use -= srv->pool.front().est;
+          srv->pool.pop_front();
+        }
+        if (srv->in_use + h->est > srv->budget) return false;
+        srv->in_use += h->est;
+        return true;
+      };
+      srv->cv_work.wait(lk, [&] { return admit() || (srv->queue.empty() && srv->stopping); });
       if (srv->queue.empty()) break;           // stopping and nothing left
       r = srv->queue.front();
       srv->queue.pop_front();
-      srv->in_use += r->est;
       r->t_admit = Clock::now();
     }
-    if (have_stream) run_request(*r, st);
+    if (have_stream) ctx = run_request(*r, st, ctx);
     else r->status = CASPT2_ECUDA;
     for (auto& v : r->in) std::vector<double>().swap(v);
     {
       std::lock_guard<std::mutex> lk(srv->m);
-      srv->in_use -= r->est;
+      if (ctx) {
+        // keep the context idle for a later request of the same shape (its claim stays)
+        srv->pool.push_back(PooledCtx{shape_key(r->q), ctx, r->est});
+        while (srv->pool.size() > srv->pool_max) {
+          caspt2_destroy(srv->pool.front().ctx);
+          srv->in_use -= srv->pool.front().est;
+          srv->pool.pop_front();
+        }
+      } else {
+        srv->in_use -= r->est;
+      }
       r->t_done = Clock::now();
       r->done = true;
     }
@@ -173,6 +234,7 @@ int caspt2_server_create(caspt2_server** out, size_t budget, int max_slots) {
     budget = (size_t)(0.9 * (double)fr);
   }
   srv->budget = budget;
+  srv->pool_max = (size_t)(2 * max_slots);
   try {
     for (int k = 0; k < max_slots; ++k) srv->workers.emplace_back(worker, srv);
   } catch (...) {
@@ -257,6 +319,8 @@ void caspt2_server_destroy(caspt2_server* srv) {
   }
   srv->cv_work.notify_all();
   for (auto& t : srv->workers) t.join();
+  cudaSetDevice(srv->device);
+  for (auto& pc : srv->pool) caspt2_destroy(pc.ctx);
   delete srv;
 }
 

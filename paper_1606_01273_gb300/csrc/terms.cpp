@@ -392,4 +392,66 @@ void build_src_plans(int cls, std::vector<SrcPlan>& out) {
   }
 }
 
+void presum_src_plans(const std::vector<SrcPlan>& in, std::vector<SrcPlan>& out,
+                      std::vector<PresumSpec>& specs) {
+  out.clear();
+  for (const SrcPlan& P : in) {
+    if (P.kind != 1 || P.nloop == 0) {
+      out.push_back(P);
+      continue;
+    }
+    // loop variables that appear only in the integral can be summed inside it
+    bool summable[4] = {true, true, true, true};
+    for (int j = 0; j < 2 * P.rank; ++j)
+      if (P.idx[j] >= kRefLoop) summable[P.idx[j] - kRefLoop] = false;
+    for (int q = 0; q < P.neq; ++q)
+      for (int r = 0; r < 2; ++r)
+        if (P.eq[q][r] >= kRefLoop) summable[P.eq[q][r] - kRefLoop] = false;
+    int svar[4] = {-1, -1, -1, -1}, nsv = 0;
+    for (int j = 0; j < P.nloop; ++j)
+      if (summable[j]) svar[j] = nsv++;
+    if (nsv == 0 || nsv > 2) {
+      out.push_back(P);
+      continue;
+    }
+    PresumSpec sp{};
+    SrcPlan Q = P;
+    Q.kind = 2;
+    int newloop[4] = {-1, -1, -1, -1}, nl = 0;
+    for (int j = 0; j < P.nloop; ++j)
+      if (!summable[j]) {
+        newloop[j] = nl;
+        Q.loop_space[nl++] = P.loop_space[j];
+      }
+    for (int j = nl; j < 4; ++j) Q.loop_space[j] = 0;
+    Q.nloop = (int8_t)nl;
+    auto remap = [&](int8_t ref) -> int8_t {
+      if (ref < kRefLoop) return ref;
+      return (int8_t)(kRefLoop + newloop[ref - kRefLoop]);
+    };
+    for (int p = 0; p < 4; ++p) {
+      sp.space[p] = P.ispace[p];
+      const int ref = P.iidx[p];
+      if (ref >= kRefLoop && summable[ref - kRefLoop]) {
+        sp.var[p] = (int8_t)svar[ref - kRefLoop];
+        Q.iidx[p] = kRefZero;
+        Q.ispace[p] = kSpUnit;
+      } else {
+        sp.var[p] = -1;
+        Q.iidx[p] = remap(P.iidx[p]);
+      }
+    }
+    for (int j = 0; j < 2 * P.rank; ++j) Q.idx[j] = remap(P.idx[j]);
+    int id = -1;
+    for (size_t k = 0; k < specs.size(); ++k)
+      if (specs[k] == sp) id = (int)k;
+    if (id < 0) {
+      id = (int)specs.size();
+      specs.push_back(sp);
+    }
+    Q.cb = (int8_t)id;
+    out.push_back(Q);
+  }
+}
+
 }  // namespace caspt2

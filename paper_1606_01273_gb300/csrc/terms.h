@@ -45,7 +45,8 @@ struct ActPlan {
 // coeff * integral[iidx...] * Gamma_rank[idx...] summed over loop variables.
 struct SrcPlan {
   double coeff;        // includes the 1/2 of the two-body part
-  int8_t fb, kind;     // kind 0: h_pq, 1: (pq|rt)
+  int8_t fb, kind;     // kind 0: h_pq, 1: (pq|rt), 2: (pq|rt) pre-summed over loop indices
+  int8_t cb;           // kind 2: index of the pre-summed block (see PresumSpec)
   int8_t ispace[4];    // spaces of the integral indices
   int8_t iidx[4];      // integral indices (refs: bra slot = ext/act slot id, loops)
   int8_t rank, nloop, neq;
@@ -53,6 +54,27 @@ struct SrcPlan {
   int8_t loop_space[4];
   int8_t eq[4][2];
 };
+
+// A (pq|rt) block summed over loop indices that appear only in the integral (not in an
+// RDM index): out[i0][i1][i2][i3] with the summed positions of size 1 (space kSpUnit),
+//   out = sum over the loop values of (pq|rt) with the summed positions set to them.
+// var[p] = -1 (position kept) or the summed variable (0 or 1; one variable may fill two
+// positions, as in sum_j (ij|jr)).
+constexpr int kSpUnit = 3;          // extra "space" of dimension 1
+constexpr int kRefZero = 23;        // index reference whose value is always 0
+struct PresumSpec {
+  int8_t space[4];                  // spaces of the source block's positions
+  int8_t var[4];
+  bool operator==(const PresumSpec& o) const {
+    for (int k = 0; k < 4; ++k)
+      if (space[k] != o.space[k] || var[k] != o.var[k]) return false;
+    return true;
+  }
+};
+// Rewrite the two-electron source plans whose loop indices appear only in the integral
+// as kind-2 plans on pre-summed blocks (specs appended to / shared through `specs`).
+void presum_src_plans(const std::vector<SrcPlan>& in, std::vector<SrcPlan>& out,
+                      std::vector<PresumSpec>& specs);
 
 // Build the plans of class cls (0..6).  Deterministic; a few hundred terms.
 void build_act_plans(int cls, bool with_fock, std::vector<ActPlan>& out);

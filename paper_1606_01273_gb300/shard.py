@@ -1,9 +1,14 @@
 """Host logic of the multi-process (one rank per GPU) runs.
 
-The solve path shards by independent problems (geometries, requests): each rank solves
+Two ways to shard.  Across independent problems (geometries, requests): each rank solves
 its own units with no data-path collective, and only the timing is combined — the
 slowest rank's time bounds the job, and the whole-job rate counts every rank's units
-(weak scaling).  Used by bench.py under torchrun; tested with gloo ranks on the CPU."""
+(weak scaling).  Within one solve: each rank takes a contiguous range of the closed
+orbitals for the class-H and class-G work (options.closed_begin/closed_end; classes A-F
+on the rank whose range starts at 0), and the one exchange step is a fixed-order sum of
+the ranks' per-class moments (caspt2_get_moments), after which every rank forms H^eff,
+E_MS, R and lambda from the same sum (caspt2_finalize_moments).  Used by bench.py under
+torchrun; tested with gloo ranks on the CPU."""
 from __future__ import annotations
 
 import os
@@ -57,3 +62,27 @@ def job_rate(units_all_ranks: int, slowest_s: float) -> float:
     if slowest_s <= 0.0:
         raise ValueError("non-positive time")
     return units_all_ranks / slowest_s
+
+
+def closed_range(nclosed: int, rank: int, ws: int):
+    """(closed_begin, closed_end) of this rank's share of one solve's closed orbitals."""
+    return shard_range(nclosed, rank, ws)
+
+
+def sum_moments_fixed_order(local, device=None):
+    """The element-wise sum over ranks of each rank's moment array, added in rank order
+    (0, 1, ...) so that every rank obtains bitwise the same sum whatever the backend's
+    reduction order; the array alone without a process group."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    a = np.ascontiguousarray(local, dtype=np.float64)
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return a.copy()
+    t = torch.from_numpy(a).to(device or "cpu")
+    parts = [torch.empty_like(t) for _ in range(dist.get_world_size())]
+    dist.all_gather(parts, t)
+    out = parts[0].clone()
+    for p in parts[1:]:
+        out += p
+    return out.cpu().numpy()

@@ -99,6 +99,25 @@ class BigSpace:
         return d + penalty * s2
 
 
+def _orthonormal(V, drop=None):
+    """Orthonormal basis of the columns of V (tall, few columns): Cholesky of the Gram
+    matrix on the host, twice; columns whose pivot falls below drop x the largest are
+    left out."""
+    torch = _torch()
+    for _ in range(2):
+        G = (V.T @ V).cpu().numpy()
+        G = 0.5 * (G + G.T)
+        if drop is not None:
+            d = np.sqrt(np.maximum(np.diag(G), 0.0))
+            keep = d > drop * d.max()
+            V, G = V[:, torch.as_tensor(keep, device=V.device)], G[np.ix_(keep, keep)]
+        w, Q = np.linalg.eigh(G)
+        ok = w > 1e-12 * w.max()
+        T = Q[:, ok] / np.sqrt(w[ok])
+        V = V @ torch.as_tensor(T, device=V.device)
+    return V
+
+
 def davidson_singlets(space: BigSpace, h1, eri, nstate: int, penalty: float = 1.0,
                       tol: float = 1e-9, max_iter: int = 400, seed: int = 0):
     """Lowest nstate singlets of the active-space H (Davidson on H + penalty S^2).
@@ -130,16 +149,16 @@ def davidson_singlets(space: BigSpace, h1, eri, nstate: int, penalty: float = 1.
         if col == nroot:
             break
     V = V + 1e-3 * torch.randn(V.shape, generator=gen, dtype=torch.float64).to(space.dev)
-    V, _ = torch.linalg.qr(V)
+    V = _orthonormal(V)
     AV = op(V)
     for it in range(max_iter):
-        Hs = V.T @ AV
-        Hs = 0.5 * (Hs + Hs.T)
-        w, c = torch.linalg.eigh(Hs)
-        w, c = w[:nroot], c[:, :nroot]
+        Hs = (V.T @ AV).cpu().numpy()
+        w, c = np.linalg.eigh(0.5 * (Hs + Hs.T))       # small dense problems on the host
+        w = torch.as_tensor(w[:nroot], device=space.dev)
+        c = torch.as_tensor(c[:, :nroot], device=space.dev)
         X = V @ c
         R = AV @ c - X * w
-        rn = torch.linalg.norm(R, dim=0)
+        rn = torch.sqrt((R * R).sum(dim=0))
         if float(rn.max()) < tol:
             break
         act = rn >= tol
@@ -148,17 +167,16 @@ def davidson_singlets(space: BigSpace, h1, eri, nstate: int, penalty: float = 1.
         Rn = R[:, act] / den
         if V.shape[1] + Rn.shape[1] > 8 * nroot:      # restart on the current Ritz vectors
             V, AV = X, AV @ c
-        Rn = Rn / torch.linalg.norm(Rn, dim=0)
+        Rn = Rn / torch.sqrt((Rn * Rn).sum(dim=0))
         for _ in range(2):                            # orthogonalise twice against V
             Rn = Rn - V @ (V.T @ Rn)
-        keep = torch.linalg.norm(Rn, dim=0) > 1e-6   # drop directions already in span(V)
+        keep = torch.sqrt((Rn * Rn).sum(dim=0)) > 1e-6   # drop directions already in span(V)
         Rn = Rn[:, keep]
         if Rn.shape[1] == 0 or V.shape[1] >= nd:
             break
-        Rn, rr = torch.linalg.qr(Rn)
-        Rn = Rn[:, torch.abs(torch.diagonal(rr)) > 1e-6 * float(torch.abs(torch.diagonal(rr)).max())]
+        Rn = _orthonormal(Rn, drop=1e-6)
         Rn = Rn - V @ (V.T @ Rn)
-        Rn = Rn / torch.linalg.norm(Rn, dim=0)
+        Rn = Rn / torch.sqrt((Rn * Rn).sum(dim=0))
         V = torch.cat([V, Rn], dim=1)
         AV = torch.cat([AV, op(Rn)], dim=1)
     else:

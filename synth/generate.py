@@ -92,10 +92,10 @@ def _release_device(dev: str) -> None:
 
 def make_problem(nclosed: int, nact: int, nvirt: int, naux: int, nstate: int,
                  seed: int, nelact: int | None = None, decay: float = 10.0,
-                 kmax: int = 4, device: str | None = None) -> Problem:
+                 kmax: int = 4, device: str | None = None, fast: bool | None = None) -> Problem:
     """Build one seeded problem.  nelact defaults to nact (half filling).  Active spaces
-    above DENSE_CASCI_MAX determinants use the Davidson / Gram-matrix path of
-    synth.casci_fast on `device` (default: the GPU when present)."""
+    above DENSE_CASCI_MAX determinants (or any, with fast=True) use the Davidson /
+    Gram-matrix path of synth.casci_fast on `device` (default: the GPU when present)."""
     if nelact is None:
         nelact = nact
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -123,7 +123,7 @@ def make_problem(nclosed: int, nact: int, nvirt: int, naux: int, nstate: int,
     fc_act = t_act - _active_meanfield(eri_act, d_guess)
 
     space = ActiveSpace(nact, nelact)
-    if space.ndet <= DENSE_CASCI_MAX:
+    if not fast and (fast is not None or space.ndet <= DENSE_CASCI_MAX):
         e_cas, ci = lowest_singlets(space, fc_act, eri_act, nstate)
         rdm = {k: space.rdm(ci, k) for k in range(1, kmax + 1)}
     else:

@@ -64,12 +64,23 @@ def test_split_form_vs_oracle(cp, slices, etol, drel, opt):
 
 
 def test_split_form_vs_plain_at_bench_size(cp):
-    """c20 a8 v200 naux700 n3: the 7-slice form reproduces the plain FP64 form."""
+    """c20 a8 v200 naux700 n3: the 7-slice form reproduces the plain FP64 form.  The two
+    forms round the sector transforms differently, and this workload's class-C
+    near-intruder (|D| = 2.7e-4 Eh) turns that into E_MS differences of order
+    (norm + 2 E_s |M3|) d(omega); E_MS is compared at 1e-8 Eh plus that first-order bound
+    with d(omega) = 1e-12 Eh (as in test_gpu_classes.test_bench_workload_all_classes),
+    the class pieces at 1e-9 relative."""
+    from oracle import o2_rdm as o2
+    from oracle import o2_classes as oc
     p = make_problem(**WORKLOADS["c20a8v200x700n3"])
     opt = dict(xms=1, scheme=0, shift=0.2)
     ref = cp.solve_problem(p, densities=True, **opt)
     got = cp.solve_problem(p, densities=True, precision=cp.BF16X, slices=7, **opt)
-    assert np.abs(got.Ems - ref.Ems).max() <= 1e-8
+    st = o2.setup(p, xms=True, kmax=4)
+    mom = oc.all_moments(p, st, shift=0.2, scheme="msmr")
+    bound = max(1e-12 * sum(np.diagonal(mom[c][1])[L] + 2 * 0.2 * abs(mom[c][2][L]) for c in mom)
+                for L in range(p.nstate))
+    assert np.abs(got.Ems - ref.Ems).max() <= 1e-8 + bound
     for cls in "ABCDEFGH":
         scale = max(1.0, np.abs(ref.e_class[cls]).max())
         assert np.abs(got.e_class[cls] - ref.e_class[cls]).max() <= 1e-9 * scale, cls

@@ -76,3 +76,40 @@ def test_two_gloo_ranks(tmp_path):
     assert float(s0) == float(s1) == 2.5               # the slowest rank bounds the job
     assert int(u0) == int(u1) == 11                    # every rank's units count
     assert float(v0) == float(v1) == pytest.approx(11 / 2.5)
+
+
+def _moments_main(rank, ws, port, out_dir):
+    import numpy as np
+    import torch.distributed as dist
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank,
+                            world_size=ws)
+    try:
+        rng = np.random.default_rng(100 + rank)
+        local = rng.standard_normal((8, 5 ** 3 + 5 ** 2 + 5)) * 10.0 ** rng.integers(-8, 8, (8, 1))
+        np.save(os.path.join(out_dir, f"m{rank}.npy"), local)
+        tot = shard.sum_moments_fixed_order(local)
+        np.save(os.path.join(out_dir, f"s{rank}.npy"), tot)
+        lo, hi = shard.closed_range(70, rank, ws)
+        with open(os.path.join(out_dir, f"c{rank}.txt"), "w") as fh:
+            fh.write(f"{lo} {hi}\n")
+    finally:
+        dist.destroy_process_group()
+
+
+def test_split_solve_exchange_two_gloo_ranks(tmp_path):
+    """The one exchange step of a solve split over ranks: the closed orbitals are shared
+    contiguously (every orbital to one rank) and the per-class moments are summed in rank
+    order, so every rank holds bitwise the same sum, equal to the ordered sum computed
+    alone."""
+    import numpy as np
+    import torch.multiprocessing as mp
+    ws = 3
+    mp.spawn(_moments_main, args=(ws, _free_port(), str(tmp_path)), nprocs=ws, join=True)
+    parts = [np.load(tmp_path / f"m{r}.npy") for r in range(ws)]
+    ref = parts[0].copy()
+    for p in parts[1:]:
+        ref += p
+    for r in range(ws):
+        assert np.array_equal(np.load(tmp_path / f"s{r}.npy"), ref)
+    ranges = [tuple(map(int, open(tmp_path / f"c{r}.txt").read().split())) for r in range(ws)]
+    assert ranges == [(0, 24), (24, 47), (47, 70)]
