@@ -47,7 +47,8 @@ BENCH = {
               "3 states, shift 0.2 Eh, seed 1"),
         step="caspt2_solve + caspt2_densities (d1, d2, D1 in DF form of state 0)"),
 }
-WORKLOAD = "c70a10v600x2000n5"
+DEFAULT_WORKLOAD = "c70a10v600x2000n5"
+WORKLOAD = DEFAULT_WORKLOAD
 OPTS = BENCH[WORKLOAD]["opts"]
 WORKLOAD_DESC = BENCH[WORKLOAD]["desc"]
 FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 rate (no measured FP64 peak is provided)
@@ -615,7 +616,7 @@ def main():
     ap.add_argument("--precision", choices=["fp64", "bf16x"], default="bf16x")
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--slices", type=int, default=7)
-    ap.add_argument("--workload", choices=sorted(BENCH), default=WORKLOAD)
+    ap.add_argument("--workload", choices=sorted(BENCH), default=DEFAULT_WORKLOAD)
     ap.add_argument("--quick-compare", action="store_true", default=None,
                     help="the FP64-form and end-to-end arms take min(steps, 3) steps "
                          "(default on for the copper-corrole workload)")
