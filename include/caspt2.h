@@ -90,6 +90,11 @@ typedef struct {
                          /* per-class moments of the partitions summed (caspt2_get_moments)   */
                          /* and passed to caspt2_finalize_moments give the whole solve.       */
                          /* Default 0, -1 (all closed orbitals).                              */
+    int    dens_offdiag; /* 1: caspt2_densities also forms the closed-active, active-virtual   */
+                         /* and closed-virtual blocks of d2 (the one-body couplings between    */
+                         /* classes, Sec. II.D); needs every class's amplitudes and lambda    */
+                         /* over all index tuples in device memory at once (class H: c^2 v^2  */
+                         /* n^2 doubles each).  Default 0 (those blocks are zero).            */
 } caspt2_options;
 
 /* Fill *opt with defaults: XMS, MS-MR, shift 0, 1e-9, enuc 0, target 0, all classes,
@@ -215,8 +220,11 @@ int caspt2_get_status(caspt2_ctx* ctx, caspt2_report* out);
  *                 mean fields, Sec. II.F) — classes A-G;
  *   d2[p][q]      derivative with respect to the Fock matrix f on the closed-closed,
  *                 active-active and virtual-virtual blocks (the blocks that the
- *                 block-diagonal f of the solve carries; other blocks are zero), including
- *                 the E0 dependence of the denominators (-N_L <L~|E_pq|L~>);
+ *                 block-diagonal f of the solve carries), including the E0 dependence of
+ *                 the denominators (-N_L <L~|E_pq|L~>); with opt.dens_offdiag also the
+ *                 closed-active, active-virtual and closed-virtual blocks
+ *                 dbar2_xy = sum_L <Psi_lambda_L|E_xy|Psi1_L> (the couplings between
+ *                 classes that an off-diagonal f would bring), else those blocks are zero;
  *   gdf[Q][p][q]  derivative with respect to the DF factors B[Q][p][q] of the two-electron
  *                 source terms (D(1) contracted with B, Sec. II.D DF form).
  * All three are returned symmetrised (x + x^T)/2 per matrix: the integrals are
@@ -224,8 +232,9 @@ int caspt2_get_status(caspt2_ctx* ctx, caspt2_report* out);
  * Call after a successful (or WINTRUDER) caspt2_solve with target_state >= 0; runs on
  * cuda_stream (NULL = default stream) and synchronises it.  The first call allocates
  * the density work space (about 6 x the largest class's amplitude array plus 3 (c v)^2
- * doubles for class H).  Errors: EINVAL (mask outside the solved classes, target_state
- * < 0, nact > 16), ESTATE (no solve), ENOMEM, ECUDA. */
+ * doubles for class H; with dens_offdiag, the all-tuple amplitude and lambda arrays of
+ * every class).  Errors: EINVAL (mask outside the solved classes, target_state < 0,
+ * nact > 16), ESTATE (no solve), ENOMEM, ECUDA. */
 int caspt2_densities(caspt2_ctx* ctx, unsigned class_mask, void* cuda_stream);
 
 /* Copy the densities of the last caspt2_densities call: d1 and d2 [nmo][nmo], NL [n], gdf

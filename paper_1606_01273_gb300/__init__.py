@@ -35,7 +35,7 @@ class Options(C.Structure):
                 ("ovl_thresh", C.c_double), ("enuc", C.c_double), ("target_state", C.c_int),
                 ("class_mask", C.c_uint), ("precision", C.c_int), ("slices", C.c_int),
                 ("degen_thresh", C.c_double), ("closed_begin", C.c_int),
-                ("closed_end", C.c_int)]
+                ("closed_end", C.c_int), ("dens_offdiag", C.c_int)]
 
 
 class Request(C.Structure):

@@ -11,6 +11,7 @@
 #include <map>
 
 #include "class_ag.cuh"
+#include "cross.cuh"
 #include "class_dev.cuh"
 #include "kernels.cuh"
 #include "linalg.cuh"
@@ -76,6 +77,13 @@ struct caspt2_ctx {
   // precision form: split BF16 tensor-core GEMMs, class-H pair integrals kept for the densities
   OzWork oz{};
   double *hK = nullptr, *hKK = nullptr, *hpack = nullptr;
+  // one-body couplings between classes: dbar2 off-diagonal blocks (opt.dens_offdiag)
+  bool x_alloc = false;
+  CrossWork xw{};
+  double* xT[8] = {};
+  double* xL[8] = {};
+  double *xW = nullptr, *xZ = nullptr, *xpart = nullptr;
+  long xwmax = 0, xzmax = 0, xpartmax = 0;
   // energy gradient (allocated on the first caspt2_gradient call)
   bool grad_alloc = false;
   GradWork gw{};
@@ -146,6 +154,7 @@ void caspt2_default_options(caspt2_options* o) {
   o->degen_thresh = 1e-8;
   o->closed_begin = 0;
   o->closed_end = -1;
+  o->dens_offdiag = 0;
 }
 
 unsigned caspt2_supported_classes(void) { return (1u << CASPT2_NCLASS) - 1u; }
@@ -817,6 +826,63 @@ int alloc_densities(caspt2_ctx* c) {
   return st;
 }
 
+// The closed-active, active-virtual and closed-virtual blocks of d2 (dbar2 through the
+// one-body couplings between classes) for the classes of class_mask, added to c->dd2.
+int dens_offdiag(caspt2_ctx* c, unsigned class_mask, cudaStream_t s) {
+  const Dims& d = c->d;
+  const caspt2_options& o = c->opt;
+  const int n = d.n, P = o.target_state;
+  const bool h_on = (class_mask >> CASPT2_CLASS_H & 1u) && d.c > 0 && d.v > 0;
+  if (!c->x_alloc) {
+    std::vector<CrossPlan> all;
+    cross_setup(c->xw, all);
+    int st = c->alloc(&c->xw.plans, all.size());
+    if (st != CASPT2_OK) return st;
+    CASPT2_CUDA_TRY(cudaMemcpy(c->xw.plans, all.data(), sizeof(CrossPlan) * all.size(),
+                               cudaMemcpyHostToDevice));
+    cross_work_size(c->xw, d, &c->xwmax, &c->xzmax, &c->xpartmax);
+    for (int k = 0; k < 7 && st == CASPT2_OK; ++k) {
+      if (!c->cw_on[k]) continue;
+      const size_t sz = (size_t)all_tuples(c->cw[k]) * n * c->cw[k].m;
+      st = c->alloc(&c->xT[k], sz);
+      if (st == CASPT2_OK) st = c->alloc(&c->xL[k], sz);
+    }
+    if (st == CASPT2_OK && (c->opt.class_mask >> CASPT2_CLASS_H & 1u) && d.c > 0 && d.v > 0) {
+      const size_t sz = (size_t)d.c * d.c * d.v * d.v * n * n;
+      st = c->alloc(&c->xT[7], sz);
+      if (st == CASPT2_OK) st = c->alloc(&c->xL[7], sz);
+    }
+    if (st == CASPT2_OK) st = c->alloc(&c->xW, (size_t)c->xwmax);
+    if (st == CASPT2_OK) st = c->alloc(&c->xZ, (size_t)c->xzmax);
+    if (st == CASPT2_OK) st = c->alloc(&c->xpart, (size_t)c->xpartmax);
+    if (st != CASPT2_OK) return st;
+    c->x_alloc = true;
+  }
+  double* T[8] = {};
+  double* L[8] = {};
+  for (int k = 0; k < 7; ++k) {
+    if (!(class_mask >> k & 1u) || !c->cw_on[k] || !c->xT[k]) continue;
+    DensWork tmp = c->dw;
+    tmp.T = c->xT[k];
+    tmp.Lam = c->xL[k];
+    tmp.tall = all_tuples(c->cw[k]) * n * c->cw[k].m;
+    const int st = class_tuple_amplitudes(c->cw[k], tmp, d, o.shift, c->E0, c->eps, c->R, P,
+                                          &c->oz, s);
+    if (st != CASPT2_OK) return st;
+    T[k] = c->xT[k];
+    L[k] = c->xL[k];
+  }
+  if (h_on && c->xT[7]) {
+    CASPT2_CUDA_TRY(launch_h_tuple_amps(c->hd.K, c->hw.eps, c->hw.W, c->hw.shifts, c->R, P, d,
+                                        o.scheme, o.shift, c->xT[7], c->xL[7], s));
+    T[7] = c->xT[7];
+    L[7] = c->xL[7];
+  }
+  RdmPtrs g{{nullptr, c->rdm1r, c->rdm2r, c->rdm3r, c->rdm4r}};
+  return cross_dbar2(c->xw, d, g, T, L, c->xW, c->xZ, c->xpart, c->xwmax, c->xzmax, c->xpartmax,
+                     c->dd2, s);
+}
+
 long block_size(const Dims& d, int key) {
   const int dims3[3] = {d.c, d.a, d.v};
   return (long)dims3[key / 27] * dims3[(key / 9) % 3] * dims3[(key / 3) % 3] * dims3[key % 3];
@@ -869,6 +935,10 @@ int caspt2_densities(caspt2_ctx* c, unsigned class_mask, void* stream) {
     const int st = classH_densities(c->B, d, c->hw, o.scheme, o.shift, c->R, P,
                                     c->lamNL + (long)CASPT2_CLASS_H * n, c->rdm1r, c->hd, c->dd2,
                                     c->dgdf, &c->oz, c->hK != nullptr && c->hd.K == c->hK, s);
+    if (st != CASPT2_OK) return st;
+  }
+  if (o.dens_offdiag) {
+    const int st = dens_offdiag(c, class_mask, s);
     if (st != CASPT2_OK) return st;
   }
   CASPT2_CUDA_TRY(launch_symmetrize(c->dd1, (int)nmo, 1, s));

@@ -224,36 +224,41 @@ k_tridiag(double* __restrict__ A, int m, double* __restrict__ vbuf, double* __re
 // Blocked Householder reduction, one cooperative launch per panel of b columns
 // k0 .. k0+b-1 (the LAPACK dlatrd scheme, written from its definition): the trailing
 // matrix is left as it stands during the panel and its true value is
-// A22 - V W^T - W V^T, with V the panel's reflectors (rows of vbuf) and W the vectors
+// A22 - V W^T - W V^T, with V the panel's reflectors and W the vectors
 // w = p - (tau/2)(p.v) v, p = tau (A22 - V W^T - W V^T) v.  After the panel the host
 // applies A22 -= V W^T + W V^T as two FP64 GEMMs.  Per column k = k0 + j, three bounded
 // grid barriers; blocks own contiguous runs of the rows (and of the columns of row k+1):
 //   A: every block forms the reflector of row k from the row (already up to date) into
 //      shared memory -- the reductions run in a fixed order, so every copy is the same;
-//      block 0 stores it (vbuf, tau, d, e);
-//   B: p_raw = A22 v (a warp per row) and partial sums of W^T v and V^T v;   | barrier
-//   C: p = tau (p_raw - V (W^T v) - W (V^T v)) and partial sums of p.v;     | barrier
+//      block 0 stores it (vbuf row k, column j of Vr, tau, d, e);
+//   B: p_raw = A22 v (a warp per row, four loads in flight per lane) and partial sums of
+//      W^T v and V^T v;                                                  | barrier
+//   C: p = tau (p_raw - V (W^T v) - W (V^T v)) (a warp per owned row, lanes over the
+//      panel columns) and partial sums of p.v;                           | barrier
 //   D: alpha = (tau/2) p.v, W[:, j] = p - alpha v, and the owned columns of row k+1
-//      brought up to date with the panel's columns 0..j.                    | barrier
-// W is [m][nb] row-major; p, pr [m]; part [grid][2 nb + 1]; sync[0..1] barrier, [2] error.
-// Dynamic shared memory: v [m].
+//      brought up to date with the panel's columns 0..j.                 | barrier
+// W and Vr are [m][nb] row-major (Vr holds the panel's reflectors by row, so that a row's
+// panel entries are contiguous); p, pr [m]; part [grid][2 nb + 1]; sync[0..1] barrier,
+// [2] error.  Dynamic shared memory: v [m].
 constexpr int kLatrdPanel = 64;
 constexpr int kLatrdMin = 1024;     // sizes at which the blocked reduction is used (when
                                     // the rows do not fit in shared memory)
 __global__ void __launch_bounds__(512)
 k_latrd(double* __restrict__ A, int m, int k0, int b, double* __restrict__ vbuf,
         double* __restrict__ tau, double* __restrict__ d, double* __restrict__ e,
-        double* __restrict__ W, double* __restrict__ p, double* __restrict__ pr,
-        double* __restrict__ part, unsigned* sync) {
+        double* __restrict__ W, double* __restrict__ Vr, double* __restrict__ p,
+        double* __restrict__ pr, double* __restrict__ part, unsigned* sync) {
   constexpr int nb = kLatrdPanel;
   extern __shared__ double vs[];                      // v of the current column, by row
   __shared__ double red[32];
   __shared__ double sh[4];
   __shared__ double xy[2 * nb];
+  __shared__ double rk[2 * nb];                       // row k+1 of V and W (panel columns)
   int* err = reinterpret_cast<int*>(sync + 2);
   const int G = gridDim.x, bid = blockIdx.x;
   const int warp = (bid * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   const int nw = (G * blockDim.x) >> 5;
+  const int wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
   for (int j = 0; j < b; ++j) {
     const int k = k0 + j;
     const int n1 = m - k - 1;
@@ -288,7 +293,10 @@ k_latrd(double* __restrict__ A, int m, int k0, int b, double* __restrict__ vbuf,
       for (int i = threadIdx.x; i < n1; i += blockDim.x) {
         const double vi = (i == 0) ? 1.0 : __ldcg(x + i) * scale;
         vs[k + 1 + i] = vi;
-        if (bid == 0) vbuf[(long)k * m + k + 1 + i] = vi;
+        if (bid == 0) {
+          vbuf[(long)k * m + k + 1 + i] = vi;
+          Vr[(long)(k + 1 + i) * nb + j] = vi;
+        }
       }
       __syncthreads();
     }
@@ -298,26 +306,27 @@ k_latrd(double* __restrict__ A, int m, int k0, int b, double* __restrict__ vbuf,
     // ---- B: p_raw = A22 v over rows >= k+1; partials of W^T v, V^T v (columns l < j)
     for (int i = warp; i < n1; i += nw) {
       const double* row = A + (long)(k + 1 + i) * m;
-      double s0 = 0.0, s1 = 0.0;
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
       int q = k + 1 + lane;
-      for (; q + 32 < m; q += 64) {
-        s0 = fma(__ldcg(row + q), vs[q], s0);
-        s1 = fma(__ldcg(row + q + 32), vs[q + 32], s1);
+      for (; q + 96 < m; q += 128) {
+        const double a0 = __ldcg(row + q), a1 = __ldcg(row + q + 32);
+        const double a2 = __ldcg(row + q + 64), a3 = __ldcg(row + q + 96);
+        s0 = fma(a0, vs[q], s0);
+        s1 = fma(a1, vs[q + 32], s1);
+        s2 = fma(a2, vs[q + 64], s2);
+        s3 = fma(a3, vs[q + 96], s3);
       }
-      if (q < m) s0 = fma(__ldcg(row + q), vs[q], s0);
-      double sum = s0 + s1;
+      for (; q < m; q += 32) s0 = fma(__ldcg(row + q), vs[q], s0);
+      double sum = (s0 + s1) + (s2 + s3);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
       if (lane == 0) pr[k + 1 + i] = sum;
     }
     if (threadIdx.x < 2 * j) {
       const int tq = threadIdx.x;
-      const int l = tq < j ? tq : tq - j;
+      const double* src = tq < j ? W + tq : Vr + (tq - j);
       double acc = 0.0;
-      for (int i = r0; i < r1; ++i) {
-        const double c = tq < j ? __ldcg(W + (long)i * nb + l) : __ldcg(vbuf + (long)(k0 + l) * m + i);
-        acc = fma(c, vs[i], acc);
-      }
+      for (int i = r0; i < r1; ++i) acc = fma(__ldcg(src + (long)i * nb), vs[i], acc);
       part[(long)bid * (2 * nb + 1) + tq] = acc;
     }
     if (!grid_sync_bounded(sync, sync + 1, err)) return;
@@ -330,15 +339,17 @@ k_latrd(double* __restrict__ A, int m, int k0, int b, double* __restrict__ vbuf,
     __syncthreads();
     {
       double sp = 0.0;
-      for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-        double c = __ldcg(pr + i);
-        for (int l = 0; l < j; ++l)
-          c -= __ldcg(vbuf + (long)(k0 + l) * m + i) * xy[l] + __ldcg(W + (long)i * nb + l) * xy[j + l];
-        c *= t;
-        p[i] = c;
-        sp = fma(c, vs[i], sp);
+      for (int i = r0 + wib; i < r1; i += wpb) {
+        double c = 0.0;
+        for (int l = lane; l < j; l += 32)
+          c = fma(__ldcg(Vr + (long)i * nb + l), xy[l], fma(__ldcg(W + (long)i * nb + l), xy[j + l], c));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        const double pv = t * (__ldcg(pr + i) - c);
+        if (lane == 0) p[i] = pv;
+        sp = fma(pv, vs[i], sp);
       }
-      sp = block_sum(sp, red);
+      sp = block_sum(lane == 0 ? sp : 0.0, red);
       if (threadIdx.x == 0) part[(long)bid * (2 * nb + 1) + 2 * nb] = sp;
     }
     if (!grid_sync_bounded(sync, sync + 1, err)) return;
@@ -359,18 +370,21 @@ k_latrd(double* __restrict__ A, int m, int k0, int b, double* __restrict__ vbuf,
     if (j + 1 < b) {
       const int k1 = k + 1;
       // row k1 of V and W over l <= j (W[k1][j] formed here; p[k1] is visible)
-      const double wk1j = __ldcg(p + k1) - alpha * vs[k1];
-      for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-        double a = __ldcg(A + (long)k1 * m + i);
-        for (int l = 0; l <= j; ++l) {
-          const double* vl = vbuf + (long)(k0 + l) * m;
-          const double vk = (l == j) ? vs[k1] : __ldcg(vl + k1);
-          const double vi = (l == j) ? vs[i] : __ldcg(vl + i);
-          const double wk = (l == j) ? wk1j : __ldcg(W + (long)k1 * nb + l);
-          const double wi = (l == j) ? (__ldcg(p + i) - alpha * vs[i]) : __ldcg(W + (long)i * nb + l);
-          a -= vk * wi + wk * vi;
+      for (int l = threadIdx.x; l <= j; l += blockDim.x) {
+        rk[l] = (l == j) ? vs[k1] : __ldcg(Vr + (long)k1 * nb + l);
+        rk[nb + l] = (l == j) ? __ldcg(p + k1) - alpha * vs[k1] : __ldcg(W + (long)k1 * nb + l);
+      }
+      __syncthreads();
+      for (int i = r0 + wib; i < r1; i += wpb) {
+        double c = 0.0;
+        for (int l = lane; l < j; l += 32)
+          c = fma(rk[l], __ldcg(W + (long)i * nb + l), fma(rk[nb + l], __ldcg(Vr + (long)i * nb + l), c));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        if (lane == 0) {
+          const double wij = __ldcg(p + i) - alpha * vs[i];
+          A[(long)k1 * m + i] = __ldcg(A + (long)k1 * m + i) - c - (rk[j] * wij + rk[nb + j] * vs[i]);
         }
-        A[(long)k1 * m + i] = a;
       }
     }
     if (!grid_sync_bounded(sync, sync + 1, err)) return;
@@ -875,6 +889,69 @@ __global__ void k_ns_coef(double* __restrict__ G, int m, unsigned long long* __r
   if ((threadIdx.x & 31) == 0 && mx) atomicMax(dev, mx);
 }
 
+// Orthonormality probe of the eigenvector matrix Z (columns): with two fixed +-1 vectors
+// r1, r2, dev = max_k |(Z^T Z r)_k - r_k| over both (two passes over Z instead of the m^3
+// Gram product).  A column set orthonormal to within e gives dev <~ e sqrt(m); a larger
+// dev sends the caller to the full Gram matrix.
+__device__ __forceinline__ double probe_sign(int k, int which) {
+  const unsigned h = (unsigned)k * 2654435761u + (which ? 0x9E3779B9u : 0x7F4A7C15u);
+  return ((h >> 13) & 1u) ? 1.0 : -1.0;
+}
+// u[q][i] = sum_k Z[i][k] r_q[k]: a warp per row
+__global__ void __launch_bounds__(256)
+k_ortho_probe1(const double* __restrict__ Z, int m, double* __restrict__ u) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int i = warp; i < m; i += nw) {
+    const double* row = Z + (long)i * m;
+    double s1 = 0.0, s2 = 0.0;
+    for (int k = lane; k < m; k += 32) {
+      const double z = row[k];
+      s1 = fma(z, probe_sign(k, 0), s1);
+      s2 = fma(z, probe_sign(k, 1), s2);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s1 += __shfl_down_sync(0xffffffffu, s1, o);
+      s2 += __shfl_down_sync(0xffffffffu, s2, o);
+    }
+    if (lane == 0) {
+      u[i] = s1;
+      u[m + i] = s2;
+    }
+  }
+}
+// w_q[c] = sum_i Z[i][c] u_q[i] (32 columns x 8 row groups per block, fixed-order sum over
+// the groups) and dev = max |w_q[c] - r_q[c]| (integer maximum of the bit patterns)
+__global__ void __launch_bounds__(256)
+k_ortho_probe2(const double* __restrict__ Z, int m, const double* __restrict__ u,
+               unsigned long long* __restrict__ dev) {
+  __shared__ double part[2][8][33];
+  const int cx = threadIdx.x & 31, rg = threadIdx.x >> 5;
+  const int c = blockIdx.x * 32 + cx;
+  double s1 = 0.0, s2 = 0.0;
+  if (c < m)
+    for (int i = rg; i < m; i += 8) {
+      const double z = Z[(long)i * m + c];
+      s1 = fma(z, u[i], s1);
+      s2 = fma(z, u[m + i], s2);
+    }
+  part[0][rg][cx] = s1;
+  part[1][rg][cx] = s2;
+  __syncthreads();
+  if (rg == 0 && c < m) {
+    double w1 = 0.0, w2 = 0.0;
+    for (int g = 0; g < 8; ++g) {
+      w1 += part[0][g][cx];
+      w2 += part[1][g][cx];
+    }
+    const double e = fmax(fabs(w1 - probe_sign(c, 0)), fabs(w2 - probe_sign(c, 1)));
+    const unsigned long long b = (unsigned long long)__double_as_longlong(e);
+    if (e == e) atomicMax(dev, b);
+    else atomicMax(dev, 0x7FF8000000000000ull);
+  }
+}
+
 // r[c] = sum_i v[i] Z[k+1+i][c]: 32 columns x 8 row groups per block (coalesced rows),
 // fixed-order reduction over the row groups in shared memory.
 __global__ void __launch_bounds__(256)
@@ -1136,19 +1213,23 @@ int sym_eig_tridiag(double* A, int m, double* w, double* V, double* work, cudaSt
     double* pp = u1;
     double* pr = u1 + m;
     double* part = u1 + 2 * (long)m;                   // [grid][2 panel + 1]
+    double* Vr = u2;                                   // [m][kLatrdPanel]
     if (sizeof(double) * (size_t)m > kBisectSmemMax) return CASPT2_EINVAL;
     CASPT2_CUDA_TRY(cudaFuncSetAttribute(k_latrd, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kBisectSmemMax));
     int per = 0;
     CASPT2_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_latrd, 512,
                                                                   sizeof(double) * (size_t)m));
-    const int grid = std::max(1, std::min(nsm * std::max(per, 1), nsm));
+    // two blocks per SM when they fit (more warps in flight for the latency-bound
+    // matrix-vector products), one otherwise
+    const int grid = std::max(1, nsm * std::max(1, std::min(per, 2)));
+    if ((long)grid * (2 * kLatrdPanel + 1) > mm - 2 * (long)m) return CASPT2_EINVAL;
     CASPT2_CUDA_TRY(cudaMemsetAsync(sync, 0, 4 * sizeof(unsigned), s));
     if (tm && tm->e0) CASPT2_CUDA_TRY(cudaEventRecord(tm->e0, s));
     for (int k0 = 0; k0 < m - 2; k0 += kLatrdPanel) {
       const int b = std::min(kLatrdPanel, m - 2 - k0);
-      void* args[] = {&A, (void*)&m, (void*)&k0, (void*)&b, &vbuf, &tau, &d, &e, &Wp, &pp, &pr,
-                      &part, &sync};
+      void* args[] = {&A, (void*)&m, (void*)&k0, (void*)&b, &vbuf, &tau, &d, &e, &Wp, &Vr, &pp,
+                      &pr, &part, &sync};
       ++launch_counter();
       CASPT2_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_latrd, grid, 512, args,
                                                   sizeof(double) * (size_t)m, s));
@@ -1259,22 +1340,39 @@ int sym_eig_tridiag(double* A, int m, double* w, double* V, double* work, cudaSt
   CASPT2_CUDA_TRY(cudaGetLastError());
   // 4. Newton-Schulz: Z <- Z (1.5 I - 0.5 Z^T Z), skipped when Z is already orthonormal to
   //    1e-13 (the step would change it by less than that)
+  //    The probe Z^T Z r (two passes over Z) decides first; only when it is above 1e-13 is
+  //    the m^3 Gram matrix formed and the element-wise test applied.
   unsigned long long* ns_dev = reinterpret_cast<unsigned long long*>(r + m);
   CASPT2_CUDA_TRY(cudaMemsetAsync(ns_dev, 0, sizeof(unsigned long long), s));
-  CASPT2_CUDA_TRY(dgemm_sym(m, m, 1.0, Z, m, true, Z, m, false, 0.0, G, m, s));
   ++launch_counter();
-  k_ns_coef<<<nblocks(mm), kT, 0, s>>>(G, m, ns_dev);
+  k_ortho_probe1<<<nblocks(32L * m), kT, 0, s>>>(Z, m, G);
+  ++launch_counter();
+  k_ortho_probe2<<<(m + 31) / 32, 256, 0, s>>>(Z, m, G, ns_dev);
   CASPT2_CUDA_TRY(cudaGetLastError());
   unsigned long long hdev = 0;
   CASPT2_CUDA_TRY(cudaMemcpyAsync(&hdev, ns_dev, sizeof(hdev), cudaMemcpyDeviceToHost, s));
   CASPT2_CUDA_TRY(cudaStreamSynchronize(s));
-  double dev_ortho;
-  std::memcpy(&dev_ortho, &hdev, sizeof(double));
-  if (!(dev_ortho == dev_ortho)) return CASPT2_ENAN;
-  if (dev_ortho <= 1e-13)
+  double dev_probe;
+  std::memcpy(&dev_probe, &hdev, sizeof(double));
+  if (!(dev_probe == dev_probe)) return CASPT2_ENAN;
+  if (dev_probe <= 1e-13) {
     CASPT2_CUDA_TRY(cudaMemcpyAsync(V, Z, sizeof(double) * mm, cudaMemcpyDeviceToDevice, s));
-  else
-    CASPT2_CUDA_TRY(dgemm(m, m, m, 1.0, Z, m, false, G, m, false, 0.0, V, m, s));
+  } else {
+    CASPT2_CUDA_TRY(cudaMemsetAsync(ns_dev, 0, sizeof(unsigned long long), s));
+    CASPT2_CUDA_TRY(dgemm_sym(m, m, 1.0, Z, m, true, Z, m, false, 0.0, G, m, s));
+    ++launch_counter();
+    k_ns_coef<<<nblocks(mm), kT, 0, s>>>(G, m, ns_dev);
+    CASPT2_CUDA_TRY(cudaGetLastError());
+    CASPT2_CUDA_TRY(cudaMemcpyAsync(&hdev, ns_dev, sizeof(hdev), cudaMemcpyDeviceToHost, s));
+    CASPT2_CUDA_TRY(cudaStreamSynchronize(s));
+    double dev_ortho;
+    std::memcpy(&dev_ortho, &hdev, sizeof(double));
+    if (!(dev_ortho == dev_ortho)) return CASPT2_ENAN;
+    if (dev_ortho <= 1e-13)
+      CASPT2_CUDA_TRY(cudaMemcpyAsync(V, Z, sizeof(double) * mm, cudaMemcpyDeviceToDevice, s));
+    else
+      CASPT2_CUDA_TRY(dgemm(m, m, m, 1.0, Z, m, false, G, m, false, 0.0, V, m, s));
+  }
   // 5. back-transformation V = H_0 ... H_{m-3} Z: blocked (compact WY panels as FP64
   //    GEMMs) for large matrices, else column-owned in one launch.  Z, G and the
   //    inverse-iteration scratch are free here.

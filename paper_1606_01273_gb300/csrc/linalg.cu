@@ -285,10 +285,125 @@ __global__ void k_sort_pairs(const double* __restrict__ w, const double* __restr
   }
 }
 
+// The whole cyclic Jacobi iteration of one small matrix (m <= kJacobiFusedMax) in one
+// block with A and V resident in shared memory: the rounds of k_jacobi_round, a fixed-order
+// off-diagonal norm after each sweep with the same stopping rule as the multi-launch path,
+// then the eigenvalues, and the pairs sorted ascending into w and V (A is left rotated).
+// status[0] = 1 when converged, 0 otherwise, -1 on NaN.
+constexpr int kJacobiFusedMax = 32;
+__global__ void __launch_bounds__(256)
+k_jacobi_fused(double* __restrict__ A, int m, double* __restrict__ w, double* __restrict__ V,
+               int* __restrict__ status) {
+  constexpr int MM = kJacobiFusedMax * kJacobiFusedMax;
+  __shared__ double sA[2][MM], sV[2][MM];
+  __shared__ double red[32];
+  __shared__ double sw[kJacobiFusedMax];
+  __shared__ int flag;
+  const long mm = (long)m * m;
+  for (long t = threadIdx.x; t < mm; t += blockDim.x) {
+    sA[0][t] = A[t];
+    sV[0][t] = (t / m == t % m) ? 1.0 : 0.0;
+  }
+  if (threadIdx.x == 0) flag = (m == 1) ? 1 : 0;
+  __syncthreads();
+  const int mp = m + (m & 1);
+  const int npair = mp / 2;
+  const long nblk = (long)npair * npair;
+  const long total = nblk + (long)m * npair;
+  int cur = 0;
+  double prev = -1.0;
+  for (int sweep = 0; sweep < 60 && flag == 0; ++sweep) {
+    for (int r = 0; r < mp - 1; ++r) {
+      const double* Ac = sA[cur];
+      double* An = sA[cur ^ 1];
+      const double* Vc = sV[cur];
+      double* Vn = sV[cur ^ 1];
+      for (long t = threadIdx.x; t < total; t += blockDim.x) {
+        if (t < nblk) {
+          const int I = t / npair, J = t % npair;
+          int pI, qI, pJ, qJ;
+          jac_pair(I, r, mp, pI, qI);
+          jac_pair(J, r, mp, pJ, qJ);
+          double cI, sI, cJ, sJ;
+          jac_rot(Ac, m, pI, qI, cI, sI);
+          jac_rot(Ac, m, pJ, qJ, cJ, sJ);
+          const bool vq_I = qI < m, vq_J = qJ < m;
+          const double a00 = Ac[pI * m + pJ];
+          const double a01 = vq_J ? Ac[pI * m + qJ] : 0.0;
+          const double a10 = vq_I ? Ac[qI * m + pJ] : 0.0;
+          const double a11 = (vq_I && vq_J) ? Ac[qI * m + qJ] : 0.0;
+          const double r00 = cI * a00 - sI * a10, r01 = cI * a01 - sI * a11;
+          const double r10 = sI * a00 + cI * a10, r11 = sI * a01 + cI * a11;
+          double n00 = r00 * cJ - r01 * sJ, n01 = r00 * sJ + r01 * cJ;
+          double n10 = r10 * cJ - r11 * sJ, n11 = r10 * sJ + r11 * cJ;
+          if (I == J && vq_I) { n01 = 0.0; n10 = 0.0; }
+          An[pI * m + pJ] = n00;
+          if (vq_J) An[pI * m + qJ] = n01;
+          if (vq_I) An[qI * m + pJ] = n10;
+          if (vq_I && vq_J) An[qI * m + qJ] = n11;
+        } else {
+          const long u = t - nblk;
+          const int row = u / npair, J = u % npair;
+          int pJ, qJ;
+          jac_pair(J, r, mp, pJ, qJ);
+          double cJ, sJ;
+          jac_rot(Ac, m, pJ, qJ, cJ, sJ);
+          const double vp = Vc[row * m + pJ];
+          if (qJ < m) {
+            const double vq = Vc[row * m + qJ];
+            Vn[row * m + pJ] = cJ * vp - sJ * vq;
+            Vn[row * m + qJ] = sJ * vp + cJ * vq;
+          } else {
+            Vn[row * m + pJ] = vp;
+          }
+        }
+      }
+      __syncthreads();
+      cur ^= 1;
+    }
+    double off = 0.0, dia = 0.0;
+    for (long t = threadIdx.x; t < mm; t += blockDim.x) {
+      const double x = sA[cur][t];
+      if (t / m == t % m) dia += x * x; else off += x * x;
+    }
+    off = block_sum(off, red);
+    __syncthreads();
+    dia = block_sum(dia, red);
+    if (threadIdx.x == 0) {
+      if (!(off == off)) flag = -1;
+      else if (off == 0.0 || off <= 1e-34 * dia) flag = 1;
+      else if (off <= 1e-20 * dia && prev >= 0.0 && off > 0.25 * prev) flag = 1;
+      prev = off;
+    }
+    __syncthreads();
+  }
+  for (long t = threadIdx.x; t < mm; t += blockDim.x) A[t] = sA[cur][t];
+  for (int i = threadIdx.x; i < m; i += blockDim.x) sw[i] = sA[cur][i * m + i];
+  __syncthreads();
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    int rk = 0;
+    for (int k = 0; k < m; ++k) rk += (sw[k] < sw[j] || (sw[k] == sw[j] && k < j)) ? 1 : 0;
+    w[rk] = sw[j];
+    for (int i = 0; i < m; ++i) V[(long)i * m + rk] = sV[cur][i * m + j];
+  }
+  if (threadIdx.x == 0) status[0] = flag;
+}
+
 // Eigenpairs of symmetric A (m x m, row-major, overwritten): w[m], V[m][m] (columns).
 // work: 2*m*m doubles + 2.  Ascending.  Synchronises the stream once per sweep.
 int sym_eig_jacobi(double* A, int m, double* w, double* V, double* work, cudaStream_t s) {
   if (m <= 0) return CASPT2_OK;
+  if (m <= kJacobiFusedMax) {
+    int* st_dev = reinterpret_cast<int*>(work + 2L * m * m);
+    ++launch_counter();
+    k_jacobi_fused<<<1, 256, 0, s>>>(A, m, w, V, st_dev);
+    CASPT2_CUDA_TRY(cudaGetLastError());
+    int st = 0;
+    CASPT2_CUDA_TRY(cudaMemcpyAsync(&st, st_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CASPT2_CUDA_TRY(cudaStreamSynchronize(s));
+    if (st < 0) return CASPT2_ENAN;
+    return st == 1 ? CASPT2_OK : CASPT2_ENOTCONV;
+  }
   double* A2 = work;
   double* V2 = work + (long)m * m;
   double* nrm = work + 2L * m * m;

@@ -454,4 +454,162 @@ void presum_src_plans(const std::vector<SrcPlan>& in, std::vector<SrcPlan>& out,
   }
 }
 
+namespace {
+// class H for the couplings: E_ai,bj, slots a i b j; external positions i, j, a, b
+const ClassDef kClassH = {1, {{0, 1, 2, 3}, {0, 0, 0, 0}}, 4, {SP_V, SP_C, SP_V, SP_C}, 3,
+                          {1, 3, 0}, 0, {0, 0, 0}, -1, -1};
+const int kHExt[4] = {1, 3, 0, 2};
+const ClassDef& xdef(int cls) { return cls == 7 ? kClassH : kClasses[cls]; }
+int xnext(int cls) { return cls == 7 ? 4 : kClasses[cls].next; }
+int xext(int cls, int k) { return cls == 7 ? kHExt[k] : kClasses[cls].ext[k]; }
+// (closed holes, virtual particles) of each class
+const int kCount[8][2] = {{1, 0}, {2, 0}, {0, 1}, {1, 1}, {2, 1}, {0, 2}, {1, 2}, {2, 2}};
+constexpr int kLabX = 8, kLabY = 9;
+}  // namespace
+
+XClassInfo xclass_info(int cls) {
+  const ClassDef& C = xdef(cls);
+  XClassInfo I{};
+  I.nfam = C.nfam;
+  I.next = xnext(cls);
+  I.nact = C.nact;
+  for (int k = 0; k < I.next; ++k) I.ext_space[k] = C.slot_space[xext(cls, k)];
+  return I;
+}
+
+void build_cross_groups(int X, int Y, std::vector<CrossGroup>& out) {
+  const int dh = (Y == SP_C) - (X == SP_C), dp = (X == SP_V) - (Y == SP_V);
+  for (int Kp = 0; Kp < 8; ++Kp) {
+    int K = -1;
+    for (int q = 0; q < 8; ++q)
+      if (kCount[q][0] == kCount[Kp][0] + dh && kCount[q][1] == kCount[Kp][1] + dp) K = q;
+    if (K < 0) continue;
+    const ClassDef& CB = xdef(K);
+    const ClassDef& CK = xdef(Kp);
+    std::map<int, Space> sp;
+    for (int s = 0; s < 4; ++s) {
+      sp[s] = CB.slot_space[s];
+      sp[kLabKet + s] = CK.slot_space[s];
+    }
+    sp[kLabX] = (Space)X;
+    sp[kLabY] = (Space)Y;
+    auto bra_pos = [&](int lab) {          // external position of a bra slot label
+      for (int k = 0; k < xnext(K); ++k)
+        if (xext(K, k) == lab) return k;
+      return -1;
+    };
+    auto ket_pos = [&](int lab) {
+      for (int k = 0; k < xnext(Kp); ++k)
+        if (kLabKet + xext(Kp, k) == lab) return k;
+      return -1;
+    };
+    auto act_ref = [&](int lab) -> int {
+      for (int k = 0; k < CB.nact; ++k)
+        if (lab == CB.act[k]) return kRefBra + k;
+      for (int k = 0; k < CK.nact; ++k)
+        if (lab == kLabKet + CK.act[k]) return kRefKet + k;
+      if ((lab == kLabX && X == SP_A) || (lab == kLabY && Y == SP_A)) return kRefT;
+      return -1;
+    };
+    const size_t first = out.size();
+    for (int fb = 0; fb < CB.nfam; ++fb)
+      for (int fk = 0; fk < CK.nfam; ++fk) {
+        std::vector<FOp> ops;
+        OpBuilder b;
+        const int* pb = CB.fam[fb];
+        const int* pk = CK.fam[fk];
+        b.E2(ops, pb[1], pb[0], pb[3], pb[2]);      // (E_{pq,rs})^dagger = E_{qp,sr}
+        b.E(ops, kLabX, kLabY);
+        b.E2(ops, kLabKet + pk[0], kLabKet + pk[1], kLabKet + pk[2], kLabKet + pk[3]);
+        for (const auto& kv : reduce(ops, sp)) {
+          if (kv.second == 0) continue;
+          CrossGroup g{};
+          g.K = K;
+          g.Kp = Kp;
+          g.X = X;
+          g.Y = Y;
+          g.t_xy = X == SP_A ? 0 : (Y == SP_A ? 1 : -1);
+          for (int k = 0; k < 4; ++k) g.ket_src[k] = -1;
+          g.side = -1;
+          UnionFind uf;
+          for (auto d : kv.first.first) {
+            const int l0 = d.first, l1 = d.second;
+            if (sp.at(l0) == SP_A) {
+              uf.join(l0, l1);
+              continue;
+            }
+            // external delta: bra-ket, bra-f or ket-f
+            int lb = -1, lk = -1, lf = -1;
+            for (int l : {l0, l1}) {
+              if (l == kLabX || l == kLabY) lf = l;
+              else if (l >= kLabKet) lk = l;
+              else lb = l;
+            }
+            if (lb >= 0 && lk >= 0) {
+              g.ket_src[ket_pos(lk)] = bra_pos(lb);
+            } else if (lf >= 0 && (lb >= 0 || lk >= 0)) {
+              const int side = lb >= 0 ? 0 : 1;
+              if (g.side >= 0 && g.side != side) throw std::logic_error("mixed external sides");
+              g.side = side;
+              g.fe_xy[g.nfe] = lf == kLabX ? 0 : 1;
+              g.fe_pos[g.nfe] = side == 0 ? bra_pos(lb) : ket_pos(lk);
+              ++g.nfe;
+            } else {
+              throw std::logic_error("unexpected external delta");
+            }
+          }
+          if (g.nfe == 0 || g.side < 0) throw std::logic_error("f index not external");
+          if (g.nfe == 2 && g.fe_xy[0] == 1) {        // x first
+            std::swap(g.fe_xy[0], g.fe_xy[1]);
+            std::swap(g.fe_pos[0], g.fe_pos[1]);
+          }
+          CrossPlan P{};
+          P.coeff = (double)kv.second;
+          P.fb = (int8_t)fb;
+          P.fk = (int8_t)fk;
+          std::vector<int> labs;
+          for (int k = 0; k < CB.nact; ++k) labs.push_back(CB.act[k]);
+          for (int k = 0; k < CK.nact; ++k) labs.push_back(kLabKet + CK.act[k]);
+          if (g.t_xy >= 0) labs.push_back(g.t_xy == 0 ? kLabX : kLabY);
+          std::map<int, int> ref;
+          for (int lab : labs) {
+            const int r = uf.find(lab), o = act_ref(lab);
+            if (!ref.count(r)) {
+              ref[r] = o;
+            } else {
+              if (P.neq >= 6) throw std::logic_error("too many active equalities");
+              P.eq[P.neq][0] = (int8_t)ref[r];
+              P.eq[P.neq][1] = (int8_t)o;
+              ++P.neq;
+            }
+          }
+          const auto& rd = kv.first.second;
+          if (rd.size() > 4) throw std::logic_error("RDM rank above 4");
+          P.rank = (int8_t)rd.size();
+          for (size_t j = 0; j < rd.size(); ++j) {
+            P.idx[2 * j] = (int8_t)ref.at(uf.find(rd[j].first));
+            P.idx[2 * j + 1] = (int8_t)ref.at(uf.find(rd[j].second));
+          }
+          // append to the group with the same pattern
+          bool placed = false;
+          for (size_t q = first; q < out.size() && !placed; ++q) {
+            CrossGroup& h = out[q];
+            bool same = h.side == g.side && h.nfe == g.nfe;
+            for (int k = 0; k < g.nfe && same; ++k)
+              same = h.fe_xy[k] == g.fe_xy[k] && h.fe_pos[k] == g.fe_pos[k];
+            for (int k = 0; k < 4 && same; ++k) same = h.ket_src[k] == g.ket_src[k];
+            if (same) {
+              h.terms.push_back(P);
+              placed = true;
+            }
+          }
+          if (!placed) {
+            g.terms.push_back(P);
+            out.push_back(std::move(g));
+          }
+        }
+      }
+  }
+}
+
 }  // namespace caspt2

@@ -80,4 +80,40 @@ void presum_src_plans(const std::vector<SrcPlan>& in, std::vector<SrcPlan>& out,
 void build_act_plans(int cls, bool with_fock, std::vector<ActPlan>& out);
 void build_src_plans(int cls, std::vector<SrcPlan>& out);
 
+// ------------------------------------------------------------------ one-body couplings
+// <M~| E_bra(K)^dag E_xy E_ket(K') |N~> for x, y in different orbital spaces (closed-active,
+// active-virtual, closed-virtual and the transposes): the operator E_xy changes the (closed
+// holes, virtual particles) count of a function of class K' into that of class K.  Classes
+// 0..6 are A..G (ClassDef), 7 is H (E_ai,bj, external slots in the order i, j, a, b).
+// Every closed or virtual index of a term is tied by one Kronecker delta to exactly one
+// other, so a term factorises into an external pattern (which bra slot, ket slot or f
+// index each external index is tied to) and an active factor (deltas among the bra and ket
+// active slots and the active one of x, y, times one RDM).  Terms are grouped by pattern.
+constexpr int kRefT = 24;           // index reference of the active one of x, y
+struct CrossPlan {                  // the active factor of one term
+  double coeff;
+  int8_t fb, fk, rank, neq;
+  int8_t idx[8];                    // RDM indices (refs: kRefBra + k, kRefKet + k, kRefT)
+  int8_t eq[6][2];
+};
+struct CrossGroup {
+  int K, Kp;                        // bra and ket class (0..7)
+  int X, Y;                         // spaces of x and y
+  int side;                         // 0: the external f indices are tied to bra slots, 1: ket
+  int nfe;                          // external f indices (1 or 2)
+  int fe_xy[2];                     // 0: x, 1: y
+  int fe_pos[2];                    // their bra (side 0) or ket (side 1) external positions
+  int t_xy;                         // which of x, y is active (-1: none)
+  int ket_src[4];                   // per ket external position: the bra position tied to it,
+                                    // or -1 (tied to an f index)
+  std::vector<CrossPlan> terms;
+};
+struct XClassInfo {                 // layout facts of a class for the couplings
+  int nfam, next, nact;
+  int ext_space[4];                 // spaces of the external positions (output order)
+};
+XClassInfo xclass_info(int cls);    // cls 0..7
+// All groups of the couplings through E_xy with x in space X, y in space Y (X != Y).
+void build_cross_groups(int X, int Y, std::vector<CrossGroup>& out);
+
 }  // namespace caspt2
