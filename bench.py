@@ -229,27 +229,33 @@ def conditioning_bound(g, shift, dw=1e-14):
     return b
 
 
-SERVE_DESC = ("Poisson arrivals (mean 20/s) of XMS-CASPT2 requests (MS-MR, shift 0.2, all "
-              "classes, target-state densities for every other request) drawn from 12 "
-              "synthetic problems with nclosed 4-16, nact 2-6, nvirt 20-120, 1-3 states, "
-              "naux ~ 3 nmo (the C5 size range reduced to what the generator builds here)")
+SERVE_DESC = ("256 Poisson arrivals (mean 20/s) of XMS-CASPT2 requests (MS-MR, shift 0.2, "
+              "all classes, target-state densities for every other request) drawn from 16 "
+              "synthetic problems with sizes uniform over nclosed 4-42, nact 4-8, nvirt "
+              "20-350, 1-4 states, naux = 3 nmo (the serving-stream size range with nact "
+              "capped at 8: a 12-orbital request carries a 55 GB 4-RDM)")
 
 
-def serve_problems(count=12, seed=5000):
-    """The serving pool: distinct seeded problems of mixed size (inputs only)."""
+def serve_problems(count=16, seed=5000):
+    """The serving pool: distinct seeded problems of mixed size (inputs only), sizes uniform
+    over nclosed 4-42, nact 4-8, nvirt 20-350, 1-4 states (CASCI, RDMs and the DF factor
+    product on the GPU when there is one)."""
     from synth import make_problem
+    from synth.generate import _default_device
+    dev = _default_device()
     rng = np.random.default_rng(seed)
     out = []
     for k in range(count):
-        nact = int(rng.integers(2, 7))
-        c, v, n = int(rng.integers(4, 17)), int(rng.integers(20, 121)), int(rng.integers(1, 4))
+        nact = int(rng.integers(4, 9))
+        c, v, n = int(rng.integers(4, 43)), int(rng.integers(20, 351)), int(rng.integers(1, 5))
         nel = nact if nact % 2 == 0 else nact - 1
         out.append(make_problem(nclosed=c, nact=nact, nvirt=v, naux=3 * (c + nact + v),
-                                nstate=n, seed=seed + k, nelact=nel))
+                                nstate=n, seed=seed + k, nelact=nel, fast=True,
+                                df_device=dev if dev != "cpu" else None))
     return out
 
 
-def run_serve(nreq=32, rate=20.0, slots=4, seed=7):
+def run_serve(nreq=256, rate=20.0, slots=4, seed=7):
     """Submit nreq requests at Poisson arrival times, wait for all; latencies measured by
     the server (submit -> results ready)."""
     import threading

@@ -281,7 +281,7 @@ int caspt2_create(caspt2_ctx** out, const caspt2_dims* dims, const caspt2_option
   ALLOC(c->lamLV, (size_t)CASPT2_NCLASS * n * n);
   // classes A-G: plans, class matrices, sources, sector work space, integral blocks
   {
-    long m2max = 0, wmax = 0, pmax = 0, vmax = 0;
+    long m2max = 0, wmax = 0, pmax = 0, vmax = 0, srcx_max = 0, srcg_max = 0;
     long packmax = 0;
     std::map<int, long> eri_need;
     for (int k = 0; k < 7 && st == CASPT2_OK; ++k) {
@@ -308,12 +308,28 @@ int caspt2_create(caspt2_ctx** out, const caspt2_dims* dims, const caspt2_option
           packmax = std::max(packmax, (long)X * dims3[t.ispace[2]] * dims3[t.ispace[3]]);
         }
       }
-      presum_src_plans(V, w.hVs, c->presum);
+      {
+        std::vector<SrcPlan> pre;
+        presum_src_plans(V, pre, c->presum);
+        split_src_plans(k, pre, w.hVs, w.hG);
+      }
       if (c->presum.size() > (size_t)kMaxPresum) st = CASPT2_EINVAL;
       ALLOC(w.dS, S.size());
       ALLOC(w.dF, F.size());
       ALLOC(w.dV, V.size());
       ALLOC(w.dVs, w.hVs.size());
+      {
+        size_t nx = 0;
+        const long ncol = w.A * n * n;
+        for (const SrcGemmGroup& G : w.hG) {
+          nx += G.x.size();
+          long K = 1;
+          for (int q = 0; q < G.g.ns; ++q) K *= a;
+          srcg_max = std::max(srcg_max, K * ncol);
+          srcx_max = std::max(srcx_max, K * all_tuples(w));
+        }
+        if (nx > 0) ALLOC(w.dX, nx);
+      }
       if (st == CASPT2_OK && class_upload_plans(w, S, F, V) != cudaSuccess) st = CASPT2_ECUDA;
       ALLOC(w.Sact, 2 * (size_t)w.m * w.m);
       ALLOC(w.Fact, 2 * (size_t)w.m * w.m);
@@ -354,6 +370,10 @@ int caspt2_create(caspt2_ctx** out, const caspt2_dims* dims, const caspt2_option
       // part2 also holds the per-eigenvector denominator minima and the refinement list
       q.p2size = std::max<long>(q.nb2 * pcol, mx + 1);
       ALLOC(q.W, q.wcap); ALLOC(q.part, q.pcap); ALLOC(q.part2, q.p2size);
+      // source GEMM groups: X in row chunks of at most 2^26 doubles
+      q.srcXcap = std::max<long>(1, std::min<long>(srcx_max, 1L << 26));
+      q.srcGcap = std::max<long>(1, srcg_max);
+      ALLOC(q.srcX, q.srcXcap); ALLOC(q.srcG, q.srcGcap);
       ALLOC(c->h, nmo * nmo);
       ALLOC(c->fact, a2);
       ALLOC(c->eps, nmo);

@@ -136,6 +136,115 @@ __global__ void k_src_eval(const SrcPlan* __restrict__ plans, int nplan, DevClas
   }
 }
 
+// Source GEMM groups (terms.h, split_src_plans): X[(row)][k] over the external tuples
+// row0 .. row0 + nrow (row-major in the class's external order) and k over the shared loops
+// (a^ns, the first loop slowest): the group's integral terms summed, each with its
+// integral-only loops and external deltas.
+__global__ void k_src_x(const SrcXTerm* __restrict__ xt, int nx, DevClass C, Dims d, int ns,
+                        const double* __restrict__ h, EriBlocks eri, PresumBlocks pb, long row0,
+                        long nrow, double* __restrict__ X) {
+  const int a = d.a, nmo = d.nmo();
+  const int dimsp[4] = {d.c, d.a, d.v, 1};
+  const int offsp[3] = {0, d.c, d.c + d.a};
+  const long K = ipow(a, ns);
+  const long total = nrow * K;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    int vals[32];
+    vals[kRefZero] = 0;
+    long q = e % K;
+    for (int p = ns - 1; p >= 0; --p) {
+      vals[kRefLoop + p] = (int)(q % a);
+      q /= a;
+    }
+    long r = row0 + e / K;
+    for (int k = C.next - 1; k >= 0; --k) {
+      const int dm = dimsp[C.slot_space[C.ext[k]]];
+      vals[kRefBra + C.ext[k]] = (int)(r % dm);
+      r /= dm;
+    }
+    double acc = 0.0;
+    for (int t = 0; t < nx; ++t) {
+      const SrcXTerm& T = xt[t];
+      bool ok = true;
+      for (int u = 0; u < T.neq; ++u)
+        if (vals[T.eq[u][0]] != vals[T.eq[u][1]]) ok = false;
+      if (!ok) continue;
+      const double* blk = nullptr;
+      long bd[4] = {1, 1, 1, 1};
+      if (T.kind == 1) {
+        const int key = ((T.ispace[0] * 3 + T.ispace[1]) * 3 + T.ispace[2]) * 3 + T.ispace[3];
+        blk = eri.p[key];
+        for (int j = 0; j < 4; ++j) bd[j] = dimsp[T.ispace[j]];
+      } else if (T.kind == 2) {
+        blk = pb.p[T.cb];
+        for (int j = 0; j < 4; ++j) bd[j] = dimsp[T.ispace[j]];
+      }
+      long niter = 1;
+      for (int j = 0; j < T.nloop; ++j) niter *= dimsp[T.loop_space[j]];
+      double sum = 0.0;
+      for (long it = 0; it < niter; ++it) {
+        long w = it;
+        for (int j = 0; j < T.nloop; ++j) {
+          const int dm = dimsp[T.loop_space[j]];
+          vals[kRefLoop + ns + j] = (int)(w % dm);
+          w /= dm;
+        }
+        if (T.kind == 0)
+          sum += h[(long)(offsp[T.ispace[0]] + vals[T.iidx[0]]) * nmo + offsp[T.ispace[1]] +
+                   vals[T.iidx[1]]];
+        else
+          sum += blk[((vals[T.iidx[0]] * bd[1] + vals[T.iidx[1]]) * bd[2] + vals[T.iidx[2]]) *
+                         bd[3] + vals[T.iidx[3]]];
+      }
+      acc += T.coeff * sum;
+    }
+    X[e] = acc;
+  }
+}
+
+// G[k][(act..., M, L)] of a source GEMM group: the RDM element (bra state M, ket L) summed
+// over the RDM-only loops, zero where an active delta fails.
+__global__ void k_src_g(SrcGSig g, DevClass C, Dims d, RdmPtrs rdm, double* __restrict__ G) {
+  const int n = d.n, a = d.a;
+  const long A = ipow(a, C.nact);
+  const long ncol = A * n * n;
+  const long total = ipow(a, g.ns) * ncol;
+  const long nit = ipow(a, g.nloop);
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    int vals[32];
+    vals[kRefZero] = 0;
+    long col = e % ncol;
+    const int L = (int)(col % n);
+    const int M = (int)((col / n) % n);
+    long r = col / ((long)n * n);
+    for (int k = C.nact - 1; k >= 0; --k) {
+      vals[kRefBra + C.act[k]] = (int)(r % a);
+      r /= a;
+    }
+    long q = e / ncol;
+    for (int p = g.ns - 1; p >= 0; --p) {
+      vals[kRefLoop + p] = (int)(q % a);
+      q /= a;
+    }
+    bool ok = true;
+    for (int u = 0; u < g.neq; ++u)
+      if (vals[g.eq[u][0]] != vals[g.eq[u][1]]) ok = false;
+    double sum = 0.0;
+    if (ok)
+      for (long it = 0; it < nit; ++it) {
+        long w = it;
+        for (int j = 0; j < g.nloop; ++j) {
+          vals[kRefLoop + g.ns + j] = (int)(w % a);
+          w /= a;
+        }
+        sum += rdm_at(rdm.p, g.rank, n, a, M, L, vals, g.idx);
+      }
+    G[e] = sum;
+  }
+}
+
 // Same sources with one thread per (fam, ext, act) holding all n^2 (M, L) results (n <=
 // NS): each plan term's integral value and RDM offset are formed once and applied to the
 // n^2 state pairs (Gamma[M][L][off] at stride a^(2 rank)).
@@ -1031,6 +1140,17 @@ cudaError_t class_upload_plans(ClassWork& w, const std::vector<ActPlan>& S,
                                cudaMemcpyHostToDevice)) != cudaSuccess)
     return e;
   w.nVs = (int)w.hVs.size();
+  if (w.dX) {
+    std::vector<SrcXTerm> all;
+    w.gx_off.clear();
+    for (const SrcGemmGroup& G : w.hG) {
+      w.gx_off.push_back((int)all.size());
+      all.insert(all.end(), G.x.begin(), G.x.end());
+    }
+    if ((e = cudaMemcpy(w.dX, all.data(), sizeof(SrcXTerm) * all.size(),
+                        cudaMemcpyHostToDevice)) != cudaSuccess)
+      return e;
+  }
   w.nS = (int)S.size();
   w.nF = (int)F.size();
   w.nV = (int)V.size();
@@ -1064,6 +1184,37 @@ int class_solve(ClassWork& w, SectorWork& sw, const Dims& d, int scheme, double 
                                                       w.V, w.vsize);
   }
   CASPT2_CUDA_TRY(cudaGetLastError());
+  // the terms of the GEMM groups: V[fam] += X G, X in row chunks
+  if (!w.hG.empty()) {
+    const long rows = all_tuples(w);
+    const long ncol = w.A * n * n;
+    for (size_t gi = 0; gi < w.hG.size(); ++gi) {
+      const SrcGemmGroup& G = w.hG[gi];
+      const long K = ipow_host(d.a, G.g.ns);
+      if (K * ncol > sw.srcGcap) return CASPT2_EINVAL;
+      ++launch_counter();
+      k_src_g<<<launch_blocks(K * ncol), 256, 0, s>>>(G.g, w.dc, d, rdm, sw.srcG);
+      CASPT2_CUDA_TRY(cudaGetLastError());
+      const long chunk = std::min<long>(rows, sw.srcXcap / K);
+      if (chunk < 1) return CASPT2_EINVAL;
+      for (long r0 = 0; r0 < rows; r0 += chunk) {
+        const long nr = std::min(chunk, rows - r0);
+        ++launch_counter();
+        k_src_x<<<launch_blocks(nr * K), 256, 0, s>>>(w.dX + w.gx_off[gi], (int)G.x.size(), w.dc,
+                                                      d, G.g.ns, h, eri, pb, r0, nr, sw.srcX);
+        CASPT2_CUDA_TRY(cudaGetLastError());
+        double* Vc = w.V + ((long)G.fb * rows + r0) * ncol;
+        if (oz && oz->on && oz->S >= kOzMaxSlices) {
+          const OzView vx{sw.srcX, K, 1, K, 0}, vg{sw.srcG, 1, ncol, K, 0};
+          CASPT2_CUDA_TRY(oz_matmul(*oz, vx, vg, false, (int)nr, (int)ncol, (int)K, 1.0, 1.0, Vc,
+                                    ncol, s));
+        } else {
+          CASPT2_CUDA_TRY(dgemm((int)nr, (int)ncol, (int)K, 1.0, sw.srcX, (int)K, false, sw.srcG,
+                                (int)ncol, false, 1.0, Vc, (int)ncol, s));
+        }
+      }
+    }
+  }
 
   const int nsec = w.dc.pair0 < 0 ? 1 : 2;
   for (int sec = 0; sec < nsec; ++sec) {
@@ -1082,7 +1233,8 @@ int class_solve(ClassWork& w, SectorWork& sw, const Dims& d, int scheme, double 
       CASPT2_CUDA_TRY(cudaGetLastError());
       SectorKeep& K = w.keep[sec * nsel + is];
       K.nk = 0;
-      int st = sym_eig(sw.Ssec, msec, sw.s, sw.Qs, sw.jac, s, tm);
+      OzWork* ozn = (oz && oz->on && oz->S >= kOzMaxSlices) ? oz : nullptr;
+      int st = sym_eig(sw.Ssec, msec, sw.s, sw.Qs, sw.jac, s, tm, ozn);
       if (st != CASPT2_OK) return st;
       // number of overlap eigenvalues at or above the threshold (ascending order)
       std::vector<double> hs(msec);
@@ -1111,7 +1263,7 @@ int class_solve(ClassWork& w, SectorWork& sw, const Dims& d, int scheme, double 
         CASPT2_CUDA_TRY(dgemm_sym(nk, msec, 1.0, sw.X, nk, true, sw.FX, nk, false, 0.0, sw.Ft, nk,
                                   s));
       }
-      st = sym_eig(sw.Ft, nk, K.omega, sw.Qf, sw.jac, s, tm);
+      st = sym_eig(sw.Ft, nk, K.omega, sw.Qf, sw.jac, s, tm, ozn);
       if (st != CASPT2_OK) return st;
       if (ozx) {
         const OzView vx{sw.X, nk, 1, nk, 0}, vq{sw.Qf, 1, nk, nk, 0};

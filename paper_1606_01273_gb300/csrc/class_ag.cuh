@@ -46,8 +46,11 @@ struct ClassWork {
   ActPlan* dS = nullptr; int nS = 0;
   ActPlan* dF = nullptr; int nF = 0;
   SrcPlan* dV = nullptr; int nV = 0;
-  SrcPlan* dVs = nullptr; int nVs = 0;   // the solve's variant: loop-only integrals pre-summed
-  std::vector<SrcPlan> hVs;
+  SrcPlan* dVs = nullptr; int nVs = 0;   // the solve's variant: loop-only integrals pre-summed,
+  std::vector<SrcPlan> hVs;              // without the terms that run as GEMM groups
+  std::vector<SrcGemmGroup> hG;          // source terms as X G products (see terms.h)
+  SrcXTerm* dX = nullptr;                // every group's X terms, group g at dX + gx_off[g]
+  std::vector<int> gx_off;
   double *Sact = nullptr, *Fact = nullptr, *V = nullptr;
   std::vector<SectorKeep> keep;   // one per (sector, SS-SR state), see class_keep_layout
 };
@@ -60,6 +63,8 @@ struct SectorWork {
                              // chunks that fit them)
   long nb2 = 0;              // row blocks of the first column-sum stage (part2: nb2 x pcol)
   long p2size = 0;           // doubles held by part2
+  double *srcX = nullptr, *srcG = nullptr;   // source GEMM groups: X rows chunk, G
+  long srcXcap = 0, srcGcap = 0;
 };
 // Upper bounds on the solve's sector work arrays W and part (doubles): larger sectors are
 // processed in tuple chunks.

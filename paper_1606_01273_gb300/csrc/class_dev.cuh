@@ -79,6 +79,12 @@ __device__ __forceinline__ long tuple_index(const DevClass& C, const int* extdim
   return t;
 }
 
+inline long ipow_host(int a, int k) {
+  long r = 1;
+  for (int i = 0; i < k; ++i) r *= a;
+  return r;
+}
+
 inline int launch_blocks(long total, int threads = 256) {
   long b = (total + threads - 1) / threads;
   return (int)std::max<long>(1, std::min<long>(b, 152L * 32));

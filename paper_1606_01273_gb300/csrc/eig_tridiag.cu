@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "class_ag.cuh"
+#include "ozaki.cuh"
 #include "linalg.cuh"
 
 namespace caspt2 {
@@ -867,6 +868,12 @@ k_cluster_cgs2(const double* __restrict__ w, int m, double tol, int smem_bytes,
       Z[(t / c) * m + j0 + t % c] = cs[t];
 }
 
+// G[i][i] -= x
+__global__ void k_sub_diag(double* __restrict__ G, int m, double x) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) G[(long)i * m + i] -= x;
+}
+
 // G = 1.5 I - 0.5 G (in place)
 // and dev = max |G - I| (order-independent integer maximum of the bit patterns)
 __global__ void k_ns_coef(double* __restrict__ G, int m, unsigned long long* __restrict__ dev) {
@@ -1150,7 +1157,7 @@ int backtransform_wy(const double* vbuf, const double* tau, int m, double* V, do
 }  // namespace
 
 int sym_eig_tridiag(double* A, int m, double* w, double* V, double* work, cudaStream_t s,
-                    KernelTimer* tm) {
+                    KernelTimer* tm, OzWork* oz) {
   if (m <= 0) return CASPT2_OK;
   const long mm = (long)m * m;
   double* vbuf = work;            // m*m reflectors
@@ -1368,10 +1375,27 @@ int sym_eig_tridiag(double* A, int m, double* w, double* V, double* work, cudaSt
     double dev_ortho;
     std::memcpy(&dev_ortho, &hdev, sizeof(double));
     if (!(dev_ortho == dev_ortho)) return CASPT2_ENAN;
-    if (dev_ortho <= 1e-13)
+    if (dev_ortho <= 1e-13) {
       CASPT2_CUDA_TRY(cudaMemcpyAsync(V, Z, sizeof(double) * mm, cudaMemcpyDeviceToDevice, s));
-    else
+    } else if (oz && oz->on) {
+      // V = Z + Z Ec, Ec = (1/2)(I - Z^T Z) (G - I): the correction is of the size of the
+      // orthogonality error, so a split product with S slices (error below about
+      // 2^(1-7S) m max|Z| max|Ec|) is kept under 1e-17 with S = ceil((57 + log2(m dev/2)) / 7)
+      ++launch_counter();
+      k_sub_diag<<<(m + 255) / 256, 256, 0, s>>>(G, m, 1.0);
+      CASPT2_CUDA_TRY(cudaGetLastError());
+      CASPT2_CUDA_TRY(cudaMemcpyAsync(V, Z, sizeof(double) * mm, cudaMemcpyDeviceToDevice, s));
+      const double lg = std::log2(std::max(1e-300, 0.5 * (double)m * dev_ortho));
+      const int S = std::max(2, std::min(kOzMaxSlices, (int)std::ceil((57.0 + lg) / 7.0)));
+      const int S0 = oz->S;
+      oz->S = S;
+      const OzView vz{Z, m, 1, m, 0}, vg{G, m, 1, m, 0};   // G symmetric: B(j, k) = G[j][k]
+      const cudaError_t e = oz_matmul(*oz, vz, vg, false, m, m, m, 1.0, 1.0, V, m, s);
+      oz->S = S0;
+      CASPT2_CUDA_TRY(e);
+    } else {
       CASPT2_CUDA_TRY(dgemm(m, m, m, 1.0, Z, m, false, G, m, false, 0.0, V, m, s));
+    }
   }
   // 5. back-transformation V = H_0 ... H_{m-3} Z: blocked (compact WY panels as FP64
   //    GEMMs) for large matrices, else column-owned in one launch.  Z, G and the

@@ -36,13 +36,17 @@ int sym_eig_jacobi(double* A, int m, double* w, double* V, double* work, cudaStr
 // inverse iteration and back-transformation (eig_tridiag.cu).  A is destroyed; w[m]
 // ascending; V[m][m] eigenvectors as columns.  work >= sym_eig_tridiag_work(m) doubles.
 size_t sym_eig_tridiag_work(int m);
+// oz (optional, on): the Newton-Schulz correction Z (1/2)(I - Z^T Z), a term of the size of
+// the orthogonality error, runs as a split-BF16 product with just enough slices.
+struct OzWork;
 int sym_eig_tridiag(double* A, int m, double* w, double* V, double* work, cudaStream_t s,
-                    KernelTimer* tm = nullptr);
+                    KernelTimer* tm = nullptr, OzWork* oz = nullptr);
 
 // Dispatch: Jacobi for small matrices, tridiagonal method otherwise.
 inline int sym_eig(double* A, int m, double* w, double* V, double* work, cudaStream_t s,
-                   KernelTimer* tm = nullptr) {
-  return m <= 32 ? sym_eig_jacobi(A, m, w, V, work, s) : sym_eig_tridiag(A, m, w, V, work, s, tm);
+                   KernelTimer* tm = nullptr, OzWork* oz = nullptr) {
+  return m <= 32 ? sym_eig_jacobi(A, m, w, V, work, s)
+                 : sym_eig_tridiag(A, m, w, V, work, s, tm, oz);
 }
 inline size_t sym_eig_work(int m) {
   return std::max<size_t>((size_t)2 * m * m + 2, sym_eig_tridiag_work(m));

@@ -392,6 +392,107 @@ void build_src_plans(int cls, std::vector<SrcPlan>& out) {
   }
 }
 
+void split_src_plans(int cls, const std::vector<SrcPlan>& in, std::vector<SrcPlan>& rest,
+                     std::vector<SrcGemmGroup>& groups) {
+  const ClassDef& C = kClasses[cls];
+  rest.clear();
+  groups.clear();
+  auto is_bra = [](int r) { return r >= kRefBra && r < kRefBra + 8; };
+  auto slot_sp = [&](int r) { return C.slot_space[r - kRefBra]; };
+  for (const SrcPlan& P : in) {
+    const int ni = P.kind == 0 ? 2 : 4;
+    bool ok = true;
+    for (int j = 0; j < ni; ++j)
+      if (is_bra(P.iidx[j]) && slot_sp(P.iidx[j]) == SP_A) ok = false;
+    int cls_of[4] = {0, 0, 0, 0};          // 1 shared, 2 integral-only, 3 RDM-only
+    for (int j = 0; j < P.nloop && ok; ++j) {
+      bool inI = false, inR = false;
+      for (int q = 0; q < ni; ++q) inI = inI || P.iidx[q] == kRefLoop + j;
+      for (int q = 0; q < 2 * P.rank; ++q) inR = inR || P.idx[q] == kRefLoop + j;
+      for (int q = 0; q < P.neq; ++q)
+        if (P.eq[q][0] == kRefLoop + j || P.eq[q][1] == kRefLoop + j) ok = false;
+      cls_of[j] = inI && inR ? 1 : (inI ? 2 : (inR ? 3 : 0));
+      if (cls_of[j] == 0) ok = false;
+      if ((cls_of[j] == 1 || cls_of[j] == 3) && P.loop_space[j] != SP_A) ok = false;
+    }
+    if (!ok) {
+      rest.push_back(P);
+      continue;
+    }
+    // canonical numbering: shared and RDM-only loops by first appearance in the RDM
+    // indices, integral-only loops in order
+    int pos[4] = {-1, -1, -1, -1};
+    int ns = 0, nr = 0, nx = 0;
+    for (int q = 0; q < 2 * P.rank; ++q) {
+      const int r = P.idx[q];
+      if (r >= kRefLoop && r < kRefLoop + 4 && cls_of[r - kRefLoop] == 1 && pos[r - kRefLoop] < 0)
+        pos[r - kRefLoop] = ns++;
+    }
+    for (int q = 0; q < 2 * P.rank; ++q) {
+      const int r = P.idx[q];
+      if (r >= kRefLoop && r < kRefLoop + 4 && cls_of[r - kRefLoop] == 3 && pos[r - kRefLoop] < 0)
+        pos[r - kRefLoop] = nr++;
+    }
+    for (int j = 0; j < P.nloop; ++j)
+      if (cls_of[j] == 2) pos[j] = nx++;
+    if (ns > 2 || nr > 3) {
+      rest.push_back(P);
+      continue;
+    }
+    auto gref = [&](int r) -> int8_t {
+      if (r >= kRefLoop && r < kRefLoop + 4) {
+        const int j = r - kRefLoop;
+        return (int8_t)(kRefLoop + (cls_of[j] == 1 ? pos[j] : ns + pos[j]));
+      }
+      return (int8_t)r;
+    };
+    SrcGSig g{};
+    g.rank = P.rank;
+    g.ns = (int8_t)ns;
+    g.nloop = (int8_t)nr;
+    for (int q = 0; q < 2 * P.rank; ++q) g.idx[q] = gref(P.idx[q]);
+    SrcXTerm x{};
+    x.coeff = P.coeff;
+    x.kind = P.kind;
+    x.cb = P.cb;
+    for (int q = 0; q < 4; ++q) {
+      x.ispace[q] = P.ispace[q];
+      x.iidx[q] = q < ni ? gref(P.iidx[q]) : 0;
+    }
+    x.nloop = (int8_t)nx;
+    for (int j = 0; j < P.nloop; ++j)
+      if (cls_of[j] == 2) x.loop_space[pos[j]] = P.loop_space[j];
+    for (int q = 0; q < P.neq; ++q) {
+      const int r0 = P.eq[q][0], r1 = P.eq[q][1];
+      if (slot_sp(r0) == SP_A) {
+        g.eq[g.neq][0] = (int8_t)std::min(r0, r1);
+        g.eq[g.neq][1] = (int8_t)std::max(r0, r1);
+        ++g.neq;
+      } else {
+        x.eq[x.neq][0] = (int8_t)r0;
+        x.eq[x.neq][1] = (int8_t)r1;
+        ++x.neq;
+      }
+    }
+    bool placed = false;
+    for (SrcGemmGroup& G : groups) {
+      if (G.fb != P.fb || G.g.rank != g.rank || G.g.ns != g.ns || G.g.nloop != g.nloop ||
+          G.g.neq != g.neq)
+        continue;
+      bool same = true;
+      for (int q = 0; q < 2 * g.rank && same; ++q) same = G.g.idx[q] == g.idx[q];
+      for (int q = 0; q < g.neq && same; ++q)
+        same = G.g.eq[q][0] == g.eq[q][0] && G.g.eq[q][1] == g.eq[q][1];
+      if (same) {
+        G.x.push_back(x);
+        placed = true;
+        break;
+      }
+    }
+    if (!placed) groups.push_back(SrcGemmGroup{P.fb, g, {x}});
+  }
+}
+
 void presum_src_plans(const std::vector<SrcPlan>& in, std::vector<SrcPlan>& out,
                       std::vector<PresumSpec>& specs) {
   out.clear();

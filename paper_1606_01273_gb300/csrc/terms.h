@@ -76,6 +76,39 @@ struct PresumSpec {
 void presum_src_plans(const std::vector<SrcPlan>& in, std::vector<SrcPlan>& out,
                       std::vector<PresumSpec>& specs);
 
+// Source terms recast as matrix products.  A term whose integral carries only external
+// slots and loop indices (no active output slot) factorises as
+//   V[fam][ext][(act..., M, L)] += sum_k X[ext][k] G[k][(act..., M, L)],
+// k running over the loop indices shared by the integral and the RDM: X = coeff x integral
+// (summed over integral-only loops, Kronecker deltas among external slots), G = RDM (summed
+// over RDM-only loops, deltas among active slots).  Terms with the same G are grouped and
+// their X summed, so a group is one GEMM with K = a^ns.
+struct SrcXTerm {
+  double coeff;
+  int8_t kind, cb;
+  int8_t ispace[4];
+  int8_t iidx[4];      // refs: bra slots, kRefLoop + p (shared, p < ns), kRefLoop + ns + q
+                       // (integral-only loop q), kRefZero
+  int8_t nloop;        // integral-only loops
+  int8_t loop_space[4];
+  int8_t neq;          // deltas among external slots
+  int8_t eq[4][2];
+};
+struct SrcGSig {
+  int8_t rank, ns, nloop, neq;  // nloop: RDM-only loops (active)
+  int8_t idx[8];                // refs: bra active slots, kRefLoop + p (shared), kRefLoop + ns + q
+  int8_t eq[4][2];              // deltas among active slots
+};
+struct SrcGemmGroup {
+  int fb;
+  SrcGSig g;
+  std::vector<SrcXTerm> x;
+};
+// Split the (pre-summed) source plans of class cls into GEMM groups and the terms that stay
+// with the plan interpreter.
+void split_src_plans(int cls, const std::vector<SrcPlan>& in, std::vector<SrcPlan>& rest,
+                     std::vector<SrcGemmGroup>& groups);
+
 // Build the plans of class cls (0..6).  Deterministic; a few hundred terms.
 void build_act_plans(int cls, bool with_fock, std::vector<ActPlan>& out);
 void build_src_plans(int cls, std::vector<SrcPlan>& out);

@@ -56,13 +56,24 @@ class Problem:
         return [self.rdm[k] for k in range(1, kmax + 1)]
 
 
-def df_factors(rng: np.random.Generator, naux: int, nmo: int, decay: float, c0: float = 0.5):
+def df_factors(rng: np.random.Generator, naux: int, nmo: int, decay: float, c0: float = 0.5,
+               device: str | None = None):
+    """device: None forms the product with numpy (the stored oracle results depend on those
+    bytes); a torch device name forms the same product there (other rounding)."""
     k = np.arange(naux)
     sigma = np.exp(-k / decay)
     alpha = math.sqrt(c0 / (naux * float(np.sum(sigma ** 2))))
     U = rng.standard_normal((naux, naux))
     G = rng.standard_normal((naux, nmo, nmo))
     W = 0.5 * (G + G.transpose(0, 2, 1))
+    if device is not None:
+        import torch
+        Ut = torch.from_numpy(U * sigma[None, :]).to(device)
+        Wt = torch.from_numpy(W.reshape(naux, nmo * nmo)).to(device)
+        B = (alpha * (Ut @ Wt)).cpu().numpy().reshape(naux, nmo, nmo)
+        del Ut, Wt
+        _release_device(device)
+        return B
     B = alpha * ((U * sigma[None, :]) @ W.reshape(naux, nmo * nmo)).reshape(naux, nmo, nmo)
     return B
 
@@ -92,15 +103,17 @@ def _release_device(dev: str) -> None:
 
 def make_problem(nclosed: int, nact: int, nvirt: int, naux: int, nstate: int,
                  seed: int, nelact: int | None = None, decay: float = 10.0,
-                 kmax: int = 4, device: str | None = None, fast: bool | None = None) -> Problem:
+                 kmax: int = 4, device: str | None = None, fast: bool | None = None,
+                 df_device: str | None = None) -> Problem:
     """Build one seeded problem.  nelact defaults to nact (half filling).  Active spaces
     above DENSE_CASCI_MAX determinants (or any, with fast=True) use the Davidson /
-    Gram-matrix path of synth.casci_fast on `device` (default: the GPU when present)."""
+    Gram-matrix path of synth.casci_fast on `device` (default: the GPU when present).
+    df_device: form the DF factors' product on that torch device (see df_factors)."""
     if nelact is None:
         nelact = nact
     rng = np.random.Generator(np.random.PCG64(seed))
     nmo = nclosed + nact + nvirt
-    B = df_factors(rng, naux, nmo, decay)
+    B = df_factors(rng, naux, nmo, decay, device=df_device)
     eps_c = np.sort(rng.uniform(-2.5, -0.4, nclosed))
     eps_v = np.sort(np.exp(rng.uniform(math.log(0.2), math.log(4.0), nvirt)))
     t = rng.uniform(-0.3, 0.3, (nact, nact))
