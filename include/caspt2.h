@@ -185,7 +185,9 @@ int caspt2_get_core_energy(caspt2_ctx* ctx, double* ecore);
  * [5] the Householder tridiagonalisation kernel summed over its launches, [6] its
  * algorithmic flops (4/3 m^3 per launch), [7] its number of launches, [8] the last
  * caspt2_densities call (0 before one), [9] the tridiagonalisation's algorithmic DRAM bytes
- * (the matrix read and the reflectors written once: 8 m^2 + 4 m (m - 1) per launch).
+ * (the matrix read and the reflectors written once: 8 m^2 + 4 m (m - 1) per launch),
+ * [10] the FP64 GEMM launches of the solve summed (device time by event pairs, the first
+ * 4096 launches), [11] their algorithmic flops (2 M N K), [12] their number.
  *   times[k] is written for k < *count on input; *count = number of entries on output. */
 int caspt2_get_timings(caspt2_ctx* ctx, double* times, int* count);
 

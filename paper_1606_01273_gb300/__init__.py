@@ -227,8 +227,8 @@ class Context:
                     _check(lib().caspt2_get_class_lambda(self._h, k, _dp(a_), _dp(b_)),
                            "caspt2_get_class_lambda")
                     lam_NL[name], lam_lv[name] = a_, b_
-        t = np.zeros(10)
-        cnt = C.c_int(10)
+        t = np.zeros(32)
+        cnt = C.c_int(32)
         _check(lib().caspt2_get_timings(self._h, _dp(t), C.byref(cnt)), "caspt2_get_timings")
         return Result(U, E0, Href, Heff, Ems, R, ec.value, e_cls, n_cls, status,
                       list(t[: cnt.value]), int(lib().caspt2_get_kernel_launches(self._h)),

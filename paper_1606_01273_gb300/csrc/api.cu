@@ -22,8 +22,9 @@ using namespace caspt2;
 namespace {
 
 constexpr int kNumStages = 4;  // setup, class H, classes A-G, H^eff
-constexpr int kNumTimes = kNumStages + 6;  // + class-H kernel, tridiagonalisation ms/flops/launches,
-                                           //   densities, tridiagonalisation bytes
+constexpr int kNumTimes = kNumStages + 9;  // + class-H kernel, tridiagonalisation ms/flops/launches,
+                                           //   densities, tridiagonalisation bytes, FP64 GEMM
+                                           //   ms/flops/launches
 
 }  // namespace
 
@@ -100,6 +101,7 @@ struct caspt2_ctx {
   double times[kNumTimes] = {};
   long launches = 0;
   KernelTimer tri{};
+  GemmTimer* gemm = nullptr;          // FP64 GEMM launches of a solve (device time, flops)
 
   template <class T>
   int alloc(T** p, size_t count) {
@@ -191,6 +193,10 @@ void caspt2_destroy(caspt2_ctx* ctx) {
   if (ctx->tri.e0) cudaEventDestroy(ctx->tri.e0);
   if (ctx->dev0) cudaEventDestroy(ctx->dev0);
   oz_release(ctx->oz);
+  if (ctx->gemm) {
+    gemm_timer_release(*ctx->gemm);
+    delete ctx->gemm;
+  }
   if (ctx->dev1) cudaEventDestroy(ctx->dev1);
   if (ctx->tri.e1) cudaEventDestroy(ctx->tri.e1);
   cudaSetDevice(cur);
@@ -517,6 +523,19 @@ int solve_impl(caspt2_ctx* c, void* stream) {
   const long launches0 = launch_counter();
   c->tri.ms = c->tri.flops = c->tri.bytes = 0.0;
   c->tri.launches = 0;
+  if (!c->gemm) {
+    c->gemm = new (std::nothrow) GemmTimer();
+    if (c->gemm && gemm_timer_init(*c->gemm) != cudaSuccess) {
+      gemm_timer_release(*c->gemm);
+      delete c->gemm;
+      c->gemm = nullptr;
+    }
+  }
+  if (c->gemm) c->gemm->used = 0;
+  struct TimerScope {
+    explicit TimerScope(GemmTimer* t) { set_gemm_timer(t); }
+    ~TimerScope() { set_gemm_timer(nullptr); }
+  } timer_scope(c->gemm);
   CASPT2_CUDA_TRY(cudaMemsetAsync(c->status, 0, sizeof(int), s));
   CASPT2_CUDA_TRY(cudaMemcpyAsync(c->mindenom, &big, sizeof(double), cudaMemcpyHostToDevice, s));
   CASPT2_CUDA_TRY(cudaMemsetAsync(c->ecls, 0, sizeof(double) * CASPT2_NCLASS * n * n, s));
@@ -643,6 +662,15 @@ int solve_impl(caspt2_ctx* c, void* stream) {
   c->times[kNumStages + 3] = (double)c->tri.launches;
   c->times[kNumStages + 5] = c->tri.bytes;
   c->times[kNumStages + 4] = 0.0;
+  c->times[kNumStages + 6] = c->times[kNumStages + 7] = c->times[kNumStages + 8] = 0.0;
+  if (c->gemm) {
+    double gms = 0.0, gfl = 0.0;
+    long gn = 0;
+    CASPT2_CUDA_TRY(gemm_timer_collect(*c->gemm, &gms, &gfl, &gn));
+    c->times[kNumStages + 6] = gms;
+    c->times[kNumStages + 7] = gfl;
+    c->times[kNumStages + 8] = (double)gn;
+  }
   c->launches = launch_counter() - launches0;
   c->solved = true;
   c->dens_done = false;

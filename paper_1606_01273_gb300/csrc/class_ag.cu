@@ -585,7 +585,7 @@ __global__ void k_sector_energy_ml(const double* __restrict__ Vt, const double* 
       for (int N = 0; N < NS; ++N) {
         const double vn = r[N] * inv;
 #pragma unroll
-        for (int q = 0; q < NS; ++q) m1[N * NS + q] = fma(vn, r[q], m1[N * NS + q]);
+        for (int q = N; q < NS; ++q) m1[N * NS + q] = fma(vn, r[q], m1[N * NS + q]);   // q >= N
         m2[N] = fma(r[N], wL, m2[N]);
       }
       m3 = fma(rL * rL * inv, inv * inv, m3);
@@ -597,7 +597,7 @@ __global__ void k_sector_energy_ml(const double* __restrict__ Vt, const double* 
       double* o = part + (((tl * nL + Li) * n) + N) * w;
 #pragma unroll
       for (int q = 0; q < NS; ++q)
-        if (q < n) o[q] = m1[N * NS + q];
+        if (q < n) o[q] = q >= N ? m1[N * NS + q] : m1[q * NS + N];   // M1 symmetric in (N, q)
       o[n] = m2[N];
       o[n + 1] = (N == L) ? m3 : 0.0;
     }

@@ -130,10 +130,65 @@ k_dgemm_s(int M, int N, int K, double alpha, const double* __restrict__ A, int l
   }
 }
 
+namespace {
+thread_local GemmTimer* tl_gemm_timer = nullptr;
+
+// Start of a timed launch: the slot of its event pair, or -1.
+int gemm_timer_begin(cudaStream_t s) {
+  GemmTimer* t = tl_gemm_timer;
+  if (!t || !t->ready || t->used >= kGemmTimerPairs) return -1;
+  const int slot = t->used++;
+  cudaEventRecord(t->ev[2 * slot], s);
+  return slot;
+}
+void gemm_timer_end(int slot, double flops, cudaStream_t s) {
+  if (slot < 0) return;
+  GemmTimer* t = tl_gemm_timer;
+  cudaEventRecord(t->ev[2 * slot + 1], s);
+  t->flops[slot] = flops;
+}
+}  // namespace
+
+cudaError_t gemm_timer_init(GemmTimer& t) {
+  if (t.ready) return cudaSuccess;
+  for (auto& e : t.ev) {
+    const cudaError_t r = cudaEventCreate(&e);
+    if (r != cudaSuccess) return r;
+  }
+  t.used = 0;
+  t.ready = true;
+  return cudaSuccess;
+}
+
+void gemm_timer_release(GemmTimer& t) {
+  for (auto& e : t.ev)
+    if (e) cudaEventDestroy(e);
+  t.ready = false;
+}
+
+void set_gemm_timer(GemmTimer* t) { tl_gemm_timer = t; }
+
+cudaError_t gemm_timer_collect(GemmTimer& t, double* ms, double* flops, long* launches) {
+  double tot = 0.0, fl = 0.0;
+  for (int k = 0; k < t.used; ++k) {
+    float x = 0.f;
+    const cudaError_t r = cudaEventElapsedTime(&x, t.ev[2 * k], t.ev[2 * k + 1]);
+    if (r != cudaSuccess) return r;
+    tot += x;
+    fl += t.flops[k];
+  }
+  *ms = tot;
+  *flops = fl;
+  *launches = t.used;
+  t.used = 0;
+  return cudaSuccess;
+}
+
 cudaError_t dgemm(int M, int N, int K, double alpha, const double* A, int lda, bool ta,
                   const double* B, int ldb, bool tb, double beta, double* C, int ldc,
                   cudaStream_t s, int batch, long sA, long sB, long sC) {
   if (M <= 0 || N <= 0 || batch <= 0) return cudaSuccess;
+  const int slot = gemm_timer_begin(s);
   // padded work of the 64 x 64 tiles against tiles fitted to M and N (<= 32)
   const double pad64 = (double)((M + kGT - 1) / kGT * kGT) * ((N + kGT - 1) / kGT * kGT) /
                        ((double)M * N);
@@ -149,6 +204,7 @@ cudaError_t dgemm(int M, int N, int K, double alpha, const double* A, int lda, b
     k_dgemm<<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, ta ? 1 : 0, B, ldb, tb ? 1 : 0, beta, C,
                                  ldc, sA, sB, sC, 0);
   }
+  gemm_timer_end(slot, 2.0 * M * N * (double)K * batch, s);
   return cudaGetLastError();
 }
 
@@ -160,9 +216,11 @@ cudaError_t dgemm_sym(int N, int K, double alpha, const double* A, int lda, bool
   if (N <= 0 || pad64 > 1.3 || T > 2048)
     return dgemm(N, N, K, alpha, A, lda, ta, B, ldb, tb, beta, C, ldc, s);
   ++launch_counter();
+  const int slot = gemm_timer_begin(s);
   dim3 grid((unsigned)((long)T * (T + 1) / 2), 1, 1);
   k_dgemm<<<grid, 256, 0, s>>>(N, N, K, alpha, A, lda, ta ? 1 : 0, B, ldb, tb ? 1 : 0, beta, C,
                                ldc, 0, 0, 0, 1);
+  gemm_timer_end(slot, 2.0 * kGT * kGT * (double)K * ((double)T * (T + 1) / 2), s);
   return cudaGetLastError();
 }
 

@@ -15,6 +15,22 @@ struct KernelTimer {
   long launches = 0;
 };
 
+// Optional record of the FP64 GEMM launches of one host thread: an event pair around each
+// launch (device time) and its algorithmic flops (2 M N K; the symmetric-output form its
+// computed tiles).  Up to kGemmTimerPairs launches per collection; later ones run untimed.
+constexpr int kGemmTimerPairs = 4096;
+struct GemmTimer {
+  cudaEvent_t ev[2 * kGemmTimerPairs] = {};
+  double flops[kGemmTimerPairs] = {};
+  int used = 0;
+  bool ready = false;
+};
+cudaError_t gemm_timer_init(GemmTimer& t);
+void gemm_timer_release(GemmTimer& t);
+void set_gemm_timer(GemmTimer* t);   // this thread's dgemm launches are recorded (nullptr: off)
+// Sum of the recorded launches (call after the stream has synchronised); resets the record.
+cudaError_t gemm_timer_collect(GemmTimer& t, double* ms, double* flops, long* launches);
+
 // Row-major C = alpha * op(A) op(B) + beta * C, op = transpose when the flag is set.
 // Batched over `batch` with element strides sA, sB, sC.
 cudaError_t dgemm(int M, int N, int K, double alpha, const double* A, int lda, bool ta,

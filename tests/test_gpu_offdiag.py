@@ -8,7 +8,8 @@ the one-body couplings between classes (opt.dens_offdiag), against
   * the RDM-form oracle (oracle/o2_offdiag.py) at nact 8 with several closed and virtual
     orbitals (ragged reduction chunks, both pair sectors populated), every element.
 
-The diagonal blocks must not change when the option is on."""
+The diagonal blocks do not change when the option is on (to the last bits of the atomic
+scatter sums of d1)."""
 import os
 
 import numpy as np
@@ -94,8 +95,10 @@ def test_offdiag_vs_rdm_oracle_nact8(cp, opt):
     d1_off, d2_off = _densities(cp, p, opt, 0)
     d1_on, d2_on = _densities(cp, p, opt, 1)
     diag, off = _blocks(p)
-    assert np.array_equal(d1_on, d1_off)
-    assert np.array_equal(d2_on * diag, d2_off * diag)
+    # d1 carries atomic scatter sums (last bits vary run to run); d2's diagonal blocks do not
+    # depend on the option
+    assert float(np.abs(d1_on - d1_off).max()) <= 1e-12 * max(1.0, float(np.abs(d1_off).max()))
+    assert float(np.abs((d2_on - d2_off) * diag).max()) <= 1e-12 * max(1.0, float(np.abs(d2_off).max()))
     assert float(np.abs(d2_off * off).max()) == 0.0
     scheme = "sssr" if opt["scheme"] else "msmr"
     st = o2.setup(p, xms=bool(opt["xms"]), kmax=4)
