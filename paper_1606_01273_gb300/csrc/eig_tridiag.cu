@@ -601,16 +601,36 @@ __device__ int sturm_nodiv(const double* __restrict__ d, const double* __restric
   return cnt;
 }
 
+// Sturm count in single precision by the ratio recurrence q_i = d_i - x - e_(i-1)^2 / q_(i-1)
+// (q raised to -pivmin where it vanishes): the count is exact for a tridiagonal matrix whose
+// elements carry relative errors of a few float roundings, so it brackets every eigenvalue
+// to within a few 2^-24 tnorm.
+__device__ int sturm_f32(const float* __restrict__ d, const float* __restrict__ e2, int m, float x,
+                         float pivmin) {
+  float q = d[0] - x;
+  if (fabsf(q) < pivmin) q = -pivmin;
+  int cnt = q < 0.f ? 1 : 0;
+  for (int i = 1; i < m; ++i) {
+    q = (d[i] - x) - __fdividef(e2[i - 1], q);
+    if (fabsf(q) < pivmin) q = -pivmin;
+    cnt += q < 0.f ? 1 : 0;
+  }
+  return cnt;
+}
+
 // j-th smallest eigenvalue by 4-way multisection inside the Gershgorin interval: four
 // lanes per eigenvalue evaluate the Sturm count at the three interior quarter points
 // (lane 3 idles), so each step removes two bits; stop at an absolute width of tol.
 __global__ void k_bisect(const double* __restrict__ dg, const double* __restrict__ e,
                          const double* __restrict__ e2g, int m, double glo, double ghi, double tol,
                          double* __restrict__ w) {
-  extern __shared__ double sde[];      // d[m], e2[m] staged per block
+  extern __shared__ double sde[];      // d[m], e2[m] staged per block (and float copies)
+  float* sdf = reinterpret_cast<float*>(sde + 2 * m);
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
     sde[i] = dg[i];
     sde[m + i] = e2g[i];
+    sdf[i] = (float)dg[i];
+    sdf[m + i] = (float)e2g[i];
   }
   __syncthreads();
   const double* d = sde;
@@ -625,6 +645,41 @@ __global__ void k_bisect(const double* __restrict__ dg, const double* __restrict
   if ((gid & ~7) >= (m << 3)) return;          // whole group beyond m
   const bool live = j < m;
   double lo = glo, hi = ghi;
+  // single-precision phase (the float units run many times the FP64 rate): octasection to
+  // a width of 64 float roundings of the norm, then the bracket widened by as much and
+  // checked with two FP64 counts (the full interval again if it fails)
+  const double span = fmax(fabs(glo), fabs(ghi));
+  const double fgap = 64.0 * 0x1p-24 * span;
+  if (span > 0.0 && span < 1e30 && ghi - glo > 4.0 * fgap) {
+    const float pivmin = (float)fmax(1e-30, 0x1p-24 * 1e-8 * span);
+    float flo = (float)glo, fhi = (float)ghi;
+    for (int it = 0; it < 40; ++it) {
+      if ((double)fhi - (double)flo <= fgap) break;
+      const float h = 0.125f * (fhi - flo);
+      const float x = flo + h * (float)(q + 1);
+      const bool above = live && q < 7 && x > flo && x < fhi &&
+                         sturm_f32(sdf, sdf + m, m, x, pivmin) > j;
+      const unsigned b = (__ballot_sync(grp, above) >> sh) & 0x7Fu;
+      const int first = b ? (__ffs(b) - 1) : 7;
+      const float nhi = first < 7 ? flo + h * (float)(first + 1) : fhi;
+      const float nlo = first > 0 ? flo + h * (float)first : flo;
+      if (!(nhi < fhi || nlo > flo)) break;
+      flo = nlo;
+      fhi = nhi;
+    }
+    const double clo = fmax(glo, (double)flo - fgap), chi = fmin(ghi, (double)fhi + fgap);
+    // lane 0 checks count(clo) <= j, lane 1 count(chi) > j
+    bool good = true;
+    if (live && q < 2) {
+      const int cnt = sturm_nodiv(d, e2, m, q == 0 ? clo : chi);
+      good = q == 0 ? (clo <= glo || cnt <= j) : (chi >= ghi || cnt > j);
+    }
+    const unsigned bad = (__ballot_sync(grp, !good) >> sh) & 0x3u;
+    if (!bad) {
+      lo = clo;
+      hi = chi;
+    }
+  }
   for (int it = 0; it < 60; ++it) {
     if (hi - lo <= tol) break;
     const double h = 0.125 * (hi - lo);
@@ -1127,7 +1182,7 @@ constexpr int kWyMinSize = 1024;    // blocked back-transformation from this siz
 // panel.  vbuf rows hold the reflectors with zeros left of their first entry, so a panel's
 // rows of vbuf are Vp^T as it stands.  scratch >= 2 b m + 2 b^2 + part doubles.
 int backtransform_wy(const double* vbuf, const double* tau, int m, double* V, double* scratch,
-                     long scratch_size, cudaStream_t s) {
+                     long scratch_size, cudaStream_t s, OzWork* oz) {
   const int nref = m - 2;
   const int nb = kWyPanel;
   double* W = scratch;
@@ -1146,11 +1201,24 @@ int backtransform_wy(const double* vbuf, const double* tau, int m, double* V, do
     ++launch_counter();
     k_wy_T<<<1, b, 0, s>>>(Gp, tau, k0, b, T);
     CASPT2_CUDA_TRY(cudaGetLastError());
-    CASPT2_CUDA_TRY(dgemm(b, m, r, 1.0, Vt + k0 + 1, m, false, V + (long)(k0 + 1) * m, m, false,
-                          0.0, W, m, s));
-    CASPT2_CUDA_TRY(dgemm(b, m, b, 1.0, T, b, false, W, m, false, 0.0, W2, m, s));
-    CASPT2_CUDA_TRY(dgemm(r, m, b, -1.0, Vt + k0 + 1, m, true, W2, m, false, 1.0,
-                          V + (long)(k0 + 1) * m, m, s));
+    if (oz && oz->on) {
+      // precision form: the two large products as FP64-accurate split products (the
+      // eigenvalues are fixed before this step; only the vectors pass through it)
+      const OzView va{Vt + k0 + 1, m, 1, r, 0};                  // rows l, K = row i
+      const OzView vb{V + (long)(k0 + 1) * m, 1, m, r, 0};       // rows col, K = row i
+      CASPT2_CUDA_TRY(oz_matmul(*oz, va, vb, false, b, m, r, 1.0, 0.0, W, m, s));
+      CASPT2_CUDA_TRY(dgemm(b, m, b, 1.0, T, b, false, W, m, false, 0.0, W2, m, s));
+      const OzView vp{Vt + k0 + 1, 1, m, b, 0};                  // rows i, K = l
+      const OzView vw{W2, 1, m, b, 0};                           // rows col, K = l
+      CASPT2_CUDA_TRY(oz_matmul(*oz, vp, vw, false, r, m, b, -1.0, 1.0, V + (long)(k0 + 1) * m,
+                                m, s));
+    } else {
+      CASPT2_CUDA_TRY(dgemm(b, m, r, 1.0, Vt + k0 + 1, m, false, V + (long)(k0 + 1) * m, m,
+                            false, 0.0, W, m, s));
+      CASPT2_CUDA_TRY(dgemm(b, m, b, 1.0, T, b, false, W, m, false, 0.0, W2, m, s));
+      CASPT2_CUDA_TRY(dgemm(r, m, b, -1.0, Vt + k0 + 1, m, true, W2, m, false, 1.0,
+                            V + (long)(k0 + 1) * m, m, s));
+    }
   }
   return CASPT2_OK;
 }
@@ -1325,10 +1393,13 @@ int sym_eig_tridiag(double* A, int m, double* w, double* V, double* work, cudaSt
   ++launch_counter();
   k_e2<<<(m + 255) / 256, 256, 0, s>>>(e, m, e2);
   ++launch_counter();
-  if (2 * sizeof(double) * (size_t)m > kBisectSmemMax) return CASPT2_EINVAL;
+  if (3 * sizeof(double) * (size_t)m > kBisectSmemMax) return CASPT2_EINVAL;
   CASPT2_CUDA_TRY(cudaFuncSetAttribute(k_bisect, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)kBisectSmemMax));
-  k_bisect<<<(8 * m + 31) / 32, 32, 2 * sizeof(double) * m, s>>>(
+  // blocks sized so that one wave covers all 8m lanes (the staged copy of the tridiagonal
+  // matrix limits residency to one block per SM at the largest sizes)
+  const int bis_t = (int)std::min<long>(1024, std::max<long>(32, ((8L * m + nsm - 1) / nsm + 31) / 32 * 32));
+  k_bisect<<<(unsigned)((8L * m + bis_t - 1) / bis_t), bis_t, 3 * sizeof(double) * m, s>>>(
       d, e, e2, m, glo, ghi, 4.0 * 2.2e-16 * std::max(1.0, tnorm), w);
   // 3. eigenvectors of T
   ++launch_counter();
@@ -1401,7 +1472,7 @@ int sym_eig_tridiag(double* A, int m, double* w, double* V, double* work, cudaSt
   //    GEMMs) for large matrices, else column-owned in one launch.  Z, G and the
   //    inverse-iteration scratch are free here.
   if (m >= kWyMinSize) {
-    const int st = backtransform_wy(vbuf, tau, m, V, Z, 7 * mm, s);
+    const int st = backtransform_wy(vbuf, tau, m, V, Z, 7 * mm, s, oz);
     if (st != CASPT2_OK) return st;
   } else if (m >= 3) {
     ++launch_counter();
