@@ -41,6 +41,11 @@ BENCH = {
               "5 states, shift 0.3 Eh, sigma_k = exp(-k/40), seed 4 (copper-corrole-shaped "
               "synthetic)"),
         step="caspt2_solve: setup, amplitudes of classes A-H, H^eff, E_MS, lambda of state 0"),
+    "c42a12v350x1200n4": dict(
+        opts=dict(xms=1, scheme=0, shift=0.2), densities=False,
+        desc=("XMS-CASPT2 MS-MR, nclosed 42, nact 12 (12e, 853776 dets), nvirt 350, naux 1200, "
+              "4 states, shift 0.2 Eh, seed 3 (benzophenone-shaped synthetic)"),
+        step="caspt2_solve: setup, amplitudes of classes A-H, H^eff, E_MS, lambda of state 0"),
     "c20a8v200x700n3": dict(
         opts=dict(xms=1, scheme=0, shift=0.2), densities=True,
         desc=("XMS-CASPT2 MS-MR, nclosed 20, nact 8 (8e, 4900 dets), nvirt 200, naux 700, "

@@ -61,6 +61,7 @@ struct caspt2_ctx {
   bool cw_on[7] = {};
   SectorWork sw{};
   double *rdm3r = nullptr, *rdm4r = nullptr, *h = nullptr, *fact = nullptr, *eps = nullptr;
+  double* hk = nullptr;               // precision form: core exchange block for h
   double *pack0 = nullptr, *pack1 = nullptr;
   std::map<int, double*> eri_blk;     // canonical space key -> (pq|rt) block
   EriBlocks eri_tab{};
@@ -381,6 +382,7 @@ int caspt2_create(caspt2_ctx** out, const caspt2_dims* dims, const caspt2_option
       q.srcGcap = std::max<long>(1, srcg_max);
       ALLOC(q.srcX, q.srcXcap); ALLOC(q.srcG, q.srcGcap);
       ALLOC(c->h, nmo * nmo);
+      if (o.precision == CASPT2_BF16X) ALLOC(c->hk, nmo * nmo);
       ALLOC(c->fact, a2);
       ALLOC(c->eps, nmo);
       if (packmax > 0) {
@@ -582,7 +584,7 @@ int solve_impl(caspt2_ctx* c, void* stream) {
     bool any = false;
     for (int k = 0; k < 7; ++k) any = any || c->cw_on[k];
     if (any) {
-      CASPT2_CUDA_TRY(launch_hcore(c->f, c->g, c->B, c->bsum, d, c->h, s));
+      CASPT2_CUDA_TRY(launch_hcore(c->f, c->g, c->B, c->bsum, d, c->h, s, &c->oz, c->hk));
       CASPT2_CUDA_TRY(launch_active_block(c->f, d, c->fact, s));
       CASPT2_CUDA_TRY(launch_eps_cv(c->f, d, c->eps, s));
       if (c->kmax >= 3)

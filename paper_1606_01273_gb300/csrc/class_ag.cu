@@ -505,34 +505,42 @@ __global__ void k_range_basis(const double* __restrict__ Q, const double* __rest
 __global__ void k_sector_src(const double* __restrict__ V, DevClass C, ExtDims ed, int a, int n,
                              int sector, int Lsel, long t0, long nt, int msec,
                              double* __restrict__ W) {
+  // one thread per (tuple, row prefix fam * A + act), the tuple fastest (coalesced writes of
+  // W); the tuple is decoded once and the n x n (M, L') block of V read contiguously
   const long A = ipow(a, C.nact);
   const long ncol = nt * n;
-  const long total = (long)msec * ncol;
+  const long nfa = Lsel < 0 ? msec / n : msec;
+  const long total = nt * nfa;
   const double isq2 = 0.70710678118654752440;
+  const long nn = (long)n * n;
   for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
        e += (long)gridDim.x * blockDim.x) {
-    const int row = e / ncol;
-    const long cidx = e % ncol;
-    const int Lp = cidx % n;
-    const long t = t0 + cidx / n;
+    const long tl = e % nt;
+    const long fa = e / nt;                     // fam * A + act
+    const long t = t0 + tl;
     int co[3], cs[3];
     sector_tuple(C, ed.d, sector, t, co, cs);
-    const int M = Lsel < 0 ? row % n : Lsel;
-    const long fa = Lsel < 0 ? row / n : row;   // fam * A + act
-    const int fam = fa / A;
+    const int fam = (int)(fa / A);
     const long act = fa % A;
     long off = fam, offs = fam;
     for (int k = 0; k < C.next; ++k) {
       off = off * ed.d[k] + co[k];
       offs = offs * ed.d[k] + cs[k];
     }
-    const long tail = (act * n + M) * n + Lp;
-    const long ia = off * A * n * n + tail, ib = offs * A * n * n + tail;
-    double w;
-    if (C.pair0 < 0) w = V[ia];
-    else if (sector == 0) w = (ia == ib) ? V[ia] : (V[ia] + V[ib]) * isq2;
-    else w = (V[ia] - V[ib]) * isq2;
-    W[e] = w;
+    const long ia0 = off * A * nn + act * nn, ib0 = offs * A * nn + act * nn;
+    const int m0 = Lsel < 0 ? 0 : Lsel, m1 = Lsel < 0 ? n : Lsel + 1;
+    for (int M = m0; M < m1; ++M) {
+      const long row = Lsel < 0 ? fa * n + M : fa;
+      double* wr = W + row * ncol + tl * n;
+      for (int Lp = 0; Lp < n; ++Lp) {
+        const long ia = ia0 + (long)M * n + Lp, ib = ib0 + (long)M * n + Lp;
+        double w;
+        if (C.pair0 < 0) w = V[ia];
+        else if (sector == 0) w = (ia == ib) ? V[ia] : (V[ia] + V[ib]) * isq2;
+        else w = (V[ia] - V[ib]) * isq2;
+        wr[Lp] = w;
+      }
+    }
   }
 }
 
@@ -605,6 +613,37 @@ __global__ void k_sector_energy_ml(const double* __restrict__ Vt, const double* 
   __shared__ double red[32];
   dmin = block_min(dmin, red);
   if (threadIdx.x == 0) atomicMin_double(mindenom, dmin);
+}
+
+// e_ext(t) of every tuple of a sector (one decode per tuple), for k_mu_mindenom_ee.
+__global__ void k_sector_eext(const double* __restrict__ eps, DevClass C, ExtDims ed, int c,
+                              int sector, long ntup, double* __restrict__ ee) {
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < ntup;
+       t += (long)gridDim.x * blockDim.x) {
+    int co[3], cs[3];
+    sector_tuple(C, ed.d, sector, t, co, cs);
+    double x = 0.0;
+    for (int k = 0; k < C.next; ++k)
+      x += (C.slot_space[C.ext[k]] == SP_V) ? eps[c + co[k]] : -eps[co[k]];
+    ee[t] = x;
+  }
+}
+
+// k_mu_mindenom from the stored e_ext of the tuples.
+__global__ void k_mu_mindenom_ee(const double* __restrict__ omega, const double* __restrict__ E0,
+                                 const double* __restrict__ ee, int n, int Lsel, long ntup,
+                                 double shift, double* __restrict__ mdn) {
+  __shared__ double red[32];
+  const int mu = blockIdx.y;
+  const int nL = Lsel < 0 ? n : 1;
+  double dmin = 1e300;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < ntup;
+       t += (long)gridDim.x * blockDim.x) {
+    const double x = ee[t] + omega[mu];
+    for (int Li = 0; Li < nL; ++Li) dmin = fmin(dmin, fabs(x - E0[Lsel < 0 ? Li : Lsel] + shift));
+  }
+  dmin = block_min(dmin, red);
+  if (threadIdx.x == 0) atomicMin_double(mdn + mu, dmin);
 }
 
 // Smallest |e_ext(t) + omega_mu - E0_L + E_s| over the tuples of the sector and the states
@@ -951,9 +990,33 @@ cudaError_t launch_lambda(const double* mom, const double* R, int n, int P, doub
   return cudaGetLastError();
 }
 
+// h = f - g_act - 2 J + Kc with the exchange part Kc[x][y] = sum_(P, j) B_Pxj B_Pjy given
+__global__ void k_hcore_j(const double* __restrict__ f, const double* __restrict__ gact,
+                          const double* __restrict__ B, const double* __restrict__ bsum, int X,
+                          int nmo, const double* __restrict__ Kc, double* __restrict__ h) {
+  const long total = (long)nmo * nmo;
+  for (long xy = blockIdx.x * (long)blockDim.x + threadIdx.x; xy < total;
+       xy += (long)gridDim.x * blockDim.x) {
+    double jc = 0.0;
+    for (int P = 0; P < X; ++P) jc += B[(long)P * total + xy] * bsum[P];
+    h[xy] = f[xy] - gact[xy] - (2.0 * jc - Kc[xy]);
+  }
+}
+
 cudaError_t launch_hcore(const double* f, const double* g_act, const double* B, const double* bsum,
-                         const Dims& d, double* h, cudaStream_t s) {
+                         const Dims& d, double* h, cudaStream_t s, OzWork* oz, double* ktmp) {
   const long tot = (long)d.nmo() * d.nmo();
+  if (oz && oz->on && oz->S >= kOzMaxSlices && ktmp && d.c > 0) {
+    // precision form: the core exchange sum_(P, j) B_Pxj B_Pjy as one split Gram product
+    // over K = (P, j) (B symmetric in its orbital pair)
+    const int nmo = d.nmo();
+    const OzView vb{B, 1, nmo, d.c, (long)nmo * nmo};        // rows x, K = (P, j)
+    cudaError_t e = oz_matmul(*oz, vb, vb, true, nmo, nmo, d.X * d.c, 1.0, 0.0, ktmp, nmo, s);
+    if (e != cudaSuccess) return e;
+    ++launch_counter();
+    k_hcore_j<<<launch_blocks(tot, 128), 128, 0, s>>>(f, g_act, B, bsum, d.X, nmo, ktmp, h);
+    return cudaGetLastError();
+  }
   ++launch_counter();
   k_hcore<<<launch_blocks(tot, 128), 128, 0, s>>>(f, g_act, B, bsum, d.X, d.nmo(), d.c, h);
   return cudaGetLastError();
@@ -1280,9 +1343,20 @@ int class_solve(ClassWork& w, SectorWork& sw, const Dims& d, int scheme, double 
         const double big = 1e300;
         ++launch_counter();
         k_fill<<<launch_blocks(nk), 256, 0, s>>>(mdn, nk, big);
-        ++launch_counter();
-        k_mu_mindenom<<<dim3((unsigned)std::min<long>((ntup + 255) / 256, 64), nk), 256, 0, s>>>(
-            K.omega, E0, eps_cv, w.dc, w.ed, d.c, n, sec, Lsel, ntup, nk, shift, mdn);
+        if (ntup <= sw.wcap) {
+          // the tuples' external energies once into W (free until the sector sources)
+          ++launch_counter();
+          k_sector_eext<<<launch_blocks(ntup), 256, 0, s>>>(eps_cv, w.dc, w.ed, d.c, sec, ntup,
+                                                            sw.W);
+          ++launch_counter();
+          k_mu_mindenom_ee<<<dim3((unsigned)std::min<long>((ntup + 255) / 256, 64), nk), 256, 0,
+                             s>>>(K.omega, E0, sw.W, n, Lsel, ntup, shift, mdn);
+        } else {
+          ++launch_counter();
+          k_mu_mindenom<<<dim3((unsigned)std::min<long>((ntup + 255) / 256, 64), nk), 256, 0,
+                          s>>>(K.omega, E0, eps_cv, w.dc, w.ed, d.c, n, sec, Lsel, ntup, nk,
+                               shift, mdn);
+        }
         CASPT2_CUDA_TRY(cudaGetLastError());
         std::vector<double> hm(nk);
         CASPT2_CUDA_TRY(cudaMemcpyAsync(hm.data(), mdn, sizeof(double) * nk, cudaMemcpyDeviceToHost, s));
@@ -1346,7 +1420,7 @@ int class_solve(ClassWork& w, SectorWork& sw, const Dims& d, int scheme, double 
       for (long t0 = tb; t0 < te; t0 += chunk) {
         const long nt = std::min(chunk, te - t0);
         ++launch_counter();
-        k_sector_src<<<launch_blocks((long)msec * nt * n), 256, 0, s>>>(
+        k_sector_src<<<launch_blocks((long)(scheme == CASPT2_SSSR ? msec : msec / n) * nt), 256, 0, s>>>(
             w.V, w.dc, w.ed, d.a, n, sec, Lsel, t0, nt, msec, sw.W);
         CASPT2_CUDA_TRY(cudaGetLastError());
         if (oz && oz->on && oz->S >= kOzMaxSlices) {

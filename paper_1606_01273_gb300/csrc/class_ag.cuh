@@ -187,7 +187,9 @@ cudaError_t eri_block(const double* B, const Dims& d, const int sp[4], double* p
                       double* out, cudaStream_t s, OzWork* oz = nullptr);
 
 // h = f - g(d_core) - g(d_act), g(d_core)_xy = sum_j [2 (xy|jj) - (xj|jy)]
+// oz (on, 7 slices) with ktmp [nmo][nmo]: the core exchange as a split Gram product.
 cudaError_t launch_hcore(const double* f, const double* g_act, const double* B, const double* bsum,
-                         const Dims& d, double* h, cudaStream_t s);
+                         const Dims& d, double* h, cudaStream_t s, OzWork* oz = nullptr,
+                         double* ktmp = nullptr);
 
 }  // namespace caspt2

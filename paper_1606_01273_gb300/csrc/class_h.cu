@@ -292,7 +292,9 @@ __global__ void k_classH_sums(const double* __restrict__ KK, const double* __res
   const double sh = shifts[k];
   const long cv = (long)c * v;
   double e = 0.0, nr = 0.0, n3 = 0.0;
-  float dminf = 3.0e38f;   // smallest |D| (single precision suffices for the warning)
+  // smallest |D| with KK != 0, kept as the bit pattern of |D| (non-negative doubles order
+  // like their bit patterns, so the minimum runs on the integer units)
+  unsigned long long dminb = 0x7FF0000000000000ull;
   // rows (i, a) over the blocks, (j, b) of a row over the threads: index arithmetic once
   // per row and per j, not per element
   for (long ia = (long)i0 * v + blockIdx.x; ia < (long)i1 * v; ia += gridDim.x) {
@@ -310,11 +312,13 @@ __global__ void k_classH_sums(const double* __restrict__ KK, const double* __res
         e += x;
         nr = fma(x, inv, nr);
         n3 = fma(x * inv, inv, n3);
-        if ((__double_as_longlong(num) << 1) != 0) dminf = fminf(dminf, fabsf((float)D));
+        const unsigned long long db =
+            (unsigned long long)__double_as_longlong(D) & 0x7FFFFFFFFFFFFFFFull;
+        if ((__double_as_longlong(num) << 1) != 0 && db < dminb) dminb = db;
       }
     }
   }
-  double dmin = dminf < 3.0e38f ? (double)dminf : 1e300;
+  double dmin = dminb < 0x7FF0000000000000ull ? __longlong_as_double((long long)dminb) : 1e300;
   const int ncol = 3 * nshift + 1;
   double* out = partial + ((long)blockIdx.y * gridDim.x + blockIdx.x) * ncol;
   for (int t = threadIdx.x; t < 3 * nshift; t += blockDim.x) out[t] = 0.0;
@@ -440,9 +444,11 @@ cudaError_t launch_classH_split(const double* f, const double* B, const double* 
   k_classH_num<<<(int)std::min<long>((total + 255) / 256, 152L * 32), 256, 0, s>>>(K, d.c, d.v, i0,
                                                                                   i1, KK);
   const int nblk = (int)std::max<long>(1, std::min<long>(w.nblocks / nshift, 152L * 4));
+  // one pass over b per (i, a, j) when v fits a block (no idle tail of lanes)
+  const int hthreads = d.v <= 1024 ? std::max(64, (d.v + 31) / 32 * 32) : 256;
   ++launch_counter();
-  k_classH_sums<<<dim3(nblk, nshift), 256, 0, s>>>(KK, w.eps, w.shifts, nshift, d.c, d.v, i0, i1,
-                                                   w.partial);
+  k_classH_sums<<<dim3(nblk, nshift), hthreads, 0, s>>>(KK, w.eps, w.shifts, nshift, d.c, d.v, i0,
+                                                        i1, w.partial);
   const int ncol = 3 * nshift + 1;
   ++launch_counter();
   k_reduce_cols<<<ncol, 256, 0, s>>>(w.partial, (long)nblk * nshift, ncol, w.sums);

@@ -164,4 +164,7 @@ WORKLOADS = {
     # copper-corrole shape: 10 active orbitals, 10 electrons (63504 determinants)
     "c70a10v600x2000n5": dict(nclosed=70, nact=10, nvirt=600, naux=2000, nstate=5, seed=4,
                               decay=40.0),
+    # benzophenone shape: 12 active orbitals, 12 electrons (853776 determinants)
+    "c42a12v350x1200n4": dict(nclosed=42, nact=12, nvirt=350, naux=1200, nstate=4, seed=3,
+                              decay=10.0),
 }
