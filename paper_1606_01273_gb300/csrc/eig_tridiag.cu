@@ -232,19 +232,19 @@ k_tridiag(double* __restrict__ A, int m, double* __restrict__ vbuf, double* __re
 //   A: every block forms the reflector of row k from the row (already up to date) into
 //      shared memory -- the reductions run in a fixed order, so every copy is the same;
 //      block 0 stores it (vbuf row k, column j of Vr, tau, d, e);
-//   B: p_raw = A22 v (a warp per row, four loads in flight per lane) and partial sums of
-//      W^T v and V^T v;                                                  | barrier
+//   B: p_raw = A22 v (a warp per half row, eight loads in flight per lane) and partial
+//      sums of W^T v and V^T v;                                          | barrier
 //   C: p = tau (p_raw - V (W^T v) - W (V^T v)) (a warp per owned row, lanes over the
 //      panel columns) and partial sums of p.v;                           | barrier
 //   D: alpha = (tau/2) p.v, W[:, j] = p - alpha v, and the owned columns of row k+1
 //      brought up to date with the panel's columns 0..j.                 | barrier
 // W and Vr are [m][nb] row-major (Vr holds the panel's reflectors by row, so that a row's
-// panel entries are contiguous); p, pr [m]; part [grid][2 nb + 1]; sync[0..1] barrier,
+// panel entries are contiguous); p [m]; pr [2][m]; part [grid][2 nb + 1]; sync[0..1] barrier,
 // [2] error.  Dynamic shared memory: v [m].
 constexpr int kLatrdPanel = 64;
 constexpr int kLatrdMin = 1024;     // sizes at which the blocked reduction is used (when
                                     // the rows do not fit in shared memory)
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(512, 2)
 k_latrd(double* __restrict__ A, int m, int k0, int b, double* __restrict__ vbuf,
         double* __restrict__ tau, double* __restrict__ d, double* __restrict__ e,
         double* __restrict__ W, double* __restrict__ Vr, double* __restrict__ p,
@@ -304,24 +304,32 @@ k_latrd(double* __restrict__ A, int m, int k0, int b, double* __restrict__ vbuf,
     const double t = sh[0];
     const int R = (n1 + G - 1) / G;                   // rows (and row-k+1 columns) owned
     const int r0 = k + 1 + bid * R, r1 = min(m, r0 + R);
-    // ---- B: p_raw = A22 v over rows >= k+1; partials of W^T v, V^T v (columns l < j)
-    for (int i = warp; i < n1; i += nw) {
-      const double* row = A + (long)(k + 1 + i) * m;
-      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-      int q = k + 1 + lane;
-      for (; q + 96 < m; q += 128) {
-        const double a0 = __ldcg(row + q), a1 = __ldcg(row + q + 32);
-        const double a2 = __ldcg(row + q + 64), a3 = __ldcg(row + q + 96);
-        s0 = fma(a0, vs[q], s0);
-        s1 = fma(a1, vs[q + 32], s1);
-        s2 = fma(a2, vs[q + 64], s2);
-        s3 = fma(a3, vs[q + 96], s3);
-      }
-      for (; q < m; q += 32) s0 = fma(__ldcg(row + q), vs[q], s0);
-      double sum = (s0 + s1) + (s2 + s3);
+    // ---- B: p_raw = A22 v over rows >= k+1 as two half-row items per row (a warp per
+    //      item, eight loads in flight per lane; pr holds the halves, [0, m) and [m, 2m));
+    //      partials of W^T v, V^T v (columns l < j)
+    {
+      const int n1h = ((n1 + 1) / 2 + 31) / 32 * 32;
+      for (int it = warp; it < 2 * n1; it += nw) {
+        const int i = it >> 1, half = it & 1;
+        const double* row = A + (long)(k + 1 + i) * m;
+        const int qe = half ? m : min(m, k + 1 + n1h);
+        double sa[8];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
-      if (lane == 0) pr[k + 1 + i] = sum;
+        for (int u = 0; u < 8; ++u) sa[u] = 0.0;
+        int q = k + 1 + (half ? n1h : 0) + lane;
+        for (; q + 7 * 32 < qe; q += 8 * 32) {
+          double av[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) av[u] = __ldcg(row + q + 32 * u);
+#pragma unroll
+          for (int u = 0; u < 8; ++u) sa[u] = fma(av[u], vs[q + 32 * u], sa[u]);
+        }
+        for (; q < qe; q += 32) sa[0] = fma(__ldcg(row + q), vs[q], sa[0]);
+        double sum = ((sa[0] + sa[1]) + (sa[2] + sa[3])) + ((sa[4] + sa[5]) + (sa[6] + sa[7]));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
+        if (lane == 0) pr[half * m + k + 1 + i] = sum;
+      }
     }
     if (threadIdx.x < 2 * j) {
       const int tq = threadIdx.x;
@@ -332,10 +340,14 @@ k_latrd(double* __restrict__ A, int m, int k0, int b, double* __restrict__ vbuf,
     }
     if (!grid_sync_bounded(sync, sync + 1, err)) return;
     // ---- C: p = tau (p_raw - V x - W y), x = W^T v, y = V^T v; partials of p . v
-    for (int q = threadIdx.x; q < 2 * j; q += blockDim.x) {
+    //      (each x, y entry summed over the blocks' partials by one warp: lanes stride the
+    //      blocks, then a fixed shuffle tree)
+    for (int q = wib; q < 2 * j; q += wpb) {
       double acc = 0.0;
-      for (int g = 0; g < G; ++g) acc += __ldcg(part + (long)g * (2 * nb + 1) + q);
-      xy[q] = acc;
+      for (int g = lane; g < G; g += 32) acc += __ldcg(part + (long)g * (2 * nb + 1) + q);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) xy[q] = acc;
     }
     __syncthreads();
     {
@@ -346,7 +358,7 @@ k_latrd(double* __restrict__ A, int m, int k0, int b, double* __restrict__ vbuf,
           c = fma(__ldcg(Vr + (long)i * nb + l), xy[l], fma(__ldcg(W + (long)i * nb + l), xy[j + l], c));
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-        const double pv = t * (__ldcg(pr + i) - c);
+        const double pv = t * ((__ldcg(pr + i) + __ldcg(pr + m + i)) - c);
         if (lane == 0) p[i] = pv;
         sp = fma(pv, vs[i], sp);
       }
@@ -357,10 +369,12 @@ k_latrd(double* __restrict__ A, int m, int k0, int b, double* __restrict__ vbuf,
     // ---- D: alpha = (tau/2) p.v (fixed order over the blocks), W[:, j] = p - alpha v;
     //         the owned columns of row k+1 brought up to date (not after the panel's last
     //         column: the trailing GEMM update takes over there)
-    if (threadIdx.x == 0) {
+    if (wib == 0) {
       double sum = 0.0;
-      for (int g = 0; g < G; ++g) sum += __ldcg(part + (long)g * (2 * nb + 1) + 2 * nb);
-      sh[2] = 0.5 * t * sum;
+      for (int g = lane; g < G; g += 32) sum += __ldcg(part + (long)g * (2 * nb + 1) + 2 * nb);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+      if (lane == 0) sh[2] = 0.5 * t * sum;
     }
     __syncthreads();
     const double alpha = sh[2];
@@ -1286,8 +1300,8 @@ int sym_eig_tridiag(double* A, int m, double* w, double* V, double* work, cudaSt
     unsigned* sync = reinterpret_cast<unsigned*>(r);   // r is free until the back-transform
     double* Wp = u0;                                   // [m][kLatrdPanel]
     double* pp = u1;
-    double* pr = u1 + m;
-    double* part = u1 + 2 * (long)m;                   // [grid][2 panel + 1]
+    double* pr = u1 + m;                               // [2][m] (the two row halves)
+    double* part = u1 + 3 * (long)m;                   // [grid][2 panel + 1]
     double* Vr = u2;                                   // [m][kLatrdPanel]
     if (sizeof(double) * (size_t)m > kBisectSmemMax) return CASPT2_EINVAL;
     CASPT2_CUDA_TRY(cudaFuncSetAttribute(k_latrd, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1298,7 +1312,7 @@ int sym_eig_tridiag(double* A, int m, double* w, double* V, double* work, cudaSt
     // two blocks per SM when they fit (more warps in flight for the latency-bound
     // matrix-vector products), one otherwise
     const int grid = std::max(1, nsm * std::max(1, std::min(per, 2)));
-    if ((long)grid * (2 * kLatrdPanel + 1) > mm - 2 * (long)m) return CASPT2_EINVAL;
+    if ((long)grid * (2 * kLatrdPanel + 1) > mm - 3 * (long)m) return CASPT2_EINVAL;
     CASPT2_CUDA_TRY(cudaMemsetAsync(sync, 0, 4 * sizeof(unsigned), s));
     if (tm && tm->e0) CASPT2_CUDA_TRY(cudaEventRecord(tm->e0, s));
     for (int k0 = 0; k0 < m - 2; k0 += kLatrdPanel) {
