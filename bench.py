@@ -420,7 +420,8 @@ def run_ours(args):
         torch.cuda.synchronize(dev)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(steps)]
-        rec = {"kern_ms": [], "tri": [], "gemm": [], "dens_ms": [], "launches": 0, "status": []}
+        rec = {"kern_ms": [], "tri": [], "gemm": [], "panel": [], "dens_ms": [], "launches": 0,
+               "status": []}
         if ws > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize(dev)
@@ -441,6 +442,8 @@ def run_ours(args):
                                    r.timings_ms[9]))
                 rec["gemm"].append(tuple(r.timings_ms[10:13]) if len(r.timings_ms) >= 13
                                    else (0.0, 0.0, 0.0))
+                rec["panel"].append(tuple(r.timings_ms[13:16]) if len(r.timings_ms) >= 16
+                                    else (0.0, 0.0, 0.0))
                 rec["launches"] += r.launches
             torch.cuda.synchronize(dev)
         if ws > 1:
@@ -457,6 +460,7 @@ def run_ours(args):
     kern_ms, tri, dens_ms, launches, clk = (main["kern_ms"], main["tri"], main["dens_ms"],
                                             main["launches"], main["clk"])
     gemm = main["gemm"]
+    panel = main["panel"]
     value = job_rate(sum_over_ranks(args.steps, dev), total_s)
     # the plain FP64 form and the end-to-end run take fewer steps than the headline when the
     # workload is large (each still after 3 warm-up steps)
@@ -529,6 +533,11 @@ def run_ours(args):
     g_fl = sum(t[1] for t in gemm)
     g_n = sum(t[2] for t in gemm)
     g_achieved = g_fl / max(g_ms * 1e-3, 1e-12) / 1e12
+    p_ms = sum(t[0] for t in panel)
+    p_by = sum(t[1] for t in panel)
+    p_n = sum(t[2] for t in panel)
+    p_gbs = p_by / max(p_ms * 1e-3, 1e-12) / 1e9
+    hbm_peak, hbm_kind = measured_peak("hbm_gbs", 6800.0)
     sflops = solve_flops(p.nclosed, p.nact, p.nvirt, p.naux, p.nstate)
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws,
@@ -546,16 +555,24 @@ def run_ours(args):
                        p.B.nbytes // 2 ** 20)},
         "tflops_algorithmic": sflops / (total_s / args.steps) / 1e12,
         "solve_flops": sflops,
-        # dominant kernel by device time (profiles/): the FP64 GEMM of the eigensolvers
-        # (compact-WY back-transformations, blocked-reduction trailing updates, Z^T Z),
-        # 2 M N K flops per launch, event-timed launch by launch inside the solve
-        "roofline": {"bound": "alu", "achieved": g_achieved, "peak": FP64_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": g_achieved / FP64_PEAK_TFLOPS,
-                     "traffic": None,
-                     "kernel": "k_dgemm", "kernel_ms": g_ms / max(g_n, 1),
-                     "launches_per_step": g_n / max(len(gemm), 1),
-                     "flops_per_launch": g_fl / max(g_n, 1),
-                     "peak_kind": "nominal FP64 (no measured FP64 peak in MEASURED_PEAKS)"},
+        # dominant kernel by device time (profiles/launches_c70a10v600x2000n5_*): the panel
+        # kernel of the blocked Householder reduction, event-timed launch by launch inside
+        # the solve; its algorithmic bytes are the trailing matrix its matrix-vector
+        # products read, 8 n1^2 per column (64 columns per launch)
+        "roofline": {"bound": "hbm", "achieved": p_gbs, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": p_gbs / hbm_peak, "traffic": None,
+                     "kernel": "k_latrd", "kernel_ms": p_ms / max(p_n, 1),
+                     "launches_per_step": p_n / max(len(panel), 1),
+                     "alg_bytes_per_launch": p_by / max(p_n, 1),
+                     "peak_kind": "HBM copy, " + hbm_kind},
+        # the FP64 GEMM of the eigensolvers (blocked-reduction trailing updates, Z^T Z, the
+        # small sectors' transforms), 2 M N K flops per launch, event-timed per launch
+        "roofline_dgemm": {"bound": "alu", "achieved": g_achieved, "peak": FP64_PEAK_TFLOPS,
+                           "unit": "TFLOP/s", "frac": g_achieved / FP64_PEAK_TFLOPS,
+                           "kernel": "k_dgemm", "kernel_ms": g_ms / max(g_n, 1),
+                           "launches_per_step": g_n / max(len(gemm), 1),
+                           "flops_per_launch": g_fl / max(g_n, 1),
+                           "peak_kind": "nominal FP64 (no measured FP64 peak in MEASURED_PEAKS)"},
         # the Householder tridiagonalisation (panels and their GEMM updates), 4/3 m^3 flops
         "roofline_tridiag": {"bound": "alu", "achieved": tri_achieved,
                              "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",

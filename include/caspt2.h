@@ -187,7 +187,10 @@ int caspt2_get_core_energy(caspt2_ctx* ctx, double* ecore);
  * caspt2_densities call (0 before one), [9] the tridiagonalisation's algorithmic DRAM bytes
  * (the matrix read and the reflectors written once: 8 m^2 + 4 m (m - 1) per launch),
  * [10] the FP64 GEMM launches of the solve summed (device time by event pairs, the first
- * 4096 launches), [11] their algorithmic flops (2 M N K), [12] their number.
+ * 4096 launches), [11] their algorithmic flops (2 M N K), [12] their number, [13] the panel
+ * launches of the blocked Householder reduction (sectors too wide for shared memory) summed,
+ * [14] the bytes of the trailing matrix their matrix-vector products read (8 n1^2 per
+ * column, n1 the trailing size), [15] their number.
  *   times[k] is written for k < *count on input; *count = number of entries on output. */
 int caspt2_get_timings(caspt2_ctx* ctx, double* times, int* count);
 

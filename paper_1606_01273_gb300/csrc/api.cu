@@ -22,9 +22,10 @@ using namespace caspt2;
 namespace {
 
 constexpr int kNumStages = 4;  // setup, class H, classes A-G, H^eff
-constexpr int kNumTimes = kNumStages + 9;  // + class-H kernel, tridiagonalisation ms/flops/launches,
-                                           //   densities, tridiagonalisation bytes, FP64 GEMM
-                                           //   ms/flops/launches
+constexpr int kNumTimes = kNumStages + 12;  // + class-H kernel, tridiagonalisation ms/flops/launches,
+                                            //   densities, tridiagonalisation bytes, FP64 GEMM
+                                            //   ms/flops/launches, blocked-reduction panels
+                                            //   ms/bytes/launches
 
 }  // namespace
 
@@ -200,6 +201,8 @@ void caspt2_destroy(caspt2_ctx* ctx) {
   }
   if (ctx->dev1) cudaEventDestroy(ctx->dev1);
   if (ctx->tri.e1) cudaEventDestroy(ctx->tri.e1);
+  for (cudaEvent_t e : ctx->tri.pev)
+    if (e) cudaEventDestroy(e);
   cudaSetDevice(cur);
   delete ctx;
 }
@@ -525,6 +528,8 @@ int solve_impl(caspt2_ctx* c, void* stream) {
   const long launches0 = launch_counter();
   c->tri.ms = c->tri.flops = c->tri.bytes = 0.0;
   c->tri.launches = 0;
+  c->tri.pms = c->tri.pbytes = 0.0;
+  c->tri.plaunches = 0;
   if (!c->gemm) {
     c->gemm = new (std::nothrow) GemmTimer();
     if (c->gemm && gemm_timer_init(*c->gemm) != cudaSuccess) {
@@ -673,6 +678,9 @@ int solve_impl(caspt2_ctx* c, void* stream) {
     c->times[kNumStages + 7] = gfl;
     c->times[kNumStages + 8] = (double)gn;
   }
+  c->times[kNumStages + 9] = c->tri.pms;
+  c->times[kNumStages + 10] = c->tri.pbytes;
+  c->times[kNumStages + 11] = (double)c->tri.plaunches;
   c->launches = launch_counter() - launches0;
   c->solved = true;
   c->dens_done = false;

@@ -1314,14 +1314,34 @@ int sym_eig_tridiag(double* A, int m, double* w, double* V, double* work, cudaSt
     const int grid = std::max(1, nsm * std::max(1, std::min(per, 2)));
     if ((long)grid * (2 * kLatrdPanel + 1) > mm - 3 * (long)m) return CASPT2_EINVAL;
     CASPT2_CUDA_TRY(cudaMemsetAsync(sync, 0, 4 * sizeof(unsigned), s));
-    if (tm && tm->e0) CASPT2_CUDA_TRY(cudaEventRecord(tm->e0, s));
+    const int npanel = (m - 2 + kLatrdPanel - 1) / kLatrdPanel;
+    if (tm && tm->e0) {
+      while ((int)tm->pev.size() < 2 * npanel) {
+        cudaEvent_t ev = nullptr;
+        CASPT2_CUDA_TRY(cudaEventCreate(&ev));
+        tm->pev.push_back(ev);
+      }
+      CASPT2_CUDA_TRY(cudaEventRecord(tm->e0, s));
+    }
+    std::vector<double> pbytes;
     for (int k0 = 0; k0 < m - 2; k0 += kLatrdPanel) {
       const int b = std::min(kLatrdPanel, m - 2 - k0);
       void* args[] = {&A, (void*)&m, (void*)&k0, (void*)&b, &vbuf, &tau, &d, &e, &Wp, &Vr, &pp,
                       &pr, &part, &sync};
+      const int pi = k0 / kLatrdPanel;
+      if (tm && tm->e0) {
+        CASPT2_CUDA_TRY(cudaEventRecord(tm->pev[2 * pi], s));
+        double by = 0.0;
+        for (int j = 0; j < b; ++j) {
+          const double n1 = (double)(m - k0 - j - 1);
+          by += 8.0 * n1 * n1;
+        }
+        pbytes.push_back(by);
+      }
       ++launch_counter();
       CASPT2_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_latrd, grid, 512, args,
                                                   sizeof(double) * (size_t)m, s));
+      if (tm && tm->e0) CASPT2_CUDA_TRY(cudaEventRecord(tm->pev[2 * pi + 1], s));
       const int rr = m - k0 - b;
       if (rr > 0) {
         double* A22 = A + (long)(k0 + b) * m + k0 + b;
@@ -1343,6 +1363,13 @@ int sym_eig_tridiag(double* A, int m, double* w, double* V, double* work, cudaSt
       tm->ms += ms;
       tm->flops += 4.0 / 3.0 * (double)m * m * m;   // Householder tridiagonalisation
       tm->bytes += 8.0 * m * m + 4.0 * m * (m - 1.0);
+      for (size_t q = 0; q < pbytes.size(); ++q) {
+        float pm = 0.f;
+        CASPT2_CUDA_TRY(cudaEventElapsedTime(&pm, tm->pev[2 * q], tm->pev[2 * q + 1]));
+        tm->pms += pm;
+        tm->pbytes += pbytes[q];
+        ++tm->plaunches;
+      }
       ++tm->launches;
     }
   } else if (m > 64) {

@@ -1,5 +1,6 @@
 // FP64 dense helpers (internal): GEMM and symmetric eigensolver.
 #pragma once
+#include <vector>
 #include <algorithm>
 
 #include "common.cuh"
@@ -13,6 +14,12 @@ struct KernelTimer {
   double flops = 0.0;    // summed algorithmic flops
   double bytes = 0.0;    // summed algorithmic DRAM bytes
   long launches = 0;
+  // the panel launches of the blocked reduction alone (k_latrd): an event pair per launch
+  // (grown on demand, owned by the timer's holder), device time and the bytes of the
+  // trailing matrix its matrix-vector products read (8 n1^2 per column)
+  std::vector<cudaEvent_t> pev;
+  double pms = 0.0, pbytes = 0.0;
+  long plaunches = 0;
 };
 
 // Optional record of the FP64 GEMM launches of one host thread: an event pair around each
