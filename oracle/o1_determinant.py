@@ -203,13 +203,17 @@ class O1Result:
     NL: np.ndarray = None
     gammaP: np.ndarray = None   # <P|E_xy|P>
     Gamma2P: np.ndarray = None  # <P|E_xy,zw|P>
+    h: np.ndarray = None        # one-electron operator of H (f - g(d_sa) unless given)
+    d_sa: np.ndarray = None     # state-averaged density over all orbitals (closed 2 delta)
 
 
 def solve(nclosed: int, nact: int, nvirt: int, nelact: int, f: np.ndarray, B: np.ndarray,
           ci: np.ndarray, det_alpha, det_beta, *, xms: bool = True, scheme: str = "msmr",
           shift: float = 0.0, thresh: float = 1e-9, target: int = 0, enuc: float = 0.0,
           h: np.ndarray | None = None, densities: bool = True, space: FullSpace | None = None,
-          density_classes: str = "ABCDEFGH") -> O1Result:
+          density_classes: str = "ABCDEFGH", U_fixed: np.ndarray | None = None) -> O1Result:
+    """U_fixed: use this rotation of the reference states instead of the one XMS
+    determines (for derivatives at fixed rotated states |M~>, Sec. II.D)."""
     nmo = nclosed + nact + nvirt
     n = ci.shape[1]
     eri = np.einsum("Ppq,Prs->pqrs", B, B)
@@ -227,7 +231,9 @@ def solve(nclosed: int, nact: int, nvirt: int, nelact: int, f: np.ndarray, B: np
 
     # XMS rotation (Sec. II.A)
     fref = ref.T @ (fhat @ ref)
-    if xms:
+    if U_fixed is not None:
+        U = np.array(U_fixed, dtype=float)
+    elif xms:
         w, U = np.linalg.eigh(0.5 * (fref + fref.T))
         U = _canon_columns(U)
     else:
@@ -331,6 +337,7 @@ def solve(nclosed: int, nact: int, nvirt: int, nelact: int, f: np.ndarray, B: np
 
     res = O1Result(U, E0, Href, Heff, Ems, R, Ems_explicit, Ecore, e_class, norm_class,
                    ts, lams, colsL, SL, bL)
+    res.h, res.d_sa = h, d_sa
     if not densities:
         return res
 
