@@ -108,18 +108,24 @@ int caspt2_create(caspt2_ctx** ctx, const caspt2_dims* dims, const caspt2_option
 /* Copy the inputs into the context (Sec. II.A, II.B: reference states through their
  * RDMs, the state-averaged Fock matrix f and the DF factors defining (xy|zw)).
  *   mem   CASPT2_MEM_HOST or CASPT2_MEM_DEVICE (pointers on the context's device)
- *   fock  [nmo][nmo] symmetric SA Fock matrix f = h + g(d_sa), block diagonal: the
- *         closed-active, active-virtual and closed-virtual blocks are zero and the closed
- *         and virtual blocks are diagonal (canonical orbitals).  The classes then decouple
- *         and each is solved exactly in one step (Eq. ampeq); a Fock matrix with inter-class
- *         coupling needs the iterative solve of Sec. II.B, which this library does not do,
- *         so such an f is refused rather than solved with its coupling dropped.
+ *   fock  [nmo][nmo] symmetric SA Fock matrix f = h + g(d_sa) with zero closed-active,
+ *         active-virtual and closed-virtual blocks.  The classes then decouple and each is
+ *         solved exactly in one step (Eq. ampeq); a Fock matrix with coupling between the
+ *         spaces needs the iterative solve of Sec. II.B, which this library does not do,
+ *         so such an f is refused rather than solved with its coupling dropped.  If the
+ *         closed or the virtual block is not diagonal (orbitals not canonical), the call
+ *         rotates the closed and the virtual orbitals on the device to the eigenvectors of
+ *         those blocks (f <- C^T f C, B_P <- C^T B_P C, C = blockdiag(Q_c, 1, Q_v)): every
+ *         energy is invariant under such rotations (Sec. II.A), and the densities,
+ *         caspt2_gradient and caspt2_orbital_derivative return their results rotated back
+ *         to the caller's orbitals (C M C^T); caspt2_get_amplitudes / caspt2_get_lambda
+ *         then return EINVAL (their closed and virtual indices would be the rotated ones).
  *   dfB   [naux][nmo][nmo] DF factors, (xy|zw) = sum_P B[P][x][y] B[P][z][w], symmetric in x,y
  *   rdm1  [n][n][a][a], rdm2 [n][n][a^4]   (required)
  *   rdm3, rdm4 may be NULL while only classes that do not need them are enabled.
  * Errors: EINVAL (NULL required pointer; f not symmetric, or an entry of a coupling block
- * or an off-diagonal closed/virtual entry above 1e-10 x max(1, max|f|) in magnitude — the
- * context then holds no inputs), ECUDA. */
+ * above 1e-10 x max(1, max|f|) in magnitude — the context then holds no inputs), ENOMEM,
+ * ENOTCONV (the eigensolver of a closed or virtual block), ECUDA. */
 int caspt2_set_inputs(caspt2_ctx* ctx, int mem, const double* fock, const double* dfB,
                       const double* rdm1, const double* rdm2, const double* rdm3,
                       const double* rdm4);
@@ -169,8 +175,9 @@ long caspt2_amplitude_size(const caspt2_ctx* ctx, int cls);
  * memory (mem = CASPT2_MEM_HOST or CASPT2_MEM_DEVICE).  The vector is rebuilt from the
  * sector eigenbases the solve keeps (the solve never stores amplitudes); the call runs on
  * cuda_stream and returns after the result is in out.  Errors: EINVAL (bad index, class H
- * (its amplitudes are never formed), class not enabled, or lambda with target_state < 0),
- * ESTATE (no solve yet), ETIMEOUT (a bounded wait of a split GEMM gave up). */
+ * (its amplitudes are never formed), class not enabled, lambda with target_state < 0, or
+ * inputs canonicalised by caspt2_set_inputs), ESTATE (no solve yet), ETIMEOUT (a bounded
+ * wait of a split GEMM gave up). */
 int caspt2_get_amplitudes(caspt2_ctx* ctx, int cls, int L, int N, int mem, double* out,
                           void* cuda_stream);
 int caspt2_get_lambda(caspt2_ctx* ctx, int cls, int L, int N, int mem, double* out,
@@ -255,18 +262,37 @@ int caspt2_get_densities(caspt2_ctx* ctx, int mem, double* d1, double* d2, doubl
  * library's inputs, the Fock matrix f and the DF factors B, with the reference RDMs held
  * fixed (Sec. II.D: the densities chained through h = f - g(B, d_sa), the reference
  * Hamiltonian and the denominators):
- *   grad_f[p][q]     = dE_P/df_pq  = gamma_P + d1 + d2, d2 on the parts of f the solve
- *                      reads (closed diagonal, active block, virtual diagonal);
+ *   grad_f[p][q]     = dE_P/df_pq  = gamma_P + d1 + d2 on the closed-closed,
+ *                      active-active and virtual-virtual blocks (the blocks of an f the
+ *                      solve takes, see caspt2_set_inputs; off-diagonal closed and
+ *                      virtual entries included);
  *   grad_B[Q][p][q]  = dE_P/dB_Qpq at fixed f;
  * both symmetrised, in the layouts of the inputs, to host or device buffers (mem).  MS
- * only (opt.xms = 0): the XMS rotation response is not formed.  Because the solve takes a
- * block-diagonal f (see caspt2_set_inputs), grad_f is the derivative along the blocks
- * it reads; its closed-active, active-virtual and closed-virtual entries and the
- * off-diagonal closed/virtual entries are left zero (their derivative needs the
- * inter-class coupling of Sec. II.D's d-bar(2), not built).  Recomputes the densities
- * of all solved classes.  Errors: EINVAL (xms, target_state < 0), ESTATE (no solve),
- * ENOMEM, ECUDA. */
+ * only (opt.xms = 0): the XMS rotation response is not formed.  The closed-active,
+ * active-virtual and closed-virtual entries of grad_f are left zero: an f with those
+ * blocks is refused, and their derivative is d-bar(2) of those blocks (caspt2_densities
+ * with opt.dens_offdiag).  Recomputes the densities of all solved classes.
+ * Errors: EINVAL (xms, target_state < 0), ESTATE (no solve), ENOMEM, ECUDA. */
 int caspt2_gradient(caspt2_ctx* ctx, int mem, double* grad_f, double* grad_B, void* cuda_stream);
+
+/* Orbital derivative of the target state's CASPT2 Lagrangian (Sec. II.D, Eq. orbderiv:
+ * Y_xy = dL_PT2/dkappa_xy, the orbital part of the Z-vector source), from the relaxed
+ * densities, in the density-fitted form
+ *   Y = 2 [ h G + sum_Q B_Q Gb_Q ],
+ *   G     = dL/dh   = gamma_P + d1 + d2        (every block of d2),
+ *   Gb_Q  = dL/dB_Q at fixed h (the DF form of D(1), the reference two-electron part and
+ *           d2 through f = h + g(B, d_sa)),
+ * h = f - g(B, d_sa).  Convention: the orbitals change as phi'_y = phi_y + sum_x phi_x
+ * kappa_xy with the reference CI vectors, the XMS rotation U and d_sa held fixed, every
+ * integral following the orbitals; along an antisymmetric generator the change of L is
+ * sum_xy kappa_xy (Y_xy - Y_yx).  For XMS this is the derivative at fixed rotated states
+ * |M~>; the XMS term Y' (through w_MN, which needs the CI derivative) is not included.
+ *   Y   [nmo][nmo] (not symmetric), to a host or device buffer (mem).
+ * Needs opt.target_state >= 0 and, when nact > 0, opt.dens_offdiag = 1 (the closed-active,
+ * active-virtual and closed-virtual blocks of d2 enter G).  Recomputes the densities of all
+ * solved classes.  Errors: EINVAL (NULL, target_state < 0, dens_offdiag off), ESTATE (no
+ * solve), ENOMEM, ECUDA. */
+int caspt2_orbital_derivative(caspt2_ctx* ctx, int mem, double* Y, void* cuda_stream);
 
 /* Per-class moment sums of the last solve (Sec. II.B, Eq. ampeq solved in each class's
  * orthonormal sector basis mu: M1[L][N][L'] = sum Vt_N Vt_L' / D_L, M2[L][N] =
@@ -315,9 +341,9 @@ const char* caspt2_strerror(int status);
  * array: calls that overlap on the GPU (other threads or streams) race and must be
  * serialised by the caller.  Returns ESCRATCH when the problem needs more scratch than
  * the array holds (about 4 MiB: n <= 16 and nclosed + nvirt up to ~2e5 fit), EINVAL for
- * bad sizes, NULL pointers or an f that is not block diagonal (as caspt2_set_inputs; f is
- * read back to host memory for that check), ENOTCONV / ENAN / ECUDA, or WINTRUDER as
- * caspt2_solve. */
+ * bad sizes, NULL pointers or an f that is not block diagonal with diagonal closed and
+ * virtual blocks (this entry point takes canonical orbitals only; f is read back to host
+ * memory for that check), ENOTCONV / ENAN / ECUDA, or WINTRUDER as caspt2_solve. */
 int caspt2_classH_noalloc(const caspt2_dims* dims, const caspt2_options* opt,
                           const double* fock, const double* dfB, const double* rdm1,
                           double* e, double* norm, void* cuda_stream);

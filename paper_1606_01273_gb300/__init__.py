@@ -83,6 +83,7 @@ def lib():
         L.caspt2_densities.argtypes = [P, C.c_uint, P]
         L.caspt2_get_densities.argtypes = [P, C.c_int, P, P, P, P]
         L.caspt2_gradient.argtypes = [P, C.c_int, P, P, P]
+        L.caspt2_orbital_derivative.argtypes = [P, C.c_int, P, P]
         L.caspt2_get_status.argtypes = [P, C.POINTER(Report)]
         L.caspt2_amplitude_size.argtypes = [P, C.c_int]
         L.caspt2_amplitude_size.restype = C.c_long
@@ -266,6 +267,16 @@ class Context:
         _check(lib().caspt2_gradient(self._h, MEM_HOST, C.c_void_p(gf.ctypes.data),
                                      C.c_void_p(gB.ctypes.data), s), "caspt2_gradient")
         return gf, gB
+
+    def orbital_derivative(self, stream=None):
+        """caspt2_orbital_derivative: host copy of Y [nmo][nmo] = dL/dkappa (the orbital
+        part of the Z-vector source) of the target state; needs dens_offdiag=1."""
+        nmo = self.dims.nclosed + self.dims.nact + self.dims.nvirt
+        Y = np.zeros((nmo, nmo))
+        s = C.c_void_p(stream) if stream is not None else None
+        _check(lib().caspt2_orbital_derivative(self._h, MEM_HOST, C.c_void_p(Y.ctypes.data), s),
+               "caspt2_orbital_derivative")
+        return Y
 
     def densities(self, class_mask=None, stream=None):
         """compute_densities + get_densities: host copies (d1, d2, gdf), each symmetrised."""

@@ -91,6 +91,14 @@ struct caspt2_ctx {
   bool grad_alloc = false;
   GradWork gw{};
   double *gradf = nullptr, *gradB = nullptr;
+  // canonical closed/virtual orbitals: the inputs were rotated by canonC (set_inputs with
+  // an f whose closed or virtual block is not diagonal); outputs are rotated back
+  bool canon = false;
+  double *canonC = nullptr, *canon_t1 = nullptr, *canon_t2 = nullptr;
+  long canon_chunk = 0;
+  // orbital derivative (allocated on the first caspt2_orbital_derivative call)
+  bool orb_alloc = false;
+  double *orb_h = nullptr, *orb_gf = nullptr, *orb_y = nullptr;
   cudaEvent_t dev0 = nullptr, dev1 = nullptr;
   // results
   double *heff = nullptr, *ems = nullptr, *R = nullptr;
@@ -454,17 +462,29 @@ int caspt2_set_inputs(caspt2_ctx* c, int mem, const double* fock, const double* 
   c->have_inputs = false;
   c->solved = false;
   c->dens_done = false;
+  c->canon = false;
+  int fclass = 0;
   {
-    // the solve reads only the blocks of a block-diagonal f: refuse any other f
+    // the classes decouple only without closed-active, active-virtual and closed-virtual
+    // coupling: refuse any other f; rotated closed/virtual blocks are canonicalised below
     std::vector<double> hf(nmo * nmo);
     CASPT2_CUDA_TRY(cudaMemcpy(hf.data(), fock, sizeof(double) * nmo * nmo,
                                mem == CASPT2_MEM_HOST ? cudaMemcpyHostToHost
                                                       : cudaMemcpyDeviceToHost));
-    const int st = check_block_diagonal_fock(hf.data(), d);
-    if (st != CASPT2_OK) return st;
+    fclass = classify_fock(hf.data(), d);
+    if (fclass < 0) return fclass;
   }
   CASPT2_CUDA_TRY(cudaMemcpy(c->f, fock, sizeof(double) * nmo * nmo, k));
   CASPT2_CUDA_TRY(cudaMemcpy(c->B, dfB, sizeof(double) * d.X * nmo * nmo, k));
+  if (fclass == 1) {
+    if (!c->canonC) {
+      const int st = c->alloc(&c->canonC, nmo * nmo);
+      if (st != CASPT2_OK) return st;
+    }
+    const int st = canonicalize_inputs(c->f, c->B, d, c->canonC, cudaStreamPerThread);
+    if (st != CASPT2_OK) return st;
+    c->canon = true;
+  }
   CASPT2_CUDA_TRY(cudaMemcpy(c->rdm1, rdm1, sizeof(double) * n * n * a2, k));
   CASPT2_CUDA_TRY(cudaMemcpy(c->rdm2, rdm2, sizeof(double) * n * n * a2 * a2, k));
   if ((c->kmax >= 3 && !rdm3) || (c->kmax >= 4 && !rdm4)) return CASPT2_EINVAL;
@@ -941,6 +961,32 @@ int dens_offdiag(caspt2_ctx* c, unsigned class_mask, cudaStream_t s) {
                      c->dd2, s);
 }
 
+// Copy `batch` nmo x nmo device matrices src (derivatives in the orbital basis the solve
+// used) to dst in the caller's basis: C M C^T after a canonicalisation of the inputs, a
+// plain copy otherwise.
+int copy_out(caspt2_ctx* c, const double* src, long batch, double* dst, cudaMemcpyKind k) {
+  const int nmo = c->d.nmo();
+  const long nn = (long)nmo * nmo;
+  if (!c->canon) {
+    CASPT2_CUDA_TRY(cudaMemcpy(dst, src, sizeof(double) * batch * nn, k));
+    return CASPT2_OK;
+  }
+  if (!c->canon_t1) {
+    c->canon_chunk = std::max<long>(1, std::min<long>(std::max(c->d.X, 1), (1L << 26) / nn));
+    int st = c->alloc(&c->canon_t1, (size_t)(c->canon_chunk * nn));
+    if (st == CASPT2_OK) st = c->alloc(&c->canon_t2, (size_t)(c->canon_chunk * nn));
+    if (st != CASPT2_OK) return st;
+  }
+  cudaStream_t s = cudaStreamPerThread;
+  for (long b0 = 0; b0 < batch; b0 += c->canon_chunk) {
+    const int nb = (int)std::min<long>(c->canon_chunk, batch - b0);
+    CASPT2_CUDA_TRY(canon_back(c->canonC, src + b0 * nn, nmo, nb, c->canon_t1, c->canon_t2, s));
+    CASPT2_CUDA_TRY(cudaStreamSynchronize(s));
+    CASPT2_CUDA_TRY(cudaMemcpy(dst + b0 * nn, c->canon_t2, sizeof(double) * nb * nn, k));
+  }
+  return CASPT2_OK;
+}
+
 long block_size(const Dims& d, int key) {
   const int dims3[3] = {d.c, d.a, d.v};
   return (long)dims3[key / 27] * dims3[(key / 9) % 3] * dims3[(key / 3) % 3] * dims3[key % 3];
@@ -1039,6 +1085,8 @@ int get_class_vector(caspt2_ctx* c, int cls, int L, int N, int mem, double* out,
   if (!c->cw_on[cls] || L < 0 || L >= d.n || N < 0 || N >= d.n || d.a > 16 || c->partial())
     return CASPT2_EINVAL;
   if (lam && o.target_state < 0) return CASPT2_EINVAL;
+  // amplitudes carry closed and virtual indices of the canonical orbitals the solve used
+  if (c->canon) return CASPT2_EINVAL;
   CASPT2_CUDA_TRY(cudaSetDevice(c->device));
   if (!c->dens_alloc) {
     const int st = alloc_densities(c);
@@ -1085,8 +1133,10 @@ int caspt2_get_densities(caspt2_ctx* c, int mem, double* d1, double* d2, double*
   CASPT2_CUDA_TRY(cudaSetDevice(c->device));
   const cudaMemcpyKind k = mem == CASPT2_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
   const size_t nmo = c->d.nmo();
-  if (d1) CASPT2_CUDA_TRY(cudaMemcpy(d1, c->dd1, sizeof(double) * nmo * nmo, k));
-  if (d2) CASPT2_CUDA_TRY(cudaMemcpy(d2, c->dd2, sizeof(double) * nmo * nmo, k));
+  int st = CASPT2_OK;
+  if (d1 && st == CASPT2_OK) st = copy_out(c, c->dd1, 1, d1, k);
+  if (d2 && st == CASPT2_OK) st = copy_out(c, c->dd2, 1, d2, k);
+  if (st != CASPT2_OK) return st;
   if (NL) {
     // N_L summed over the classes in a fixed order (per-class shares of the last solve)
     const int n = c->d.n;
@@ -1098,11 +1148,37 @@ int caspt2_get_densities(caspt2_ctx* c, int mem, double* d1, double* d2, double*
                                mem == CASPT2_MEM_HOST ? cudaMemcpyHostToHost
                                                       : cudaMemcpyHostToDevice));
   }
-  if (gdf) CASPT2_CUDA_TRY(cudaMemcpy(gdf, c->dgdf, sizeof(double) * c->d.X * nmo * nmo, k));
+  if (gdf) return copy_out(c, c->dgdf, c->d.X, gdf, k);
   return CASPT2_OK;
 }
 
 }  // extern "C"
+
+namespace {
+// Work arrays of the gradient and orbital-derivative assembly (first call only).
+int alloc_grad_work(caspt2_ctx* c) {
+  if (c->grad_alloc) return CASPT2_OK;
+  const Dims& d = c->d;
+  const size_t nmo = d.nmo(), a = d.a, X = d.X;
+  int e = CASPT2_OK;
+#define ALLOC(ptr, cnt) \
+  if (e == CASPT2_OK) e = c->alloc(&(ptr), (cnt))
+  ALLOC(c->gw.g1, a * a);
+  ALLOC(c->gw.g2, a * a * a * a);
+  ALLOC(c->gw.D, nmo * nmo);
+  ALLOC(c->gw.dsa, nmo * nmo);
+  ALLOC(c->gw.gD, X);
+  ALLOC(c->gw.tq, X);
+  ALLOC(c->gw.T, X * nmo * nmo);
+  ALLOC(c->gw.M, X * nmo * nmo);
+  ALLOC(c->gradf, nmo * nmo);
+  ALLOC(c->gradB, X * nmo * nmo);
+#undef ALLOC
+  if (e != CASPT2_OK) return e;
+  c->grad_alloc = true;
+  return CASPT2_OK;
+}
+}  // namespace
 
 extern "C" int caspt2_gradient(caspt2_ctx* c, int mem, double* grad_f, double* grad_B,
                                void* stream) {
@@ -1116,26 +1192,10 @@ extern "C" int caspt2_gradient(caspt2_ctx* c, int mem, double* grad_f, double* g
   int st = caspt2_densities(c, o.class_mask, stream);
   if (st != CASPT2_OK) return st;
   const Dims& d = c->d;
-  const size_t nmo = d.nmo(), a = d.a, X = d.X;
-  if (!c->grad_alloc) {
-    int e = CASPT2_OK;
-#define ALLOC(ptr, cnt) \
-  if (e == CASPT2_OK) e = c->alloc(&(ptr), (cnt))
-    ALLOC(c->gw.g1, a * a);
-    ALLOC(c->gw.g2, a * a * a * a);
-    ALLOC(c->gw.D, nmo * nmo);
-    ALLOC(c->gw.dsa, nmo * nmo);
-    ALLOC(c->gw.gD, X);
-    ALLOC(c->gw.tq, X);
-    ALLOC(c->gw.T, X * nmo * nmo);
-    ALLOC(c->gw.M, X * nmo * nmo);
-    ALLOC(c->gradf, nmo * nmo);
-    ALLOC(c->gradB, X * nmo * nmo);
-#undef ALLOC
-    if (e != CASPT2_OK) return e;
-    c->grad_alloc = true;
-  }
-  if (a == 0) {
+  const size_t nmo = d.nmo(), X = d.X;
+  st = alloc_grad_work(c);
+  if (st != CASPT2_OK) return st;
+  if (d.a == 0) {
     CASPT2_CUDA_TRY(cudaMemsetAsync(c->gw.g1, 0, sizeof(double), s));
   }
   st = assemble_gradient(d, c->B, c->R, o.target_state, c->rdm1r, c->rdm2r, c->dact, c->bsum,
@@ -1143,7 +1203,47 @@ extern "C" int caspt2_gradient(caspt2_ctx* c, int mem, double* grad_f, double* g
   if (st != CASPT2_OK) return st;
   CASPT2_CUDA_TRY(cudaStreamSynchronize(s));
   const cudaMemcpyKind k = mem == CASPT2_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
-  if (grad_f) CASPT2_CUDA_TRY(cudaMemcpy(grad_f, c->gradf, sizeof(double) * nmo * nmo, k));
-  if (grad_B) CASPT2_CUDA_TRY(cudaMemcpy(grad_B, c->gradB, sizeof(double) * X * nmo * nmo, k));
+  if (grad_f) {
+    st = copy_out(c, c->gradf, 1, grad_f, k);
+    if (st != CASPT2_OK) return st;
+  }
+  if (grad_B) return copy_out(c, c->gradB, X, grad_B, k);
   return CASPT2_OK;
+}
+
+// Orbital derivative Y_xy = dL/dk_xy of the target state's Lagrangian (Sec. II.D, Eq.
+// orbderiv) from the densities of every block: see include/caspt2.h.
+extern "C" int caspt2_orbital_derivative(caspt2_ctx* c, int mem, double* Y, void* stream) {
+  if (!c || !Y) return CASPT2_EINVAL;
+  if (mem != CASPT2_MEM_HOST && mem != CASPT2_MEM_DEVICE) return CASPT2_EINVAL;
+  if (!c->solved) return CASPT2_ESTATE;
+  const caspt2_options& o = c->opt;
+  if (o.target_state < 0) return CASPT2_EINVAL;
+  // the closed-active, active-virtual and closed-virtual blocks of d2 enter Y
+  if (c->d.a > 0 && !o.dens_offdiag) return CASPT2_EINVAL;
+  CASPT2_CUDA_TRY(cudaSetDevice(c->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int st = caspt2_densities(c, o.class_mask, stream);
+  if (st != CASPT2_OK) return st;
+  const Dims& d = c->d;
+  const size_t nmo = d.nmo();
+  st = alloc_grad_work(c);
+  if (st != CASPT2_OK) return st;
+  if (!c->orb_alloc) {
+    int e = c->alloc(&c->orb_h, nmo * nmo);
+    if (e == CASPT2_OK) e = c->alloc(&c->orb_gf, nmo * nmo);
+    if (e == CASPT2_OK) e = c->alloc(&c->orb_y, nmo * nmo);
+    if (e != CASPT2_OK) return e;
+    c->orb_alloc = true;
+  }
+  if (d.a == 0) {
+    CASPT2_CUDA_TRY(cudaMemsetAsync(c->gw.g1, 0, sizeof(double), s));
+  }
+  st = assemble_orbital_derivative(d, c->f, c->g, c->B, c->R, o.target_state, c->rdm1r,
+                                   c->rdm2r, c->dact, c->bsum, c->gam, c->dd1, c->dd2, c->dgdf,
+                                   c->gw, c->orb_h, c->orb_gf, c->gradB, c->orb_y, s);
+  if (st != CASPT2_OK) return st;
+  CASPT2_CUDA_TRY(cudaStreamSynchronize(s));
+  const cudaMemcpyKind k = mem == CASPT2_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  return copy_out(c, c->orb_y, 1, Y, k);
 }

@@ -179,6 +179,16 @@ int assemble_gradient(const Dims& d, const double* B, const double* R, int P,
                       const double* gdf, const GradWork& gw, double* grad_f, double* grad_B,
                       cudaStream_t s);
 
+// Orbital derivative Y [nmo][nmo] of the Lagrangian (Sec. II.D, Eq. orbderiv) from the
+// densities d1, d2 (every block), Gamma (gdf) and the reference pieces; also returns
+// gf = dL/dh [nmo][nmo], gBh = dL/dB at fixed h [X][nmo][nmo] and h (see gradient.cu).
+int assemble_orbital_derivative(const Dims& d, const double* f, const double* g_act,
+                                const double* B, const double* R, int P, const double* rdm1,
+                                const double* rdm2, const double* dact, const double* bsum,
+                                const double* gam, const double* d1, const double* d2,
+                                const double* gdf, const GradWork& gw, double* h, double* gf,
+                                double* gBh, double* Y, cudaStream_t s);
+
 // x <- (x + x^T) / 2 for `batch` square nmo x nmo matrices.
 cudaError_t launch_symmetrize(double* x, int nmo, long batch, cudaStream_t s);
 

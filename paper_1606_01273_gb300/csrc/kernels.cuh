@@ -15,6 +15,20 @@ struct Dims {
 // Returns CASPT2_OK, CASPT2_EINVAL (coupling found) or CASPT2_ENAN.
 int check_block_diagonal_fock(const double* f, const Dims& d);
 
+// ---- canonical closed and virtual orbitals (canon.cu) ------------------------
+// Host classification of f [nmo][nmo]: 0 = block diagonal with diagonal closed and
+// virtual blocks; 1 = no closed-active, active-virtual or closed-virtual coupling but an
+// off-diagonal closed-closed or virtual-virtual entry (tolerance as above); CASPT2_EINVAL
+// (asymmetric, or coupling between the spaces) or CASPT2_ENAN.
+int classify_fock(const double* f, const Dims& d);
+// Rotate the device inputs in place to the eigenvectors of f's closed and virtual blocks:
+// C [nmo][nmo] = blockdiag(Q_c, 1, Q_v), f <- canonical part of C^T f C, B_P <- C^T B_P C.
+// Synchronises s.  Returns CASPT2_OK, ENOMEM, ENOTCONV, ENAN or ECUDA.
+int canonicalize_inputs(double* f, double* B, const Dims& d, double* C, cudaStream_t s);
+// out[b] = C M[b] C^T for `batch` nmo x nmo matrices (tmp: batch * nmo^2 doubles).
+cudaError_t canon_back(const double* C, const double* M, int nmo, int batch, double* tmp,
+                       double* out, cudaStream_t s);
+
 // ---- setup (setup.cu) --------------------------------------------------------
 // d_act = (1/n) sum_N rdm1[N][N]                         (Sec. II.B, d^(0)sa)
 cudaError_t launch_dsa(const double* rdm1, const Dims& d, double* dact, cudaStream_t s);

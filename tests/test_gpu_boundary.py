@@ -1,5 +1,6 @@
-"""The C-ABI contract at its edges: the Fock matrices the solve refuses (inter-class
-coupling that the one-step class solve would drop), the degenerate-XMS warning, and
+"""The C-ABI contract at its edges: the Fock matrices the solve refuses (coupling between
+the closed, active and virtual spaces, which the one-step class solve would drop), the
+degenerate-XMS warning, and
 N_L through caspt2_get_densities, each against the determinant-space brute force."""
 import os
 
@@ -29,20 +30,21 @@ def small():
 
 @pytest.mark.parametrize("device", [False, True], ids=["host", "device"])
 def test_coupled_fock_is_refused(cp, small, device):
-    """A closed/virtual-rotated f and an f with one closed-virtual coupling entry are
-    refused with EINVAL (host and device inputs); the block-diagonal f is accepted."""
+    """An f with one closed-virtual coupling entry is refused with EINVAL (host and device
+    inputs); the block-diagonal f and a closed/virtual-rotated f (solved through the
+    canonical orbitals of those blocks) are accepted."""
     import torch
     p = small
     f_rot, f_cpl = rotated_fock(p)
     _, B, *rd = cp.problem_inputs(p)
     ctx = cp.Context(p.nclosed, p.nact, p.nvirt, p.naux, p.nstate)
     try:
-        for f in (f_rot, f_cpl, p.f):
+        for f in (f_cpl, f_rot, f_cpl, p.f):
             args = [f, B, *rd]
             if device:
                 args = [None if x is None else torch.from_numpy(np.ascontiguousarray(x)).cuda()
                         for x in args]
-            if f is p.f:
+            if f is p.f or f is f_rot:
                 ctx.set_inputs(*args)
             else:
                 with pytest.raises(cp.CASPT2Error) as e:
