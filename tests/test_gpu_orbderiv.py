@@ -45,8 +45,8 @@ def _problem(name):
     return _cache[name]
 
 
-def _gpu_y(cp, p, opt, calls=1):
-    ctx = cp.Context(p.nclosed, p.nact, p.nvirt, p.naux, p.nstate, dens_offdiag=1, **opt)
+def _gpu_y(cp, p, opt, calls=1, offdiag=1):
+    ctx = cp.Context(p.nclosed, p.nact, p.nvirt, p.naux, p.nstate, dens_offdiag=offdiag, **opt)
     try:
         ctx.set_inputs(*cp.problem_inputs(p))
         assert ctx.solve() == cp.OK
@@ -68,6 +68,32 @@ def test_orbital_derivative_vs_brute_force(cp, name, opt):
     assert err <= RTOL * scale, f"Y max |diff| {err:.3e} (scale {scale:.3e})"
     # the orbital gradient (antisymmetric part) is populated, not only the symmetric part
     assert float(np.abs(want - want.T).max()) > 1e-4
+
+
+# more DF factors than the 32 partial products of sum_Q B_Q Gb_Q (chunks of two, one
+# left over), and no active orbitals (class H alone; no inter-space blocks of d2 exist, so
+# the off-diagonal density option is not needed)
+EXTRA = {
+    "c2a4v3x37n2": (dict(nclosed=2, nact=4, nvirt=3, naux=37, nstate=2, seed=5), 1),
+    "c3a0v4x30n1": (dict(nclosed=3, nact=0, nvirt=4, naux=30, nstate=1, seed=3), 0),
+}
+
+
+@pytest.mark.parametrize("name", list(EXTRA))
+@pytest.mark.parametrize("opt", [dict(xms=1, scheme=0, shift=0.2), dict(xms=0, scheme=1, shift=0.0)],
+                         ids=["xms_msmr_s0.2", "ms_sssr_s0"])
+def test_orbital_derivative_chunks_and_no_active(cp, name, opt):
+    spec, offdiag = EXTRA[name]
+    if name not in _cache:
+        _cache[name] = make_problem(**spec)
+    p = _cache[name]
+    (Y,) = _gpu_y(cp, p, opt, offdiag=offdiag)
+    ref = o1.solve_problem(p, xms=bool(opt["xms"]), scheme="sssr" if opt["scheme"] else "msmr",
+                           shift=opt["shift"])
+    want = orbital_derivative(ref, p.B)
+    scale = max(1.0, float(np.abs(want).max()))
+    err = float(np.abs(Y - want).max())
+    assert err <= RTOL * scale, f"Y max |diff| {err:.3e} (scale {scale:.3e})"
 
 
 def test_orbital_derivative_contract(cp):
