@@ -1,9 +1,10 @@
 """Differentiation form: dE_MS/df and dE_MS/dB of the target state (MS, reference RDMs
 fixed) from caspt2_gradient and through torch.autograd, checked against central finite
-differences of the library's own energies in random symmetric directions (for f, inside
-the blocks a block-diagonal f carries: the library refuses any other f) and, for the
-parts of f that every form of the method shares (closed and virtual diagonals, active
-block), against the determinant-space oracle's densities."""
+differences of the library's own energies in random symmetric directions (for f, on the
+closed and virtual diagonals and the active block; directions with off-diagonal closed or
+virtual entries, which the library solves through canonical orbitals, are checked in
+test_gpu_canonical.py) and, on the closed-closed, active-active and virtual-virtual
+blocks, against the determinant-space oracle's densities."""
 import os
 
 import numpy as np
@@ -73,9 +74,9 @@ def test_gradient_matches_finite_differences(cp, case, opt):
         ctx.close()
     rng = np.random.default_rng(case * 10 + opt.get("target_state", 0) + 7 * opt["scheme"])
     for _ in range(2):
-        # directions inside the blocks of f the solve accepts (closed and virtual
-        # diagonals, active block): any other direction makes f non-block-diagonal,
-        # which caspt2_set_inputs refuses
+        # directions on the closed and virtual diagonals and the active block (a direction
+        # with a closed-active, active-virtual or closed-virtual entry makes f one that
+        # caspt2_set_inputs refuses)
         df = rng.standard_normal(p.f.shape)
         df = df + df.T
         df *= _read_mask(p)
