@@ -644,3 +644,90 @@ def class_densities(prob, st, cls, shift, scheme, R, P, thresh=1e-9):
     for L in range(n):
         d2[rng["a"], rng["a"]] -= NL[L] * g1r[L, L]
     return d1, GDF, d2, NL
+
+
+def class_residual(prob, st, cls, shift, scheme, T, thresh=1e-9, h=None):
+    """Relative residual of given first-order amplitudes in the amplitude equation of
+    class cls (Eq. ampeq with block-diagonal f), in the class's own metric:
+        r = X^T [ (F + (e_ext - E0_L + E_s) S) t + V ]   per sector, tuple and state L,
+    t the sector amplitudes of T (layout of class_amplitudes: [L][fam, ext..., act..., M];
+    a pair (x, y) enters the + and - sectors as (T(x,y) +- T(y,x))/sqrt2, x = y the +
+    sector as T(x,x)), X the orthonormalised basis of the kept overlap eigenvalues.
+    Returns ||r|| / ||X^T V|| over all sectors, tuples and states: about the unit
+    roundoff for an exact solve, whatever the conditioning of the denominators, because a
+    rounding error of a sector eigenvalue moves t along directions where the equation is
+    nearly singular and leaves r small."""
+    from .o2_rdm import g_of
+    c, a, v, n = prob.nclosed, prob.nact, prob.nvirt, prob.nstate
+    fams, ext, pair, act = CLASS_DEF[cls]
+    sp = _space_of_slot(cls)
+    dims = {"c": c, "a": a, "v": v}
+    nf = len(fams)
+    ext_shape = [dims[sp[e]] for e in ext]
+    if any(d_ == 0 for d_ in ext_shape) or a == 0:
+        return 0.0
+    if h is None:
+        nmo = prob.nmo
+        d = np.zeros((nmo, nmo))
+        d[np.arange(c), np.arange(c)] = 2.0
+        g1 = prob.rdm[1].reshape(n, n, a, a)
+        d[c:c + a, c:c + a] = sum(g1[m, m] for m in range(n)) / n
+        h = prob.f - g_of(prob.B, d)
+    mats = active_matrices(cls, st.rdm, n, a, prob.f[c:c + a, c:c + a])
+    V = sources(cls, st.rdm, n, a, integral_blocks(prob, h))
+    eps = np.diag(prob.f)
+    ec, ev = eps[:c], eps[c + a:]
+    m = nf * a ** len(act) * n
+    S = {k: x_.reshape(m, m) for k, x_ in mats["S"].items()}
+    F = {k: x_.reshape(m, m) for k, x_ in mats["F"].items()}
+    ntot = int(np.prod(ext_shape))
+    grids = np.meshgrid(*[np.arange(r_) for r_ in ext_shape], indexing="ij")
+    tup_all = np.stack([g_.ravel() for g_ in grids], axis=1)
+    eext_all = np.zeros(len(tup_all))
+    for k, e_ in enumerate(ext):
+        eext_all += ev[tup_all[:, k]] if sp[e_] == "v" else -ec[tup_all[:, k]]
+    Vflat = V.reshape((nf, ntot, a ** len(act), n, n))
+    Tflat = np.asarray(T).reshape((n, nf, ntot, a ** len(act), n))
+    num = den = 0.0
+    sectors = [("+", 1.0), ("-", -1.0)] if pair is not None else [("id", 0.0)]
+    for name, sgn in sectors:
+        if pair is None:
+            Ssec, Fsec = S["id"], F["id"]
+            sel = np.arange(ntot)
+            vmat = Vflat[:, sel]
+            tmat = Tflat[:, :, sel]
+        else:
+            Ssec, Fsec = S["id"] + sgn * S["sw"], F["id"] + sgn * F["sw"]
+            pi_, pj_ = ext.index(pair[0]), ext.index(pair[1])
+            ti, tj = tup_all[:, pi_], tup_all[:, pj_]
+            sel = np.nonzero((ti < tj) if name == "-" else (ti <= tj))[0]
+            swp = tup_all[sel].copy()
+            swp[:, [pi_, pj_]] = swp[:, [pj_, pi_]]
+            partner = np.ravel_multi_index(tuple(swp.T), ext_shape)
+            diag = (ti[sel] == tj[sel])
+            v1, v2 = Vflat[:, sel], Vflat[:, partner]
+            vmat = np.where(diag[None, :, None, None, None], v1, (v1 + sgn * v2) / np.sqrt(2.0))
+            t1, t2 = Tflat[:, :, sel], Tflat[:, :, partner]
+            tmat = np.where(diag[None, None, :, None, None], t1, (t1 + sgn * t2) / np.sqrt(2.0))
+        if len(sel) == 0:
+            continue
+        Ssec = 0.5 * (Ssec + Ssec.T)
+        Fsec = 0.5 * (Fsec + Fsec.T)
+        ee = eext_all[sel]
+        Vm = np.moveaxis(vmat, 1, 3).reshape(m, len(sel), n)               # rows (fam, act, M)
+        Tm = np.moveaxis(tmat, 2, 4).reshape(n, m, len(sel))               # [L][rows, tuple]
+        for Lsel in (range(n) if scheme == "sssr" else [None]):
+            keep_idx = np.arange(m) if Lsel is None else np.arange(Lsel, m, n)
+            Ss = Ssec[np.ix_(keep_idx, keep_idx)]
+            Fs = Fsec[np.ix_(keep_idx, keep_idx)]
+            s_, q_ = np.linalg.eigh(Ss)
+            keep = s_ >= thresh
+            if not keep.any():
+                continue
+            X = q_[:, keep] / np.sqrt(s_[keep])
+            for L in (range(n) if Lsel is None else [Lsel]):
+                t = Tm[L][keep_idx]
+                r = Fs @ t + (Ss @ t) * (ee - st.E0[L] + shift)[None, :] + Vm[keep_idx, :, L]
+                num += float(np.sum((X.T @ r) ** 2))
+                den += float(np.sum((X.T @ Vm[keep_idx, :, L]) ** 2))
+    return float(np.sqrt(num / den)) if den > 0 else 0.0
