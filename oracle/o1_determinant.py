@@ -205,6 +205,9 @@ class O1Result:
     Gamma2P: np.ndarray = None  # <P|E_xy,zw|P>
     h: np.ndarray = None        # one-electron operator of H (f - g(d_sa) unless given)
     d_sa: np.ndarray = None     # state-averaged density over all orbitals (closed 2 delta)
+    X: list = None              # per L: orthonormal basis of range(S), classes side by side
+    A: list = None              # per L: X^T F X - (E0_L - E_s) 1 (every class coupling)
+    Xcls: list = None           # per L: the class of each column of X
 
 
 def solve(nclosed: int, nact: int, nvirt: int, nelact: int, f: np.ndarray, B: np.ndarray,
@@ -270,6 +273,7 @@ def solve(nclosed: int, nact: int, nvirt: int, nelact: int, f: np.ndarray, B: np
     Vall = np.stack(vecs_all, axis=1) if vecs_all else np.zeros((space.dim, 0))
 
     ts, lams, colsL, SL, bL, AL_solve = [], [], [], [], [], []
+    XL, AL, XclsL = [], [], []
     for L in range(n):
         sel = [k for k, c in enumerate(cols_all) if scheme == "msmr" or c[2] == L]
         V = Vall[:, sel]
@@ -278,7 +282,7 @@ def solve(nclosed: int, nact: int, nvirt: int, nelact: int, f: np.ndarray, B: np
         F = V.T @ (fhat @ V)
         b = {Lp: V.T @ Hrot[:, Lp] for Lp in range(n)}
         # orthonormal basis of range(S), per class (overlap eigenvalues < thresh dropped)
-        blocks = []
+        blocks, xcls = [], []
         for cls in CLASSES:
             idx = [k for k, c in enumerate(cols) if c[0] == cls]
             if not idx:
@@ -288,6 +292,7 @@ def solve(nclosed: int, nact: int, nvirt: int, nelact: int, f: np.ndarray, B: np
             x = np.zeros((len(cols), int(keep.sum())))
             x[idx] = q_[:, keep] / np.sqrt(s_[keep])
             blocks.append(x)
+            xcls += [cls] * int(keep.sum())
         X = np.concatenate(blocks, axis=1) if blocks else np.zeros((len(cols), 0))
         A = X.T @ F @ X - (E0[L] - shift) * np.eye(X.shape[1])
         A = 0.5 * (A + A.T)
@@ -301,6 +306,9 @@ def solve(nclosed: int, nact: int, nvirt: int, nelact: int, f: np.ndarray, B: np
         SL.append(S)
         bL.append(b)
         AL_solve.append(solver)
+        XL.append(X)
+        AL.append(A)
+        XclsL.append(xcls)
 
     # effective Hamiltonian (Sec. II.B)
     Heff = Href.copy()
@@ -338,6 +346,7 @@ def solve(nclosed: int, nact: int, nvirt: int, nelact: int, f: np.ndarray, B: np
     res = O1Result(U, E0, Href, Heff, Ems, R, Ems_explicit, Ecore, e_class, norm_class,
                    ts, lams, colsL, SL, bL)
     res.h, res.d_sa = h, d_sa
+    res.X, res.A, res.Xcls = XL, AL, XclsL
     if not densities:
         return res
 
