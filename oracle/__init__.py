@@ -15,4 +15,9 @@ inputs of the `synth` package.
                   engine), pinned against o1_determinant.
   o2_offdiag      off-diagonal blocks of the density d-bar(2) (class-to-class couplings
                   through E_xy), pinned against o1_determinant.
+  o1_orbderiv     orbital derivative Y of the Lagrangian from o1_determinant's densities.
+  o1_cideriv      CI derivative, XMS multipliers w_MN and the XMS terms Y', y~'.
+  o1_iterative    iterative solve of the coupled amplitude equations (subspace residual
+                  minimisation), with warm starts.
+  (each pinned against finite differences or the direct solve of o1_determinant)
 """
