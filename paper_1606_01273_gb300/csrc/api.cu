@@ -128,24 +128,9 @@ struct caspt2_ctx {
 namespace caspt2 {
 
 int check_block_diagonal_fock(const double* f, const Dims& d) {
-  const int nmo = d.nmo();
-  double fmax = 0.0;
-  for (long k = 0; k < (long)nmo * nmo; ++k) {
-    if (!(f[k] == f[k]) || std::fabs(f[k]) > 1e300) return CASPT2_ENAN;
-    fmax = std::max(fmax, std::fabs(f[k]));
-  }
-  const double tol = 1e-10 * std::max(1.0, fmax);
-  auto space = [&](int p) { return p < d.c ? 0 : (p < d.c + d.a ? 1 : 2); };
-  for (int p = 0; p < nmo; ++p)
-    for (int q = 0; q < nmo; ++q) {
-      const double x = f[(long)p * nmo + q];
-      if (std::fabs(x - f[(long)q * nmo + p]) > tol) return CASPT2_EINVAL;
-      if (p == q) continue;
-      const int sp = space(p), sq = space(q);
-      // coupling blocks, and off-diagonal entries of the closed and virtual blocks
-      if ((sp != sq || sp != 1) && std::fabs(x) > tol) return CASPT2_EINVAL;
-    }
-  return CASPT2_OK;
+  // the canonical case of classify_fock; rotated closed/virtual blocks are refused here
+  const int st = classify_fock(f, d);
+  return st == 1 ? CASPT2_EINVAL : st;
 }
 
 }  // namespace caspt2
